@@ -1,0 +1,156 @@
+/*
+ * rsfde.h -- C ABI of the GB300 (sm_103a) solver for one implicit time step of
+ * the volume-penalized 2D Riesz space-fractional diffusion scheme, solved by
+ * flexible GMRES with the sine-transform (tau) preconditioner of Huang & Sun,
+ * arXiv 2102.11576.
+ *
+ * Notation (Section 2):  the box (ax,bx) x (ay,by) holds the convex domain
+ * Omega; its interior grid is n1 x n2 with h_x = (bx-ax)/(n1+1),
+ * h_y = (by-ay)/(n2+1).  Each step solves Eq. 2.17,
+ *     M u^k = u^{k-1} + dt f^{k-1},   M = I - A + D,
+ *     A = I (x) A_x + A_y (x) I,  A_x = c_x G_{n1}^{(alpha1)}, A_y = c_y G_{n2}^{(alpha2)},
+ * with c_x = dt k_x c_{alpha1} / h_x^{alpha1}, G the symmetric Toeplitz matrix of
+ * Eq. 2.16 built from the weights of Eq. 2.6, and D = (dt/eta) Phi the penalty
+ * (Phi = 1 outside Omega).  The preconditioner is Eq. 4.6:
+ *     P^-1 = (I - Phi)(I - tau_1(A))^-1 + Phi((1 + dt/eta) I - tau_1(A))^-1.
+ *
+ * Layout: every grid array holds N = n1*n2 values, x fastest
+ * (u[j*n1 + i], i the x-index, j the y-index), as u^k is ordered in Section 2.
+ *
+ * Ownership and streams: unless an argument says "host", array arguments are
+ * caller-owned DEVICE pointers (16-byte aligned, e.g. from torch or
+ * cudaMalloc) on the context's device.  The context owns its workspace.  Every
+ * call is enqueued on the context's stream (rsfde_opts.stream, or
+ * rsfde_set_stream); calls that report statistics synchronise that stream
+ * before returning.  A context must not be used from two host threads at once.
+ *
+ * Errors: every int-returning call returns RSFDE_OK (0) or a negative code;
+ * nothing aborts the process.  rsfde_strerror() names a code.  After
+ * RSFDE_ECUDA the context should be destroyed.
+ */
+#ifndef RSFDE_H
+#define RSFDE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSFDE_OK 0
+#define RSFDE_EINVAL (-1)      /* bad argument: alpha outside (1,2), k/dt/eta <= 0, n < 1, NULL, ... */
+#define RSFDE_ENOMEM (-2)      /* device or host allocation failed */
+#define RSFDE_ECUDA (-3)       /* a CUDA runtime call failed */
+#define RSFDE_ENOTCONV (-4)    /* max_iter reached; x holds the last iterate, stats its residual */
+#define RSFDE_ENONFINITE (-5)  /* NaN or Inf met in the right side or in the Arnoldi process */
+#define RSFDE_ETIMEOUT (-6)    /* a bounded device-side wait gave up */
+
+/* Precision of the preconditioner apply (Eq. 4.6).  The operator, the true
+ * residual, the Arnoldi orthogonalisation and the Givens least squares are
+ * FP64 in every mode. */
+#define RSFDE_FP64 0
+#define RSFDE_FP32 1
+
+/* Arnoldi orthogonalisation: classical Gram-Schmidt, or with one re-orthogonalisation pass. */
+#define RSFDE_CGS 0
+#define RSFDE_CGS2 1
+
+typedef struct rsfde_ctx rsfde_ctx;
+
+/* Section 2: the box Omega-bar = (ax,bx) x (ay,by) and its interior grid n1 x n2. */
+typedef struct {
+  int32_t n1, n2;
+  double ax, bx, ay, by;
+} rsfde_grid;
+
+typedef struct {
+  int32_t restart;      /* m of FGMRES(m); Section 5 uses 20.  1..64 */
+  int32_t max_iter;     /* cap on inner iterations per solve */
+  double tol;           /* stop when ||b - M x||_2 <= tol ||b||_2 */
+  int32_t precond_prec; /* RSFDE_FP64 | RSFDE_FP32 */
+  int32_t arnoldi;      /* RSFDE_CGS | RSFDE_CGS2 */
+  int32_t use_precond;  /* 1: P-hat of Eq. 4.6; 0: unpreconditioned GMRES */
+  void* stream;         /* cudaStream_t; NULL = the legacy default stream */
+} rsfde_opts;
+
+typedef struct {
+  int32_t iters;     /* inner (Arnoldi) iterations of the last solve */
+  int32_t restarts;  /* restarts of the last solve */
+  int32_t converged; /* 1 if ||b - M x|| <= tol ||b|| was met */
+  int32_t status;    /* RSFDE_OK, RSFDE_ENOTCONV or RSFDE_ENONFINITE */
+  double rel_res;    /* final true ||b - M x||_2 / ||b||_2 */
+  double bnorm;      /* ||b||_2 */
+} rsfde_stats;
+
+/* Defaults: restart 20, max_iter 10000, tol 1e-10, FP64 preconditioner, CGS,
+ * preconditioned, default stream. */
+void rsfde_opts_default(rsfde_opts* o);
+
+/* Section 2 / Eq. 2.16 / Section 4.1 (setup of one linear system).
+ * mask: DEVICE pointer to N uint8, 1 where the grid point lies in Omega,
+ * 0 in the extension region (copied; the caller keeps ownership).
+ * alpha1, alpha2 in (1,2); kx, ky, dt, eta > 0.  opts may be NULL (defaults).
+ * Builds the Toeplitz and tau tables on the host in FP64 and uploads them.
+ * Returns RSFDE_EINVAL, RSFDE_ENOMEM or RSFDE_ECUDA on failure (*out = NULL). */
+int rsfde_setup(rsfde_ctx** out, const rsfde_grid* grid, const uint8_t* mask, double alpha1,
+                double alpha2, double kx, double ky, double dt, double eta, const rsfde_opts* opts);
+
+/* Re-runs the parameter-dependent setup (c_x, c_y, dt/eta, spectra) for new
+ * k_x, k_y, dt; grid, mask, alpha and eta are kept. */
+int rsfde_set_params(rsfde_ctx* ctx, double kx, double ky, double dt);
+
+/* Replaces the options (restart must not exceed the one given at setup). */
+int rsfde_set_opts(rsfde_ctx* ctx, const rsfde_opts* opts);
+int rsfde_set_stream(rsfde_ctx* ctx, void* stream);
+
+/* Eq. 2.17 solved for x: M x = b by right-preconditioned flexible GMRES(m).
+ * b: device, N doubles.  x: device, N doubles, in: initial guess, out: the
+ * solution (or the last iterate with RSFDE_ENOTCONV).  stats may be NULL.
+ * Synchronises the stream. */
+int rsfde_solve(rsfde_ctx* ctx, const double* b, double* x, rsfde_stats* stats);
+
+/* One implicit step of Eq. 2.17 with the built-in source f(u) = u - u^3 (+ src),
+ * zero outside Omega (Section 2):  b = u^{k-1} + dt (1-Phi)(u^{k-1} - (u^{k-1})^3 + src),
+ * initial guess u^{k-1} if u_prevprev is NULL, else 2u^{k-1} - u^{k-2} (Section 5).
+ * u_prev: device N doubles; u_prevprev, src: device N doubles or NULL;
+ * u_next: device N doubles (may alias neither input).  Synchronises the stream. */
+int rsfde_step(rsfde_ctx* ctx, const double* u_prev, const double* u_prevprev, const double* src,
+               double* u_next, rsfde_stats* stats);
+
+/* rsfde_step with HOST arrays: copies the inputs to the device, runs the
+ * step, copies u^k back (all on the context's stream).  Host arrays may be
+ * pageable or pinned. */
+int rsfde_step_host(rsfde_ctx* ctx, const double* u_prev_host, const double* u_prevprev_host,
+                    const double* src_host, double* u_next_host, rsfde_stats* stats);
+
+/* Adjoint solve for the backward time march: M^T mu = lam.  M is symmetric
+ * (Lemma 2.3), so this is the forward solver applied to lam; mu: in initial
+ * guess, out solution.  Synchronises the stream. */
+int rsfde_adjoint(rsfde_ctx* ctx, const double* lam, double* mu, rsfde_stats* stats);
+
+/* ---- operator-level entry points (each one step of the hot path) --------- */
+/* Eq. 2.14-2.17: w = M z.  z, w device N doubles (distinct). */
+int rsfde_apply_M(rsfde_ctx* ctx, const double* z, double* w);
+/* Eq. 4.6: z = P-hat^-1 v in the context's preconditioner precision (result in FP64). */
+int rsfde_apply_precond(rsfde_ctx* ctx, const double* v, double* z);
+/* Section 4.1: out = (S_{n2} (x) S_{n1}) v, the orthonormal 2D sine transform, FP64. */
+int rsfde_dst2(rsfde_ctx* ctx, const double* v, double* out);
+/* Right side and initial guess of rsfde_step: b and x0 device N doubles. */
+int rsfde_rhs(rsfde_ctx* ctx, const double* u_prev, const double* u_prevprev, const double* src,
+              double* b, double* x0);
+/* Setup tables copied to HOST arrays: eigenvalues of tau(A_x) (n1) and tau(A_y) (n2),
+ * and the scaled Toeplitz first columns t_x (n1), t_y (n2).  Any pointer may be NULL. */
+int rsfde_get_tables(rsfde_ctx* ctx, double* lam_x, double* lam_y, double* t_x, double* t_y);
+/* c_x, c_y, dt/eta, h_x, h_y to a HOST array of 5 doubles. */
+int rsfde_get_params(rsfde_ctx* ctx, double* out5);
+
+/* Number of this library's kernel launches since the context was made (host counter). */
+int64_t rsfde_kernel_launches(const rsfde_ctx* ctx);
+
+void rsfde_destroy(rsfde_ctx* ctx);
+const char* rsfde_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSFDE_H */

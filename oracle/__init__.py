@@ -43,6 +43,7 @@ def _load():
     lib.or_get_toeplitz.argtypes = [vp, _dp, _dp]
     lib.or_get_tau_eigs.argtypes = [vp, _dp, _dp]
     lib.or_apply_M.argtypes = [vp, _dp, _dp]
+    lib.or_apply_M_points.argtypes = [vp, _dp, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _dp]
     lib.or_dst2.argtypes = [vp, _dp, _dp]
     lib.or_apply_precond.argtypes = [vp, _dp, _dp]
     lib.or_fgmres.restype = i
@@ -180,6 +181,15 @@ class Problem:
         w = np.empty_like(z)
         _load().or_apply_M(self._h, _p(z), _p(w))
         return w
+
+    def apply_M_points(self, z, idx):
+        """(M z) at flat indices idx only."""
+        z = self._grid(z)
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        out = np.empty(idx.size)
+        _load().or_apply_M_points(self._h, _p(z), idx.size,
+                                  idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _p(out))
+        return out
 
     def dst2(self, v):
         v = self._grid(v)

@@ -222,6 +222,21 @@ void or_apply_M(const or_ctx* c, const double* z, double* w) {
   }
 }
 
+/* (M z) at the flat grid indices idx[0..npts-1] only: the same sums as
+ * or_apply_M, for spot checks of grids too large for a full product. */
+void or_apply_M_points(const or_ctx* c, const double* z, long npts, const long* idx, double* out) {
+  const int n1 = c->n1, n2 = c->n2;
+  for (long q = 0; q < npts; ++q) {
+    long p = idx[q];
+    int j = (int)(p / n1), i = (int)(p % n1);
+    double ax = 0.0, ay = 0.0;
+    for (int l = 0; l < n1; ++l) ax += c->tx[abs(i - l)] * z[(long)j * n1 + l];
+    for (int l = 0; l < n2; ++l) ay += c->ty[abs(j - l)] * z[(long)l * n1 + i];
+    double d = c->phi[p] ? c->pen : 0.0;
+    out[q] = z[p] - ax - ay + d * z[p];
+  }
+}
+
 /* (S_{n2} (x) S_{n1}) v: sine transform of every row (x), then every column (y). */
 void or_dst2(const or_ctx* c, const double* v, double* out) {
   const int n1 = c->n1, n2 = c->n2;

@@ -1,0 +1,597 @@
+// api.cu -- the C ABI (include/rsfde.h): context, FP64 host setup of the
+// Toeplitz and tau tables, and the orchestration of flexible GMRES on one
+// CUDA stream.
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fft.cuh"
+#include "internal.h"
+
+using namespace rsfde;
+
+namespace {
+
+// ---- host setup (FP64) -----------------------------------------------------
+// Section 1: c_alpha = -1 / (2 cos(alpha pi / 2)).
+double riesz_c(double alpha) { return -1.0 / (2.0 * std::cos(alpha * M_PI / 2.0)); }
+
+// Eq. 2.16 first column of c * G_n^(alpha), from the weights of Eq. 2.6.
+std::vector<double> toeplitz_first_column(double alpha, double c, int n) {
+  std::vector<double> g(n + 2);
+  g[0] = 1.0;
+  for (int l = 1; l < n + 2; ++l) g[l] = g[l - 1] * (1.0 - (alpha + 1.0) / l);
+  std::vector<double> t(n);
+  for (int k = 0; k < n; ++k) t[k] = c * (k == 0 ? 2.0 * g[1] : k == 1 ? g[0] + g[2] : g[k + 1]);
+  return t;
+}
+
+// Section 4.1: eigenvalues of tau(T_n) for symmetric Toeplitz T_n with first
+// column t: lambda_k = t_0 + 2 sum_{j=1}^{n-1} t_j cos(pi j k / (n+1)), the
+// values S_n tau(T_n) S_n takes on its diagonal.
+std::vector<double> tau_eigenvalues(const std::vector<double>& t) {
+  const int n = (int)t.size();
+  const long period = 2L * (n + 1);
+  std::vector<double> cosv(period);
+  for (long m = 0; m < period; ++m) cosv[m] = std::cos(M_PI * (double)m / (double)(n + 1));
+  std::vector<double> lam(n);
+  for (int k = 1; k <= n; ++k) {
+    double s = 0.0;
+    for (int j = n - 1; j >= 1; --j) s += t[j] * cosv[((long)j * k) % period];
+    lam[k - 1] = t[0] + 2.0 * s;
+  }
+  return lam;
+}
+
+void host_dif(std::vector<double>& re, std::vector<double>& im, int L, int log2L, const std::vector<double>& tw) {
+  int s;
+  if (log2L & 1) {
+    for (int k = 0; k < L / 2; ++k) dif_r2(re.data(), im.data(), L, k, tw.data());
+    s = L >> 3;
+  } else {
+    s = L >> 2;
+  }
+  for (; s >= 1; s >>= 2)
+    for (int q = 0; q < L / 4; ++q) dif_r4(re.data(), im.data(), L, s, q, tw.data());
+}
+
+struct HostAxis {
+  int n = 0, L = 0, log2L = 0;
+  std::vector<double> t, lam, tw, sigma, chirp, chirp_out, bspec;
+};
+
+HostAxis build_axis(int n, double alpha, double c) {
+  HostAxis a;
+  a.n = n;
+  a.L = 4;
+  a.log2L = 2;
+  while (a.L < 2 * n - 1) {
+    a.L <<= 1;
+    a.log2L++;
+  }
+  const int L = a.L;
+  a.t = toeplitz_first_column(alpha, c, n);
+  a.lam = tau_eigenvalues(a.t);
+  a.tw.resize(2 * L);
+  for (int j = 0; j < L; ++j) {
+    a.tw[2 * j] = std::cos(2.0 * M_PI * j / L);
+    a.tw[2 * j + 1] = -std::sin(2.0 * M_PI * j / L);
+  }
+  // circulant embedding of the symmetric Toeplitz matrix; its spectrum is real
+  std::vector<double> re(L, 0.0), im(L, 0.0);
+  re[0] = a.t[0];
+  for (int k = 1; k < n; ++k) re[k] = re[L - k] = a.t[k];
+  host_dif(re, im, L, a.log2L, a.tw);
+  a.sigma.resize(L);
+  for (int l = 0; l < L; ++l) a.sigma[l] = re[l] / L;
+  // Bluestein chirps for S_n: exp(i pi k^2 / (2(n+1))), phase reduced mod 4(n+1)
+  const long per = 4L * (n + 1);
+  const double nrm = std::sqrt(2.0 / (n + 1));
+  a.chirp.resize(2 * n);
+  a.chirp_out.resize(2 * n);
+  for (int k = 1; k <= n; ++k) {
+    const long m = ((long)k * k) % per;
+    const double ang = M_PI * (double)m / (2.0 * (n + 1));
+    a.chirp[2 * (k - 1)] = std::cos(ang);
+    a.chirp[2 * (k - 1) + 1] = std::sin(ang);
+    a.chirp_out[2 * (k - 1)] = nrm * std::cos(ang);
+    a.chirp_out[2 * (k - 1) + 1] = nrm * std::sin(ang);
+  }
+  std::fill(re.begin(), re.end(), 0.0);
+  std::fill(im.begin(), im.end(), 0.0);
+  for (int d = 0; d < n; ++d) {
+    const long m = ((long)d * d) % per;
+    const double ang = -M_PI * (double)m / (2.0 * (n + 1));
+    re[d] = std::cos(ang);
+    im[d] = std::sin(ang);
+    if (d > 0) {
+      re[L - d] = re[d];
+      im[L - d] = im[d];
+    }
+  }
+  host_dif(re, im, L, a.log2L, a.tw);
+  a.bspec.resize(2 * L);
+  for (int l = 0; l < L; ++l) {
+    a.bspec[2 * l] = re[l] / L;
+    a.bspec[2 * l + 1] = im[l] / L;
+  }
+  return a;
+}
+
+// Device copy of one axis' tables in precision T (one allocation).
+template <typename T>
+struct DevAxis {
+  void* mem = nullptr;
+  AxisTables<T> tab{};
+  void release() {
+    if (mem) cudaFree(mem);
+    mem = nullptr;
+  }
+  cudaError_t upload(const HostAxis& h, cudaStream_t s) {
+    const size_t L = h.L, n = h.n;
+    const size_t count = 2 * L + L + 2 * n + 2 * n + 2 * L + n;
+    std::vector<T> buf(count);
+    size_t o = 0;
+    auto put = [&](const std::vector<double>& v) {
+      size_t start = o;
+      for (double d : v) buf[o++] = T(d);
+      return start;
+    };
+    size_t o_tw = put(h.tw), o_sig = put(h.sigma), o_ch = put(h.chirp), o_cho = put(h.chirp_out),
+           o_bs = put(h.bspec), o_lam = put(h.lam);
+    if (!mem) {
+      cudaError_t e = cudaMalloc(&mem, count * sizeof(T));
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaMemcpyAsync(mem, buf.data(), count * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    const T* b = static_cast<const T*>(mem);
+    tab.n = h.n;
+    tab.L = h.L;
+    tab.log2L = h.log2L;
+    tab.tw = b + o_tw;
+    tab.sigma = b + o_sig;
+    tab.chirp = b + o_ch;
+    tab.chirp_out = b + o_cho;
+    tab.bspec = b + o_bs;
+    tab.lam = b + o_lam;
+    return e;
+  }
+};
+
+}  // namespace
+
+struct rsfde_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n1 = 0, n2 = 0;
+  size_t N = 0;
+  double ax = 0, bx = 0, ay = 0, by = 0;
+  double alpha1 = 0, alpha2 = 0, kx = 0, ky = 0, dt = 0, eta = 0;
+  double hx = 0, hy = 0, cx = 0, cy = 0, pen = 0;
+  rsfde_opts opts{};
+  int m_alloc = 0;
+  HostAxis hx_axis, hy_axis;
+  DevAxis<double> x64, y64;
+  DevAxis<float> x32, y32;
+  uint8_t* phi = nullptr;
+  double* V = nullptr;      // (m+1) x N
+  void* Z = nullptr;        // m x N (double or float)
+  double* tmpx = nullptr;   // N
+  void* T1 = nullptr;       // N (double-sized)
+  void* T2a = nullptr;
+  void* T2b = nullptr;
+  double* b = nullptr;
+  double* x = nullptr;
+  double* hbuf = nullptr;   // 3N for the host-array step
+  double* partials = nullptr;
+  size_t npartials = 0;
+  SolverState* st = nullptr;
+  SolverState* st_host = nullptr;  // pinned
+  int64_t launches = 0;
+};
+
+namespace {
+
+bool bad_alpha(double a) { return !(a > 1.0 && a < 2.0); }
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaSuccess) return RSFDE_OK;
+  if (e == cudaErrorMemoryAllocation) return RSFDE_ENOMEM;
+  return RSFDE_ECUDA;
+}
+
+int check_launch(rsfde_ctx* c) { return cuda_fail(cudaGetLastError()); }
+
+int build_tables(rsfde_ctx* c) {
+  c->hx = (c->bx - c->ax) / (c->n1 + 1);  // Section 2
+  c->hy = (c->by - c->ay) / (c->n2 + 1);
+  c->cx = c->dt * c->kx * riesz_c(c->alpha1) / std::pow(c->hx, c->alpha1);
+  c->cy = c->dt * c->ky * riesz_c(c->alpha2) / std::pow(c->hy, c->alpha2);
+  c->pen = c->dt / c->eta;
+  c->hx_axis = build_axis(c->n1, c->alpha1, c->cx);
+  c->hy_axis = build_axis(c->n2, c->alpha2, c->cy);
+  cudaError_t e;
+  if ((e = c->x64.upload(c->hx_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
+  if ((e = c->y64.upload(c->hy_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
+  if ((e = c->x32.upload(c->hx_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
+  if ((e = c->y32.upload(c->hy_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
+  return RSFDE_OK;
+}
+
+void free_ctx(rsfde_ctx* c) {
+  if (!c) return;
+  c->x64.release();
+  c->y64.release();
+  c->x32.release();
+  c->y32.release();
+  void* ptrs[] = {c->phi, c->V, c->Z, c->tmpx, c->T1, c->T2a, c->T2b, c->b, c->x, c->hbuf, c->partials, c->st};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  delete c;
+}
+
+bool fp32_precond(const rsfde_ctx* c) { return c->opts.precond_prec == RSFDE_FP32; }
+
+// ---- enqueue helpers ---------------------------------------------------------
+// w = M z (Eq. 2.17), z in precision Tz.
+template <typename Tz>
+void enqueue_apply_M(rsfde_ctx* c, const Tz* z, double* w, const int* gate) {
+  launch_toeplitz_rows<double, Tz>(z, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
+  launch_toeplitz_cols<double, Tz>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2,
+                                   c->y64.tab, gate, nullptr, nullptr, c->stream);
+  c->launches += 2;
+}
+
+// V_0 = b - M x, beta = ||V_0||, then restart_prep (device).
+void enqueue_residual(rsfde_ctx* c, const int* gate) {
+  launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
+  launch_toeplitz_cols<double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1, c->n2,
+                                       c->y64.tab, gate, c->partials, c->st, c->stream);
+  c->launches += 2;
+}
+
+// z = P-hat^-1 (scale * v) (Eq. 4.6) into z of precision Tz.
+template <typename T, typename Tz>
+void enqueue_precond_t(rsfde_ctx* c, const double* v, const double* vscale, Tz* z, const int* gate,
+                       const AxisTables<T>& tx, const AxisTables<T>& ty) {
+  T* t1 = static_cast<T*>(c->T1);
+  T* t2a = static_cast<T*>(c->T2a);
+  T* t2b = static_cast<T*>(c->T2b);
+  launch_dst_rows<T, T>(v, vscale, t1, c->n1, c->n2, tx, gate, c->stream);
+  launch_precond_cols<T>(t1, t2a, t2b, c->n1, c->n2, ty, tx.lam, c->pen, gate, c->stream);
+  launch_precond_rows<T, Tz>(t2a, t2b, c->phi, z, c->n1, c->n2, tx, gate, c->stream);
+  c->launches += 3;
+}
+
+// One FGMRES(m) cycle: m gated Arnoldi iterations, the solution update and
+// the true residual with the restart decision.  Nothing is read on the host.
+template <typename Tz>
+void enqueue_cycle_t(rsfde_ctx* c) {
+  const size_t N = c->N;
+  const int m = c->opts.restart;
+  const int* gi = &c->st->run_iter;
+  const int* gc = &c->st->run_cycle;
+  Tz* Z = static_cast<Tz*>(c->Z);
+  for (int j = 0; j < m; ++j) {
+    const double* vj = c->V + (size_t)j * N;
+    Tz* zj = Z + (size_t)j * N;
+    if (c->opts.use_precond) {
+      if (fp32_precond(c))
+        enqueue_precond_t<float, Tz>(c, vj, &c->st->s[j], zj, gi, c->x32.tab, c->y32.tab);
+      else
+        enqueue_precond_t<double, Tz>(c, vj, &c->st->s[j], zj, gi, c->x64.tab, c->y64.tab);
+    } else {
+      launch_scale_copy<Tz>(vj, &c->st->s[j], zj, N, gi, c->stream);  // P = I: z_j = v_j
+      c->launches += 1;
+    }
+    enqueue_apply_M<Tz>(c, zj, c->V + (size_t)(j + 1) * N, gi);
+    const bool cgs2 = c->opts.arnoldi == RSFDE_CGS2;
+    launch_multidot(c->V, N, j, 0, c->partials, c->st, c->stream);
+    launch_update(c->V, N, j, cgs2 ? 0 : 1, c->partials, c->st, c->stream);
+    c->launches += 2;
+    if (cgs2) {
+      launch_multidot(c->V, N, j, 1, c->partials, c->st, c->stream);
+      launch_update(c->V, N, j, 1, c->partials, c->st, c->stream);
+      c->launches += 2;
+    }
+  }
+  launch_solve_y(c->st, c->stream);
+  launch_xupdate<Tz>(c->x, Z, N, c->st, c->stream);
+  c->launches += 2;
+  enqueue_residual(c, gc);
+}
+
+void enqueue_cycle(rsfde_ctx* c) {
+  if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float>(c);
+  else enqueue_cycle_t<double>(c);
+}
+
+// Solve M x = b with b = c->b, x = c->x (initial guess), st->bnorm set.
+int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
+  enqueue_residual(c, &c->st->run_cycle);
+  int rc = check_launch(c);
+  if (rc) return rc;
+  const size_t head = offsetof(SolverState, counter);
+  // each cycle does at least one iteration, so max_iter + 1 cycles bound the loop
+  for (long guard = 0;; ++guard) {
+    if (guard > (long)c->opts.max_iter + 1) return RSFDE_ENOTCONV;
+    cudaError_t e = cudaMemcpyAsync(c->st_host, c->st, head, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e);
+    if (!c->st_host->run_cycle) break;
+    enqueue_cycle(c);
+    if ((rc = check_launch(c))) return rc;
+  }
+  launch_finalize(c->x, c->N, c->st, c->stream);
+  c->launches += 1;
+  cudaError_t e = cudaMemcpyAsync(c->st_host, c->st, sizeof(SolverState), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e);
+  const SolverState& h = *c->st_host;
+  if (stats) {
+    stats->iters = h.iters;
+    stats->restarts = h.cycles > 0 ? h.cycles - 1 : 0;
+    stats->converged = h.converged;
+    stats->status = h.status;
+    stats->rel_res = h.rel_res;
+    stats->bnorm = h.bnorm;
+  }
+  return h.status;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void rsfde_opts_default(rsfde_opts* o) {
+  if (!o) return;
+  o->restart = 20;
+  o->max_iter = 10000;
+  o->tol = 1e-10;
+  o->precond_prec = RSFDE_FP64;
+  o->arnoldi = RSFDE_CGS;
+  o->use_precond = 1;
+  o->stream = nullptr;
+}
+
+const char* rsfde_strerror(int code) {
+  switch (code) {
+    case RSFDE_OK: return "ok";
+    case RSFDE_EINVAL: return "invalid argument";
+    case RSFDE_ENOMEM: return "out of memory";
+    case RSFDE_ECUDA: return "CUDA error";
+    case RSFDE_ENOTCONV: return "GMRES did not converge within max_iter";
+    case RSFDE_ENONFINITE: return "non-finite value in the right side or the Arnoldi process";
+    case RSFDE_ETIMEOUT: return "device-side wait timed out";
+    default: return "unknown error";
+  }
+}
+
+static int valid_opts(const rsfde_opts* o) {
+  if (o->restart < 1 || o->restart > kMaxRestart || o->max_iter < 1 || !(o->tol > 0.0)) return 0;
+  if (o->precond_prec != RSFDE_FP64 && o->precond_prec != RSFDE_FP32) return 0;
+  if (o->arnoldi != RSFDE_CGS && o->arnoldi != RSFDE_CGS2) return 0;
+  return 1;
+}
+
+int rsfde_setup(rsfde_ctx** out, const rsfde_grid* g, const uint8_t* mask, double alpha1, double alpha2,
+                double kx, double ky, double dt, double eta, const rsfde_opts* opts) {
+  if (!out) return RSFDE_EINVAL;
+  *out = nullptr;
+  if (!g || !mask || bad_alpha(alpha1) || bad_alpha(alpha2) || !(kx > 0) || !(ky > 0) || !(dt > 0) ||
+      !(eta > 0) || g->n1 < 1 || g->n2 < 1 || g->n1 > 2048 || g->n2 > 2048 || !(g->bx > g->ax) ||
+      !(g->by > g->ay))
+    return RSFDE_EINVAL;
+  rsfde_opts o;
+  rsfde_opts_default(&o);
+  if (opts) o = *opts;
+  if (!valid_opts(&o)) return RSFDE_EINVAL;
+  rsfde_ctx* c = new (std::nothrow) rsfde_ctx();
+  if (!c) return RSFDE_ENOMEM;
+  cudaGetDevice(&c->device);
+  c->stream = static_cast<cudaStream_t>(o.stream);
+  c->opts = o;
+  c->m_alloc = o.restart;
+  c->n1 = g->n1;
+  c->n2 = g->n2;
+  c->N = (size_t)g->n1 * g->n2;
+  c->ax = g->ax;
+  c->bx = g->bx;
+  c->ay = g->ay;
+  c->by = g->by;
+  c->alpha1 = alpha1;
+  c->alpha2 = alpha2;
+  c->kx = kx;
+  c->ky = ky;
+  c->dt = dt;
+  c->eta = eta;
+  const size_t N = c->N, m = o.restart;
+  c->npartials = (size_t)(kMaxRestart + 2) * (size_t)vec_grid(N);
+  if (c->npartials < (size_t)kMaxPartials) c->npartials = kMaxPartials;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  alloc((void**)&c->phi, N);
+  alloc((void**)&c->V, (m + 1) * N * sizeof(double));
+  alloc(&c->Z, m * N * sizeof(double));
+  alloc((void**)&c->tmpx, N * sizeof(double));
+  alloc(&c->T1, N * sizeof(double));
+  alloc(&c->T2a, N * sizeof(double));
+  alloc(&c->T2b, N * sizeof(double));
+  alloc((void**)&c->b, N * sizeof(double));
+  alloc((void**)&c->x, N * sizeof(double));
+  alloc((void**)&c->partials, c->npartials * sizeof(double));
+  alloc((void**)&c->st, sizeof(SolverState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->st_host, sizeof(SolverState));
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(e);
+  }
+  cudaMemsetAsync(c->st, 0, sizeof(SolverState), c->stream);
+  launch_mask_to_phi(mask, c->phi, N, c->stream);
+  c->launches += 1;
+  int rc = build_tables(c);
+  if (rc == RSFDE_OK) rc = check_launch(c);
+  if (rc == RSFDE_OK) rc = cuda_fail(cudaStreamSynchronize(c->stream));
+  if (rc != RSFDE_OK) {
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return RSFDE_OK;
+}
+
+int rsfde_set_params(rsfde_ctx* c, double kx, double ky, double dt) {
+  if (!c || !(kx > 0) || !(ky > 0) || !(dt > 0)) return RSFDE_EINVAL;
+  c->kx = kx;
+  c->ky = ky;
+  c->dt = dt;
+  return build_tables(c);
+}
+
+int rsfde_set_opts(rsfde_ctx* c, const rsfde_opts* o) {
+  if (!c || !o || !valid_opts(o) || o->restart > c->m_alloc) return RSFDE_EINVAL;
+  c->opts = *o;
+  c->stream = static_cast<cudaStream_t>(o->stream);
+  return RSFDE_OK;
+}
+
+int rsfde_set_stream(rsfde_ctx* c, void* stream) {
+  if (!c) return RSFDE_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->opts.stream = stream;
+  return RSFDE_OK;
+}
+
+int rsfde_solve(rsfde_ctx* c, const double* b, double* x, rsfde_stats* stats) {
+  if (!c || !b || !x) return RSFDE_EINVAL;
+  const size_t bytes = c->N * sizeof(double);
+  cudaMemcpyAsync(c->b, b, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
+  launch_norm_b(c->b, c->N, c->partials, c->st, c->stream);
+  c->launches += 2;
+  int rc = check_launch(c);
+  if (rc) return rc;
+  rc = run_solver(c, stats);
+  if (rc == RSFDE_ECUDA || rc == RSFDE_ENOMEM) return rc;
+  cudaError_t e = cudaMemcpyAsync(x, c->x, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return rc;
+}
+
+int rsfde_rhs(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, const double* src, double* b,
+              double* x0) {
+  if (!c || !u_prev || !b || !x0) return RSFDE_EINVAL;
+  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
+  launch_rhs(u_prev, u_prevprev, src, c->phi, c->dt, b, x0, c->N, c->partials, c->st, c->stream);
+  c->launches += 2;
+  return check_launch(c);
+}
+
+int rsfde_step(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, const double* src, double* u_next,
+               rsfde_stats* stats) {
+  if (!c || !u_prev || !u_next) return RSFDE_EINVAL;
+  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
+  launch_rhs(u_prev, u_prevprev, src, c->phi, c->dt, c->b, c->x, c->N, c->partials, c->st, c->stream);
+  c->launches += 2;
+  int rc = check_launch(c);
+  if (rc) return rc;
+  rc = run_solver(c, stats);
+  if (rc == RSFDE_ECUDA || rc == RSFDE_ENOMEM) return rc;
+  cudaError_t e = cudaMemcpyAsync(u_next, c->x, c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return rc;
+}
+
+int rsfde_step_host(rsfde_ctx* c, const double* u_prev_h, const double* u_prevprev_h, const double* src_h,
+                    double* u_next_h, rsfde_stats* stats) {
+  if (!c || !u_prev_h || !u_next_h) return RSFDE_EINVAL;
+  const size_t bytes = c->N * sizeof(double);
+  if (!c->hbuf) {
+    cudaError_t e = cudaMalloc((void**)&c->hbuf, 3 * bytes);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  double* d_u = c->hbuf;
+  double* d_uu = u_prevprev_h ? c->hbuf + c->N : nullptr;
+  double* d_src = src_h ? c->hbuf + 2 * c->N : nullptr;
+  cudaMemcpyAsync(d_u, u_prev_h, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (d_uu) cudaMemcpyAsync(d_uu, u_prevprev_h, bytes, cudaMemcpyHostToDevice, c->stream);
+  if (d_src) cudaMemcpyAsync(d_src, src_h, bytes, cudaMemcpyHostToDevice, c->stream);
+  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
+  launch_rhs(d_u, d_uu, d_src, c->phi, c->dt, c->b, c->x, c->N, c->partials, c->st, c->stream);
+  c->launches += 2;
+  int rc = check_launch(c);
+  if (rc) return rc;
+  rc = run_solver(c, stats);
+  if (rc == RSFDE_ECUDA || rc == RSFDE_ENOMEM) return rc;
+  cudaError_t e = cudaMemcpyAsync(u_next_h, c->x, bytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return rc;
+}
+
+int rsfde_adjoint(rsfde_ctx* c, const double* lam, double* mu, rsfde_stats* stats) {
+  // M is symmetric (Lemma 2.3): M^T mu = lam is the forward system.
+  return rsfde_solve(c, lam, mu, stats);
+}
+
+int rsfde_apply_M(rsfde_ctx* c, const double* z, double* w) {
+  if (!c || !z || !w) return RSFDE_EINVAL;
+  enqueue_apply_M<double>(c, z, w, nullptr);
+  return check_launch(c);
+}
+
+int rsfde_apply_precond(rsfde_ctx* c, const double* v, double* z) {
+  if (!c || !v || !z) return RSFDE_EINVAL;
+  if (fp32_precond(c)) enqueue_precond_t<float, double>(c, v, nullptr, z, nullptr, c->x32.tab, c->y32.tab);
+  else enqueue_precond_t<double, double>(c, v, nullptr, z, nullptr, c->x64.tab, c->y64.tab);
+  return check_launch(c);
+}
+
+int rsfde_dst2(rsfde_ctx* c, const double* v, double* out) {
+  if (!c || !v || !out) return RSFDE_EINVAL;
+  launch_dst_rows<double, double>(v, nullptr, c->tmpx, c->n1, c->n2, c->x64.tab, nullptr, c->stream);
+  launch_dst_cols<double, double, double>(c->tmpx, out, c->n1, c->n2, c->y64.tab, c->stream);
+  c->launches += 2;
+  return check_launch(c);
+}
+
+int rsfde_get_tables(rsfde_ctx* c, double* lam_x, double* lam_y, double* t_x, double* t_y) {
+  if (!c) return RSFDE_EINVAL;
+  if (lam_x) std::memcpy(lam_x, c->hx_axis.lam.data(), sizeof(double) * c->n1);
+  if (lam_y) std::memcpy(lam_y, c->hy_axis.lam.data(), sizeof(double) * c->n2);
+  if (t_x) std::memcpy(t_x, c->hx_axis.t.data(), sizeof(double) * c->n1);
+  if (t_y) std::memcpy(t_y, c->hy_axis.t.data(), sizeof(double) * c->n2);
+  return RSFDE_OK;
+}
+
+int rsfde_get_params(rsfde_ctx* c, double* out5) {
+  if (!c || !out5) return RSFDE_EINVAL;
+  out5[0] = c->cx;
+  out5[1] = c->cy;
+  out5[2] = c->pen;
+  out5[3] = c->hx;
+  out5[4] = c->hy;
+  return RSFDE_OK;
+}
+
+int64_t rsfde_kernel_launches(const rsfde_ctx* c) { return c ? c->launches : 0; }
+
+void rsfde_destroy(rsfde_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// common.cuh -- shared types of the GB300 solver library (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rsfde {
+
+constexpr int kMaxRestart = 64;  // largest m of FGMRES(m)
+constexpr int kBlock = 256;      // threads per block of the grid-vector kernels
+
+// Device-resident control state of one FGMRES solve.  Every kernel of an
+// Arnoldi iteration is gated by run_iter, every cycle-end kernel by
+// run_cycle, so a whole cycle can be enqueued (or replayed as a graph)
+// without the host reading anything between iterations.
+struct SolverState {
+  int run_iter;   // 1 while the current cycle keeps iterating
+  int run_cycle;  // 1 until the solve is finished
+  int status;     // 0, or RSFDE_ENOTCONV / RSFDE_ENONFINITE
+  int converged;
+  int jlast;      // Arnoldi columns built in the current cycle
+  int iters, cycles, max_iter, m;
+  int zero_solution;  // b == 0: x must be zeroed
+  unsigned int counter;  // arrivals for the last-block reductions
+  unsigned int pad;
+  double tol, bnorm, beta, rel_res;
+  double s[kMaxRestart + 1];  // v_i = s_i * V_i (normalisation deferred into the readers)
+  double H[(kMaxRestart + 1) * kMaxRestart];  // rotated Hessenberg, H[i*kMaxRestart + j]
+  double hcol[kMaxRestart + 1];
+  double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
+};
+
+// Per-axis tables of one precision T (double or float), all device pointers.
+// L is the power-of-two convolution length >= 2n-1 used by both transforms.
+template <typename T>
+struct AxisTables {
+  int n, L, log2L;
+  const T* tw;         // 2L: cos, sin of -2 pi j/L
+  const T* sigma;      // L: circulant spectrum of the Toeplitz column / L, bit-reversed
+  const T* chirp;      // 2n: exp(i pi k^2 / (2(n+1))), k = 1..n
+  const T* chirp_out;  // 2n: sqrt(2/(n+1)) exp(i pi k^2 / (2(n+1)))
+  const T* bspec;      // 2L: spectrum of exp(-i pi d^2/(2(n+1))) / L, bit-reversed
+  const T* lam;        // n: eigenvalues of tau(A_axis)
+};
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;  // valid in warp 0
+}
+
+// Last-block-done pattern: returns true in exactly one block, after every
+// block has published its partial results.  That block resets the counter.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int total) {
+  __shared__ int is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(counter, 1u);
+    is_last = (prev == total - 1);
+    if (is_last) *counter = 0;
+  }
+  __syncthreads();
+  if (is_last) __threadfence();
+  return is_last != 0;
+}
+
+// Deterministic sum of `count` partials (fixed order for a fixed count).
+__device__ __forceinline__ double sum_partials(const double* p, int count, double* sh) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) v += __ldcg(p + i);
+  return block_sum(v, sh);
+}
+
+}  // namespace rsfde

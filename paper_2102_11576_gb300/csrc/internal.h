@@ -1,0 +1,135 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/rsfde.h"
+#include "common.cuh"
+
+namespace rsfde {
+
+constexpr int kNumSMs = 152;              // GB300: 2 dies x 76 SMs
+constexpr int kSmemBudget = 200 * 1024;   // dynamic shared memory per block we allow
+constexpr int kMaxPartials = 4096;        // per-block partial sums of one reduction
+constexpr int kDotChunk = 8;              // basis vectors per block row of the multi-dot
+constexpr int MODE_APPLY = 0;
+constexpr int MODE_RESIDUAL = 1;
+
+// ---- device-side solver control (single thread) ---------------------------
+// Called by the last block of the true-residual kernel with beta = ||b - M x||:
+// either finishes the solve or starts the next FGMRES cycle with v_0 = r / beta.
+__device__ __forceinline__ void restart_prep(SolverState* st, double beta) {
+  st->beta = beta;
+  st->jlast = 0;
+  if (st->bnorm == 0.0) {  // b = 0: the solution is x = 0
+    st->zero_solution = 1;
+    st->converged = 1;
+    st->rel_res = 0.0;
+    st->run_cycle = 0;
+    st->run_iter = 0;
+    return;
+  }
+  st->rel_res = beta / st->bnorm;
+  if (!isfinite(beta) || !isfinite(st->bnorm)) {
+    st->status = RSFDE_ENONFINITE;
+    st->run_cycle = 0;
+    st->run_iter = 0;
+    return;
+  }
+  if (beta <= st->tol * st->bnorm) {
+    st->converged = 1;
+    st->run_cycle = 0;
+    st->run_iter = 0;
+    return;
+  }
+  if (st->iters >= st->max_iter) {
+    st->status = RSFDE_ENOTCONV;
+    st->run_cycle = 0;
+    st->run_iter = 0;
+    return;
+  }
+  st->s[0] = 1.0 / beta;
+  st->g[0] = beta;
+  for (int i = 1; i <= st->m; ++i) st->g[i] = 0.0;
+  st->run_iter = 1;
+  st->cycles += 1;
+}
+
+// Arnoldi column j is complete (H[0..j][j] and hnorm = H[j+1][j]): apply the
+// stored Givens rotations, form the new one, update g and decide whether the
+// cycle goes on (Section 5: GMRES with restart).
+__device__ __forceinline__ void givens_step(SolverState* st, int j, double hnorm) {
+  constexpr int KM = kMaxRestart;
+  double* H = st->H;
+  H[(j + 1) * KM + j] = hnorm;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * KM + j], b = H[(i + 1) * KM + j];
+    H[i * KM + j] = st->cs[i] * a + st->sn[i] * b;
+    H[(i + 1) * KM + j] = -st->sn[i] * a + st->cs[i] * b;
+  }
+  const double a = H[j * KM + j], b = hnorm;
+  double c = 1.0, s = 0.0;
+  if (b != 0.0) {
+    const double r = hypot(a, b);
+    c = a / r;
+    s = b / r;
+  }
+  st->cs[j] = c;
+  st->sn[j] = s;
+  H[j * KM + j] = c * a + s * b;
+  H[(j + 1) * KM + j] = 0.0;
+  st->g[j + 1] = -s * st->g[j];
+  st->g[j] = c * st->g[j];
+  st->iters += 1;
+  st->jlast = j + 1;
+  st->s[j + 1] = hnorm > 0.0 ? 1.0 / hnorm : 0.0;
+  if (!isfinite(hnorm) || !isfinite(st->g[j + 1]) || !isfinite(H[j * KM + j])) {
+    st->status = RSFDE_ENONFINITE;
+    st->jlast = 0;
+    st->run_iter = 0;
+    st->run_cycle = 0;
+    return;
+  }
+  if (fabs(st->g[j + 1]) <= st->tol * st->bnorm || hnorm == 0.0 || j + 1 >= st->m ||
+      st->iters >= st->max_iter)
+    st->run_iter = 0;
+}
+
+// ---- launchers (transforms.cu) ---------------------------------------------
+template <typename T, typename Tin>
+void launch_toeplitz_rows(const Tin* z, double* out, int n1, int n2, const AxisTables<T>& ax, const int* gate,
+                          cudaStream_t s);
+template <typename T, typename Tin>
+void launch_toeplitz_cols(int mode, const Tin* z, const double* tmpx, const uint8_t* phi, double pen,
+                          const double* b, double* out, int n1, int n2, const AxisTables<T>& ay,
+                          const int* gate, double* partials, SolverState* st, cudaStream_t s);
+template <typename T, typename Tout>
+void launch_dst_rows(const double* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
+                     const int* gate, cudaStream_t s);
+template <typename T, typename Tin, typename Tout>
+void launch_dst_cols(const Tin* in, Tout* out, int n1, int n2, const AxisTables<T>& ay, cudaStream_t s);
+template <typename T>
+void launch_precond_cols(const T* T1, T* T2a, T* T2b, int n1, int n2, const AxisTables<T>& ay, const T* lamx,
+                         double pen, const int* gate, cudaStream_t s);
+template <typename T, typename Tz>
+void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, int n1, int n2,
+                         const AxisTables<T>& ax, const int* gate, cudaStream_t s);
+
+// ---- launchers (krylov.cu) -------------------------------------------------
+int vec_grid(size_t N);
+void launch_init_state(SolverState* st, int m, int max_iter, double tol, cudaStream_t s);
+void launch_mask_to_phi(const uint8_t* in_omega, uint8_t* phi, size_t N, cudaStream_t s);
+void launch_rhs(const double* u, const double* uu, const double* src, const uint8_t* phi, double dt, double* b,
+                double* x0, size_t N, double* partials, SolverState* st, cudaStream_t s);
+void launch_norm_b(const double* b, size_t N, double* partials, SolverState* st, cudaStream_t s);
+void launch_multidot(const double* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
+                     cudaStream_t s);
+void launch_update(double* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s);
+void launch_solve_y(SolverState* st, cudaStream_t s);
+template <typename Tz>
+void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s);
+void launch_finalize(double* x, size_t N, SolverState* st, cudaStream_t s);
+template <typename Tz>
+void launch_scale_copy(const double* v, const double* scale, Tz* z, size_t N, const int* gate, cudaStream_t s);
+
+}  // namespace rsfde

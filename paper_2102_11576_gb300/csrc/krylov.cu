@@ -1,0 +1,234 @@
+// krylov.cu -- grid-vector kernels of the flexible GMRES solve (FP64):
+// right side of Eq. 2.17, fused multi-dot and update of the classical
+// Gram-Schmidt Arnoldi step, the Givens least squares (single thread, in the
+// last block of the norm reduction) and the solution update.
+//
+// Every reduction is two-level and deterministic: fixed grid, per-block
+// partials in block order, summed in a fixed order by the last block.
+#include "internal.h"
+
+namespace rsfde {
+
+int vec_grid(size_t N) {
+  size_t blocks = (N + kBlock * 4 - 1) / (kBlock * 4);
+  const size_t cap = (size_t)kNumSMs * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+static __device__ __forceinline__ bool closed(const int* gate) { return *(volatile const int*)gate == 0; }
+
+__global__ void init_state_kernel(SolverState* st, int m, int max_iter, double tol) {
+  st->run_iter = 0;
+  st->run_cycle = 1;
+  st->status = 0;
+  st->converged = 0;
+  st->jlast = 0;
+  st->iters = 0;
+  st->cycles = 0;
+  st->max_iter = max_iter;
+  st->m = m;
+  st->zero_solution = 0;
+  st->counter = 0;
+  st->tol = tol;
+  st->bnorm = 0.0;
+  st->beta = 0.0;
+  st->rel_res = 0.0;
+}
+
+__global__ void mask_to_phi_kernel(const uint8_t* __restrict__ in_omega, uint8_t* __restrict__ phi, size_t N) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+    phi[p] = in_omega[p] ? 0 : 1;
+}
+
+// Eq. 2.17 right side with f(u) = u - u^3 + s, zero outside Omega (Section 2),
+// and the initial guess of Section 5; ||b||_2 goes to st->bnorm.
+__global__ void __launch_bounds__(kBlock) rhs_kernel(const double* __restrict__ u, const double* __restrict__ uu,
+                                                     const double* __restrict__ src, const uint8_t* __restrict__ phi,
+                                                     double dt, double* __restrict__ b, double* __restrict__ x0,
+                                                     size_t N, double* partials, SolverState* st) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    const double up = u[p];
+    const double f = up - up * up * up + (src ? src[p] : 0.0);
+    const double bp = up + (phi[p] ? 0.0 : dt * f);
+    b[p] = bp;
+    x0[p] = uu ? 2.0 * up - uu[p] : up;
+    acc += bp * bp;
+  }
+  const double bs = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+  if (arrive_last(&st->counter, gridDim.x)) {
+    const double tot = sum_partials(partials, gridDim.x, red);
+    if (threadIdx.x == 0) st->bnorm = sqrt(tot);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) norm_b_kernel(const double* __restrict__ b, size_t N, double* partials,
+                                                        SolverState* st) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    const double v = b[p];
+    acc += v * v;
+  }
+  const double bs = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+  if (arrive_last(&st->counter, gridDim.x)) {
+    const double tot = sum_partials(partials, gridDim.x, red);
+    if (threadIdx.x == 0) st->bnorm = sqrt(tot);
+  }
+}
+
+// h_i = <w, v_i> = s_i <V_{j+1}, V_i> for i = 0..j  (w is stored in slot j+1).
+// blockIdx.y selects a chunk of kDotChunk basis vectors; w is re-read per
+// chunk (it stays in L2).  accumulate = 1 adds to H (second CGS pass).
+__global__ void __launch_bounds__(kBlock) multidot_kernel(const double* __restrict__ V, size_t N, int j,
+                                                          int accumulate, double* partials, SolverState* st) {
+  if (closed(&st->run_iter)) return;
+  __shared__ double red[32];
+  const int i0 = blockIdx.y * kDotChunk;
+  const int cnt = min(kDotChunk, j + 1 - i0);
+  const double* __restrict__ w = V + (size_t)(j + 1) * N;
+  double acc[kDotChunk];
+#pragma unroll
+  for (int k = 0; k < kDotChunk; ++k) acc[k] = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    const double wp = w[p];
+#pragma unroll
+    for (int k = 0; k < kDotChunk; ++k)
+      if (k < cnt) acc[k] += wp * V[(size_t)(i0 + k) * N + p];
+  }
+  const int G = gridDim.x;
+#pragma unroll
+  for (int k = 0; k < kDotChunk; ++k) {
+    if (k < cnt) {  // uniform over the block
+      const double bs = block_sum(acc[k], red);
+      if (threadIdx.x == 0) partials[(size_t)(i0 + k) * G + blockIdx.x] = bs;
+    }
+  }
+  if (arrive_last(&st->counter, gridDim.x * gridDim.y)) {
+    for (int i = 0; i <= j; ++i) {
+      const double tot = sum_partials(partials + (size_t)i * G, G, red);
+      if (threadIdx.x == 0) {
+        const double h = st->s[i] * tot;
+        st->hcol[i] = h;
+        if (accumulate) st->H[i * kMaxRestart + j] += h;
+        else st->H[i * kMaxRestart + j] = h;
+      }
+    }
+  }
+}
+
+// V_{j+1} <- V_{j+1} - sum_i (h_i s_i) V_i and ||V_{j+1}||; on the final pass
+// the last block runs the Givens step.
+__global__ void __launch_bounds__(kBlock) update_kernel(double* __restrict__ V, size_t N, int j, int final_pass,
+                                                        double* partials, SolverState* st) {
+  if (closed(&st->run_iter)) return;
+  __shared__ double red[32];
+  __shared__ double coef[kMaxRestart + 1];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) coef[i] = st->hcol[i] * st->s[i];
+  __syncthreads();
+  double* __restrict__ w = V + (size_t)(j + 1) * N;
+  double acc = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    double val = w[p];
+    for (int i = 0; i <= j; ++i) val -= coef[i] * V[(size_t)i * N + p];
+    w[p] = val;
+    acc += val * val;
+  }
+  const double bs = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+  if (arrive_last(&st->counter, gridDim.x)) {
+    const double tot = sum_partials(partials, gridDim.x, red);
+    if (threadIdx.x == 0 && final_pass) givens_step(st, j, sqrt(tot));
+  }
+}
+
+// Back substitution R y = g for the jlast columns of the cycle.
+__global__ void solve_y_kernel(SolverState* st) {
+  if (closed(&st->run_cycle) || threadIdx.x != 0) return;
+  const int J = st->jlast;
+  for (int i = J - 1; i >= 0; --i) {
+    double s = st->g[i];
+    for (int k = i + 1; k < J; ++k) s -= st->H[i * kMaxRestart + k] * st->y[k];
+    st->y[i] = s / st->H[i * kMaxRestart + i];
+  }
+}
+
+// x <- x + sum_{i < jlast} y_i z_i  (flexible GMRES keeps the z_i).
+template <typename Tz>
+__global__ void __launch_bounds__(kBlock) xupdate_kernel(double* __restrict__ x, const Tz* __restrict__ Z, size_t N,
+                                                         SolverState* st) {
+  if (closed(&st->run_cycle)) return;
+  const int J = st->jlast;
+  if (J == 0) return;
+  __shared__ double y[kMaxRestart];
+  for (int i = threadIdx.x; i < J; i += blockDim.x) y[i] = st->y[i];
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    double v = x[p];
+    for (int i = 0; i < J; ++i) v += y[i] * double(Z[(size_t)i * N + p]);
+    x[p] = v;
+  }
+}
+
+__global__ void finalize_kernel(double* __restrict__ x, size_t N, SolverState* st) {
+  if (!st->zero_solution) return;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+    x[p] = 0.0;
+}
+
+// z = scale * v (the identity preconditioner of plain GMRES).
+template <typename Tz>
+__global__ void __launch_bounds__(kBlock) scale_copy_kernel(const double* __restrict__ v, const double* scale,
+                                                            Tz* __restrict__ z, size_t N, const int* gate) {
+  if (closed(gate)) return;
+  const double sc = *scale;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
+    z[p] = Tz(sc * v[p]);
+}
+
+// ---- launchers --------------------------------------------------------------
+void launch_init_state(SolverState* st, int m, int max_iter, double tol, cudaStream_t s) {
+  init_state_kernel<<<1, 1, 0, s>>>(st, m, max_iter, tol);
+}
+void launch_mask_to_phi(const uint8_t* in_omega, uint8_t* phi, size_t N, cudaStream_t s) {
+  mask_to_phi_kernel<<<vec_grid(N), kBlock, 0, s>>>(in_omega, phi, N);
+}
+void launch_rhs(const double* u, const double* uu, const double* src, const uint8_t* phi, double dt, double* b,
+                double* x0, size_t N, double* partials, SolverState* st, cudaStream_t s) {
+  rhs_kernel<<<vec_grid(N), kBlock, 0, s>>>(u, uu, src, phi, dt, b, x0, N, partials, st);
+}
+void launch_norm_b(const double* b, size_t N, double* partials, SolverState* st, cudaStream_t s) {
+  norm_b_kernel<<<vec_grid(N), kBlock, 0, s>>>(b, N, partials, st);
+}
+void launch_multidot(const double* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
+                     cudaStream_t s) {
+  dim3 grid(vec_grid(N), (j + 1 + kDotChunk - 1) / kDotChunk);
+  multidot_kernel<<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+}
+void launch_update(double* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s) {
+  update_kernel<<<vec_grid(N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st);
+}
+void launch_solve_y(SolverState* st, cudaStream_t s) { solve_y_kernel<<<1, 32, 0, s>>>(st); }
+template <typename Tz>
+void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s) {
+  xupdate_kernel<Tz><<<vec_grid(N), kBlock, 0, s>>>(x, Z, N, st);
+}
+template void launch_xupdate<double>(double*, const double*, size_t, SolverState*, cudaStream_t);
+template void launch_xupdate<float>(double*, const float*, size_t, SolverState*, cudaStream_t);
+void launch_finalize(double* x, size_t N, SolverState* st, cudaStream_t s) {
+  finalize_kernel<<<vec_grid(N), kBlock, 0, s>>>(x, N, st);
+}
+
+template <typename Tz>
+void launch_scale_copy(const double* v, const double* scale, Tz* z, size_t N, const int* gate, cudaStream_t s) {
+  scale_copy_kernel<Tz><<<vec_grid(N), kBlock, 0, s>>>(v, scale, z, N, gate);
+}
+template void launch_scale_copy<double>(const double*, const double*, double*, size_t, const int*, cudaStream_t);
+template void launch_scale_copy<float>(const double*, const double*, float*, size_t, const int*, cudaStream_t);
+
+}  // namespace rsfde

@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Tolerances (FP64 path): operator and transform outputs agree to 1e-12 of the
+output's max norm (the FFT evaluation differs from the oracle's dense sums by
+O(eps log L) of the operand norm); solves reach a true relative residual
+<= 1e-10 and the solution differs from the oracle's by <= 1e-9 in relative
+max norm.  FP32 preconditioner: the apply agrees to 1e-5 relative (FP32 FFTs),
+while the solve still reaches the FP64 tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_11576_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2102_11576_gb300 import Solver, RsfdeError  # noqa: E402
+
+SIZES = [(1, 1), (2, 3), (5, 7), (16, 16), (33, 20), (64, 64), (65, 127), (200, 96)]
+
+
+def pair(w, **kw):
+    args = (w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
+            w["dt"], w["eta"])
+    return oracle.Problem(*args), Solver(*args, **kw)
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n1,n2", SIZES)
+def test_tables_match_oracle(n1, n2):
+    w = workloads.random_problem(1, n1, n2)
+    orc, gpu = pair(w)
+    t = gpu.tables()
+    tx, ty = orc.toeplitz()
+    lx, ly = orc.tau_eigs()
+    np.testing.assert_allclose(t["t_x"], tx, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(t["t_y"], ty, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(t["lam_x"], lx, rtol=1e-11, atol=1e-12 * np.abs(lx).max())
+    np.testing.assert_allclose(t["lam_y"], ly, rtol=1e-11, atol=1e-12 * np.abs(ly).max())
+    p = gpu.params()
+    assert p["cx"] == pytest.approx(orc.cx, rel=1e-14) and p["pen"] == pytest.approx(orc.pen)
+
+
+@pytest.mark.parametrize("n1,n2", SIZES)
+def test_apply_M(n1, n2):
+    w = workloads.random_problem(2, n1, n2)
+    orc, gpu = pair(w)
+    z = w["field"]
+    ref = orc.apply_M(z)
+    got = host(gpu.apply_M(dev(z)))
+    # scale: the Toeplitz sums, not the (possibly cancelling) result
+    scale = (np.abs(z).max() * (1 + np.abs(orc.toeplitz()[0]).sum() * 2 + np.abs(orc.toeplitz()[1]).sum() * 2
+                                + orc.pen))
+    assert np.abs(got - ref).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("n1,n2", SIZES)
+def test_dst2(n1, n2):
+    w = workloads.random_problem(3, n1, n2)
+    orc, gpu = pair(w)
+    v = w["field"]
+    ref = orc.dst2(v)
+    got = host(gpu.dst2(dev(v)))
+    assert rel(got, ref) <= 1e-12
+    # involution S^2 = I on the GPU alone
+    back = host(gpu.dst2(dev(got)))
+    assert rel(back, v) <= 1e-12
+
+
+@pytest.mark.parametrize("n1,n2", SIZES)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_apply_precond(n1, n2, prec, tol):
+    w = workloads.random_problem(4, n1, n2)
+    orc, gpu = pair(w, precond=prec)
+    v = w["field"]
+    ref = orc.apply_precond(v)
+    got = host(gpu.apply_precond(dev(v)))
+    assert rel(got, ref) <= tol
+
+
+@pytest.mark.parametrize("n1,n2", [(1, 1), (5, 7), (33, 20), (64, 64), (65, 127)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("arnoldi", ["cgs", "cgs2"])
+def test_solve_matches_oracle(n1, n2, prec, arnoldi):
+    w = workloads.random_problem(5, n1, n2)
+    orc, gpu = pair(w, precond=prec, arnoldi=arnoldi, tol=1e-11, restart=10)
+    rng = np.random.default_rng(0)
+    b = rng.standard_normal((n2, n1))
+    x_ref, st_ref = orc.fgmres(b, restart=10, tol=1e-12)
+    x, st = gpu.solve(dev(b))
+    x = host(x)
+    assert st["converged"] and st["rel_res"] <= 1e-11
+    r = b - orc.apply_M(x)
+    assert np.linalg.norm(r) <= 1e-11 * np.linalg.norm(b) * 1.01
+    # Lemma 3.1 + Lemma 2.3: ||M^-1||_inf <= 1
+    assert np.abs(x - x_ref).max() <= np.abs(r).max() + np.abs(b - orc.apply_M(x_ref)).max() + 1e-15
+    assert rel(x, x_ref) <= 1e-9
+
+
+def test_unpreconditioned_and_dense_lu():
+    w = workloads.random_problem(6, 9, 8)
+    orc, gpu = pair(w, use_precond=False, tol=1e-12, restart=30)
+    b = np.random.default_rng(1).standard_normal((8, 9))
+    x, st = gpu.solve(dev(b))
+    x_lu = oracle.lu_solve(orc.dense_M(), b.reshape(-1)).reshape(8, 9)
+    assert st["converged"] and rel(host(x), x_lu) <= 1e-9
+
+
+def test_march_disk64_matches_oracle():
+    w = workloads.make("disk64")
+    orc, gpu = pair(w, tol=1e-12, restart=w["restart"])
+    steps = 16
+    u_ref, st_ref = orc.march(w["u0"], steps, restart=w["restart"], tol=1e-12)
+    u, st = gpu.march(dev(w["u0"]), steps)
+    u = host(u)
+    assert all(s["converged"] for s in st)
+    assert rel(u, u_ref) <= 1e-9
+    it_gpu = np.mean([s["iters"] for s in st])
+    it_ref = np.mean([s["iters"] for s in st_ref])
+    assert abs(it_gpu - it_ref) <= 0.1 * it_ref + 1  # same method, different Gram-Schmidt
+
+
+def test_step_host_equals_step():
+    w = workloads.make("disk64", n=48)
+    _, gpu = pair(w)
+    u0 = w["u0"]
+    d, _ = gpu.step(dev(u0))
+    h, _ = gpu.step_host(u0)
+    np.testing.assert_array_equal(host(d), h)
+
+
+def test_rhs_and_guess():
+    w = workloads.make("ellipse512", n=40)
+    orc, gpu = pair(w)
+    rng = np.random.default_rng(2)
+    u, uu = rng.standard_normal((40, 40)), rng.standard_normal((40, 40))
+    b, x0 = gpu.rhs(dev(u), dev(uu), dev(w["src"]))
+    np.testing.assert_allclose(host(b), orc.rhs(u, w["src"]), rtol=1e-15, atol=1e-15)
+    np.testing.assert_allclose(host(x0), orc.initial_guess(u, uu), rtol=0, atol=0)
+
+
+def test_edge_cases():
+    w = workloads.random_problem(7, 12, 10)
+    orc, gpu = pair(w)
+    # b = 0 gives x = 0 in zero iterations
+    x, st = gpu.solve(dev(np.zeros((10, 12))), dev(np.ones((10, 12))))
+    assert st["converged"] and st["iters"] == 0 and np.all(host(x) == 0)
+    # exact initial guess: no iteration
+    xs = np.random.default_rng(3).standard_normal((10, 12))
+    x, st = gpu.solve(dev(orc.apply_M(xs)), dev(xs))
+    assert st["converged"] and st["iters"] == 0
+    # NaN in the right side
+    b = np.ones((10, 12))
+    b[3, 4] = np.nan
+    with pytest.raises(RsfdeError) as e:
+        gpu.solve(dev(b))
+    assert e.value.name == "ENONFINITE"
+    # max_iter too small
+    g2 = Solver(12, 10, w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"], w["dt"],
+                w["eta"], max_iter=1, tol=1e-14)
+    with pytest.raises(RsfdeError) as e:
+        g2.solve(dev(np.random.default_rng(4).standard_normal((10, 12))))
+    assert e.value.name == "ENOTCONV"
+    # invalid arguments
+    with pytest.raises(RsfdeError) as e:
+        Solver(12, 10, w["box"], w["in_omega"], 2.5, 1.5, 1, 1, 0.1, 1e-3)
+    assert e.value.name == "EINVAL"
+    # all-inside and all-outside masks
+    for val in (0, 1):
+        w2 = dict(w, in_omega=np.full((10, 12), val, np.uint8))
+        orc2, gpu2 = pair(w2, tol=1e-12)
+        b = np.random.default_rng(5).standard_normal((10, 12))
+        x, st = gpu2.solve(dev(b))
+        x = host(x)
+        assert st["converged"]
+        assert np.linalg.norm(b - orc2.apply_M(x)) <= 1.01e-12 * np.linalg.norm(b)
+
+
+def test_full_size_polygon2048_sampled():
+    """The benchmark's 2048^2 workload, one step each preconditioner precision:
+    M z on sampled points and the true residual of the step by the oracle."""
+    w = workloads.make("polygon2048")
+    orc = oracle.Problem(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"],
+                         w["kx"], w["ky"], w["dt"], w["eta"])
+    rng = np.random.default_rng(0)
+    idx = rng.choice(w["n1"] * w["n2"], size=256, replace=False)
+    u0 = w["u0"]
+    for prec in ("fp32", "fp64"):
+        gpu = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"],
+                     w["ky"], w["dt"], w["eta"], restart=w["restart"], precond=prec)
+        z = rng.standard_normal((w["n2"], w["n1"]))
+        mz = host(gpu.apply_M(dev(z))).reshape(-1)[idx]
+        ref = orc.apply_M_points(z, idx)
+        scale = np.abs(z).max() * (1 + 2 * np.abs(orc.toeplitz()[0]).sum()
+                                   + 2 * np.abs(orc.toeplitz()[1]).sum())
+        assert np.abs(mz - ref).max() <= 1e-13 * scale
+        u1, st = gpu.step(dev(u0))
+        u1 = host(u1)
+        assert st["converged"] and st["rel_res"] <= 1e-10
+        b = orc.rhs(u0)
+        r_pts = b.reshape(-1)[idx] - orc.apply_M_points(u1, idx)
+        # pointwise residual at sampled points is consistent with the global bound
+        assert np.abs(r_pts).max() <= 1e-10 * np.linalg.norm(b)

@@ -85,6 +85,14 @@ def test_matvec_equals_pointwise_scheme(n1, n2):
                                    atol=1e-12)
 
 
+def test_matvec_points_equals_full_product():
+    rng = np.random.default_rng(9)
+    prob = tiny_problem(rng, 13, 11)
+    u = rng.standard_normal((11, 13))
+    idx = rng.choice(prob.N, size=40, replace=False)
+    np.testing.assert_array_equal(prob.apply_M_points(u, idx), prob.apply_M(u).reshape(-1)[idx])
+
+
 def test_diffusion_scale_definition():
     # c_x = dt k_x c_alpha / h_x^alpha with h_x = (b - a)/(n1 + 1)
     rng = np.random.default_rng(1)
