@@ -1,0 +1,516 @@
+#!/usr/bin/env python3
+"""Benchmark: implicit time steps per second of the volume-penalized 2D Riesz
+space-fractional diffusion scheme (Eq. 2.17), each step solved by flexible
+GMRES with the sine-transform preconditioner (Eq. 4.6) to a true relative
+residual of 1e-10, on the 2048 x 2048 convex 12-gon workload
+(paper_2102_11576_gb300.workloads, recipe "polygon2048").
+
+One "step" is one implicit time step: right side, initial guess, and the
+whole FGMRES solve.  The headline value is the mixed form (preconditioner in
+FP32, operator / residual / Arnoldi / Givens in FP64); the plain FP64 form is
+measured beside it.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the single-instance solve does not shard (every column pass would
+be an all-to-all); N ranks run N independent replicas, no collective on the
+data path.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "implicit steps/s at 2048² grid, rel.res 1e-10: mixed vs FP64; % HBM roofline"
+UNIT = "steps/s"
+WORKLOAD = "polygon2048"
+
+# ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# the kernel classes, with the hash of the CUDA sources they were taken from;
+# reported as null once the sources change.
+TRAFFIC = {}
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2102_11576_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP64 FMA rate: 152 SMs x 2 DFMA per clock per SM x 2 flop x clock (a probe of
+# dependent-chain-free DFMA streams measured 1.205 TFLOP/s at ~1.98 GHz).
+def fp64_peak_gflops(sm_mhz):
+    return 152 * 2 * 2 * sm_mhz / 1e3
+
+
+def fp32_peak_gflops(sm_mhz):
+    return 152 * 128 * 2 * sm_mhz / 1e3
+
+
+# ---------------------------------------------------------------- clocks -----
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid_hint):
+        self.uuid_hint = (uuid_hint or "").lower()
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.strip()]
+        mine = [r for r in rows if len(r) >= 10 and self.uuid_hint and self.uuid_hint in r[1].lower()]
+        if not mine:
+            idx0 = [r for r in rows if len(r) >= 10 and r[0] == rows[0][0]] if rows else []
+            mine = idx0
+        if not mine:
+            return None
+        sm = [float(r[2]) for r in mine if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in mine:
+            for k, name in enumerate(names):
+                if r[6 + k].strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(mine[0][3]) if mine[0][3].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(mine)}
+
+
+# ------------------------------------------------------------ our arm ------
+def algorithmic_bytes_per_iter(N, m, ez):
+    """Minimal HBM bytes of one FGMRES(m) iteration, averaged over a cycle:
+    precond read v / write z, matvec read z / write w, CGS dots and update over
+    the j+1 basis vectors (8N(2j+4)), the mask, and the per-cycle x update
+    and true residual spread over m iterations."""
+    cgs = 8 * N * (m - 1 + 4)           # mean over j = 0..m-1 of 8N(2j+4)
+    pre = (8 + ez) * N
+    mv = (ez + 8) * N
+    mask = N / 8
+    cyc = ((ez * m + 16) * N + 32 * N) / m
+    return pre + mv + cgs + mask + cyc
+
+
+def kernel_units(name, n1, n2, L1, L2):
+    """Algorithmic work of one launch of a kernel class (flops, unit).
+
+    Toeplitz passes: per vector two real FFTs of length L plus 3L pointwise
+    flops, 5 L log2 L + 3 L.  Sine-transform passes: the flop count of a
+    real DST-I of length n computed as a real FFT of length 2(n+1),
+    2.5 * 2(n+1) log2(2(n+1)) per vector and transform."""
+    import math
+    def dst(n):
+        m = 2 * (n + 1)
+        return 2.5 * m * math.log2(m)
+    if name == "toeplitz_rows":
+        return n2 * (5 * L1 * math.log2(L1) + 3 * L1)
+    if name == "toeplitz_cols":
+        return n1 * (5 * L2 * math.log2(L2) + 3 * L2)
+    if name == "dst_rows":
+        return n2 * dst(n1)
+    if name == "precond_cols":
+        return n1 * 3 * dst(n2)
+    if name == "precond_rows":
+        return n2 * 2 * dst(n1)
+    return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2102_11576_gb300 import Solver, workloads
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = workloads.make(args.workload)
+    n1, n2, N = w["n1"], w["n2"], w["n1"] * w["n2"]
+    mk = dict(restart=w["restart"], tol=w["tol"])
+    solver_args = (n1, n2, w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
+                   w["dt"], w["eta"])
+    u0 = torch.as_tensor(w["u0"]).to(dev)
+    peaks, peak_src = measured_peaks()
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+
+    def barrier():
+        if dist:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    def march(solver, bufs, state, nsteps, stats):
+        for _ in range(nsteps):
+            prev, prevprev = state
+            nxt = ({0, 1, 2} - {prev, prevprev}).pop()
+            _, st = solver.step(bufs[prev], None if prevprev is None else bufs[prevprev],
+                                out=bufs[nxt])
+            stats.append(st)
+            state = (nxt, prev)
+        return state
+
+    def timed_form(precond, steps, warmup, profile_steps, clocks=None):
+        solver = Solver(*solver_args, precond=precond, **mk)
+        bufs = [u0.clone(), torch.empty_like(u0), torch.empty_like(u0)]
+        state = (0, None)
+        state = march(solver, bufs, state, warmup, [])
+        barrier()
+        l0 = solver.kernel_launches
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if clocks:
+            clocks.start()
+        e0.record(stream)
+        stats = []
+        state = march(solver, bufs, state, steps, stats)
+        e1.record(stream)
+        barrier()
+        clk = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        launches = solver.kernel_launches - l0
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            ms = float(t.item())
+        # live per-kernel timing: the same march continued with every launch
+        # bracketed by CUDA events on this stream
+        prof = None
+        if profile_steps:
+            solver.profile(True)
+            pstats = []
+            march(solver, bufs, state, profile_steps, pstats)
+            prof = solver.profile_read()
+            solver.profile(False)
+            prof = {"steps": profile_steps, "kernels": prof,
+                    "iters": sum(s["iters"] for s in pstats),
+                    "cycles": sum(s["restarts"] + 1 for s in pstats)}
+        iters = [s["iters"] for s in stats]
+        out = {"ms": ms, "steps": steps, "launches": launches, "clocks": clk, "prof": prof,
+               "iters_per_step": float(np.mean(iters)), "max_rel_res": max(s["rel_res"] for s in stats),
+               "all_converged": all(s["converged"] for s in stats), "u": bufs[state[0]]}
+        solver.close()
+        return out
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    mixed = timed_form("fp32", args.steps, args.warmup, args.profile_steps, clocks)
+    plain = None
+    if not args.no_fp64:
+        plain = timed_form("fp64", args.fp64_steps, args.warmup, args.profile_steps)
+        # error of the mixed result against the FP64 form after the same march
+    value = world * args.steps / (mixed["ms"] / 1e3)
+
+    # ---- roofline of the dominant kernel (mixed form) ----
+    from paper_2102_11576_gb300 import Solver as _S  # noqa: F401
+    L1 = 4
+    while L1 < 2 * n1 - 1:
+        L1 *= 2
+    L2 = 4
+    while L2 < 2 * n2 - 1:
+        L2 *= 2
+    roof = None
+    kern = mixed["prof"]["kernels"] if mixed["prof"] else {}
+    if kern:
+        dom = max(kern, key=lambda k: kern[k][0])
+        tot_ms, nl = kern[dom]
+        iters_p, cycles_p = mixed["prof"]["iters"], mixed["prof"]["cycles"]
+        # launches that did work: one per Arnoldi iteration, plus one per true
+        # residual for the Toeplitz passes; gated no-op launches after
+        # convergence are counted in the time (a few microseconds each)
+        work = iters_p + (cycles_p + mixed["prof"]["steps"] if dom.startswith("toeplitz") else 0)
+        avg_ms = tot_ms / max(work, 1)
+        flops = kernel_units(dom, n1, n2, L1, L2)
+        sm_mhz = (mixed["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        fp64_like = dom.startswith("toeplitz")
+        peak = fp64_peak_gflops(peaks.get("sm_max_mhz", 2070.0)) if fp64_like else \
+            fp32_peak_gflops(peaks.get("sm_max_mhz", 2070.0))
+        achieved = flops / (avg_ms / 1e3) / 1e9 if flops else None
+        tr = TRAFFIC.get(dom)
+        traffic = tr["bytes_per_launch"] if tr and tr.get("src") == src_hash() else None
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 2) if achieved else None,
+                "peak": round(peak, 1), "unit": "GFLOP/s",
+                "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
+                "precision": "fp64" if fp64_like else "fp32",
+                "peak_source": "152 SMs x per-clock unit rate x sm_max_mhz (derived)",
+                "avg_launch_ms": round(avg_ms, 4), "launches_with_work": work,
+                "share_of_profiled_time": round(tot_ms / sum(v[0] for v in kern.values()), 4),
+                "per_kernel_ms": {k: round(v[0], 3) for k, v in kern.items()},
+                "per_kernel_launches": {k: v[1] for k, v in kern.items()}}
+    # whole-step HBM roofline (the metric's "% HBM roofline")
+    ez = 4
+    bpi = algorithmic_bytes_per_iter(N, w["restart"], ez)
+    bytes_step = mixed["iters_per_step"] * bpi + 40 * N
+    ach_gbs = bytes_step / (mixed["ms"] / mixed["steps"] / 1e3) / 1e9
+    hbm = {"algorithmic_bytes_per_step": bytes_step, "achieved_GBs": round(ach_gbs, 1),
+           "peak_GBs": peaks["hbm_gbs"], "frac": round(ach_gbs / peaks["hbm_gbs"], 4),
+           "peak_source": peak_src}
+
+    # ---- end to end through the C ABI with host arrays ----
+    e2e = None
+    if not args.no_e2e:
+        solver = Solver(*solver_args, precond="fp32", **mk)
+        h = [torch.empty((n2, n1), dtype=torch.float64).pin_memory() for _ in range(3)]
+        h[0].copy_(torch.as_tensor(w["u0"]))
+        hn = [t.numpy() for t in h]
+        prev, prevprev = 0, None
+        for _ in range(args.warmup):
+            nxt = ({0, 1, 2} - {prev, prevprev}).pop()
+            solver.step_host(hn[prev], None if prevprev is None else hn[prevprev], out=hn[nxt])
+            prevprev, prev = prev, nxt
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            nxt = ({0, 1, 2} - {prev, prevprev}).pop()
+            solver.step_host(hn[prev], hn[prevprev], out=hn[nxt])
+            prevprev, prev = prev, nxt
+        barrier()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            el = float(t.item())
+        solver.close()
+        e2e = {"value": round(world * args.steps / el, 4), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8}
+
+    # ---- error of the mixed result against the FP64 form ----
+    err = None
+    if plain is not None and args.fp64_steps == args.steps:
+        a, b = mixed["u"], plain["u"]
+        err = float((a - b).abs().max() / b.abs().max())
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        iters = plain["iters_per_step"] if plain else mixed["iters_per_step"]
+        cpu = oracle_sample(w, iters, args.cpu_seconds)
+
+    res = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(mixed["ms"] / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded 12-gon domain, bump initial field)",
+        "config": {"workload": f"{WORKLOAD}: {n1}x{n2} grid, convex 12-gon, alpha=(1.3,1.6), k=(1,1), "
+                               f"dt=0.02, eta=1e-8, FGMRES({w['restart']}), tol 1e-10",
+                   "form": "mixed: preconditioner FP32; operator, residual, Arnoldi, Givens FP64",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "working set > L2 (Krylov basis 41 vectors x 33.5 MB)"},
+        "iters_per_step": round(mixed["iters_per_step"], 2),
+        "max_rel_res": mixed["max_rel_res"], "all_converged": mixed["all_converged"],
+        "forms": {"fp32": {"steps_per_s": round(value / world, 4),
+                           "iters_per_step": round(mixed["iters_per_step"], 2),
+                           "ms_per_step": round(mixed["ms"] / args.steps, 3)}},
+        "hbm_roofline_step": hbm,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": mixed["launches"],
+        "clocks": mixed["clocks"],
+    }
+    if plain is not None:
+        res["forms"]["fp64"] = {"steps_per_s": round(plain["steps"] / (plain["ms"] / 1e3), 4),
+                                "iters_per_step": round(plain["iters_per_step"], 2),
+                                "ms_per_step": round(plain["ms"] / plain["steps"], 3),
+                                "max_rel_res": plain["max_rel_res"],
+                                "roofline_kernels_ms": ({k: round(v[0], 2) for k, v in
+                                                         plain["prof"]["kernels"].items()}
+                                                        if plain["prof"] else None)}
+        res["forms"]["speedup_mixed_over_fp64"] = round(
+            res["forms"]["fp32"]["steps_per_s"] / res["forms"]["fp64"]["steps_per_s"], 3)
+        res["forms"]["mixed_vs_fp64_rel_maxnorm_diff"] = err
+    return res
+
+
+# ------------------------------------------------------------ oracle -------
+def oracle_sample(w, iters_per_step, budget_s):
+    """The CPU oracle timed on a bounded sample of one FGMRES iteration of the
+    workload, scaled to steps/s.  Sample: the operator M at P random grid
+    points (or_apply_M_points) and R row and R column sine transforms of the
+    oracle's table-driven routine; one iteration costs N point products plus
+    3 x (n2 row + n1 column) transforms (Eq. 4.6 applies three 2D transforms).
+    The Gram-Schmidt vector work (~4(j+1)N flops, < 1 % of the transforms)
+    is left out."""
+    import oracle
+    n1, n2 = w["n1"], w["n2"]
+    N = n1 * n2
+    prob = oracle.Problem(n1, n2, w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"],
+                          w["ky"], w["dt"], w["eta"])
+    rng = np.random.default_rng(0)
+    z = rng.standard_normal((n2, n1))
+    share = budget_s / 3.0
+    # calibrate sample sizes to the time budget
+    P = 256
+    t = time.perf_counter()
+    prob.apply_M_points(z, rng.choice(N, P, replace=False))
+    tp = (time.perf_counter() - t) / P
+    P = int(min(N, max(256, share / max(tp, 1e-9))))
+    t = time.perf_counter()
+    prob.apply_M_points(z, rng.choice(N, P, replace=False))
+    tp = (time.perf_counter() - t) / P
+    R = 4
+    t = time.perf_counter()
+    prob.dst2_rows_sample(z, R)
+    tr = (time.perf_counter() - t) / R
+    R = int(min(n2, max(4, share / max(tr, 1e-9))))
+    t = time.perf_counter()
+    prob.dst2_rows_sample(z, R)
+    tr = (time.perf_counter() - t) / R
+    Rc = int(min(n1, max(4, share / max(tr, 1e-9))))
+    t = time.perf_counter()
+    prob.dst2_cols_sample(z, Rc)
+    tc = (time.perf_counter() - t) / Rc
+    t_iter = N * tp + 3 * (n2 * tr + n1 * tc)
+    t_step = iters_per_step * t_iter
+    return {"value": 1.0 / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one FGMRES iteration at {n1}x{n2} from M at {P} sampled points and "
+                       f"{R} row + {Rc} column sine transforms, scaled to the full grid "
+                       f"({t_iter:.1f} s/iteration) x {iters_per_step:.2f} iterations/step"),
+            "s_per_iteration": t_iter}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from paper_2102_11576_gb300 import workloads
+    w = workloads.make(args.workload)
+    iters = args.iters_per_step
+    per_step = []
+    for _ in range(args.warmup):
+        oracle_sample(w, iters, args.cpu_seconds / 4)
+    for _ in range(args.steps):
+        per_step.append(oracle_sample(w, iters, args.cpu_seconds / 4))
+    t_iter = statistics.median(p["s_per_iteration"] for p in per_step)
+    value = 1.0 / (iters * t_iter)
+    cpu = dict(per_step[-1])
+    cpu["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded 12-gon domain, bump initial field)",
+            "config": {"workload": f"{WORKLOAD}: {w['n1']}x{w['n2']} grid, convex 12-gon, "
+                                   f"FGMRES({w['restart']}), tol 1e-10",
+                       "iters_per_step": iters},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_op(args):
+    """Times one operator-level entry point of the C ABI on the benchmark
+    workload (a small, fixed command for ncu captures and per-operator
+    timing)."""
+    import torch
+    from paper_2102_11576_gb300 import Solver, workloads
+    w = workloads.make(args.workload)
+    prec = "fp64" if args.op.endswith("fp64") else "fp32"
+    s = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
+               w["dt"], w["eta"], restart=w["restart"], precond=prec)
+    rng = np.random.default_rng(0)
+    v = torch.as_tensor(rng.standard_normal((w["n2"], w["n1"]))).cuda()
+    out = torch.empty_like(v)
+    fn = {"apply_M": s.apply_M, "precond_fp32": s.apply_precond, "precond_fp64": s.apply_precond,
+          "dst2": s.dst2}[args.op]
+    fn(v, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.reps):
+        fn(v, out)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"op": args.op, "workload": args.workload, "reps": args.reps,
+                      "ms_per_call": e0.elapsed_time(e1) / args.reps}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["apply_M", "precond_fp32", "precond_fp64", "dst2"], default=None,
+                    help="time one operator entry point instead of the time march")
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--profile-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--iters-per-step", type=float, default=None,
+                    help="FGMRES iterations per step used to scale the oracle's per-iteration "
+                         "time in --impl reference (default: the workload's recorded count)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.fp64_steps is None:
+        args.fp64_steps = args.steps
+    if args.op:
+        run_op(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if args.iters_per_step is None:
+            from paper_2102_11576_gb300 import workloads
+            args.iters_per_step = workloads.make(args.workload, n=8)["iters_per_step_recorded"]
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -144,6 +144,28 @@ int rsfde_get_tables(rsfde_ctx* ctx, double* lam_x, double* lam_y, double* t_x, 
 /* c_x, c_y, dt/eta, h_x, h_y to a HOST array of 5 doubles. */
 int rsfde_get_params(rsfde_ctx* ctx, double* out5);
 
+/* ---- measurement ------------------------------------------------------------ */
+/* Kernel classes timed by the profiler. */
+#define RSFDE_K_TOEPLITZ_ROWS 0 /* (I (x) A_x) z, Eq. 2.15 */
+#define RSFDE_K_TOEPLITZ_COLS 1 /* (A_y (x) I) z fused with the rest of M (or the residual) */
+#define RSFDE_K_DST_ROWS 2      /* first row sine transform of Eq. 4.6 */
+#define RSFDE_K_PRECOND_COLS 3  /* column sine transforms and tau divides of Eq. 4.6 */
+#define RSFDE_K_PRECOND_ROWS 4  /* last row sine transforms and the masked combine of Eq. 4.6 */
+#define RSFDE_K_MULTIDOT 5      /* Arnoldi inner products */
+#define RSFDE_K_UPDATE 6        /* Arnoldi update, norm and Givens step */
+#define RSFDE_K_XUPDATE 7       /* solution update x += Z y */
+#define RSFDE_K_OTHER 8         /* right side, norms, scalar kernels */
+#define RSFDE_K_COUNT 9
+
+/* While on, every kernel launch of the context is bracketed by a pair of CUDA
+ * events on the context's stream (adds one event record per launch). */
+int rsfde_profile_enable(rsfde_ctx* ctx, int on);
+/* Synchronises the stream and writes, per kernel class, the summed device
+ * time in ms (HOST array of RSFDE_K_COUNT doubles) and the number of launches
+ * (HOST array of RSFDE_K_COUNT int64), then clears the accumulators. */
+int rsfde_profile_read(rsfde_ctx* ctx, double* ms, int64_t* launches);
+const char* rsfde_kernel_class_name(int k);
+
 /* Number of this library's kernel launches since the context was made (host counter). */
 int64_t rsfde_kernel_launches(const rsfde_ctx* ctx);
 

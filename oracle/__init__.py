@@ -45,6 +45,8 @@ def _load():
     lib.or_apply_M.argtypes = [vp, _dp, _dp]
     lib.or_apply_M_points.argtypes = [vp, _dp, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _dp]
     lib.or_dst2.argtypes = [vp, _dp, _dp]
+    lib.or_dst2_rows_sample.argtypes = [vp, _dp, i, _dp]
+    lib.or_dst2_cols_sample.argtypes = [vp, _dp, i, _dp]
     lib.or_apply_precond.argtypes = [vp, _dp, _dp]
     lib.or_fgmres.restype = i
     lib.or_fgmres.argtypes = [vp, _dp, _dp, i, d, i, i, _dp]
@@ -196,6 +198,18 @@ class Problem:
         w = np.empty_like(v)
         _load().or_dst2(self._h, _p(v), _p(w))
         return w
+
+    def dst2_rows_sample(self, v, count):
+        v = self._grid(v)
+        out = np.zeros_like(v)
+        _load().or_dst2_rows_sample(self._h, _p(v), int(count), _p(out))
+        return out
+
+    def dst2_cols_sample(self, v, count):
+        v = self._grid(v)
+        out = np.zeros_like(v)
+        _load().or_dst2_cols_sample(self._h, _p(v), int(count), _p(out))
+        return out
 
     def apply_precond(self, v):
         v = self._grid(v)

@@ -247,6 +247,17 @@ void or_dst2(const or_ctx* c, const double* v, double* out) {
   free(tmp);
 }
 
+/* The first `count` row (x) or column (y) sine transforms that or_dst2 performs,
+ * with the same table-driven routine; used to time a bounded sample of the
+ * oracle's transform work on grids too large to transform whole. */
+void or_dst2_rows_sample(const or_ctx* c, const double* v, int count, double* out) {
+  for (int j = 0; j < count && j < c->n2; ++j)
+    dst1_strided(c->n1, v + (long)j * c->n1, 1, out + (long)j * c->n1, 1, c->sinx);
+}
+void or_dst2_cols_sample(const or_ctx* c, const double* v, int count, double* out) {
+  for (int i = 0; i < count && i < c->n1; ++i) dst1_strided(c->n2, v + i, c->n1, out + i, c->n1, c->siny);
+}
+
 /* Eq. 4.6: z = P^-1 v = (I - Phi)(I - tau_1(A))^-1 v + Phi((1 + dt/eta) I - tau_1(A))^-1 v,
  * with I - tau_1(A) = (S (x) S)(I - I (x) L_x - L_y (x) I)(S (x) S) (proof of Lemma 4.2). */
 void or_apply_precond(const or_ctx* c, const double* v, double* z) {

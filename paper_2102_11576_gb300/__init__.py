@@ -84,6 +84,12 @@ def load_library(path=LIB_PATH):
     lib.rsfde_rhs.argtypes = [vp, dp, dp, dp, dp, dp]
     lib.rsfde_get_tables.argtypes = [vp, dp, dp, dp, dp]
     lib.rsfde_get_params.argtypes = [vp, dp]
+    lib.rsfde_profile_enable.argtypes = [vp, i32]
+    lib.rsfde_profile_enable.restype = ctypes.c_int
+    lib.rsfde_profile_read.argtypes = [vp, dp, dp]
+    lib.rsfde_profile_read.restype = ctypes.c_int
+    lib.rsfde_kernel_class_name.argtypes = [i32]
+    lib.rsfde_kernel_class_name.restype = ctypes.c_char_p
     lib.rsfde_kernel_launches.argtypes = [vp]
     lib.rsfde_kernel_launches.restype = ctypes.c_int64
     lib.rsfde_destroy.argtypes = [vp]
@@ -273,6 +279,20 @@ class Solver:
         out = np.empty(5)
         _check(self._lib.rsfde_get_params(self._h, ctypes.c_void_p(out.ctypes.data)), "params")
         return dict(zip(("cx", "cy", "pen", "hx", "hy"), out.tolist()))
+
+    def profile(self, on=True):
+        """Brackets every kernel launch with CUDA events on the solver's stream."""
+        _check(self._lib.rsfde_profile_enable(self._h, int(bool(on))), "profile_enable")
+
+    def profile_read(self):
+        """{kernel class: (device ms, launches)} since the last read."""
+        K = 9
+        ms = np.zeros(K)
+        n = np.zeros(K, dtype=np.int64)
+        _check(self._lib.rsfde_profile_read(self._h, ctypes.c_void_p(ms.ctypes.data),
+                                            ctypes.c_void_p(n.ctypes.data)), "profile_read")
+        return {self._lib.rsfde_kernel_class_name(k).decode(): (float(ms[k]), int(n[k]))
+                for k in range(K)}
 
     @property
     def kernel_launches(self):

@@ -193,6 +193,12 @@ struct rsfde_ctx {
   SolverState* st = nullptr;
   SolverState* st_host = nullptr;  // pinned
   int64_t launches = 0;
+  // profiler: event pairs per kernel class, recorded while prof_on
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double prof_ms[RSFDE_K_COUNT] = {0};
+  int64_t prof_n[RSFDE_K_COUNT] = {0};
 };
 
 namespace {
@@ -206,6 +212,47 @@ int cuda_fail(cudaError_t e) {
 }
 
 int check_launch(rsfde_ctx* c) { return cuda_fail(cudaGetLastError()); }
+
+cudaEvent_t prof_event(rsfde_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one launch of kernel class k with events when profiling is on.
+struct ProfScope {
+  rsfde_ctx* c;
+  int k;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(rsfde_ctx* c_, int k_) : c(c_), k(k_) {
+    c->launches += 1;
+    if (!c->prof_on) return;
+    a = prof_event(c);
+    b = prof_event(c);
+    cudaEventRecord(a, c->stream);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEventRecord(b, c->stream);
+    c->ev_pending.push_back({k, {a, b}});
+  }
+};
+
+void prof_harvest(rsfde_ctx* c) {
+  for (auto& p : c->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) c->prof_ms[p.first] += ms;
+    c->prof_n[p.first] += 1;
+    c->ev_pool.push_back(p.second.first);
+    c->ev_pool.push_back(p.second.second);
+  }
+  c->ev_pending.clear();
+}
 
 int build_tables(rsfde_ctx* c) {
   c->hx = (c->bx - c->ax) / (c->n1 + 1);  // Section 2
@@ -225,6 +272,11 @@ int build_tables(rsfde_ctx* c) {
 
 void free_ctx(rsfde_ctx* c) {
   if (!c) return;
+  for (auto& p : c->ev_pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->x64.release();
   c->y64.release();
   c->x32.release();
@@ -242,18 +294,28 @@ bool fp32_precond(const rsfde_ctx* c) { return c->opts.precond_prec == RSFDE_FP3
 // w = M z (Eq. 2.17), z in precision Tz.
 template <typename Tz>
 void enqueue_apply_M(rsfde_ctx* c, const Tz* z, double* w, const int* gate) {
-  launch_toeplitz_rows<double, Tz>(z, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
-  launch_toeplitz_cols<double, Tz>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2,
-                                   c->y64.tab, gate, nullptr, nullptr, c->stream);
-  c->launches += 2;
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
+    launch_toeplitz_rows<double, Tz>(z, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
+    launch_toeplitz_cols<double, Tz>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2,
+                                     c->y64.tab, gate, nullptr, nullptr, c->stream);
+  }
 }
 
 // V_0 = b - M x, beta = ||V_0||, then restart_prep (device).
 void enqueue_residual(rsfde_ctx* c, const int* gate) {
-  launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
-  launch_toeplitz_cols<double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1, c->n2,
-                                       c->y64.tab, gate, c->partials, c->st, c->stream);
-  c->launches += 2;
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
+    launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
+    launch_toeplitz_cols<double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1,
+                                         c->n2, c->y64.tab, gate, c->partials, c->st, c->stream);
+  }
 }
 
 // z = P-hat^-1 (scale * v) (Eq. 4.6) into z of precision Tz.
@@ -263,10 +325,28 @@ void enqueue_precond_t(rsfde_ctx* c, const double* v, const double* vscale, Tz* 
   T* t1 = static_cast<T*>(c->T1);
   T* t2a = static_cast<T*>(c->T2a);
   T* t2b = static_cast<T*>(c->T2b);
-  launch_dst_rows<T, T>(v, vscale, t1, c->n1, c->n2, tx, gate, c->stream);
-  launch_precond_cols<T>(t1, t2a, t2b, c->n1, c->n2, ty, tx.lam, c->pen, gate, c->stream);
-  launch_precond_rows<T, Tz>(t2a, t2b, c->phi, z, c->n1, c->n2, tx, gate, c->stream);
-  c->launches += 3;
+  {
+    ProfScope ps(c, RSFDE_K_DST_ROWS);
+    launch_dst_rows<T, T>(v, vscale, t1, c->n1, c->n2, tx, gate, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_PRECOND_COLS);
+    launch_precond_cols<T>(t1, t2a, t2b, c->n1, c->n2, ty, tx.lam, c->pen, gate, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_PRECOND_ROWS);
+    launch_precond_rows<T, Tz>(t2a, t2b, c->phi, z, c->n1, c->n2, tx, gate, c->stream);
+  }
+}
+
+void enqueue_init(rsfde_ctx* c) {
+  ProfScope ps(c, RSFDE_K_OTHER);
+  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
+}
+
+void enqueue_rhs(rsfde_ctx* c, const double* u, const double* uu, const double* src, double* b, double* x0) {
+  ProfScope ps(c, RSFDE_K_OTHER);
+  launch_rhs(u, uu, src, c->phi, c->dt, b, x0, c->N, c->partials, c->st, c->stream);
 }
 
 // One FGMRES(m) cycle: m gated Arnoldi iterations, the solution update and
@@ -287,23 +367,28 @@ void enqueue_cycle_t(rsfde_ctx* c) {
       else
         enqueue_precond_t<double, Tz>(c, vj, &c->st->s[j], zj, gi, c->x64.tab, c->y64.tab);
     } else {
+      ProfScope ps(c, RSFDE_K_OTHER);
       launch_scale_copy<Tz>(vj, &c->st->s[j], zj, N, gi, c->stream);  // P = I: z_j = v_j
-      c->launches += 1;
     }
     enqueue_apply_M<Tz>(c, zj, c->V + (size_t)(j + 1) * N, gi);
     const bool cgs2 = c->opts.arnoldi == RSFDE_CGS2;
-    launch_multidot(c->V, N, j, 0, c->partials, c->st, c->stream);
-    launch_update(c->V, N, j, cgs2 ? 0 : 1, c->partials, c->st, c->stream);
-    c->launches += 2;
-    if (cgs2) {
-      launch_multidot(c->V, N, j, 1, c->partials, c->st, c->stream);
-      launch_update(c->V, N, j, 1, c->partials, c->st, c->stream);
-      c->launches += 2;
+    for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
+      {
+        ProfScope ps(c, RSFDE_K_MULTIDOT);
+        launch_multidot(c->V, N, j, pass, c->partials, c->st, c->stream);
+      }
+      ProfScope ps(c, RSFDE_K_UPDATE);
+      launch_update(c->V, N, j, (!cgs2 || pass == 1) ? 1 : 0, c->partials, c->st, c->stream);
     }
   }
-  launch_solve_y(c->st, c->stream);
-  launch_xupdate<Tz>(c->x, Z, N, c->st, c->stream);
-  c->launches += 2;
+  {
+    ProfScope ps(c, RSFDE_K_OTHER);
+    launch_solve_y(c->st, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_XUPDATE);
+    launch_xupdate<Tz>(c->x, Z, N, c->st, c->stream);
+  }
   enqueue_residual(c, gc);
 }
 
@@ -324,12 +409,15 @@ int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
     cudaError_t e = cudaMemcpyAsync(c->st_host, c->st, head, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e);
+    if (c->prof_on) prof_harvest(c);
     if (!c->st_host->run_cycle) break;
     enqueue_cycle(c);
     if ((rc = check_launch(c))) return rc;
   }
-  launch_finalize(c->x, c->N, c->st, c->stream);
-  c->launches += 1;
+  {
+    ProfScope ps(c, RSFDE_K_OTHER);
+    launch_finalize(c->x, c->N, c->st, c->stream);
+  }
   cudaError_t e = cudaMemcpyAsync(c->st_host, c->st, sizeof(SolverState), cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(e);
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e);
@@ -436,8 +524,10 @@ int rsfde_setup(rsfde_ctx** out, const rsfde_grid* g, const uint8_t* mask, doubl
     return cuda_fail(e);
   }
   cudaMemsetAsync(c->st, 0, sizeof(SolverState), c->stream);
-  launch_mask_to_phi(mask, c->phi, N, c->stream);
-  c->launches += 1;
+  {
+    ProfScope ps(c, RSFDE_K_OTHER);
+    launch_mask_to_phi(mask, c->phi, N, c->stream);
+  }
   int rc = build_tables(c);
   if (rc == RSFDE_OK) rc = check_launch(c);
   if (rc == RSFDE_OK) rc = cuda_fail(cudaStreamSynchronize(c->stream));
@@ -476,9 +566,11 @@ int rsfde_solve(rsfde_ctx* c, const double* b, double* x, rsfde_stats* stats) {
   const size_t bytes = c->N * sizeof(double);
   cudaMemcpyAsync(c->b, b, bytes, cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyDeviceToDevice, c->stream);
-  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
-  launch_norm_b(c->b, c->N, c->partials, c->st, c->stream);
-  c->launches += 2;
+  enqueue_init(c);
+  {
+    ProfScope ps(c, RSFDE_K_OTHER);
+    launch_norm_b(c->b, c->N, c->partials, c->st, c->stream);
+  }
   int rc = check_launch(c);
   if (rc) return rc;
   rc = run_solver(c, stats);
@@ -492,18 +584,16 @@ int rsfde_solve(rsfde_ctx* c, const double* b, double* x, rsfde_stats* stats) {
 int rsfde_rhs(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, const double* src, double* b,
               double* x0) {
   if (!c || !u_prev || !b || !x0) return RSFDE_EINVAL;
-  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
-  launch_rhs(u_prev, u_prevprev, src, c->phi, c->dt, b, x0, c->N, c->partials, c->st, c->stream);
-  c->launches += 2;
+  enqueue_init(c);
+  enqueue_rhs(c, u_prev, u_prevprev, src, b, x0);
   return check_launch(c);
 }
 
 int rsfde_step(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, const double* src, double* u_next,
                rsfde_stats* stats) {
   if (!c || !u_prev || !u_next) return RSFDE_EINVAL;
-  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
-  launch_rhs(u_prev, u_prevprev, src, c->phi, c->dt, c->b, c->x, c->N, c->partials, c->st, c->stream);
-  c->launches += 2;
+  enqueue_init(c);
+  enqueue_rhs(c, u_prev, u_prevprev, src, c->b, c->x);
   int rc = check_launch(c);
   if (rc) return rc;
   rc = run_solver(c, stats);
@@ -528,9 +618,8 @@ int rsfde_step_host(rsfde_ctx* c, const double* u_prev_h, const double* u_prevpr
   cudaMemcpyAsync(d_u, u_prev_h, bytes, cudaMemcpyHostToDevice, c->stream);
   if (d_uu) cudaMemcpyAsync(d_uu, u_prevprev_h, bytes, cudaMemcpyHostToDevice, c->stream);
   if (d_src) cudaMemcpyAsync(d_src, src_h, bytes, cudaMemcpyHostToDevice, c->stream);
-  launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
-  launch_rhs(d_u, d_uu, d_src, c->phi, c->dt, c->b, c->x, c->N, c->partials, c->st, c->stream);
-  c->launches += 2;
+  enqueue_init(c);
+  enqueue_rhs(c, d_u, d_uu, d_src, c->b, c->x);
   int rc = check_launch(c);
   if (rc) return rc;
   rc = run_solver(c, stats);
@@ -561,9 +650,14 @@ int rsfde_apply_precond(rsfde_ctx* c, const double* v, double* z) {
 
 int rsfde_dst2(rsfde_ctx* c, const double* v, double* out) {
   if (!c || !v || !out) return RSFDE_EINVAL;
-  launch_dst_rows<double, double>(v, nullptr, c->tmpx, c->n1, c->n2, c->x64.tab, nullptr, c->stream);
-  launch_dst_cols<double, double, double>(c->tmpx, out, c->n1, c->n2, c->y64.tab, c->stream);
-  c->launches += 2;
+  {
+    ProfScope ps(c, RSFDE_K_DST_ROWS);
+    launch_dst_rows<double, double>(v, nullptr, c->tmpx, c->n1, c->n2, c->x64.tab, nullptr, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_PRECOND_COLS);
+    launch_dst_cols<double, double, double>(c->tmpx, out, c->n1, c->n2, c->y64.tab, c->stream);
+  }
   return check_launch(c);
 }
 
@@ -587,6 +681,33 @@ int rsfde_get_params(rsfde_ctx* c, double* out5) {
 }
 
 int64_t rsfde_kernel_launches(const rsfde_ctx* c) { return c ? c->launches : 0; }
+
+int rsfde_profile_enable(rsfde_ctx* c, int on) {
+  if (!c) return RSFDE_EINVAL;
+  c->prof_on = on != 0;
+  return RSFDE_OK;
+}
+
+int rsfde_profile_read(rsfde_ctx* c, double* ms, int64_t* launches) {
+  if (!c) return RSFDE_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  prof_harvest(c);
+  for (int k = 0; k < RSFDE_K_COUNT; ++k) {
+    if (ms) ms[k] = c->prof_ms[k];
+    if (launches) launches[k] = c->prof_n[k];
+    c->prof_ms[k] = 0.0;
+    c->prof_n[k] = 0;
+  }
+  return RSFDE_OK;
+}
+
+const char* rsfde_kernel_class_name(int k) {
+  static const char* names[RSFDE_K_COUNT] = {"toeplitz_rows", "toeplitz_cols", "dst_rows",
+                                             "precond_cols",  "precond_rows",  "multidot",
+                                             "update",        "xupdate",       "other"};
+  return (k >= 0 && k < RSFDE_K_COUNT) ? names[k] : "unknown";
+}
 
 void rsfde_destroy(rsfde_ctx* c) {
   if (!c) return;

@@ -140,6 +140,18 @@ def test_dst_matches_scipy_and_is_involution(n):
                                rtol=1e-13, atol=1e-15)
 
 
+def test_dst2_samples_equal_full_transform_passes():
+    rng = np.random.default_rng(8)
+    prob = tiny_problem(rng, 9, 7)
+    v = rng.standard_normal((7, 9))
+    rows = prob.dst2_rows_sample(v, 3)
+    np.testing.assert_allclose(rows[:3], scipy.fft.dst(v[:3], type=1, norm="ortho", axis=1),
+                               rtol=1e-12, atol=1e-13)
+    cols = prob.dst2_cols_sample(v, 4)
+    np.testing.assert_allclose(cols[:, :4], scipy.fft.dst(v[:, :4], type=1, norm="ortho", axis=0),
+                               rtol=1e-12, atol=1e-13)
+
+
 def test_dst2_matches_scipy():
     rng = np.random.default_rng(3)
     prob = tiny_problem(rng, 9, 6)
