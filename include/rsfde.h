@@ -144,6 +144,31 @@ int rsfde_get_tables(rsfde_ctx* ctx, double* lam_x, double* lam_y, double* t_x, 
 /* c_x, c_y, dt/eta, h_x, h_y to a HOST array of 5 doubles. */
 int rsfde_get_params(rsfde_ctx* ctx, double* out5);
 
+/* ---- allocation-free variant ------------------------------------------------ */
+/* The paper has no counterpart to this entry point: it exists for callers
+ * that cannot call cudaMalloc, such as an application or framework that owns
+ * every device allocation through its own memory pool, or code that must not
+ * allocate while it builds a CUDA graph.  They cannot make an rsfde_ctx
+ * (rsfde_setup allocates), so this call computes out = (S_{n2} (x) S_{n1}) v
+ * -- the same transform and kernels as rsfde_dst2 -- with no context.
+ *
+ * v, out: caller-owned DEVICE arrays of n1*n2 doubles, x fastest, distinct.
+ * stream: cudaStream_t or NULL.  The intermediate between the row and column
+ * passes and the transform tables live in static device arrays of the
+ * library (about 2.1 MB, held by every GPU that loads the library until the
+ * process exits), so sizes are limited: n1, n2 in 1..RSFDE_NOALLOC_MAX_N,
+ * else RSFDE_EINVAL.  Calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * The first call on each device looks up the static arrays' device
+ * addresses (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  Every call uses the same static
+ * arrays and overwrites all of it that the kernels read, so nothing carries
+ * over from one call to the next; but calls whose work overlaps on the GPU
+ * (two streams, or two host threads) race on the arrays and must be
+ * serialised by the caller. */
+#define RSFDE_NOALLOC_MAX_N 512
+int rsfde_dst2_noalloc(int32_t n1, int32_t n2, const double* v, double* out, void* stream);
+
 /* ---- measurement ------------------------------------------------------------ */
 /* Kernel classes timed by the profiler. */
 #define RSFDE_K_TOEPLITZ_ROWS 0 /* (I (x) A_x) z, Eq. 2.15 */

@@ -1,0 +1,71 @@
+"""rsfde_dst2_noalloc, the allocation-free 2D sine transform, through the C ABI.
+
+It serves callers that cannot call cudaMalloc (an application whose device
+memory all comes from its own pool, or code building a CUDA graph that must
+not allocate).  Its output must equal the context-based rsfde_dst2 within the
+tolerance the parity tests use, on consecutive calls that share its static
+device arrays, and it must not change the device's free memory.  This file is
+collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2102_11576_gb300 import Solver, load_library, workloads  # noqa: E402
+
+
+def _noalloc(lib, n1, n2, v, out):
+    fn = lib.rsfde_dst2_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    return fn(n1, n2, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_dst2_matches_rsfde_dst2_on_consecutive_calls():
+    lib = load_library()
+    rng = np.random.default_rng(11)
+    cases = [(200, 137), (512, 512), (33, 7)]
+    # first call on this device (address lookup) before anything is measured
+    warm_v = torch.zeros((2, 3), dtype=torch.float64, device="cuda")
+    warm_o = torch.empty_like(warm_v)
+    assert _noalloc(lib, 3, 2, warm_v, warm_o) == 0
+    torch.cuda.synchronize()
+    for n1, n2 in cases:
+        w = workloads.random_problem(5, n1, n2)
+        ref_solver = Solver(n1, n2, w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"],
+                            w["ky"], w["dt"], w["eta"])
+        v = torch.as_tensor(rng.standard_normal((n2, n1))).cuda()
+        ref = ref_solver.dst2(v)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        outs = []
+        for _ in range(2):  # two calls in a row through the shared static arrays
+            out = torch.full_like(v, np.nan)
+            assert _noalloc(lib, n1, n2, v, out) == 0
+            torch.cuda.synchronize()
+            outs.append(out)
+        free1 = torch.cuda.mem_get_info()[0]
+        for out in outs:
+            err = (out - ref).abs().max().item() / ref.abs().max().item()
+            assert err <= 1e-12, (n1, n2, err)
+        assert free0 == free1
+        ref_solver.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_static_arrays():
+    lib = load_library()
+    v = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+    o = torch.empty_like(v)
+    big = lib.rsfde_dst2_noalloc
+    assert _noalloc(lib, 513, 4, v, o) == -1
+    assert _noalloc(lib, 4, 0, v, o) == -1
+    assert _noalloc(lib, 4, 4, v, v) == -1  # in place is not supported
+    assert big is lib.rsfde_dst2_noalloc
