@@ -8,7 +8,7 @@
 #include <new>
 #include <vector>
 
-#include "fft.cuh"
+#include "fft.cuh"  // host butterflies for the setup spectra
 #include "internal.h"
 
 using namespace rsfde;
@@ -56,6 +56,16 @@ void host_dif(std::vector<double>& re, std::vector<double>& im, int L, int log2L
   }
   for (; s >= 1; s >>= 2)
     for (int q = 0; q < L / 4; ++q) dif_r4(re.data(), im.data(), L, s, q, tw.data());
+  // the DIF leaves the spectrum in bit-reversed order; the kernels want it natural
+  std::vector<double> r2(L), i2(L);
+  for (int l = 0; l < L; ++l) {
+    int b = 0;
+    for (int x = l, k = 0; k < log2L; ++k, x >>= 1) b = (b << 1) | (x & 1);
+    r2[b] = re[l];
+    i2[b] = im[l];
+  }
+  re.swap(r2);
+  im.swap(i2);
 }
 
 struct HostAxis {
@@ -66,8 +76,8 @@ struct HostAxis {
 HostAxis build_axis(int n, double alpha, double c) {
   HostAxis a;
   a.n = n;
-  a.L = 4;
-  a.log2L = 2;
+  a.L = 16;  // the register FFT's smallest length
+  a.log2L = 4;
   while (a.L < 2 * n - 1) {
     a.L <<= 1;
     a.log2L++;

@@ -35,14 +35,24 @@ template <typename T>
 struct AxisTables {
   int n, L, log2L;
   const T* tw;         // 2L: cos, sin of -2 pi j/L
-  const T* sigma;      // L: circulant spectrum of the Toeplitz column / L, bit-reversed
+  const T* sigma;      // L: circulant spectrum of the Toeplitz column / L, natural order
   const T* chirp;      // 2n: exp(i pi k^2 / (2(n+1))), k = 1..n
   const T* chirp_out;  // 2n: sqrt(2/(n+1)) exp(i pi k^2 / (2(n+1)))
-  const T* bspec;      // 2L: spectrum of exp(-i pi d^2/(2(n+1))) / L, bit-reversed
+  const T* bspec;      // 2L: spectrum of exp(-i pi d^2/(2(n+1))) / L, natural order
   const T* lam;        // n: eigenvalues of tau(A_axis)
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
+  if (blockDim.x < 32) {  // blocks smaller than a warp (tiny grids): serial sum in a fixed order
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+      for (int i = 0; i < (int)blockDim.x; ++i) s += sh[i];
+    __syncthreads();
+    return s;  // valid in thread 0
+  }
+  // blockDim.x is a multiple of 32 here
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -55,7 +65,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   }
   __syncthreads();
-  return v;  // valid in warp 0
+  return v;  // valid in thread 0
 }
 
 // Last-block-done pattern: returns true in exactly one block, after every

@@ -43,7 +43,7 @@ static double h_tables[2 * kTableDoubles];
 static double h_re[kMaxL], h_im[kMaxL];
 
 int pow2_at_least(int v, int* log2v) {
-  int L = 4, lg = 2;
+  int L = 16, lg = 4;
   while (L < v) {
     L <<= 1;
     ++lg;
@@ -53,7 +53,7 @@ int pow2_at_least(int v, int* log2v) {
 }
 
 // Fills one axis' sine-transform tables (twiddles, chirps, Bluestein kernel
-// spectrum in the bit-reversed order the forward transform produces) at
+// spectrum in natural order) at
 // h_tables + axis * kTableDoubles.
 void fill_axis(int axis, int n, int L, int log2L) {
   double* base = h_tables + (size_t)axis * kTableDoubles;
@@ -93,9 +93,12 @@ void fill_axis(int axis, int n, int L, int log2L) {
   }
   for (; s >= 1; s >>= 2)
     for (int q = 0; q < L / 4; ++q) dif_r4(h_re, h_im, L, s, q, tw);
+  // the DIF leaves the spectrum in bit-reversed order; the kernels want it natural
   for (int l = 0; l < L; ++l) {
-    bspec[2 * l] = h_re[l] / L;
-    bspec[2 * l + 1] = h_im[l] / L;
+    int b = 0;
+    for (int x = l, k = 0; k < log2L; ++k, x >>= 1) b = (b << 1) | (x & 1);
+    bspec[2 * b] = h_re[l] / L;
+    bspec[2 * b + 1] = h_im[l] / L;
   }
 }
 
