@@ -45,11 +45,16 @@ extern "C" {
 #define RSFDE_ENONFINITE (-5)  /* NaN or Inf met in the right side or in the Arnoldi process */
 #define RSFDE_ETIMEOUT (-6)    /* a bounded device-side wait gave up */
 
-/* Precision of the preconditioner apply (Eq. 4.6).  The operator, the true
- * residual, the Arnoldi orthogonalisation and the Givens least squares are
- * FP64 in every mode. */
+/* Precisions.  The preconditioner apply (Eq. 4.6) runs in RSFDE_FP64 or
+ * RSFDE_FP32; the operator applied to the Arnoldi vectors in RSFDE_FP64 or
+ * RSFDE_DF32.  The true residual, the Arnoldi orthogonalisation and the
+ * Givens least squares are FP64 in every mode. */
 #define RSFDE_FP64 0
 #define RSFDE_FP32 1
+/* Operator M applied to the Arnoldi vectors in double-FP32 arithmetic (pairs
+ * of FP32 numbers, ~48-bit significand, error-free transforms of Dekker and
+ * Knuth).  The true residual b - M x is always computed in FP64. */
+#define RSFDE_DF32 2
 
 /* Arnoldi orthogonalisation: classical Gram-Schmidt, or with one re-orthogonalisation pass. */
 #define RSFDE_CGS 0
@@ -70,6 +75,7 @@ typedef struct {
   int32_t precond_prec; /* RSFDE_FP64 | RSFDE_FP32 */
   int32_t arnoldi;      /* RSFDE_CGS | RSFDE_CGS2 */
   int32_t use_precond;  /* 1: P-hat of Eq. 4.6; 0: unpreconditioned GMRES */
+  int32_t matvec_prec;  /* RSFDE_FP64 | RSFDE_DF32: M applied to the Arnoldi vectors */
   void* stream;         /* cudaStream_t; NULL = the legacy default stream */
 } rsfde_opts;
 
@@ -83,7 +89,7 @@ typedef struct {
 } rsfde_stats;
 
 /* Defaults: restart 20, max_iter 10000, tol 1e-10, FP64 preconditioner, CGS,
- * preconditioned, default stream. */
+ * preconditioned, FP64 operator, default stream. */
 void rsfde_opts_default(rsfde_opts* o);
 
 /* Section 2 / Eq. 2.16 / Section 4.1 (setup of one linear system).
@@ -129,7 +135,8 @@ int rsfde_step_host(rsfde_ctx* ctx, const double* u_prev_host, const double* u_p
 int rsfde_adjoint(rsfde_ctx* ctx, const double* lam, double* mu, rsfde_stats* stats);
 
 /* ---- operator-level entry points (each one step of the hot path) --------- */
-/* Eq. 2.14-2.17: w = M z.  z, w device N doubles (distinct). */
+/* Eq. 2.14-2.17: w = M z in the context's operator precision (matvec_prec).
+ * z, w device N doubles (distinct). */
 int rsfde_apply_M(rsfde_ctx* ctx, const double* z, double* w);
 /* Eq. 4.6: z = P-hat^-1 v in the context's preconditioner precision (result in FP64). */
 int rsfde_apply_precond(rsfde_ctx* ctx, const double* v, double* z);

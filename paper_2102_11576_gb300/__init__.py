@@ -16,12 +16,12 @@ import os
 
 import numpy as np
 
-__all__ = ["Solver", "RsfdeError", "load_library", "LIB_PATH", "FP64", "FP32"]
+__all__ = ["Solver", "RsfdeError", "load_library", "LIB_PATH", "FP64", "FP32", "DF32"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librsfde.so")
 
-FP64, FP32 = 0, 1
+FP64, FP32, DF32 = 0, 1, 2
 CGS, CGS2 = 0, 1
 _ERR = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV", -5: "ENONFINITE",
         -6: "ETIMEOUT"}
@@ -42,7 +42,8 @@ class _Grid(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("precond_prec", ctypes.c_int32), ("arnoldi", ctypes.c_int32),
-                ("use_precond", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("use_precond", ctypes.c_int32), ("matvec_prec", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):
@@ -120,7 +121,7 @@ class Solver:
 
     def __init__(self, n1, n2, box, in_omega, alpha1, alpha2, kx, ky, dt, eta, restart=20,
                  max_iter=10000, tol=1e-10, precond="fp64", arnoldi="cgs", use_precond=True,
-                 stream=None):
+                 matvec="fp64", stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
@@ -140,6 +141,7 @@ class Solver:
         o.precond_prec = {"fp64": FP64, "fp32": FP32}[precond]
         o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
         o.use_precond = int(bool(use_precond))
+        o.matvec_prec = {"fp64": FP64, "df32": DF32}[matvec]
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         self._opts = o
         g = _Grid(self.n1, self.n2, *map(float, box))
@@ -185,6 +187,8 @@ class Solver:
                 o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[v]
             elif k == "use_precond":
                 o.use_precond = int(bool(v))
+            elif k == "matvec":
+                o.matvec_prec = {"fp64": FP64, "df32": DF32}[v]
             else:
                 setattr(o, k, v)
         _check(self._lib.rsfde_set_opts(self._h, ctypes.byref(o)), "set_opts")

@@ -188,6 +188,7 @@ struct rsfde_ctx {
   HostAxis hx_axis, hy_axis;
   DevAxis<double> x64, y64;
   DevAxis<float> x32, y32;
+  DevAxis<df> xdf, ydf;
   uint8_t* phi = nullptr;
   double* V = nullptr;      // (m+1) x N
   void* Z = nullptr;        // m x N (double or float)
@@ -277,6 +278,8 @@ int build_tables(rsfde_ctx* c) {
   if ((e = c->y64.upload(c->hy_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
   if ((e = c->x32.upload(c->hx_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
   if ((e = c->y32.upload(c->hy_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
+  if ((e = c->xdf.upload(c->hx_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
+  if ((e = c->ydf.upload(c->hy_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
   return RSFDE_OK;
 }
 
@@ -291,6 +294,8 @@ void free_ctx(rsfde_ctx* c) {
   c->y64.release();
   c->x32.release();
   c->y32.release();
+  c->xdf.release();
+  c->ydf.release();
   void* ptrs[] = {c->phi, c->V, c->Z, c->tmpx, c->T1, c->T2a, c->T2b, c->b, c->x, c->hbuf, c->partials, c->st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -301,18 +306,25 @@ void free_ctx(rsfde_ctx* c) {
 bool fp32_precond(const rsfde_ctx* c) { return c->opts.precond_prec == RSFDE_FP32; }
 
 // ---- enqueue helpers ---------------------------------------------------------
-// w = M z (Eq. 2.17), z in precision Tz.
-template <typename Tz>
-void enqueue_apply_M(rsfde_ctx* c, const Tz* z, double* w, const int* gate) {
+// w = M z (Eq. 2.17), z in precision Tz, arithmetic T (double or df).
+template <typename T, typename Tz>
+void enqueue_apply_M_t(rsfde_ctx* c, const Tz* z, double* w, const int* gate, const AxisTables<T>& tx,
+                       const AxisTables<T>& ty) {
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
-    launch_toeplitz_rows<double, Tz>(z, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
+    launch_toeplitz_rows<T, Tz>(z, c->tmpx, c->n1, c->n2, tx, gate, c->stream);
   }
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
-    launch_toeplitz_cols<double, Tz>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2,
-                                     c->y64.tab, gate, nullptr, nullptr, c->stream);
+    launch_toeplitz_cols<T, Tz>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2, ty, gate,
+                                nullptr, nullptr, c->stream);
   }
+}
+
+template <typename Tz>
+void enqueue_apply_M(rsfde_ctx* c, const Tz* z, double* w, const int* gate) {
+  if (c->opts.matvec_prec == RSFDE_DF32) enqueue_apply_M_t<df, Tz>(c, z, w, gate, c->xdf.tab, c->ydf.tab);
+  else enqueue_apply_M_t<double, Tz>(c, z, w, gate, c->x64.tab, c->y64.tab);
 }
 
 // V_0 = b - M x, beta = ||V_0||, then restart_prep (device).
@@ -456,6 +468,7 @@ void rsfde_opts_default(rsfde_opts* o) {
   o->precond_prec = RSFDE_FP64;
   o->arnoldi = RSFDE_CGS;
   o->use_precond = 1;
+  o->matvec_prec = RSFDE_FP64;
   o->stream = nullptr;
 }
 
@@ -476,6 +489,7 @@ static int valid_opts(const rsfde_opts* o) {
   if (o->restart < 1 || o->restart > kMaxRestart || o->max_iter < 1 || !(o->tol > 0.0)) return 0;
   if (o->precond_prec != RSFDE_FP64 && o->precond_prec != RSFDE_FP32) return 0;
   if (o->arnoldi != RSFDE_CGS && o->arnoldi != RSFDE_CGS2) return 0;
+  if (o->matvec_prec != RSFDE_FP64 && o->matvec_prec != RSFDE_DF32) return 0;
   return 1;
 }
 

@@ -5,6 +5,7 @@
 
 #include "../../include/rsfde.h"
 #include "common.cuh"
+#include "df.cuh"
 
 namespace rsfde {
 

@@ -8,6 +8,8 @@
 // positions (coalesced rows); column kernels interleave the F groups across
 // the lanes of a warp so each access touches F (or 2F) adjacent columns.
 //
+//  * Arithmetic: T = double, float, or df (double-FP32, df.cuh) for the
+//    operator applied to the Arnoldi vectors.
 //  * Toeplitz product along an axis: two real vectors are packed as the real
 //    and imaginary parts of one complex sequence (the circulant spectrum is
 //    real because the Toeplitz matrix of Eq. 2.16 is symmetric), zero padded
@@ -20,11 +22,13 @@
 //    columns S_y, the two spectral divides and both inverse S_y; rows S_x
 //    of both channels with the masked combine.
 #include "common.cuh"
+#include "df.cuh"
 #include "fft16.cuh"
 #include "internal.h"
 
 // Thread cap of one block of the FP32 transform kernels (their register
-// budget is 65536 / cap per thread); FP64 blocks are capped at 512.
+// budget is 65536 / cap per thread); FP64 and double-FP32 blocks (8-byte
+// reals) are capped at 512.
 #ifndef RSFDE_FP32_THREADS
 #define RSFDE_FP32_THREADS 1024
 #endif
@@ -36,9 +40,19 @@ __device__ __forceinline__ bool gate_closed(const int* gate) {
   return gate != nullptr && *(volatile const int*)gate == 0;
 }
 
+// Read-only loads of table entries, including double-FP32 pairs.
+template <typename T>
+__device__ __forceinline__ T ldg_t(const T* p) {
+  return __ldg(p);
+}
+template <>
+__device__ __forceinline__ df ldg_t<df>(const df* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return {v.x, v.y};
+}
 template <typename T>
 __device__ __forceinline__ cx<T> ldc(const T* p, int k) {
-  return {__ldg(p + 2 * k), __ldg(p + 2 * k + 1)};
+  return {ldg_t(p + 2 * k), ldg_t(p + 2 * k + 1)};
 }
 
 // Thread geometry of one block: F groups of G = L/16 threads.
@@ -119,7 +133,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
     fft16_forward<T>(v, buf, gi.t, L, ax.log2L, tw);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      const T sg = __ldg(ax.sigma + gi.t + k * Lq);
+      const T sg = ldg_t(ax.sigma + gi.t + k * Lq);
       v[k].r *= sg;
       v[k].i *= sg;
     }
@@ -452,6 +466,16 @@ template void launch_toeplitz_cols<double, double>(int, const double*, const dou
 template void launch_toeplitz_cols<double, float>(int, const float*, const double*, const uint8_t*, double,
                                                   const double*, double*, int, int, const AxisTables<double>&,
                                                   const int*, double*, SolverState*, cudaStream_t);
+template void launch_toeplitz_rows<df, double>(const double*, double*, int, int, const AxisTables<df>&,
+                                               const int*, cudaStream_t);
+template void launch_toeplitz_rows<df, float>(const float*, double*, int, int, const AxisTables<df>&,
+                                              const int*, cudaStream_t);
+template void launch_toeplitz_cols<df, double>(int, const double*, const double*, const uint8_t*, double,
+                                               const double*, double*, int, int, const AxisTables<df>&,
+                                               const int*, double*, SolverState*, cudaStream_t);
+template void launch_toeplitz_cols<df, float>(int, const float*, const double*, const uint8_t*, double,
+                                              const double*, double*, int, int, const AxisTables<df>&,
+                                              const int*, double*, SolverState*, cudaStream_t);
 template void launch_dst_rows<double, double>(const double*, const double*, double*, int, int,
                                               const AxisTables<double>&, const int*, cudaStream_t);
 template void launch_dst_rows<float, float>(const double*, const double*, float*, int, int,
