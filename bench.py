@@ -453,13 +453,14 @@ def run_op(args):
     from paper_2102_11576_gb300 import Solver, workloads
     w = workloads.make(args.workload)
     prec = "fp64" if args.op.endswith("fp64") else "fp32"
+    matvec = "df32" if args.op.endswith("df32") else "fp64"
     s = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
-               w["dt"], w["eta"], restart=w["restart"], precond=prec)
+               w["dt"], w["eta"], restart=w["restart"], precond=prec, matvec=matvec)
     rng = np.random.default_rng(0)
     v = torch.as_tensor(rng.standard_normal((w["n2"], w["n1"]))).cuda()
     out = torch.empty_like(v)
-    fn = {"apply_M": s.apply_M, "precond_fp32": s.apply_precond, "precond_fp64": s.apply_precond,
-          "dst2": s.dst2}[args.op]
+    fn = {"apply_M": s.apply_M, "apply_M_df32": s.apply_M, "precond_fp32": s.apply_precond,
+          "precond_fp64": s.apply_precond, "dst2": s.dst2}[args.op]
     fn(v, out)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -474,7 +475,8 @@ def run_op(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["apply_M", "precond_fp32", "precond_fp64", "dst2"], default=None,
+    ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "precond_fp32", "precond_fp64", "dst2"],
+                    default=None,
                     help="time one operator entry point instead of the time march")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--gpus", type=int, default=1)

@@ -76,6 +76,9 @@ typedef struct {
   int32_t arnoldi;      /* RSFDE_CGS | RSFDE_CGS2 */
   int32_t use_precond;  /* 1: P-hat of Eq. 4.6; 0: unpreconditioned GMRES */
   int32_t matvec_prec;  /* RSFDE_FP64 | RSFDE_DF32: M applied to the Arnoldi vectors */
+  int32_t use_graph;    /* 1: the cycles of a solve replay as one CUDA graph with a device-side
+                           loop (one host synchronisation per solve); 0: direct launches with
+                           one host check per cycle.  Profiling always uses direct launches. */
   void* stream;         /* cudaStream_t; NULL = the legacy default stream */
 } rsfde_opts;
 
@@ -89,7 +92,7 @@ typedef struct {
 } rsfde_stats;
 
 /* Defaults: restart 20, max_iter 10000, tol 1e-10, FP64 preconditioner, CGS,
- * preconditioned, FP64 operator, default stream. */
+ * preconditioned, FP64 operator, CUDA graph, default stream. */
 void rsfde_opts_default(rsfde_opts* o);
 
 /* Section 2 / Eq. 2.16 / Section 4.1 (setup of one linear system).

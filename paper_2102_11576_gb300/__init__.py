@@ -43,7 +43,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("precond_prec", ctypes.c_int32), ("arnoldi", ctypes.c_int32),
                 ("use_precond", ctypes.c_int32), ("matvec_prec", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):
@@ -121,7 +121,7 @@ class Solver:
 
     def __init__(self, n1, n2, box, in_omega, alpha1, alpha2, kx, ky, dt, eta, restart=20,
                  max_iter=10000, tol=1e-10, precond="fp64", arnoldi="cgs", use_precond=True,
-                 matvec="fp64", stream=None):
+                 matvec="fp64", use_graph=True, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
@@ -142,6 +142,7 @@ class Solver:
         o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
         o.use_precond = int(bool(use_precond))
         o.matvec_prec = {"fp64": FP64, "df32": DF32}[matvec]
+        o.use_graph = int(bool(use_graph))
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         self._opts = o
         g = _Grid(self.n1, self.n2, *map(float, box))
@@ -189,6 +190,8 @@ class Solver:
                 o.use_precond = int(bool(v))
             elif k == "matvec":
                 o.matvec_prec = {"fp64": FP64, "df32": DF32}[v]
+            elif k == "use_graph":
+                o.use_graph = int(bool(v))
             else:
                 setattr(o, k, v)
         _check(self._lib.rsfde_set_opts(self._h, ctypes.byref(o)), "set_opts")

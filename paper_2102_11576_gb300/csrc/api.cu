@@ -204,6 +204,12 @@ struct rsfde_ctx {
   SolverState* st = nullptr;
   SolverState* st_host = nullptr;  // pinned
   int64_t launches = 0;
+  // one FGMRES cycle captured as the body of a device-side WHILE loop
+  cudaStream_t cap_stream = nullptr;  // private stream used only for capture
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_key = -1;
+  int64_t launches_per_body = 0;
   // profiler: event pairs per kernel class, recorded while prof_on
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -300,6 +306,9 @@ void free_ctx(rsfde_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 
@@ -419,22 +428,80 @@ void enqueue_cycle(rsfde_ctx* c) {
   else enqueue_cycle_t<double>(c);
 }
 
+int graph_key(const rsfde_ctx* c) {
+  const rsfde_opts& o = c->opts;
+  return ((((o.restart * 4 + o.precond_prec) * 4 + o.matvec_prec) * 2 + o.arnoldi) * 2 + o.use_precond);
+}
+
+// Captures one FGMRES cycle into the body of a CUDA graph WHILE node whose
+// condition the device sets after every cycle (loop_cond_kernel).
+int build_cycle_graph(rsfde_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  c->graph_key = -1;
+  cudaError_t e;
+  if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = cudaGraphCreate(&c->graph, 0)) != cudaSuccess) return cuda_fail(e);
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+    return cuda_fail(e);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &np)) != cudaSuccess) return cuda_fail(e);
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t user = c->stream;
+  const bool prof = c->prof_on;
+  const int64_t l0 = c->launches;
+  c->stream = c->cap_stream;
+  c->prof_on = false;
+  e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    enqueue_cycle(c);
+    launch_loop_cond(h, c->st, c->stream);
+    e = cudaStreamEndCapture(c->stream, &body);
+  }
+  c->launches_per_body = c->launches - l0 + 1;
+  c->launches = l0;
+  c->stream = user;
+  c->prof_on = prof;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph_exec, c->graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e);
+  }
+  c->graph_key = graph_key(c);
+  return RSFDE_OK;
+}
+
 // Solve M x = b with b = c->b, x = c->x (initial guess), st->bnorm set.
 int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
   enqueue_residual(c, &c->st->run_cycle);
   int rc = check_launch(c);
   if (rc) return rc;
-  const size_t head = offsetof(SolverState, counter);
-  // each cycle does at least one iteration, so max_iter + 1 cycles bound the loop
-  for (long guard = 0;; ++guard) {
-    if (guard > (long)c->opts.max_iter + 1) return RSFDE_ENOTCONV;
-    cudaError_t e = cudaMemcpyAsync(c->st_host, c->st, head, cudaMemcpyDeviceToHost, c->stream);
+  if (c->opts.use_graph && !c->prof_on) {
+    if (c->graph_key != graph_key(c) && (rc = build_cycle_graph(c))) return rc;
+    cudaError_t e = cudaGraphLaunch(c->graph_exec, c->stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e);
-    if (c->prof_on) prof_harvest(c);
-    if (!c->st_host->run_cycle) break;
-    enqueue_cycle(c);
-    if ((rc = check_launch(c))) return rc;
+  } else {
+    const size_t head = offsetof(SolverState, counter);
+    // each cycle does at least one iteration, so max_iter + 1 cycles bound the loop
+    for (long guard = 0;; ++guard) {
+      if (guard > (long)c->opts.max_iter + 1) return RSFDE_ENOTCONV;
+      cudaError_t e = cudaMemcpyAsync(c->st_host, c->st, head, cudaMemcpyDeviceToHost, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e);
+      if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e);
+      if (c->prof_on) prof_harvest(c);
+      if (!c->st_host->run_cycle) break;
+      enqueue_cycle(c);
+      if ((rc = check_launch(c))) return rc;
+    }
   }
   {
     ProfScope ps(c, RSFDE_K_OTHER);
@@ -444,6 +511,7 @@ int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
   if (e != cudaSuccess) return cuda_fail(e);
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e);
   const SolverState& h = *c->st_host;
+  if (c->opts.use_graph && !c->prof_on) c->launches += (int64_t)h.body_runs * c->launches_per_body;
   if (stats) {
     stats->iters = h.iters;
     stats->restarts = h.cycles > 0 ? h.cycles - 1 : 0;
@@ -469,6 +537,7 @@ void rsfde_opts_default(rsfde_opts* o) {
   o->arnoldi = RSFDE_CGS;
   o->use_precond = 1;
   o->matvec_prec = RSFDE_FP64;
+  o->use_graph = 1;
   o->stream = nullptr;
 }
 

@@ -130,6 +130,7 @@ void launch_solve_y(SolverState* st, cudaStream_t s);
 template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s);
 void launch_finalize(double* x, size_t N, SolverState* st, cudaStream_t s);
+void launch_loop_cond(cudaGraphConditionalHandle h, SolverState* st, cudaStream_t s);
 template <typename Tz>
 void launch_scale_copy(const double* v, const double* scale, Tz* z, size_t N, const int* gate, cudaStream_t s);
 

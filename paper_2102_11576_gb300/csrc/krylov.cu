@@ -30,6 +30,7 @@ __global__ void init_state_kernel(SolverState* st, int m, int max_iter, double t
   st->max_iter = max_iter;
   st->m = m;
   st->zero_solution = 0;
+  st->body_runs = 0;
   st->counter = 0;
   st->tol = tol;
   st->bnorm = 0.0;
@@ -191,6 +192,22 @@ __global__ void __launch_bounds__(kBlock) scale_copy_kernel(const double* __rest
     z[p] = Tz(sc * v[p]);
 }
 
+// Condition of the device-side loop over FGMRES cycles (a CUDA graph WHILE
+// node): go on while the solve is running.  Each cycle with run_cycle set
+// either ends the solve or counts one restart, so the loop is bounded; the
+// cap below is a second, independent bound.
+__global__ void loop_cond_kernel(cudaGraphConditionalHandle h, SolverState* st) {
+  int go = st->run_cycle;
+  st->body_runs += 1;
+  if (go && st->body_runs > st->max_iter + 2) {
+    st->status = RSFDE_ENOTCONV;
+    st->run_cycle = 0;
+    st->run_iter = 0;
+    go = 0;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // ---- launchers --------------------------------------------------------------
 void launch_init_state(SolverState* st, int m, int max_iter, double tol, cudaStream_t s) {
   init_state_kernel<<<1, 1, 0, s>>>(st, m, max_iter, tol);
@@ -220,6 +237,9 @@ void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStrea
 }
 template void launch_xupdate<double>(double*, const double*, size_t, SolverState*, cudaStream_t);
 template void launch_xupdate<float>(double*, const float*, size_t, SolverState*, cudaStream_t);
+void launch_loop_cond(cudaGraphConditionalHandle h, SolverState* st, cudaStream_t s) {
+  loop_cond_kernel<<<1, 1, 0, s>>>(h, st);
+}
 void launch_finalize(double* x, size_t N, SolverState* st, cudaStream_t s) {
   finalize_kernel<<<vec_grid(N), kBlock, 0, s>>>(x, N, st);
 }

@@ -118,6 +118,23 @@ def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec):
     assert rel(x, x_ref) <= 1e-9
 
 
+@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32")])
+def test_graph_loop_equals_direct_launches(prec, matvec):
+    """The device-side graph loop and the host-driven loop run the same
+    kernels in the same order with deterministic reductions: identical bits."""
+    w = workloads.random_problem(8, 70, 45)
+    rng = np.random.default_rng(3)
+    b = dev(rng.standard_normal((45, 70)))
+    res = []
+    for use_graph in (True, False):
+        _, gpu = pair(w, precond=prec, matvec=matvec, restart=6, tol=1e-12, use_graph=use_graph)
+        for _ in range(2):  # the second solve replays the captured graph
+            x, st = gpu.solve(b)
+        res.append((host(x), st))
+    np.testing.assert_array_equal(res[0][0], res[1][0])
+    assert res[0][1]["iters"] == res[1][1]["iters"] and res[0][1]["restarts"] == res[1][1]["restarts"] > 0
+
+
 def test_unpreconditioned_and_dense_lu():
     w = workloads.random_problem(6, 9, 8)
     orc, gpu = pair(w, use_precond=False, tol=1e-12, restart=30)
