@@ -153,6 +153,23 @@ def kernel_units(name, n1, n2, L1, L2):
     return None
 
 
+def max_over_ranks(value, device=None):
+    """Maximum of a per-rank float over all ranks (identity for one rank).
+    The timed region's duration is the slowest rank's."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second of the slowest rank (replicas)."""
+    return world * units_per_rank / seconds
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2102_11576_gb300 import Solver, workloads
@@ -186,7 +203,7 @@ def run_ours(args, rank, world, local_rank):
         return state
 
     def timed_form(precond, matvec, steps, warmup, profile_steps, clocks=None):
-        solver = Solver(*solver_args, precond=precond, matvec=matvec, **mk)
+        solver = Solver(*solver_args, precond=precond, matvec=matvec, use_graph=not args.no_graph, **mk)
         bufs = [u0.clone(), torch.empty_like(u0), torch.empty_like(u0)]
         state = (0, None)
         state = march(solver, bufs, state, warmup, [])
@@ -204,10 +221,7 @@ def run_ours(args, rank, world, local_rank):
         clk = clocks.stop() if clocks else None
         ms = e0.elapsed_time(e1)
         launches = solver.kernel_launches - l0
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         # live per-kernel timing: the same march continued with every launch
         # bracketed by CUDA events on this stream
         prof = None
@@ -243,7 +257,7 @@ def run_ours(args, rank, world, local_rank):
         others["fp32_op64"] = timed_form("fp32", "fp64", args.steps, args.warmup, args.profile_steps)
         others["fp64"] = timed_form("fp64", "fp64", args.fp64_steps, args.warmup, args.profile_steps)
     plain = others.get("fp64")
-    value = world * args.steps / (mixed["ms"] / 1e3)
+    value = whole_job_rate(args.steps, world, mixed["ms"] / 1e3)
 
     # ---- roofline of the dominant kernel (mixed form) ----
     from paper_2102_11576_gb300 import Solver as _S  # noqa: F401
@@ -316,13 +330,9 @@ def run_ours(args, rank, world, local_rank):
             solver.step_host(hn[prev], hn[prevprev], out=hn[nxt])
             prevprev, prev = prev, nxt
         barrier()
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(time.perf_counter() - t0, dev)
         solver.close()
-        e2e = {"value": round(world * args.steps / el, 4), "unit": UNIT,
+        e2e = {"value": round(whole_job_rate(args.steps, world, el), 4), "unit": UNIT,
                "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8}
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
@@ -493,6 +503,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="direct kernel launches instead of the graph loop (ncu cannot profile "
+                         "kernels inside graphs with conditional nodes)")
     args = ap.parse_args()
     if args.fp64_steps is None:
         args.fp64_steps = args.steps

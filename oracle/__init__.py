@@ -56,6 +56,8 @@ def _load():
     lib.or_initial_guess.argtypes = [ctypes.c_long, _dp, _dp, _dp]
     lib.or_step.restype = i
     lib.or_step.argtypes = [vp, _dp, _dp, _dp, _dp, i, d, i, _dp]
+    lib.or_adjoint_march.restype = d
+    lib.or_adjoint_march.argtypes = [vp, _dp, _dp, i, _dp, i, d, _dp, _dp, _dp, _dp]
     lib.or_assemble_dense.argtypes = [vp, _dp]
     lib.or_lu_solve.restype = i
     lib.or_lu_solve.argtypes = [ctypes.c_long, _dp, _dp]
@@ -271,6 +273,18 @@ class Problem:
             stats.append(st)
             prevprev, prev = prev, nxt
         return prev, stats
+
+    def adjoint_march(self, u0, steps, target, src=None, restart=20, tol=1e-13):
+        """Loss ||u^steps - target||^2 of the march and its exact gradients
+        (discrete adjoint): returns (loss, u_final, dL/du0, dL/ds, (dL/dkx, dL/dky))."""
+        u = self._grid(u0)
+        tg = self._grid(target)
+        s = None if src is None else self._grid(src)
+        uf, gu, gs = np.empty_like(u), np.empty_like(u), np.empty_like(u)
+        gk = np.zeros(2)
+        loss = _load().or_adjoint_march(self._h, _p(u), _p(s), int(steps), _p(tg), restart, tol, _p(uf),
+                                         _p(gu), _p(gs), _p(gk))
+        return loss, uf, gu, gs, (float(gk[0]), float(gk[1]))
 
     def dense_M(self):
         Md = np.empty((self.N, self.N))

@@ -546,6 +546,81 @@ int or_step(const or_ctx* c, const double* u_prev, const double* u_prevprev, con
 }
 
 /* ---------------------------------------------------------------------- */
+/* Discrete adjoint of the march (the paper has no gradient; this is the
+ * exact derivative of the scheme of Eq. 2.17 with f(u) = u - u^3 + s):
+ * L = sum_cells (u^m - target)^2.  With lambda^m = 2 (u^m - target), for
+ * k = m..1:  M mu^k = lambda^k  (M symmetric, Lemma 2.3),
+ *            lambda^{k-1} = mu^k + dt (1 - phi)(1 - 3 (u^{k-1})^2) mu^k,
+ *            dL/ds += dt (1 - phi) mu^k,
+ *            dL/dk_x += <mu^k, (I (x) A_x) u^k> / k_x   (A_x is linear in k_x),
+ *            dL/dk_y += <mu^k, (A_y (x) I) u^k> / k_y,
+ * and dL/du0 = lambda^0.  All states are kept (small grids only).
+ * Returns the loss; g_k = [dL/dk_x, dL/dk_y]. */
+static void apply_Ax(const or_ctx* c, const double* z, double* w) {
+  for (int j = 0; j < c->n2; ++j)
+    for (int i = 0; i < c->n1; ++i) {
+      double a = 0.0;
+      for (int l = 0; l < c->n1; ++l) a += c->tx[abs(i - l)] * z[(long)j * c->n1 + l];
+      w[(long)j * c->n1 + i] = a;
+    }
+}
+static void apply_Ay(const or_ctx* c, const double* z, double* w) {
+  for (int j = 0; j < c->n2; ++j)
+    for (int i = 0; i < c->n1; ++i) {
+      double a = 0.0;
+      for (int l = 0; l < c->n2; ++l) a += c->ty[abs(j - l)] * z[(long)l * c->n1 + i];
+      w[(long)j * c->n1 + i] = a;
+    }
+}
+
+double or_adjoint_march(const or_ctx* c, const double* u0, const double* src, int steps, const double* target,
+                        int m, double tol, double* u_final, double* g_u0, double* g_src, double* g_k) {
+  const long N = (long)c->n1 * c->n2;
+  double* U = (double*)malloc(sizeof(double) * (size_t)N * (size_t)(steps + 1));
+  double* lam = (double*)malloc(sizeof(double) * (size_t)N);
+  double* mu = (double*)malloc(sizeof(double) * (size_t)N);
+  double* t = (double*)malloc(sizeof(double) * (size_t)N);
+  memcpy(U, u0, sizeof(double) * (size_t)N);
+  for (int k = 1; k <= steps; ++k)
+    or_step(c, U + (long)(k - 1) * N, k >= 2 ? U + (long)(k - 2) * N : NULL, src, U + (long)k * N, m, tol,
+            100000, NULL);
+  const double* um = U + (long)steps * N;
+  double loss = 0.0;
+  for (long p = 0; p < N; ++p) {
+    double d = um[p] - target[p];
+    loss += d * d;
+    lam[p] = 2.0 * d;
+  }
+  if (u_final) memcpy(u_final, um, sizeof(double) * (size_t)N);
+  if (g_src) memset(g_src, 0, sizeof(double) * (size_t)N);
+  g_k[0] = g_k[1] = 0.0;
+  for (int k = steps; k >= 1; --k) {
+    const double* uk = U + (long)k * N;
+    const double* ukm1 = U + (long)(k - 1) * N;
+    memset(mu, 0, sizeof(double) * (size_t)N);
+    or_fgmres(c, lam, mu, m, tol, 100000, 1, NULL);
+    apply_Ax(c, uk, t);
+    double sx = 0.0, sy = 0.0;
+    for (long p = 0; p < N; ++p) sx += mu[p] * t[p];
+    apply_Ay(c, uk, t);
+    for (long p = 0; p < N; ++p) sy += mu[p] * t[p];
+    g_k[0] += sx / c->kx;
+    g_k[1] += sy / c->ky;
+    for (long p = 0; p < N; ++p) {
+      double out = c->phi[p] ? 0.0 : 1.0;
+      if (g_src) g_src[p] += c->dt * out * mu[p];
+      lam[p] = mu[p] + c->dt * out * (1.0 - 3.0 * ukm1[p] * ukm1[p]) * mu[p];
+    }
+  }
+  if (g_u0) memcpy(g_u0, lam, sizeof(double) * (size_t)N);
+  free(U);
+  free(lam);
+  free(mu);
+  free(t);
+  return loss;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Dense path for tiny grids: M assembled column by column from Eq. 2.17
  * (M e_q), then textbook LU with partial pivoting. */
 void or_assemble_dense(const or_ctx* c, double* Md /* N*N row-major */) {

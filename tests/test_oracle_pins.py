@@ -346,3 +346,36 @@ def test_first_order_convergence():
         errs.append(ex.error(u))
     r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
     assert 1.6 < r1 < 2.4 and 1.6 < r2 < 2.4
+
+
+# ---- discrete adjoint against central finite differences of the forward loss --
+def _march_loss(n1, n2, box, mask, a1, a2, kx, ky, dt, eta, u0, src, steps, target):
+    prob = oracle.Problem(n1, n2, box, mask, a1, a2, kx, ky, dt, eta)
+    u, _ = prob.march(u0, steps, src=src, restart=12, tol=1e-13)
+    return float(((u - target) ** 2).sum())
+
+
+def test_adjoint_gradients_match_central_differences():
+    rng = np.random.default_rng(21)
+    n1, n2, steps = 7, 6, 4
+    box = (-1.0, 1.0, -1.0, 1.0)
+    mask = rand_mask(rng, n2, n1, 0.7)
+    a1, a2, kx, ky, dt, eta = 1.35, 1.65, 0.8, 1.3, 0.05, 1e-3
+    u0 = rng.random((n2, n1)) * mask
+    src = rng.standard_normal((n2, n1))
+    target = rng.random((n2, n1))
+    prob = oracle.Problem(n1, n2, box, mask, a1, a2, kx, ky, dt, eta)
+    loss, _, gu, gs, (gkx, gky) = prob.adjoint_march(u0, steps, target, src=src, restart=12)
+    args = (n1, n2, box, mask, a1, a2)
+    f = lambda kx_, ky_, u0_, s_: _march_loss(*args, kx_, ky_, dt, eta, u0_, s_, steps, target)
+    assert loss == pytest.approx(f(kx, ky, u0, src), rel=1e-12)
+    h = 1e-6
+    assert gkx == pytest.approx((f(kx + h, ky, u0, src) - f(kx - h, ky, u0, src)) / (2 * h), rel=1e-6)
+    assert gky == pytest.approx((f(kx, ky + h, u0, src) - f(kx, ky - h, u0, src)) / (2 * h), rel=1e-6)
+    for (j, i) in [(2, 3), (0, 0), (5, 6)]:
+        e = np.zeros((n2, n1))
+        e[j, i] = h
+        fd_u = (f(kx, ky, u0 + e, src) - f(kx, ky, u0 - e, src)) / (2 * h)
+        fd_s = (f(kx, ky, u0, src + e) - f(kx, ky, u0, src - e)) / (2 * h)
+        assert gu[j, i] == pytest.approx(fd_u, rel=1e-6, abs=1e-9)
+        assert gs[j, i] == pytest.approx(fd_s, rel=1e-6, abs=1e-9)
