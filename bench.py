@@ -19,6 +19,7 @@ data path.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -483,8 +484,49 @@ def run_op(args):
                       "ms_per_call": e0.elapsed_time(e1) / args.reps}), flush=True)
 
 
+def run_adjoint(args):
+    """Times one differentiable march of the differentiation workload
+    (disk1024: 1024^2, unit disk, alpha = 1.5, 200 steps, sqrt-m
+    checkpointing): forward march, then the hand-written adjoint backward
+    (gradients wrt u0, k_x, k_y and the per-cell source)."""
+    import torch
+    from paper_2102_11576_gb300 import Solver, workloads
+    from paper_2102_11576_gb300.adjoint import march
+    w = workloads.make("disk1024")
+    steps = args.steps if args.steps != 10 else w["steps"]
+    s = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
+               w["dt"], w["eta"], restart=w["restart"], tol=w["tol"], precond="fp32", matvec="df32")
+    dev = torch.device("cuda")
+    u0 = torch.as_tensor(w["u0"]).to(dev).requires_grad_(True)
+    src = torch.zeros_like(u0).requires_grad_(True)
+    kx = torch.tensor(w["kx"], dtype=torch.float64, requires_grad=True)
+    ky = torch.tensor(w["ky"], dtype=torch.float64, requires_grad=True)
+    target = torch.as_tensor(w["target"]).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    uT = march(s, u0, kx, ky, src, steps=steps)
+    loss = ((uT - target) ** 2).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    print(json.dumps({"workload": f"disk1024: 1024x1024 unit disk, alpha=(1.5,1.5), {steps} steps, "
+                                  f"checkpoint every {math.ceil(math.sqrt(steps))}",
+                      "form": "FP32 preconditioner, double-FP32 Arnoldi operator, FP64 residual",
+                      "loss": loss.item(), "forward_s": t1 - t0, "backward_s": t2 - t1,
+                      "gradient_evals_per_s": 1.0 / (t2 - t0),
+                      "forward_steps_per_s": steps / (t1 - t0),
+                      "backward_steps_per_s": steps / (t2 - t1),
+                      "dL_dkx": kx.grad.item(), "dL_dky": ky.grad.item(),
+                      "grad_u0_norm": u0.grad.norm().item(), "grad_src_norm": src.grad.norm().item()}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time one differentiable march of the 1024^2 differentiation workload")
     ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "precond_fp32", "precond_fp64", "dst2"],
                     default=None,
                     help="time one operator entry point instead of the time march")
@@ -511,6 +553,9 @@ def main():
         args.fp64_steps = args.steps
     if args.op:
         run_op(args)
+        return
+    if args.adjoint:
+        run_adjoint(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

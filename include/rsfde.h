@@ -137,6 +137,20 @@ int rsfde_step_host(rsfde_ctx* ctx, const double* u_prev_host, const double* u_p
  * guess, out solution.  Synchronises the stream. */
 int rsfde_adjoint(rsfde_ctx* ctx, const double* lam, double* mu, rsfde_stats* stats);
 
+/* One backward step of the discrete adjoint of the time march (gradient of a
+ * loss of u^m; the paper itself states no gradient -- this is the exact
+ * derivative of the scheme of Eq. 2.17 with f(u) = u - u^3 + s).  Given
+ * u^{k-1}, u^k and lam = dL/du^k:
+ *   solves M mu = lam (M symmetric, Lemma 2.3), mu holding the initial guess;
+ *   lam_prev = mu + dt (1 - Phi)(1 - 3 (u^{k-1})^2) mu          (= dL/du^{k-1});
+ *   grad_src += dt (1 - Phi) mu                                  (if not NULL);
+ *   grad_k[0] += <mu, (I (x) A_x) u^k> / k_x,  grad_k[1] += <mu, (A_y (x) I) u^k> / k_y
+ *   (A_x, A_y are linear in k_x, k_y).
+ * u_prev, u_k, lam, mu, lam_prev, grad_src: device N doubles (lam_prev may
+ * alias lam); grad_k: DEVICE array of 2 doubles.  Synchronises the stream. */
+int rsfde_adjoint_step(rsfde_ctx* ctx, const double* u_prev, const double* u_k, const double* lam, double* mu,
+                       double* lam_prev, double* grad_src, double* grad_k, rsfde_stats* stats);
+
 /* ---- operator-level entry points (each one step of the hot path) --------- */
 /* Eq. 2.14-2.17: w = M z in the context's operator precision (matvec_prec).
  * z, w device N doubles (distinct). */

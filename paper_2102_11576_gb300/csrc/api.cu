@@ -728,6 +728,31 @@ int rsfde_adjoint(rsfde_ctx* c, const double* lam, double* mu, rsfde_stats* stat
   return rsfde_solve(c, lam, mu, stats);
 }
 
+int rsfde_adjoint_step(rsfde_ctx* c, const double* u_prev, const double* u_k, const double* lam, double* mu,
+                       double* lam_prev, double* grad_src, double* grad_k, rsfde_stats* stats) {
+  if (!c || !u_prev || !u_k || !lam || !mu || !lam_prev || !grad_k) return RSFDE_EINVAL;
+  int rc = rsfde_solve(c, lam, mu, stats);  // M^T = M (Lemma 2.3)
+  if (rc == RSFDE_ECUDA || rc == RSFDE_ENOMEM || rc == RSFDE_EINVAL) return rc;
+  if (rc != RSFDE_OK) return rc;
+  double* ay_u = static_cast<double*>(c->T2a);  // scratch, free after the solve
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
+    launch_toeplitz_rows<double, double>(u_k, c->tmpx, c->n1, c->n2, c->x64.tab, nullptr, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
+    launch_toeplitz_cols<double, double>(MODE_RAW, u_k, c->tmpx, c->phi, c->pen, nullptr, ay_u, c->n1, c->n2,
+                                         c->y64.tab, nullptr, nullptr, nullptr, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_OTHER);
+    launch_adjoint_accum(u_prev, mu, c->tmpx, ay_u, c->phi, c->dt, 1.0 / c->kx, 1.0 / c->ky, lam_prev, grad_src,
+                         grad_k, c->N, c->partials, c->st, c->stream);
+  }
+  if ((rc = check_launch(c))) return rc;
+  return cuda_fail(cudaStreamSynchronize(c->stream));
+}
+
 int rsfde_apply_M(rsfde_ctx* c, const double* z, double* w) {
   if (!c || !z || !w) return RSFDE_EINVAL;
   enqueue_apply_M<double>(c, z, w, nullptr);

@@ -15,6 +15,7 @@ constexpr int kMaxPartials = 4096;        // per-block partial sums of one reduc
 constexpr int kDotChunk = 8;              // basis vectors per block row of the multi-dot
 constexpr int MODE_APPLY = 0;
 constexpr int MODE_RESIDUAL = 1;
+constexpr int MODE_RAW = 2;  // column pass writes A_y z alone
 
 // ---- device-side solver control (single thread) ---------------------------
 // Called by the last block of the true-residual kernel with beta = ||b - M x||:
@@ -97,11 +98,12 @@ __device__ __forceinline__ void givens_step(SolverState* st, int j, double hnorm
 }
 
 // ---- launchers (transforms.cu) ---------------------------------------------
+// tmpx: scratch of N values of the arithmetic type T (A_x z between the passes)
 template <typename T, typename Tin>
-void launch_toeplitz_rows(const Tin* z, double* out, int n1, int n2, const AxisTables<T>& ax, const int* gate,
+void launch_toeplitz_rows(const Tin* z, void* tmpx, int n1, int n2, const AxisTables<T>& ax, const int* gate,
                           cudaStream_t s);
 template <typename T, typename Tin>
-void launch_toeplitz_cols(int mode, const Tin* z, const double* tmpx, const uint8_t* phi, double pen,
+void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi, double pen,
                           const double* b, double* out, int n1, int n2, const AxisTables<T>& ay,
                           const int* gate, double* partials, SolverState* st, cudaStream_t s);
 template <typename T, typename Tout>
@@ -131,6 +133,10 @@ template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s);
 void launch_finalize(double* x, size_t N, SolverState* st, cudaStream_t s);
 void launch_loop_cond(cudaGraphConditionalHandle h, SolverState* st, cudaStream_t s);
+void launch_adjoint_accum(const double* u_prev, const double* mu, const double* ax_u, const double* ay_u,
+                          const uint8_t* phi, double dt, double ikx, double iky, double* lam_prev,
+                          double* grad_src, double* grad_k, size_t N, double* partials, SolverState* st,
+                          cudaStream_t s);
 template <typename Tz>
 void launch_scale_copy(const double* v, const double* scale, Tz* z, size_t N, const int* gate, cudaStream_t s);
 

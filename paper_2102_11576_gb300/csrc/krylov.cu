@@ -208,6 +208,43 @@ __global__ void loop_cond_kernel(cudaGraphConditionalHandle h, SolverState* st) 
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
+// Adjoint step (after M mu = lam is solved): lam_prev, the source gradient and
+// the two k-gradient inner products, reduced deterministically; the last
+// block adds <mu, A_x u> / k_x and <mu, A_y u> / k_y into grad_k.
+__global__ void __launch_bounds__(kBlock)
+    adjoint_accum_kernel(const double* __restrict__ u_prev, const double* __restrict__ mu,
+                         const double* __restrict__ ax_u, const double* __restrict__ ay_u,
+                         const uint8_t* __restrict__ phi, double dt, double ikx, double iky,
+                         double* __restrict__ lam_prev, double* __restrict__ grad_src, double* grad_k, size_t N,
+                         double* partials, SolverState* st) {
+  __shared__ double red[32];
+  double sx = 0.0, sy = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    const double m = mu[p];
+    const bool inside = !phi[p];
+    const double up = u_prev[p];
+    lam_prev[p] = inside ? m + dt * (1.0 - 3.0 * up * up) * m : m;
+    if (grad_src && inside) grad_src[p] += dt * m;
+    sx += m * ax_u[p];
+    sy += m * ay_u[p];
+  }
+  const int G = gridDim.x;
+  const double bx = block_sum(sx, red);
+  const double by = block_sum(sy, red);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = bx;
+    partials[G + blockIdx.x] = by;
+  }
+  if (arrive_last(&st->counter, G)) {
+    const double tx = sum_partials(partials, G, red);
+    const double ty = sum_partials(partials + G, G, red);
+    if (threadIdx.x == 0) {
+      grad_k[0] += tx * ikx;
+      grad_k[1] += ty * iky;
+    }
+  }
+}
+
 // ---- launchers --------------------------------------------------------------
 void launch_init_state(SolverState* st, int m, int max_iter, double tol, cudaStream_t s) {
   init_state_kernel<<<1, 1, 0, s>>>(st, m, max_iter, tol);
@@ -237,6 +274,13 @@ void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStrea
 }
 template void launch_xupdate<double>(double*, const double*, size_t, SolverState*, cudaStream_t);
 template void launch_xupdate<float>(double*, const float*, size_t, SolverState*, cudaStream_t);
+void launch_adjoint_accum(const double* u_prev, const double* mu, const double* ax_u, const double* ay_u,
+                          const uint8_t* phi, double dt, double ikx, double iky, double* lam_prev,
+                          double* grad_src, double* grad_k, size_t N, double* partials, SolverState* st,
+                          cudaStream_t s) {
+  adjoint_accum_kernel<<<vec_grid(N), kBlock, 0, s>>>(u_prev, mu, ax_u, ay_u, phi, dt, ikx, iky, lam_prev,
+                                                      grad_src, grad_k, N, partials, st);
+}
 void launch_loop_cond(cudaGraphConditionalHandle h, SolverState* st, cudaStream_t s) {
   loop_cond_kernel<<<1, 1, 0, s>>>(h, st);
 }

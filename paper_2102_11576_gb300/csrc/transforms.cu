@@ -93,14 +93,15 @@ __device__ __forceinline__ T dst_out(const AxisTables<T>& ax, int pos, cx<T> y) 
 }
 
 // ---------------------------------------------------------------------------
-// Toeplitz product along rows (COLS = false: out = A_x z, MODE_APPLY only) or
-// columns (COLS = true), two vectors per group.  Column epilogues:
+// Toeplitz product along rows (COLS = false: tmpx = A_x z, MODE_APPLY only) or
+// columns (COLS = true), two vectors per group; tmpx holds A_x z in the
+// arithmetic type T between the two passes.  Column epilogues:
 //   MODE_APPLY:    out = z - tmpx - A_y z + (dt/eta) phi z
 //   MODE_RESIDUAL: out = b - (z - tmpx - A_y z + (dt/eta) phi z), ||out||^2
 //                  reduced, and the last block restarts the solver.
 template <typename T, typename Tin, int MODE, bool COLS>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    toeplitz_kernel(const Tin* __restrict__ z, const double* __restrict__ tmpx, const uint8_t* __restrict__ phi,
+    toeplitz_kernel(const Tin* __restrict__ z, T* __restrict__ tmpx, const uint8_t* __restrict__ phi,
                     double pen, const double* __restrict__ b, double* __restrict__ out, int n1, int n2,
                     AxisTables<T> ax, int F, int gstride, const int* gate, double* partials, SolverState* st) {
   if (gate_closed<T>(gate)) return;
@@ -147,16 +148,20 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
         for (int h = 0; h < 2; ++h) {
           if (h == 1 && !second) break;
           const size_t p = vaddr<COLS>(a + h, pos, n1);
-          const double az = double(h ? v[k].i : v[k].r);
+          const T az = h ? v[k].i : v[k].r;
           if (!COLS) {
-            out[p] = az;
+            tmpx[p] = az;  // A_x z, kept in the arithmetic type T
           } else {
-            const double zz = double(z[p]);
-            const double w = zz - tmpx[p] - az + (phi[p] ? pen * zz : 0.0);
-            if (MODE == MODE_APPLY) {
-              out[p] = w;
+            // z - A_x z - A_y z + (dt/eta) phi z in T; only the result is rounded to FP64
+            const T zz = T(z[p]);
+            T w = zz - tmpx[p] - az;
+            if (phi[p]) w = w + T(pen) * zz;
+            if (MODE == MODE_RAW) {
+              out[p] = double(az);
+            } else if (MODE == MODE_APPLY) {
+              out[p] = double(w);
             } else {
-              const double r = b[p] - w;
+              const double r = b[p] - double(w);
               out[p] = r;
               acc += r * r;
             }
@@ -380,19 +385,20 @@ static void set_smem(K kernel, size_t bytes) {
 }
 
 template <typename T, typename Tin>
-void launch_toeplitz_rows(const Tin* z, double* out, int n1, int n2, const AxisTables<T>& ax, const int* gate,
+void launch_toeplitz_rows(const Tin* z, void* tmpx, int n1, int n2, const AxisTables<T>& ax, const int* gate,
                           cudaStream_t s) {
   const int npairs = (n2 + 1) / 2;
   const int F = pick_groups<T>(ax.L, npairs);
   const size_t sm = group_smem<T>(ax.L, F, false);
   auto k = toeplitz_kernel<T, Tin, MODE_APPLY, false>;
   set_smem(k, sm);
-  k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(z, nullptr, nullptr, 0.0, nullptr, out, n1, n2, ax, F,
-                                                      group_stride<T>(ax.L, F, false), gate, nullptr, nullptr);
+  k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), nullptr, 0.0, nullptr, nullptr,
+                                                      n1, n2, ax, F, group_stride<T>(ax.L, F, false), gate,
+                                                      nullptr, nullptr);
 }
 
 template <typename T, typename Tin>
-void launch_toeplitz_cols(int mode, const Tin* z, const double* tmpx, const uint8_t* phi, double pen,
+void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi, double pen,
                           const double* b, double* out, int n1, int n2, const AxisTables<T>& ay,
                           const int* gate, double* partials, SolverState* st, cudaStream_t s) {
   const int npairs = (n1 + 1) / 2;
@@ -400,15 +406,22 @@ void launch_toeplitz_cols(int mode, const Tin* z, const double* tmpx, const uint
   const size_t sm = group_smem<T>(ay.L, F, true);
   const int gs = group_stride<T>(ay.L, F, true);
   int grid = (npairs + F - 1) / F;
-  if (mode == MODE_APPLY) {
+  if (mode == MODE_RAW) {
+    auto k = toeplitz_kernel<T, Tin, MODE_RAW, true>;
+    set_smem(k, sm);
+    k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
+                                        partials, st);
+  } else if (mode == MODE_APPLY) {
     auto k = toeplitz_kernel<T, Tin, MODE_APPLY, true>;
     set_smem(k, sm);
-    k<<<grid, F * (ay.L / 16), sm, s>>>(z, tmpx, phi, pen, b, out, n1, n2, ay, F, gs, gate, partials, st);
+    k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
+                                        partials, st);
   } else {
     if (grid > kMaxPartials) grid = kMaxPartials;
     auto k = toeplitz_kernel<T, Tin, MODE_RESIDUAL, true>;
     set_smem(k, sm);
-    k<<<grid, F * (ay.L / 16), sm, s>>>(z, tmpx, phi, pen, b, out, n1, n2, ay, F, gs, gate, partials, st);
+    k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
+                                        partials, st);
   }
 }
 
@@ -456,24 +469,24 @@ void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, 
 }
 
 // explicit instantiations used by the solver
-template void launch_toeplitz_rows<double, double>(const double*, double*, int, int, const AxisTables<double>&,
+template void launch_toeplitz_rows<double, double>(const double*, void*, int, int, const AxisTables<double>&,
                                                    const int*, cudaStream_t);
-template void launch_toeplitz_rows<double, float>(const float*, double*, int, int, const AxisTables<double>&,
+template void launch_toeplitz_rows<double, float>(const float*, void*, int, int, const AxisTables<double>&,
                                                   const int*, cudaStream_t);
-template void launch_toeplitz_cols<double, double>(int, const double*, const double*, const uint8_t*, double,
+template void launch_toeplitz_cols<double, double>(int, const double*, void*, const uint8_t*, double,
                                                    const double*, double*, int, int, const AxisTables<double>&,
                                                    const int*, double*, SolverState*, cudaStream_t);
-template void launch_toeplitz_cols<double, float>(int, const float*, const double*, const uint8_t*, double,
+template void launch_toeplitz_cols<double, float>(int, const float*, void*, const uint8_t*, double,
                                                   const double*, double*, int, int, const AxisTables<double>&,
                                                   const int*, double*, SolverState*, cudaStream_t);
-template void launch_toeplitz_rows<df, double>(const double*, double*, int, int, const AxisTables<df>&,
+template void launch_toeplitz_rows<df, double>(const double*, void*, int, int, const AxisTables<df>&,
                                                const int*, cudaStream_t);
-template void launch_toeplitz_rows<df, float>(const float*, double*, int, int, const AxisTables<df>&,
+template void launch_toeplitz_rows<df, float>(const float*, void*, int, int, const AxisTables<df>&,
                                               const int*, cudaStream_t);
-template void launch_toeplitz_cols<df, double>(int, const double*, const double*, const uint8_t*, double,
+template void launch_toeplitz_cols<df, double>(int, const double*, void*, const uint8_t*, double,
                                                const double*, double*, int, int, const AxisTables<df>&,
                                                const int*, double*, SolverState*, cudaStream_t);
-template void launch_toeplitz_cols<df, float>(int, const float*, const double*, const uint8_t*, double,
+template void launch_toeplitz_cols<df, float>(int, const float*, void*, const uint8_t*, double,
                                               const double*, double*, int, int, const AxisTables<df>&,
                                               const int*, double*, SolverState*, cudaStream_t);
 template void launch_dst_rows<double, double>(const double*, const double*, double*, int, int,

@@ -240,3 +240,28 @@ def test_full_size_polygon2048_sampled():
         r_pts = b.reshape(-1)[idx] - orc.apply_M_points(u1, idx)
         # pointwise residual at sampled points is consistent with the global bound
         assert np.abs(r_pts).max() <= 1e-10 * np.linalg.norm(b)
+
+
+def test_ellipse512_march_with_source():
+    """The 512^2 ellipse workload (alpha = (1.2, 1.8), k = (2, 0.5), Gaussian
+    source, FGMRES(30)): four steps in the mixed form; every step's true
+    residual recomputed by the oracle, and the solution within the bound
+    ||x - x*||_inf <= ||r||_inf that Lemma 3.1 with Lemma 2.3 gives."""
+    w = workloads.make("ellipse512")
+    orc, gpu = pair(w, restart=w["restart"], tol=w["tol"], precond="fp32", matvec="df32")
+    _, g64 = pair(w, restart=w["restart"], tol=1e-13, precond="fp64", matvec="fp64")
+    src = dev(w["src"])
+    prev, prevprev = dev(w["u0"]), None
+    for k in range(4):
+        nxt, st = gpu.step(prev, prevprev, src)
+        assert st["converged"] and st["rel_res"] <= 1e-10
+        b = orc.rhs(host(prev), w["src"])
+        x0 = orc.initial_guess(host(prev), None if prevprev is None else host(prevprev))
+        r = b - orc.apply_M(host(nxt))
+        assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b) * 1.01
+        # a tighter FP64 solve from the same data: within the Lemma 3.1 bound
+        ref, _ = g64.solve(dev(b), dev(x0))
+        diff = np.abs(host(nxt) - host(ref)).max()
+        assert diff <= np.abs(r).max() + np.abs(b - orc.apply_M(host(ref))).max() + 1e-15
+        assert diff / np.abs(host(ref)).max() <= 1e-9
+        prevprev, prev = prev, nxt
