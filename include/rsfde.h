@@ -56,6 +56,15 @@ extern "C" {
  * Knuth).  The true residual b - M x is always computed in FP64. */
 #define RSFDE_DF32 2
 
+/* Krylov variant.  RSFDE_FGMRES_RIGHT (default): right-preconditioned flexible
+ * GMRES, stop when the true ||b - M x||_2 <= tol ||b||_2.  RSFDE_GMRES_LEFT:
+ * the left-preconditioned GMRES(m) of the paper's experiments (Section 5),
+ * applied to P^-1 M x = P^-1 b and stopped when
+ * ||P^-1 (b - M x)||_2 <= tol ||P^-1 b||_2 (rel_res then reports that ratio);
+ * with use_precond = 0 it is plain GMRES. */
+#define RSFDE_FGMRES_RIGHT 0
+#define RSFDE_GMRES_LEFT 1
+
 /* Arnoldi orthogonalisation: classical Gram-Schmidt, or with one re-orthogonalisation pass. */
 #define RSFDE_CGS 0
 #define RSFDE_CGS2 1
@@ -76,6 +85,7 @@ typedef struct {
   int32_t arnoldi;      /* RSFDE_CGS | RSFDE_CGS2 */
   int32_t use_precond;  /* 1: P-hat of Eq. 4.6; 0: unpreconditioned GMRES */
   int32_t matvec_prec;  /* RSFDE_FP64 | RSFDE_DF32: M applied to the Arnoldi vectors */
+  int32_t variant;      /* RSFDE_FGMRES_RIGHT | RSFDE_GMRES_LEFT */
   int32_t use_graph;    /* 1: the cycles of a solve replay as one CUDA graph with a device-side
                            loop (one host synchronisation per solve); 0: direct launches with
                            one host check per cycle.  Profiling always uses direct launches. */
@@ -92,7 +102,8 @@ typedef struct {
 } rsfde_stats;
 
 /* Defaults: restart 20, max_iter 10000, tol 1e-10, FP64 preconditioner, CGS,
- * preconditioned, FP64 operator, CUDA graph, default stream. */
+ * preconditioned, FP64 operator, right-preconditioned FGMRES, CUDA graph,
+ * default stream. */
 void rsfde_opts_default(rsfde_opts* o);
 
 /* Section 2 / Eq. 2.16 / Section 4.1 (setup of one linear system).

@@ -22,6 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librsfde.so")
 
 FP64, FP32, DF32 = 0, 1, 2
+_VARIANTS = {"fgmres_right": 0, "gmres_left": 1}
 CGS, CGS2 = 0, 1
 _ERR = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV", -5: "ENONFINITE",
         -6: "ETIMEOUT"}
@@ -43,7 +44,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("tol", ctypes.c_double),
                 ("precond_prec", ctypes.c_int32), ("arnoldi", ctypes.c_int32),
                 ("use_precond", ctypes.c_int32), ("matvec_prec", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("variant", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):
@@ -121,7 +123,7 @@ class Solver:
 
     def __init__(self, n1, n2, box, in_omega, alpha1, alpha2, kx, ky, dt, eta, restart=20,
                  max_iter=10000, tol=1e-10, precond="fp64", arnoldi="cgs", use_precond=True,
-                 matvec="fp64", use_graph=True, stream=None):
+                 matvec="fp64", variant="fgmres_right", use_graph=True, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
@@ -142,6 +144,7 @@ class Solver:
         o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
         o.use_precond = int(bool(use_precond))
         o.matvec_prec = {"fp64": FP64, "df32": DF32}[matvec]
+        o.variant = _VARIANTS[variant]
         o.use_graph = int(bool(use_graph))
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         self._opts = o
@@ -192,6 +195,8 @@ class Solver:
                 o.matvec_prec = {"fp64": FP64, "df32": DF32}[v]
             elif k == "use_graph":
                 o.use_graph = int(bool(v))
+            elif k == "variant":
+                o.variant = _VARIANTS[v]
             else:
                 setattr(o, k, v)
         _check(self._lib.rsfde_set_opts(self._h, ctypes.byref(o)), "set_opts")

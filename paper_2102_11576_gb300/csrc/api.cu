@@ -336,8 +336,53 @@ void enqueue_apply_M(rsfde_ctx* c, const Tz* z, double* w, const int* gate) {
   else enqueue_apply_M_t<double, Tz>(c, z, w, gate, c->x64.tab, c->y64.tab);
 }
 
+bool left_variant(const rsfde_ctx* c) { return c->opts.variant == RSFDE_GMRES_LEFT; }
+
+template <typename T, typename Tz>
+void enqueue_precond_t(rsfde_ctx* c, const double* v, const double* vscale, Tz* z, const int* gate,
+                       const AxisTables<T>& tx, const AxisTables<T>& ty);
+
+// z = P-hat^-1 (scale * v) into an FP64 vector, in the context's preconditioner precision.
+void enqueue_precond64(rsfde_ctx* c, const double* v, const double* vscale, double* z, const int* gate) {
+  if (fp32_precond(c)) enqueue_precond_t<float, double>(c, v, vscale, z, gate, c->x32.tab, c->y32.tab);
+  else enqueue_precond_t<double, double>(c, v, vscale, z, gate, c->x64.tab, c->y64.tab);
+}
+
+// Left-preconditioned GMRES: V_0 = P^-1 (b - M x) (or b - M x without a
+// preconditioner), beta = ||V_0||, then restart_prep.
+void enqueue_residual_left(rsfde_ctx* c, const int* gate) {
+  double* r = c->opts.use_precond ? static_cast<double*>(c->Z) : c->V;
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
+    launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
+    launch_toeplitz_cols<double, double>(MODE_RESID_ONLY, c->x, c->tmpx, c->phi, c->pen, c->b, r, c->n1, c->n2,
+                                         c->y64.tab, gate, nullptr, nullptr, c->stream);
+  }
+  if (c->opts.use_precond) enqueue_precond64(c, r, nullptr, c->V, gate);
+  ProfScope ps(c, RSFDE_K_OTHER);
+  launch_restart_norm(c->V, c->N, c->partials, c->st, gate, c->stream);
+}
+
+// ||b|| for the stop test: ||P^-1 b|| for left-preconditioned GMRES (st->bnorm).
+void enqueue_bnorm(rsfde_ctx* c) {
+  const double* v = c->b;
+  if (left_variant(c) && c->opts.use_precond) {
+    enqueue_precond64(c, c->b, nullptr, static_cast<double*>(c->Z), nullptr);
+    v = static_cast<double*>(c->Z);
+  }
+  ProfScope ps(c, RSFDE_K_OTHER);
+  launch_norm_b(v, c->N, c->partials, c->st, c->stream);
+}
+
 // V_0 = b - M x, beta = ||V_0||, then restart_prep (device).
 void enqueue_residual(rsfde_ctx* c, const int* gate) {
+  if (left_variant(c)) {
+    enqueue_residual_left(c, gate);
+    return;
+  }
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
     launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
@@ -423,14 +468,57 @@ void enqueue_cycle_t(rsfde_ctx* c) {
   enqueue_residual(c, gc);
 }
 
+// One cycle of left-preconditioned GMRES(m) (Section 5): w = P^-1 M v_j,
+// the same Gram-Schmidt and Givens kernels, x += V y, residual P^-1 (b - M x).
+void enqueue_cycle_left(rsfde_ctx* c) {
+  const size_t N = c->N;
+  const int m = c->opts.restart;
+  const int* gi = &c->st->run_iter;
+  double* tmp = static_cast<double*>(c->Z);  // Z is unused by this variant
+  for (int j = 0; j < m; ++j) {
+    const double* vj = c->V + (size_t)j * N;
+    double* w = c->V + (size_t)(j + 1) * N;
+    if (c->opts.use_precond) {
+      enqueue_apply_M<double>(c, vj, tmp, gi);    // M V_j
+      enqueue_precond64(c, tmp, &c->st->s[j], w, gi);  // P^-1 M v_j
+    } else {
+      {
+        ProfScope ps(c, RSFDE_K_OTHER);
+        launch_scale_copy<double>(vj, &c->st->s[j], tmp, N, gi, c->stream);
+      }
+      enqueue_apply_M<double>(c, tmp, w, gi);
+    }
+    const bool cgs2 = c->opts.arnoldi == RSFDE_CGS2;
+    for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
+      {
+        ProfScope ps(c, RSFDE_K_MULTIDOT);
+        launch_multidot(c->V, N, j, pass, c->partials, c->st, c->stream);
+      }
+      ProfScope ps(c, RSFDE_K_UPDATE);
+      launch_update(c->V, N, j, (!cgs2 || pass == 1) ? 1 : 0, c->partials, c->st, c->stream);
+    }
+  }
+  {
+    ProfScope ps(c, RSFDE_K_OTHER);
+    launch_solve_y(c->st, c->stream);
+  }
+  {
+    ProfScope ps(c, RSFDE_K_XUPDATE);
+    launch_xupdate_v(c->x, c->V, N, c->st, c->stream);
+  }
+  enqueue_residual_left(c, &c->st->run_cycle);
+}
+
 void enqueue_cycle(rsfde_ctx* c) {
-  if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float>(c);
+  if (left_variant(c)) enqueue_cycle_left(c);
+  else if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float>(c);
   else enqueue_cycle_t<double>(c);
 }
 
 int graph_key(const rsfde_ctx* c) {
   const rsfde_opts& o = c->opts;
-  return ((((o.restart * 4 + o.precond_prec) * 4 + o.matvec_prec) * 2 + o.arnoldi) * 2 + o.use_precond);
+  return (((((o.restart * 4 + o.precond_prec) * 4 + o.matvec_prec) * 2 + o.arnoldi) * 2 + o.use_precond) * 2 +
+          o.variant);
 }
 
 // Captures one FGMRES cycle into the body of a CUDA graph WHILE node whose
@@ -537,6 +625,7 @@ void rsfde_opts_default(rsfde_opts* o) {
   o->arnoldi = RSFDE_CGS;
   o->use_precond = 1;
   o->matvec_prec = RSFDE_FP64;
+  o->variant = RSFDE_FGMRES_RIGHT;
   o->use_graph = 1;
   o->stream = nullptr;
 }
@@ -559,6 +648,7 @@ static int valid_opts(const rsfde_opts* o) {
   if (o->precond_prec != RSFDE_FP64 && o->precond_prec != RSFDE_FP32) return 0;
   if (o->arnoldi != RSFDE_CGS && o->arnoldi != RSFDE_CGS2) return 0;
   if (o->matvec_prec != RSFDE_FP64 && o->matvec_prec != RSFDE_DF32) return 0;
+  if (o->variant != RSFDE_FGMRES_RIGHT && o->variant != RSFDE_GMRES_LEFT) return 0;
   return 1;
 }
 
@@ -660,10 +750,7 @@ int rsfde_solve(rsfde_ctx* c, const double* b, double* x, rsfde_stats* stats) {
   cudaMemcpyAsync(c->b, b, bytes, cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyDeviceToDevice, c->stream);
   enqueue_init(c);
-  {
-    ProfScope ps(c, RSFDE_K_OTHER);
-    launch_norm_b(c->b, c->N, c->partials, c->st, c->stream);
-  }
+  enqueue_bnorm(c);
   int rc = check_launch(c);
   if (rc) return rc;
   rc = run_solver(c, stats);
@@ -687,6 +774,7 @@ int rsfde_step(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, con
   if (!c || !u_prev || !u_next) return RSFDE_EINVAL;
   enqueue_init(c);
   enqueue_rhs(c, u_prev, u_prevprev, src, c->b, c->x);
+  if (left_variant(c)) enqueue_bnorm(c);
   int rc = check_launch(c);
   if (rc) return rc;
   rc = run_solver(c, stats);
@@ -713,6 +801,7 @@ int rsfde_step_host(rsfde_ctx* c, const double* u_prev_h, const double* u_prevpr
   if (d_src) cudaMemcpyAsync(d_src, src_h, bytes, cudaMemcpyHostToDevice, c->stream);
   enqueue_init(c);
   enqueue_rhs(c, d_u, d_uu, d_src, c->b, c->x);
+  if (left_variant(c)) enqueue_bnorm(c);
   int rc = check_launch(c);
   if (rc) return rc;
   rc = run_solver(c, stats);

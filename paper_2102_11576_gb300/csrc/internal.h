@@ -15,7 +15,8 @@ constexpr int kMaxPartials = 4096;        // per-block partial sums of one reduc
 constexpr int kDotChunk = 8;              // basis vectors per block row of the multi-dot
 constexpr int MODE_APPLY = 0;
 constexpr int MODE_RESIDUAL = 1;
-constexpr int MODE_RAW = 2;  // column pass writes A_y z alone
+constexpr int MODE_RAW = 2;         // column pass writes A_y z alone
+constexpr int MODE_RESID_ONLY = 3;  // column pass writes b - M z, no reduction
 
 // ---- device-side solver control (single thread) ---------------------------
 // Called by the last block of the true-residual kernel with beta = ||b - M x||:
@@ -133,6 +134,9 @@ template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s);
 void launch_finalize(double* x, size_t N, SolverState* st, cudaStream_t s);
 void launch_loop_cond(cudaGraphConditionalHandle h, SolverState* st, cudaStream_t s);
+void launch_restart_norm(const double* v, size_t N, double* partials, SolverState* st, const int* gate,
+                         cudaStream_t s);
+void launch_xupdate_v(double* x, const double* V, size_t N, SolverState* st, cudaStream_t s);
 void launch_adjoint_accum(const double* u_prev, const double* mu, const double* ax_u, const double* ay_u,
                           const uint8_t* phi, double dt, double ikx, double iky, double* lam_prev,
                           double* grad_src, double* grad_k, size_t N, double* partials, SolverState* st,

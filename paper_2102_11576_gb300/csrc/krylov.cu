@@ -245,6 +245,41 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+// beta = ||v||, then the restart decision (left-preconditioned GMRES, whose
+// residual is P^-1 (b - M x) and so is formed by separate kernels).
+__global__ void __launch_bounds__(kBlock) restart_norm_kernel(const double* __restrict__ v, size_t N,
+                                                              double* partials, SolverState* st, const int* gate) {
+  if (closed(gate)) return;
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    const double a = v[p];
+    acc += a * a;
+  }
+  const double bs = block_sum(acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+  if (arrive_last(&st->counter, gridDim.x)) {
+    const double tot = sum_partials(partials, gridDim.x, red);
+    if (threadIdx.x == 0) restart_prep(st, sqrt(tot));
+  }
+}
+
+// x <- x + sum_i y_i v_i = x + sum_i (y_i s_i) V_i (left-preconditioned GMRES).
+__global__ void __launch_bounds__(kBlock) xupdate_v_kernel(double* __restrict__ x, const double* __restrict__ V,
+                                                           size_t N, SolverState* st) {
+  if (closed(&st->run_cycle)) return;
+  const int J = st->jlast;
+  if (J == 0) return;
+  __shared__ double y[kMaxRestart];
+  for (int i = threadIdx.x; i < J; i += blockDim.x) y[i] = st->y[i] * st->s[i];
+  __syncthreads();
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    double v = x[p];
+    for (int i = 0; i < J; ++i) v += y[i] * V[(size_t)i * N + p];
+    x[p] = v;
+  }
+}
+
 // ---- launchers --------------------------------------------------------------
 void launch_init_state(SolverState* st, int m, int max_iter, double tol, cudaStream_t s) {
   init_state_kernel<<<1, 1, 0, s>>>(st, m, max_iter, tol);
@@ -280,6 +315,13 @@ void launch_adjoint_accum(const double* u_prev, const double* mu, const double* 
                           cudaStream_t s) {
   adjoint_accum_kernel<<<vec_grid(N), kBlock, 0, s>>>(u_prev, mu, ax_u, ay_u, phi, dt, ikx, iky, lam_prev,
                                                       grad_src, grad_k, N, partials, st);
+}
+void launch_restart_norm(const double* v, size_t N, double* partials, SolverState* st, const int* gate,
+                         cudaStream_t s) {
+  restart_norm_kernel<<<vec_grid(N), kBlock, 0, s>>>(v, N, partials, st, gate);
+}
+void launch_xupdate_v(double* x, const double* V, size_t N, SolverState* st, cudaStream_t s) {
+  xupdate_v_kernel<<<vec_grid(N), kBlock, 0, s>>>(x, V, N, st);
 }
 void launch_loop_cond(cudaGraphConditionalHandle h, SolverState* st, cudaStream_t s) {
   loop_cond_kernel<<<1, 1, 0, s>>>(h, st);

@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
               out[p] = double(az);
             } else if (MODE == MODE_APPLY) {
               out[p] = double(w);
+            } else if (MODE == MODE_RESID_ONLY) {
+              out[p] = b[p] - double(w);
             } else {
               const double r = b[p] - double(w);
               out[p] = r;
@@ -406,7 +408,12 @@ void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi
   const size_t sm = group_smem<T>(ay.L, F, true);
   const int gs = group_stride<T>(ay.L, F, true);
   int grid = (npairs + F - 1) / F;
-  if (mode == MODE_RAW) {
+  if (mode == MODE_RESID_ONLY) {
+    auto k = toeplitz_kernel<T, Tin, MODE_RESID_ONLY, true>;
+    set_smem(k, sm);
+    k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
+                                        partials, st);
+  } else if (mode == MODE_RAW) {
     auto k = toeplitz_kernel<T, Tin, MODE_RAW, true>;
     set_smem(k, sm);
     k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
