@@ -254,6 +254,7 @@ def run_ours(args, rank, world, local_rank):
     # FP64 form, each marched from the same u0 over the same steps
     mixed = timed_form("fp32", "df32", args.steps, args.warmup, args.profile_steps, clocks)
     others = {}
+    others["bf16x3+df32"] = timed_form("bf16x3", "df32", args.steps, args.warmup, args.profile_steps)
     if not args.no_fp64:
         others["fp32_op64"] = timed_form("fp32", "fp64", args.steps, args.warmup, args.profile_steps)
         others["fp64"] = timed_form("fp64", "fp64", args.fp64_steps, args.warmup, args.profile_steps)

@@ -45,12 +45,15 @@ extern "C" {
 #define RSFDE_ENONFINITE (-5)  /* NaN or Inf met in the right side or in the Arnoldi process */
 #define RSFDE_ETIMEOUT (-6)    /* a bounded device-side wait gave up */
 
-/* Precisions.  The preconditioner apply (Eq. 4.6) runs in RSFDE_FP64 or
- * RSFDE_FP32; the operator applied to the Arnoldi vectors in RSFDE_FP64 or
+/* Precisions.  The preconditioner apply (Eq. 4.6) runs in RSFDE_FP64,
+ * RSFDE_FP32 or RSFDE_BF16X3; the operator applied to the Arnoldi vectors in RSFDE_FP64 or
  * RSFDE_DF32.  The true residual, the Arnoldi orthogonalisation and the
  * Givens least squares are FP64 in every mode. */
 #define RSFDE_FP64 0
 #define RSFDE_FP32 1
+/* Preconditioner sine transforms as tensor-core GEMMs in split BF16
+ * (X = X_hi + X_lo; X_hi S_hi + X_hi S_lo + X_lo S_hi with FP32 accumulation). */
+#define RSFDE_BF16X3 3
 /* Operator M applied to the Arnoldi vectors in double-FP32 arithmetic (pairs
  * of FP32 numbers, ~48-bit significand, error-free transforms of Dekker and
  * Knuth).  The true residual b - M x is always computed in FP64. */
@@ -81,7 +84,7 @@ typedef struct {
   int32_t restart;      /* m of FGMRES(m); Section 5 uses 20.  1..64 */
   int32_t max_iter;     /* cap on inner iterations per solve */
   double tol;           /* stop when ||b - M x||_2 <= tol ||b||_2 */
-  int32_t precond_prec; /* RSFDE_FP64 | RSFDE_FP32 */
+  int32_t precond_prec; /* RSFDE_FP64 | RSFDE_FP32 | RSFDE_BF16X3 */
   int32_t arnoldi;      /* RSFDE_CGS | RSFDE_CGS2 */
   int32_t use_precond;  /* 1: P-hat of Eq. 4.6; 0: unpreconditioned GMRES */
   int32_t matvec_prec;  /* RSFDE_FP64 | RSFDE_DF32: M applied to the Arnoldi vectors */
@@ -215,7 +218,8 @@ int rsfde_dst2_noalloc(int32_t n1, int32_t n2, const double* v, double* out, voi
 #define RSFDE_K_UPDATE 6        /* Arnoldi update, norm and Givens step */
 #define RSFDE_K_XUPDATE 7       /* solution update x += Z y */
 #define RSFDE_K_OTHER 8         /* right side, norms, scalar kernels */
-#define RSFDE_K_COUNT 9
+#define RSFDE_K_DST_GEMM 9      /* preconditioner as split-BF16 tensor-core GEMMs (all 5 launches) */
+#define RSFDE_K_COUNT 10
 
 /* While on, every kernel launch of the context is bracketed by a pair of CUDA
  * events on the context's stream (adds one event record per launch). */

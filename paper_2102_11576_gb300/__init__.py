@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "librsfde.so")
 
 FP64, FP32, DF32 = 0, 1, 2
 _VARIANTS = {"fgmres_right": 0, "gmres_left": 1}
+_PRECONDS = {"fp64": 0, "fp32": 1, "bf16x3": 3}
 CGS, CGS2 = 0, 1
 _ERR = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV", -5: "ENONFINITE",
         -6: "ETIMEOUT"}
@@ -140,7 +141,7 @@ class Solver:
         o = _Opts()
         lib.rsfde_opts_default(ctypes.byref(o))
         o.restart, o.max_iter, o.tol = int(restart), int(max_iter), float(tol)
-        o.precond_prec = {"fp64": FP64, "fp32": FP32}[precond]
+        o.precond_prec = _PRECONDS[precond]
         o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
         o.use_precond = int(bool(use_precond))
         o.matvec_prec = {"fp64": FP64, "df32": DF32}[matvec]
@@ -186,7 +187,7 @@ class Solver:
         o = self._opts
         for k, v in kw.items():
             if k == "precond":
-                o.precond_prec = {"fp64": FP64, "fp32": FP32}[v]
+                o.precond_prec = _PRECONDS[v]
             elif k == "arnoldi":
                 o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[v]
             elif k == "use_precond":
@@ -298,7 +299,7 @@ class Solver:
 
     def profile_read(self):
         """{kernel class: (device ms, launches)} since the last read."""
-        K = 9
+        K = 10
         ms = np.zeros(K)
         n = np.zeros(K, dtype=np.int64)
         _check(self._lib.rsfde_profile_read(self._h, ctypes.c_void_p(ms.ctypes.data),

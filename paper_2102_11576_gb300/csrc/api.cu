@@ -204,6 +204,7 @@ struct rsfde_ctx {
   SolverState* st = nullptr;
   SolverState* st_host = nullptr;  // pinned
   int64_t launches = 0;
+  Bf16Plan* bf16 = nullptr;  // tensor-core preconditioner, made when first needed
   // one FGMRES cycle captured as the body of a device-side WHILE loop
   cudaStream_t cap_stream = nullptr;  // private stream used only for capture
   cudaGraph_t graph = nullptr;
@@ -309,10 +310,28 @@ void free_ctx(rsfde_ctx* c) {
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  bf16_plan_destroy(c->bf16);
   delete c;
 }
 
-bool fp32_precond(const rsfde_ctx* c) { return c->opts.precond_prec == RSFDE_FP32; }
+// Z (the preconditioned vectors) is FP32 for the FP32 and split-BF16 preconditioners.
+bool fp32_precond(const rsfde_ctx* c) {
+  return c->opts.precond_prec == RSFDE_FP32 || c->opts.precond_prec == RSFDE_BF16X3;
+}
+bool bf16_precond_on(const rsfde_ctx* c) { return c->opts.precond_prec == RSFDE_BF16X3; }
+
+int ensure_bf16(rsfde_ctx* c) {
+  if (c->bf16 || !bf16_precond_on(c)) return RSFDE_OK;
+  return bf16_plan_create(&c->bf16, c->n1, c->n2, c->x32.tab.lam, c->y32.tab.lam, c->stream);
+}
+
+// The tensor-core preconditioner z = P-hat^-1 (scale * v) (five launches).
+template <typename Tz>
+void enqueue_precond_bf16(rsfde_ctx* c, const double* v, const double* vscale, Tz* z, const int* gate) {
+  ProfScope ps(c, RSFDE_K_DST_GEMM);
+  c->launches += 4;
+  bf16_precond<Tz>(c->bf16, v, vscale, z, c->phi, c->pen, gate, c->stream);
+}
 
 // ---- enqueue helpers ---------------------------------------------------------
 // w = M z (Eq. 2.17), z in precision Tz, arithmetic T (double or df).
@@ -343,8 +362,12 @@ void enqueue_precond_t(rsfde_ctx* c, const double* v, const double* vscale, Tz* 
                        const AxisTables<T>& tx, const AxisTables<T>& ty);
 
 // z = P-hat^-1 (scale * v) into an FP64 vector, in the context's preconditioner precision.
+template <typename Tz>
+void enqueue_precond_bf16(rsfde_ctx* c, const double* v, const double* vscale, Tz* z, const int* gate);
+
 void enqueue_precond64(rsfde_ctx* c, const double* v, const double* vscale, double* z, const int* gate) {
-  if (fp32_precond(c)) enqueue_precond_t<float, double>(c, v, vscale, z, gate, c->x32.tab, c->y32.tab);
+  if (bf16_precond_on(c)) enqueue_precond_bf16<double>(c, v, vscale, z, gate);
+  else if (fp32_precond(c)) enqueue_precond_t<float, double>(c, v, vscale, z, gate, c->x32.tab, c->y32.tab);
   else enqueue_precond_t<double, double>(c, v, vscale, z, gate, c->x64.tab, c->y64.tab);
 }
 
@@ -438,7 +461,9 @@ void enqueue_cycle_t(rsfde_ctx* c) {
     const double* vj = c->V + (size_t)j * N;
     Tz* zj = Z + (size_t)j * N;
     if (c->opts.use_precond) {
-      if (fp32_precond(c))
+      if (bf16_precond_on(c))
+        enqueue_precond_bf16<Tz>(c, vj, &c->st->s[j], zj, gi);
+      else if (fp32_precond(c))
         enqueue_precond_t<float, Tz>(c, vj, &c->st->s[j], zj, gi, c->x32.tab, c->y32.tab);
       else
         enqueue_precond_t<double, Tz>(c, vj, &c->st->s[j], zj, gi, c->x64.tab, c->y64.tab);
@@ -570,8 +595,10 @@ int build_cycle_graph(rsfde_ctx* c) {
 
 // Solve M x = b with b = c->b, x = c->x (initial guess), st->bnorm set.
 int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
+  int rc = ensure_bf16(c);
+  if (rc) return rc;
   enqueue_residual(c, &c->st->run_cycle);
-  int rc = check_launch(c);
+  rc = check_launch(c);
   if (rc) return rc;
   if (c->opts.use_graph && !c->prof_on) {
     if (c->graph_key != graph_key(c) && (rc = build_cycle_graph(c))) return rc;
@@ -600,6 +627,7 @@ int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
   if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(e);
   const SolverState& h = *c->st_host;
   if (c->opts.use_graph && !c->prof_on) c->launches += (int64_t)h.body_runs * c->launches_per_body;
+  if (c->bf16 && bf16_precond_on(c) && (rc = bf16_plan_error(c->bf16, c->stream))) return rc;
   if (stats) {
     stats->iters = h.iters;
     stats->restarts = h.cycles > 0 ? h.cycles - 1 : 0;
@@ -645,7 +673,7 @@ const char* rsfde_strerror(int code) {
 
 static int valid_opts(const rsfde_opts* o) {
   if (o->restart < 1 || o->restart > kMaxRestart || o->max_iter < 1 || !(o->tol > 0.0)) return 0;
-  if (o->precond_prec != RSFDE_FP64 && o->precond_prec != RSFDE_FP32) return 0;
+  if (o->precond_prec != RSFDE_FP64 && o->precond_prec != RSFDE_FP32 && o->precond_prec != RSFDE_BF16X3) return 0;
   if (o->arnoldi != RSFDE_CGS && o->arnoldi != RSFDE_CGS2) return 0;
   if (o->matvec_prec != RSFDE_FP64 && o->matvec_prec != RSFDE_DF32) return 0;
   if (o->variant != RSFDE_FGMRES_RIGHT && o->variant != RSFDE_GMRES_LEFT) return 0;
@@ -712,6 +740,7 @@ int rsfde_setup(rsfde_ctx** out, const rsfde_grid* g, const uint8_t* mask, doubl
     launch_mask_to_phi(mask, c->phi, N, c->stream);
   }
   int rc = build_tables(c);
+  if (rc == RSFDE_OK) rc = ensure_bf16(c);
   if (rc == RSFDE_OK) rc = check_launch(c);
   if (rc == RSFDE_OK) rc = cuda_fail(cudaStreamSynchronize(c->stream));
   if (rc != RSFDE_OK) {
@@ -734,7 +763,7 @@ int rsfde_set_opts(rsfde_ctx* c, const rsfde_opts* o) {
   if (!c || !o || !valid_opts(o) || o->restart > c->m_alloc) return RSFDE_EINVAL;
   c->opts = *o;
   c->stream = static_cast<cudaStream_t>(o->stream);
-  return RSFDE_OK;
+  return ensure_bf16(c);
 }
 
 int rsfde_set_stream(rsfde_ctx* c, void* stream) {
@@ -850,6 +879,13 @@ int rsfde_apply_M(rsfde_ctx* c, const double* z, double* w) {
 
 int rsfde_apply_precond(rsfde_ctx* c, const double* v, double* z) {
   if (!c || !v || !z) return RSFDE_EINVAL;
+  if (bf16_precond_on(c)) {
+    int rc = ensure_bf16(c);
+    if (rc) return rc;
+    enqueue_precond_bf16<double>(c, v, nullptr, z, nullptr);
+    if ((rc = check_launch(c))) return rc;
+    return bf16_plan_error(c->bf16, c->stream);
+  }
   if (fp32_precond(c)) enqueue_precond_t<float, double>(c, v, nullptr, z, nullptr, c->x32.tab, c->y32.tab);
   else enqueue_precond_t<double, double>(c, v, nullptr, z, nullptr, c->x64.tab, c->y64.tab);
   return check_launch(c);
@@ -910,9 +946,9 @@ int rsfde_profile_read(rsfde_ctx* c, double* ms, int64_t* launches) {
 }
 
 const char* rsfde_kernel_class_name(int k) {
-  static const char* names[RSFDE_K_COUNT] = {"toeplitz_rows", "toeplitz_cols", "dst_rows",
-                                             "precond_cols",  "precond_rows",  "multidot",
-                                             "update",        "xupdate",       "other"};
+  static const char* names[RSFDE_K_COUNT] = {"toeplitz_rows", "toeplitz_cols", "dst_rows", "precond_cols",
+                                             "precond_rows",  "multidot",      "update",   "xupdate",
+                                             "other",         "dst_gemm"};
   return (k >= 0 && k < RSFDE_K_COUNT) ? names[k] : "unknown";
 }
 

@@ -1,0 +1,248 @@
+// dst_gemm.cu -- the preconditioner of Eq. 4.6 with every sine transform done
+// as a split-BF16 tensor-core GEMM (dst_gemm.cuh).
+//
+// P-hat^-1 v = (1-Phi) S W1 + Phi S W2 with S = S_{n2} (x) S_{n1}, W = S v,
+// W1 = W / (1 - Lx - Ly), W2 = W / (1 + dt/eta - Lx - Ly).  As matrices
+// (rows y, columns x): S v = S_y V S_x.  The passes, each "A times S" with the
+// output stored transposed so the next pass again multiplies rows by S:
+//   0. split:    A0 = split(scale * V)                      (n2 x n1)
+//   1. GEMM:     T1t = (A0 S_x)^T                            (n1 x n2)
+//   2. GEMM:     W^T = T1t S_y, epilogue: both tau divides, stored transposed
+//                as the stacked [W1; W2]                     (2 n2 x n1)
+//   3. GEMM:     Yt = ([W1; W2] S_x)^T, channels side by side (n1 x 2 ld2)
+//   4. GEMM x2:  (S_y W_c S_x)^T = Yt_c S_y; the epilogue writes z where the
+//                mask selects channel c.
+// All BF16 matrices have a leading dimension padded to a multiple of 64 and
+// are zeroed once, so tile reads past the valid extent see zeros.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "dst_gemm.cuh"
+#include "internal.h"
+
+namespace rsfde {
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+int pad64(int n) { return (n + 63) / 64 * 64; }
+
+struct Bf16Mat {
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* lo = nullptr;
+  int rows = 0, cols = 0, ld = 0;
+  CUtensorMap map_hi, map_lo;
+};
+
+bool make_map(CUtensorMap* m, void* p, int rows, int cols, int ld) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t stride[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kGemmBK, (cuuint32_t)kGemmBM};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p, dim, stride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// A = scale * V split into a BF16 pair (rows y, columns x, leading dim ld).
+__global__ void __launch_bounds__(kBlock) split_kernel(const double* __restrict__ v, const double* scale,
+                                                       __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                                       int n1, int n2, int ld, const int* gate) {
+  if (gate && *(volatile const int*)gate == 0) return;
+  const double sc = scale ? *scale : 1.0;
+  const size_t N = (size_t)n1 * n2;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    const size_t j = p / n1, i = p - j * n1;
+    const float x = (float)(sc * v[p]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[j * ld + i] = h;
+    lo[j * ld + i] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+}  // namespace
+
+struct Bf16Plan {
+  int n1 = 0, n2 = 0, ld1 = 0, ld2 = 0;
+  Bf16Mat Sx, Sy, A0, T1t, Wst, Yt;
+  const float* lamx = nullptr;
+  const float* lamy = nullptr;
+  int* err = nullptr;
+  void* mem = nullptr;
+};
+
+// S_n as a split BF16 pair: [S_n]_{ij} = sqrt(2/(n+1)) sin(pi i j/(n+1)), FP64 on the host.
+static void host_sine_matrix(int n, int ld, std::vector<__nv_bfloat16>& hi, std::vector<__nv_bfloat16>& lo) {
+  hi.assign((size_t)n * ld, __float2bfloat16(0.0f));
+  lo.assign((size_t)n * ld, __float2bfloat16(0.0f));
+  const long per = 2L * (n + 1);
+  const double sc = std::sqrt(2.0 / (n + 1));
+  std::vector<double> sn(per);
+  for (long m = 0; m < per; ++m) sn[m] = sc * std::sin(M_PI * (double)m / (double)(n + 1));
+  for (int i = 1; i <= n; ++i)
+    for (int j = 1; j <= n; ++j) {
+      const float x = (float)sn[((long)i * j) % per];
+      const __nv_bfloat16 h = __float2bfloat16(x);
+      hi[(size_t)(i - 1) * ld + (j - 1)] = h;
+      lo[(size_t)(i - 1) * ld + (j - 1)] = __float2bfloat16(x - __bfloat162float(h));
+    }
+}
+
+int bf16_plan_create(Bf16Plan** out, int n1, int n2, const float* lamx, const float* lamy, cudaStream_t s) {
+  *out = nullptr;
+  if (!encode_fn()) return RSFDE_ECUDA;
+  Bf16Plan* p = new Bf16Plan();
+  p->n1 = n1;
+  p->n2 = n2;
+  p->ld1 = pad64(n1);
+  p->ld2 = pad64(n2);
+  p->lamx = lamx;
+  p->lamy = lamy;
+  struct Spec {
+    Bf16Mat* m;
+    int rows, cols, ld;
+  } specs[] = {{&p->Sx, n1, n1, p->ld1},     {&p->Sy, n2, n2, p->ld2},      {&p->A0, n2, n1, p->ld1},
+               {&p->T1t, n1, n2, p->ld2},    {&p->Wst, 2 * n2, n1, p->ld1}, {&p->Yt, n1, 2 * p->ld2, 2 * p->ld2}};
+  size_t total = 256;
+  for (auto& sp : specs) total += 2 * (size_t)sp.rows * sp.ld * sizeof(__nv_bfloat16) + 256;
+  cudaError_t e = cudaMalloc(&p->mem, total);
+  if (e != cudaSuccess) {
+    delete p;
+    return e == cudaErrorMemoryAllocation ? RSFDE_ENOMEM : RSFDE_ECUDA;
+  }
+  cudaMemsetAsync(p->mem, 0, total, s);
+  uint8_t* base = static_cast<uint8_t*>(p->mem);
+  size_t off = 0;
+  p->err = reinterpret_cast<int*>(base);
+  off += 256;
+  for (auto& sp : specs) {
+    const size_t bytes = (size_t)sp.rows * sp.ld * sizeof(__nv_bfloat16);
+    sp.m->rows = sp.rows;
+    sp.m->cols = sp.cols;
+    sp.m->ld = sp.ld;
+    sp.m->hi = reinterpret_cast<__nv_bfloat16*>(base + off);
+    off += (bytes + 255) / 256 * 256;
+    sp.m->lo = reinterpret_cast<__nv_bfloat16*>(base + off);
+    off += (bytes + 255) / 256 * 256;
+    if (!make_map(&sp.m->map_hi, sp.m->hi, sp.rows, sp.cols, sp.ld) ||
+        !make_map(&sp.m->map_lo, sp.m->lo, sp.rows, sp.cols, sp.ld)) {
+      cudaFree(p->mem);
+      delete p;
+      return RSFDE_ECUDA;
+    }
+  }
+  std::vector<__nv_bfloat16> hi, lo;
+  host_sine_matrix(n1, p->ld1, hi, lo);
+  cudaMemcpyAsync(p->Sx.hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(p->Sx.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
+  cudaStreamSynchronize(s);
+  host_sine_matrix(n2, p->ld2, hi, lo);
+  cudaMemcpyAsync(p->Sy.hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(p->Sy.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(p->mem);
+    delete p;
+    return RSFDE_ECUDA;
+  }
+  *out = p;
+  return RSFDE_OK;
+}
+
+void bf16_plan_destroy(Bf16Plan* p) {
+  if (!p) return;
+  if (p->mem) cudaFree(p->mem);
+  delete p;
+}
+
+int bf16_plan_error(Bf16Plan* p, cudaStream_t s) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RSFDE_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RSFDE_ECUDA;
+  return h ? RSFDE_ETIMEOUT : RSFDE_OK;
+}
+
+template <int EPI>
+static void launch_gemm(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
+                        const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
+  auto k = dst_gemm_kernel<EPI>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+  dim3 grid((N + kGemmBN - 1) / kGemmBN, (M + kGemmBM - 1) / kGemmBM, channels);
+  k<<<grid, 128, kGemmSmem, s>>>(A.map_hi, A.map_lo, B.map_hi, B.map_lo, K, ep, err, gate);
+}
+
+template <typename Tz>
+int bf16_precond(Bf16Plan* p, const double* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
+                 const int* gate, cudaStream_t s) {
+  const int n1 = p->n1, n2 = p->n2;
+  const size_t N = (size_t)n1 * n2;
+  split_kernel<<<vec_grid(N), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, gate);
+  GemmEpiParams ep{};
+  // 1. T1t = (A0 S_x)^T
+  ep.M = n2;
+  ep.N = n1;
+  ep.out_hi = p->T1t.hi;
+  ep.out_lo = p->T1t.lo;
+  ep.ldo = p->ld2;
+  ep.row_b = 1 << 30;
+  launch_gemm<EPI_SPLIT_T>(p->A0, p->Sx, n2, n1, n1, 1, ep, p->err, gate, s);
+  // 2. W^T = T1t S_y; both tau divides (Eq. 4.6), stacked [W1; W2]
+  ep = GemmEpiParams{};
+  ep.M = n1;
+  ep.N = n2;
+  ep.out_hi = p->Wst.hi;
+  ep.out_lo = p->Wst.lo;
+  ep.ldo = p->ld1;
+  ep.lam_m = p->lamx;
+  ep.lam_n = p->lamy;
+  ep.pen = (float)pen;
+  ep.chb_rows = n2;
+  launch_gemm<EPI_DIVIDE_T>(p->T1t, p->Sy, n1, n2, n2, 1, ep, p->err, gate, s);
+  // 3. Yt = ([W1; W2] S_x)^T, the channels side by side (column offset ld2)
+  ep = GemmEpiParams{};
+  ep.M = 2 * n2;
+  ep.N = n1;
+  ep.out_hi = p->Yt.hi;
+  ep.out_lo = p->Yt.lo;
+  ep.ldo = 2 * p->ld2;
+  ep.row_b = n2;
+  ep.col_b = p->ld2;
+  launch_gemm<EPI_SPLIT_T>(p->Wst, p->Sx, 2 * n2, n1, n1, 1, ep, p->err, gate, s);
+  // 4. z = (1-Phi) S_y W1 S_x + Phi S_y W2 S_x (channel = blockIdx.z)
+  ep = GemmEpiParams{};
+  ep.M = n1;
+  ep.N = n2;
+  ep.z = z;
+  ep.z_double = sizeof(Tz) == 8;
+  ep.phi = phi;
+  ep.ldz = n1;
+  ep.a_koff = p->ld2;
+  launch_gemm<EPI_COMBINE_T>(p->Yt, p->Sy, n1, n2, n2, 2, ep, p->err, gate, s);
+  return cudaGetLastError() == cudaSuccess ? RSFDE_OK : RSFDE_ECUDA;
+}
+
+template int bf16_precond<float>(Bf16Plan*, const double*, const double*, float*, const uint8_t*, double,
+                                 const int*, cudaStream_t);
+template int bf16_precond<double>(Bf16Plan*, const double*, const double*, double*, const uint8_t*, double,
+                                  const int*, cudaStream_t);
+
+}  // namespace rsfde

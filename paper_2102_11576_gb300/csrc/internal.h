@@ -119,6 +119,15 @@ template <typename T, typename Tz>
 void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, int n1, int n2,
                          const AxisTables<T>& ax, const int* gate, cudaStream_t s);
 
+// ---- split-BF16 tensor-core preconditioner (dst_gemm.cu) --------------------
+struct Bf16Plan;
+int bf16_plan_create(Bf16Plan** out, int n1, int n2, const float* lamx, const float* lamy, cudaStream_t s);
+void bf16_plan_destroy(Bf16Plan* p);
+int bf16_plan_error(Bf16Plan* p, cudaStream_t s);
+template <typename Tz>
+int bf16_precond(Bf16Plan* p, const double* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
+                 const int* gate, cudaStream_t s);
+
 // ---- launchers (krylov.cu) -------------------------------------------------
 int vec_grid(size_t N);
 void launch_init_state(SolverState* st, int m, int max_iter, double tol, cudaStream_t s);

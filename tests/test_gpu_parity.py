@@ -5,7 +5,9 @@ output's max norm (the FFT evaluation differs from the oracle's dense sums by
 O(eps log L) of the operand norm); solves reach a true relative residual
 <= 1e-10 and the solution differs from the oracle's by <= 1e-9 in relative
 max norm.  FP32 preconditioner: the apply agrees to 1e-5 relative (FP32 FFTs),
-while the solve still reaches the FP64 tolerance.  Double-FP32 operator
+while the solve still reaches the FP64 tolerance.  Split-BF16 tensor-core
+preconditioner (about 16 significant bits per operand, FP32 accumulation over
+up to n terms per pass, four passes): 2e-4 relative.  Double-FP32 operator
 (~48-bit arithmetic): 2e-12 of the Toeplitz sums' scale; solves with it still
 reach the FP64 tolerances because the true residual is FP64.
 """
@@ -88,7 +90,7 @@ def test_dst2(n1, n2):
 
 
 @pytest.mark.parametrize("n1,n2", SIZES)
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5), ("bf16x3", 2e-4)])
 def test_apply_precond(n1, n2, prec, tol):
     w = workloads.random_problem(4, n1, n2)
     orc, gpu = pair(w, precond=prec)
@@ -99,7 +101,7 @@ def test_apply_precond(n1, n2, prec, tol):
 
 
 @pytest.mark.parametrize("n1,n2", [(1, 1), (5, 7), (33, 20), (64, 64), (65, 127)])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
 @pytest.mark.parametrize("arnoldi", ["cgs", "cgs2"])
 @pytest.mark.parametrize("matvec", ["fp64", "df32"])
 def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec):
@@ -144,7 +146,7 @@ def test_unpreconditioned_and_dense_lu():
     assert st["converged"] and rel(host(x), x_lu) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32")])
+@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32"), ("bf16x3", "df32")])
 def test_march_disk64_matches_oracle(prec, matvec):
     w = workloads.make("disk64")
     orc, gpu = pair(w, tol=1e-12, restart=w["restart"], precond=prec, matvec=matvec)
@@ -224,7 +226,7 @@ def test_full_size_polygon2048_sampled():
     rng = np.random.default_rng(0)
     idx = rng.choice(w["n1"] * w["n2"], size=256, replace=False)
     u0 = w["u0"]
-    for prec, matvec in (("fp32", "df32"), ("fp32", "fp64"), ("fp64", "fp64")):
+    for prec, matvec in (("fp32", "df32"), ("bf16x3", "df32"), ("fp32", "fp64"), ("fp64", "fp64")):
         gpu = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"],
                      w["ky"], w["dt"], w["eta"], restart=w["restart"], precond=prec, matvec=matvec)
         z = rng.standard_normal((w["n2"], w["n1"]))
