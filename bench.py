@@ -485,6 +485,42 @@ def run_op(args):
                       "ms_per_call": e0.elapsed_time(e1) / args.reps}), flush=True)
 
 
+def run_batched(args):
+    """Times the batched workload: 256 independent instances (grid side
+    uniform in 64..512, random alpha, k, ellipse or polygon domain), each
+    advanced by one CUDA graph launch per time step, FP32 preconditioner,
+    double-FP32 Arnoldi operator, FP64 residual to 1e-10."""
+    import torch
+    from paper_2102_11576_gb300 import Batch, workloads
+    probs = workloads.make_batch(seed=0, count=args.batch_count)
+    t0 = time.perf_counter()
+    b = Batch(probs, precond=args.batch_precond, matvec="df32")
+    for i, p in enumerate(probs):
+        b.set(i, p["u0"])
+    setup_s = time.perf_counter() - t0
+    b.run(args.warmup)  # builds the graphs, first steps
+    torch.cuda.synchronize()
+    l0 = b.kernel_launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st = b.run(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    unknowns = sum(p["n1"] * p["n2"] for p in probs)
+    iters = [s["iters"] for s in st]
+    print(json.dumps({"workload": f"batched: {len(probs)} instances, n in 64..512 (sum N = {unknowns}), "
+                                  "random alpha/k/domain, FGMRES(20), tol 1e-10",
+                      "form": f"{args.batch_precond} preconditioner, double-FP32 Arnoldi operator",
+                      "steps": args.steps, "ms_per_batch_step": ms / args.steps,
+                      "instance_steps_per_s": len(probs) * args.steps / (ms / 1e3),
+                      "unknown_steps_per_s": unknowns * args.steps / (ms / 1e3),
+                      "iters_last_step": {"mean": float(np.mean(iters)), "max": int(max(iters))},
+                      "all_converged": all(s["converged"] for s in st),
+                      "max_rel_res": max(s["rel_res"] for s in st),
+                      "gpu_launches": b.kernel_launches - l0, "setup_s": setup_s}), flush=True)
+
+
 def run_adjoint(args):
     """Times one differentiable march of the differentiation workload
     (disk1024: 1024^2, unit disk, alpha = 1.5, 200 steps, sqrt-m
@@ -526,6 +562,10 @@ def run_adjoint(args):
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--batched", action="store_true",
+                    help="time the batched workload (256 instances of uneven size)")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-precond", default="fp32")
     ap.add_argument("--adjoint", action="store_true",
                     help="time one differentiable march of the 1024^2 differentiation workload")
     ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "precond_fp32", "precond_fp64", "dst2"],
@@ -557,6 +597,9 @@ def main():
         return
     if args.adjoint:
         run_adjoint(args)
+        return
+    if args.batched:
+        run_batched(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

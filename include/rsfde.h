@@ -165,6 +165,30 @@ int rsfde_adjoint(rsfde_ctx* ctx, const double* lam, double* mu, rsfde_stats* st
 int rsfde_adjoint_step(rsfde_ctx* ctx, const double* u_prev, const double* u_k, const double* lam, double* mu,
                        double* lam_prev, double* grad_src, double* grad_k, rsfde_stats* stats);
 
+/* ---- batched instances ------------------------------------------------------ */
+/* Many independent problems (each its own grid, mask, alphas, k, dt, eta)
+ * advanced together: every time step of every instance -- right side,
+ * initial residual, the device-side loop over FGMRES cycles, the state
+ * rotation -- is one branch of a single CUDA graph, so one graph launch
+ * advances the whole batch by one step and the GPU overlaps the instances'
+ * kernels.  The paper solves one instance; this is the batched deployment of
+ * the same step.  Arguments are arrays of `count` entries (grids, masks:
+ * device pointers as in rsfde_setup); opts (may be NULL) apply to all. */
+typedef struct rsfde_batch rsfde_batch;
+int rsfde_batch_create(rsfde_batch** out, int32_t count, const rsfde_grid* grids, const uint8_t* const* masks,
+                       const double* alpha1, const double* alpha2, const double* kx, const double* ky,
+                       const double* dt, const double* eta, const rsfde_opts* opts);
+/* Sets instance i's u^0 (device, N_i doubles) and source (device or NULL); restarts its march. */
+int rsfde_batch_set(rsfde_batch* b, int32_t i, const double* u0, const double* src);
+/* Advances every instance by `steps` implicit steps (f = u - u^3 + src, Eq. 2.17).
+ * stats: HOST array of `count` (statistics of each instance's last step) or
+ * NULL.  Returns the first non-OK instance status, else RSFDE_OK.  Synchronises. */
+int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats);
+/* Copies instance i's current u^k to the device array u_out (N_i doubles). */
+int rsfde_batch_get(rsfde_batch* b, int32_t i, double* u_out);
+int64_t rsfde_batch_kernel_launches(rsfde_batch* b);
+void rsfde_batch_destroy(rsfde_batch* b);
+
 /* ---- operator-level entry points (each one step of the hot path) --------- */
 /* Eq. 2.14-2.17: w = M z in the context's operator precision (matvec_prec).
  * z, w device N doubles (distinct). */

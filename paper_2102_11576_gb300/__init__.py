@@ -16,7 +16,7 @@ import os
 
 import numpy as np
 
-__all__ = ["Solver", "RsfdeError", "load_library", "LIB_PATH", "FP64", "FP32", "DF32"]
+__all__ = ["Solver", "Batch", "RsfdeError", "load_library", "LIB_PATH", "FP64", "FP32", "DF32"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librsfde.so")
@@ -99,6 +99,16 @@ def load_library(path=LIB_PATH):
     lib.rsfde_destroy.argtypes = [vp]
     lib.rsfde_strerror.argtypes = [i32]
     lib.rsfde_strerror.restype = ctypes.c_char_p
+    lib.rsfde_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(_Grid), ctypes.POINTER(vp),
+                                       dp, dp, dp, dp, dp, dp, ctypes.POINTER(_Opts)]
+    lib.rsfde_batch_set.argtypes = [vp, i32, dp, dp]
+    lib.rsfde_batch_run.argtypes = [vp, i32, ctypes.POINTER(_Stats)]
+    lib.rsfde_batch_get.argtypes = [vp, i32, dp]
+    lib.rsfde_batch_kernel_launches.argtypes = [vp]
+    lib.rsfde_batch_kernel_launches.restype = ctypes.c_int64
+    lib.rsfde_batch_destroy.argtypes = [vp]
+    for name in ("rsfde_batch_create", "rsfde_batch_set", "rsfde_batch_run", "rsfde_batch_get"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("rsfde_setup", "rsfde_set_params", "rsfde_set_opts", "rsfde_set_stream",
                  "rsfde_solve", "rsfde_step", "rsfde_step_host", "rsfde_adjoint", "rsfde_apply_M",
                  "rsfde_apply_precond", "rsfde_dst2", "rsfde_rhs", "rsfde_get_tables",
@@ -310,3 +320,78 @@ class Solver:
     @property
     def kernel_launches(self):
         return int(self._lib.rsfde_kernel_launches(self._h))
+
+
+class Batch:
+    """Many independent problems advanced together (rsfde_batch_*): each time
+    step of every instance is one branch of a single CUDA graph.
+
+    problems: list of dicts with n1, n2, box, in_omega, alpha1, alpha2, kx,
+    ky, dt, eta; solver options as for Solver apply to all instances."""
+
+    def __init__(self, problems, restart=20, max_iter=10000, tol=1e-10, precond="fp32", matvec="df32",
+                 arnoldi="cgs", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
+        self._torch = torch
+        lib = load_library()
+        self._lib = lib
+        self.count = len(problems)
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.shapes = [(int(p["n2"]), int(p["n1"])) for p in problems]
+        self._masks = [torch.as_tensor(np.ascontiguousarray(p["in_omega"], dtype=np.uint8)).to(self.dev)
+                       for p in problems]
+        grids = (_Grid * self.count)(*[_Grid(int(p["n1"]), int(p["n2"]), *map(float, p["box"]))
+                                       for p in problems])
+        masks = (ctypes.c_void_p * self.count)(*[m.data_ptr() for m in self._masks])
+        arr = lambda key: np.ascontiguousarray([float(p[key]) for p in problems], dtype=np.float64)
+        self._params = {k: arr(k) for k in ("alpha1", "alpha2", "kx", "ky", "dt", "eta")}
+        o = _Opts()
+        lib.rsfde_opts_default(ctypes.byref(o))
+        o.restart, o.max_iter, o.tol = int(restart), int(max_iter), float(tol)
+        o.precond_prec = _PRECONDS[precond]
+        o.matvec_prec = {"fp64": FP64, "df32": DF32}[matvec]
+        o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
+        o.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        h = ctypes.c_void_p()
+        pp = lambda a: ctypes.c_void_p(a.ctypes.data)
+        _check(lib.rsfde_batch_create(ctypes.byref(h), self.count, grids, masks,
+                                      *[pp(self._params[k]) for k in ("alpha1", "alpha2", "kx", "ky",
+                                                                      "dt", "eta")],
+                                      ctypes.byref(o)), "batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rsfde_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, i, u0, src=None):
+        u0 = self._torch.as_tensor(u0, dtype=self._torch.float64).to(self.dev).contiguous()
+        s = None if src is None else self._torch.as_tensor(src, dtype=self._torch.float64).to(
+            self.dev).contiguous()
+        _check(self._lib.rsfde_batch_set(self._h, i, _ptr(u0), _ptr(s)), "batch_set")
+
+    def run(self, steps):
+        """Advances every instance by `steps` steps; per-instance stats of the last step."""
+        st = (_Stats * self.count)()
+        rc = self._lib.rsfde_batch_run(self._h, int(steps), st)
+        _check(rc, "batch_run")
+        return [x.as_dict() for x in st]
+
+    def get(self, i):
+        out = self._torch.empty(self.shapes[i], dtype=self._torch.float64, device=self.dev)
+        _check(self._lib.rsfde_batch_get(self._h, i, _ptr(out)), "batch_get")
+        return out
+
+    @property
+    def kernel_launches(self):
+        return int(self._lib.rsfde_batch_kernel_launches(self._h))

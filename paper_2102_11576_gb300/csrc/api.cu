@@ -639,6 +639,138 @@ int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
   return h.status;
 }
 
+// ---- batched instances: one CUDA graph advances every instance by a step ---
+
+// Captures fn(c) (work enqueued on c->stream) into a child-graph node of g.
+template <typename Fn>
+cudaError_t add_captured(rsfde_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, Fn fn,
+                         cudaGraphNode_t* out) {
+  cudaError_t e;
+  if (!c->cap_stream && (e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return e;
+  cudaGraph_t child;
+  if ((e = cudaGraphCreate(&child, 0)) != cudaSuccess) return e;
+  cudaStream_t user = c->stream;
+  const bool prof = c->prof_on;
+  c->stream = c->cap_stream;
+  c->prof_on = false;
+  e = cudaStreamBeginCaptureToGraph(c->stream, child, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    fn(c);
+    e = cudaStreamEndCapture(c->stream, &child);
+  }
+  c->stream = user;
+  c->prof_on = prof;
+  if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(out, g, deps, ndeps, child);
+  cudaGraphDestroy(child);
+  return e;
+}
+
+// The instance's device-side loop over FGMRES cycles (a WHILE node) after deps.
+cudaError_t add_cycle_loop(rsfde_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                           cudaGraphNode_t* out) {
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if ((e = cudaGraphAddNode(out, g, deps, nullptr, ndeps, &np)) != cudaSuccess) return e;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t user = c->stream;
+  const bool prof = c->prof_on;
+  const int64_t l0 = c->launches;
+  c->stream = c->cap_stream;
+  c->prof_on = false;
+  e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    enqueue_cycle(c);
+    launch_loop_cond(h, c->st, c->stream);
+    e = cudaStreamEndCapture(c->stream, &body);
+  }
+  c->launches_per_body = c->launches - l0 + 1;
+  c->launches = l0;
+  c->stream = user;
+  c->prof_on = prof;
+  return e;
+}
+
+}  // namespace
+
+struct rsfde_batch {
+  int count = 0;
+  std::vector<rsfde_ctx*> ctx;
+  std::vector<double*> ring;  // per instance: u^{k-1}, u^{k-2}, source (3 N doubles)
+  std::vector<int> has_src;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};  // [0]: first step (no u^{k-2}), [1]: later steps
+  int64_t launches_pro[2] = {0, 0}, launches_epi = 0;
+  int steps_done = 0;
+  int64_t launches = 0;
+};
+
+namespace {
+
+void free_batch(rsfde_batch* b) {
+  if (!b) return;
+  for (auto& x : b->exec)
+    if (x) cudaGraphExecDestroy(x);
+  for (double* r : b->ring)
+    if (r) cudaFree(r);
+  for (rsfde_ctx* c : b->ctx) free_ctx(c);
+  delete b;
+}
+
+// Builds the graph of one time step of every instance: per instance the
+// chain [right side, initial residual] -> WHILE(FGMRES cycle) -> [finalise,
+// u^{k-2} <- u^{k-1}, u^{k-1} <- u^k]; the instances' chains are independent.
+int build_batch_graph(rsfde_batch* b, int later) {
+  cudaGraph_t g;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+    rsfde_ctx* c = b->ctx[i];
+    double* u_prev = b->ring[i];
+    double* u_pp = u_prev + c->N;
+    double* src = b->has_src[i] ? u_prev + 2 * c->N : nullptr;
+    cudaGraphNode_t pro, loop, epi;
+    const int64_t l0 = c->launches;
+    e = add_captured(c, g, nullptr, 0,
+                     [&](rsfde_ctx* cc) {
+                       enqueue_init(cc);
+                       enqueue_rhs(cc, u_prev, later ? u_pp : nullptr, src, cc->b, cc->x);
+                       if (left_variant(cc)) enqueue_bnorm(cc);
+                       enqueue_residual(cc, &cc->st->run_cycle);
+                     },
+                     &pro);
+    if (i == 0) b->launches_pro[later] = c->launches - l0;
+    if (e == cudaSuccess) e = add_cycle_loop(c, g, &pro, 1, &loop);
+    const int64_t l1 = c->launches;
+    if (e == cudaSuccess)
+      e = add_captured(c, g, &loop, 1,
+                       [&](rsfde_ctx* cc) {
+                         ProfScope ps(cc, RSFDE_K_OTHER);
+                         launch_finalize(cc->x, cc->N, cc->st, cc->stream);
+                         cudaMemcpyAsync(u_pp, u_prev, cc->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         cc->stream);
+                         cudaMemcpyAsync(u_prev, cc->x, cc->N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         cc->stream);
+                       },
+                       &epi);
+    if (i == 0) b->launches_epi = c->launches - l1;
+    c->launches = l0;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[later], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e);
+  }
+  return RSFDE_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -956,6 +1088,128 @@ void rsfde_destroy(rsfde_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   free_ctx(c);
+}
+
+// ---- batched instances -------------------------------------------------------
+int rsfde_batch_create(rsfde_batch** out, int32_t count, const rsfde_grid* grids, const uint8_t* const* masks,
+                       const double* alpha1, const double* alpha2, const double* kx, const double* ky,
+                       const double* dt, const double* eta, const rsfde_opts* opts) {
+  if (!out) return RSFDE_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !grids || !masks || !alpha1 || !alpha2 || !kx || !ky || !dt || !eta) return RSFDE_EINVAL;
+  rsfde_batch* b = new (std::nothrow) rsfde_batch();
+  if (!b) return RSFDE_ENOMEM;
+  b->count = count;
+  b->stream = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+  for (int i = 0; i < count; ++i) {
+    rsfde_ctx* c = nullptr;
+    int rc = rsfde_setup(&c, &grids[i], masks[i], alpha1[i], alpha2[i], kx[i], ky[i], dt[i], eta[i], opts);
+    if (rc) {
+      free_batch(b);
+      return rc;
+    }
+    b->ctx.push_back(c);
+    double* r = nullptr;
+    cudaError_t e = cudaMalloc(&r, 3 * c->N * sizeof(double));
+    if (e != cudaSuccess) {
+      free_batch(b);
+      return cuda_fail(e);
+    }
+    cudaMemsetAsync(r, 0, 3 * c->N * sizeof(double), b->stream);
+    b->ring.push_back(r);
+    b->has_src.push_back(0);
+  }
+  *out = b;
+  return cuda_fail(cudaStreamSynchronize(b->stream));
+}
+
+int rsfde_batch_set(rsfde_batch* b, int32_t i, const double* u0, const double* src) {
+  if (!b || i < 0 || i >= b->count || !u0) return RSFDE_EINVAL;
+  rsfde_ctx* c = b->ctx[i];
+  const size_t bytes = c->N * sizeof(double);
+  cudaMemcpyAsync(b->ring[i], u0, bytes, cudaMemcpyDeviceToDevice, b->stream);
+  if (src) cudaMemcpyAsync(b->ring[i] + 2 * c->N, src, bytes, cudaMemcpyDeviceToDevice, b->stream);
+  if ((src != nullptr) != (b->has_src[i] != 0)) {  // the graphs read the source or not
+    b->has_src[i] = src != nullptr;
+    for (auto& x : b->exec)
+      if (x) {
+        cudaGraphExecDestroy(x);
+        x = nullptr;
+      }
+  }
+  b->steps_done = 0;
+  return cuda_fail(cudaStreamSynchronize(b->stream));
+}
+
+int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats) {
+  if (!b || steps < 0) return RSFDE_EINVAL;
+  for (int k = 0; k < steps; ++k) {
+    const int later = b->steps_done > 0;
+    if (!b->exec[later]) {
+      int rc = build_batch_graph(b, later);
+      if (rc) return rc;
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec[later], b->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    b->steps_done += 1;
+    b->launches += (int64_t)b->count * (b->launches_pro[later] + b->launches_epi);
+  }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const size_t head = offsetof(SolverState, counter);
+  int worst = RSFDE_OK;
+  for (int i = 0; i < b->count; ++i) {
+    rsfde_ctx* c = b->ctx[i];
+    e = cudaMemcpy(c->st_host, c->st, head, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const SolverState& h = *c->st_host;
+    if (stats) {
+      stats[i].iters = h.iters;
+      stats[i].restarts = h.cycles > 0 ? h.cycles - 1 : 0;
+      stats[i].converged = h.converged;
+      stats[i].status = h.status;
+      stats[i].rel_res = 0.0;
+      stats[i].bnorm = 0.0;
+    }
+    if (h.status != RSFDE_OK && worst == RSFDE_OK) worst = h.status;
+  }
+  if (stats) {  // the residual fields follow the counter in the state
+    for (int i = 0; i < b->count; ++i) {
+      rsfde_ctx* c = b->ctx[i];
+      double rr[4];
+      e = cudaMemcpy(rr, &c->st->tol, sizeof(rr), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e);
+      stats[i].bnorm = rr[1];
+      stats[i].rel_res = rr[3];
+    }
+  }
+  return worst;
+}
+
+int rsfde_batch_get(rsfde_batch* b, int32_t i, double* u_out) {
+  if (!b || i < 0 || i >= b->count || !u_out) return RSFDE_EINVAL;
+  rsfde_ctx* c = b->ctx[i];
+  cudaError_t e = cudaMemcpyAsync(u_out, b->ring[i], c->N * sizeof(double), cudaMemcpyDeviceToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  return cuda_fail(e);
+}
+
+int64_t rsfde_batch_kernel_launches(rsfde_batch* b) {
+  if (!b) return 0;
+  // prologue and epilogue launches per instance-step, plus every replayed cycle
+  int64_t n = b->launches;
+  for (rsfde_ctx* c : b->ctx) {
+    long long runs = 0;
+    if (cudaMemcpy(&runs, &c->st->total_body_runs, sizeof(runs), cudaMemcpyDeviceToHost) == cudaSuccess)
+      n += (int64_t)runs * c->launches_per_body;
+  }
+  return n;
+}
+
+void rsfde_batch_destroy(rsfde_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
 }
 
 }  // extern "C"

@@ -20,7 +20,8 @@ struct SolverState {
   int jlast;      // Arnoldi columns built in the current cycle
   int iters, cycles, max_iter, m;
   int zero_solution;  // b == 0: x must be zeroed
-  int body_runs;      // FGMRES cycles replayed by the device-side graph loop
+  int body_runs;      // FGMRES cycles replayed by the device-side graph loop (this solve)
+  long long total_body_runs;  // the same over the context's lifetime (never reset)
   unsigned int counter;  // arrivals for the last-block reductions
   unsigned int pad;
   double tol, bnorm, beta, rel_res;

@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(kBlock) scale_copy_kernel(const double* __rest
 __global__ void loop_cond_kernel(cudaGraphConditionalHandle h, SolverState* st) {
   int go = st->run_cycle;
   st->body_runs += 1;
+  st->total_body_runs += 1;
   if (go && st->body_runs > st->max_iter + 2) {
     st->status = RSFDE_ENOTCONV;
     st->run_cycle = 0;

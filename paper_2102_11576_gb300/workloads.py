@@ -19,6 +19,7 @@ points x_i = -1 + i h, h = 2/(n+1)):
                 (1-x^2-y^2)_+^2, T=1 in 50 steps, FGMRES(20), tol 1e-10.
   * disk1024:   n=1024, unit disk, alpha=(1.5,1.5), T=1 in 200 steps, and a
                 seeded smooth target (sum of 4 Gaussians) for the adjoint loss.
+  * make_batch: 256 independent instances of uneven size and parameters.
 """
 import numpy as np
 
@@ -106,6 +107,31 @@ def make(name, seed=0, n=None):
     w.update(name=name, n1=n, n2=n, box=BOX, in_omega=mask, tol=1e-10)
     w["dt"] = w["T"] / w["steps"]
     return w
+
+
+def make_batch(seed=0, count=256, n_range=(64, 512), steps=20):
+    """The batched workload: `count` independent instances, grid side
+    uniform in n_range, alpha1, alpha2 ~ U(1.1, 1.9), k_x, k_y ~ U[0.5, 2],
+    Omega a random ellipse (semi-axes U[0.4, 0.95], centre offset
+    U[-0.05, 0.05]^2, random rotation) or a convex polygon with 5-12 vertices
+    on the unit circle (equal odds), u0 the masked bump, T = 1 in `steps`
+    steps, eta = 1e-8."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        X, Y = grid_xy(n, n)
+        if rng.random() < 0.5:
+            a, b = rng.uniform(0.4, 0.95, size=2)
+            cx, cy = rng.uniform(-0.05, 0.05, size=2)
+            mask = ellipse_mask(X, Y, a, b, cx, cy, rng.uniform(0.0, np.pi))
+        else:
+            mask = convex_polygon_mask(X, Y, polygon_vertices(rng, int(rng.integers(5, 13))))
+        out.append(dict(n1=n, n2=n, box=BOX, in_omega=mask, alpha1=float(rng.uniform(1.1, 1.9)),
+                        alpha2=float(rng.uniform(1.1, 1.9)), kx=float(rng.uniform(0.5, 2.0)),
+                        ky=float(rng.uniform(0.5, 2.0)), eta=1e-8, T=1.0, steps=steps, dt=1.0 / steps,
+                        u0=bump(X, Y) * mask, tol=1e-10, restart=20))
+    return out
 
 
 def random_problem(seed, n1, n2, p_in=0.6):

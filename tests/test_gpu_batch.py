@@ -1,0 +1,49 @@
+"""The batched form: instances of uneven size, alpha, k and domain advanced
+together by one CUDA graph per step.  Each instance must equal the same
+problem solved alone (same kernels, deterministic reductions: identical bits)
+and its every step must meet the FP64 residual test, checked by the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_11576_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2102_11576_gb300 import Batch, Solver  # noqa: E402
+
+
+def test_batch_equals_single_instances_and_meets_tolerance():
+    probs = workloads.make_batch(seed=5, count=7, n_range=(9, 96), steps=10)
+    steps = 3
+    rng = np.random.default_rng(0)
+    srcs = [rng.standard_normal(p["u0"].shape) if i % 2 else None for i, p in enumerate(probs)]
+    b = Batch(probs, precond="fp32", matvec="df32")
+    for i, p in enumerate(probs):
+        b.set(i, p["u0"], srcs[i])
+    st = b.run(steps)
+    assert all(s["converged"] and s["rel_res"] <= 1e-10 for s in st)
+    assert b.kernel_launches > 0
+    for i, p in enumerate(probs):
+        args = (p["n1"], p["n2"], p["box"], p["in_omega"], p["alpha1"], p["alpha2"], p["kx"], p["ky"],
+                p["dt"], p["eta"])
+        single = Solver(*args, precond="fp32", matvec="df32")
+        src = None if srcs[i] is None else torch.as_tensor(srcs[i]).cuda()
+        prev, prevprev = torch.as_tensor(p["u0"]).cuda(), None
+        orc = oracle.Problem(*args)
+        for k in range(steps):
+            nxt, s1 = single.step(prev, prevprev, src)
+            bvec = orc.rhs(prev.cpu().numpy(), srcs[i])
+            r = bvec - orc.apply_M(nxt.cpu().numpy())
+            assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(bvec)
+            prevprev, prev = prev, nxt
+        np.testing.assert_array_equal(b.get(i).cpu().numpy(), prev.cpu().numpy())
+        single.close()
+    # a second run continues the marches (later-step graph) and set() restarts one
+    st2 = b.run(1)
+    assert all(s["converged"] for s in st2)
+    b.close()
