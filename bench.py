@@ -203,8 +203,12 @@ def run_ours(args, rank, world, local_rank):
             state = (nxt, prev)
         return state
 
+    tiles = {}
+
     def timed_form(precond, matvec, steps, warmup, profile_steps, clocks=None):
         solver = Solver(*solver_args, precond=precond, matvec=matvec, use_graph=not args.no_graph, **mk)
+        if not args.no_autotune:  # tile shapes by measurement (setup, outside the timed region)
+            tiles[f"{precond}+{matvec}"] = solver.autotune(reps=3)
         bufs = [u0.clone(), torch.empty_like(u0), torch.empty_like(u0)]
         state = (0, None)
         state = march(solver, bufs, state, warmup, [])
@@ -365,6 +369,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": mixed["launches"],
+        "tile_shapes": tiles,
         "clocks": mixed["clocks"],
     }
     for name, f in others.items():
@@ -497,6 +502,8 @@ def run_batched(args):
     b = Batch(probs, precond=args.batch_precond, matvec="df32")
     for i, p in enumerate(probs):
         b.set(i, p["u0"])
+    if not args.no_autotune:
+        b.autotune(reps=3)
     setup_s = time.perf_counter() - t0
     b.run(args.warmup)  # builds the graphs, first steps
     torch.cuda.synchronize()
@@ -586,6 +593,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic tile shapes")
     ap.add_argument("--no-graph", action="store_true",
                     help="direct kernel launches instead of the graph loop (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")

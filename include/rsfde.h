@@ -73,6 +73,7 @@ extern "C" {
 #define RSFDE_CGS2 1
 
 typedef struct rsfde_ctx rsfde_ctx;
+typedef struct rsfde_batch rsfde_batch;
 
 /* Section 2: the box Omega-bar = (ax,bx) x (ay,by) and its interior grid n1 x n2. */
 typedef struct {
@@ -174,7 +175,6 @@ int rsfde_adjoint_step(rsfde_ctx* ctx, const double* u_prev, const double* u_k, 
  * kernels.  The paper solves one instance; this is the batched deployment of
  * the same step.  Arguments are arrays of `count` entries (grids, masks:
  * device pointers as in rsfde_setup); opts (may be NULL) apply to all. */
-typedef struct rsfde_batch rsfde_batch;
 int rsfde_batch_create(rsfde_batch** out, int32_t count, const rsfde_grid* grids, const uint8_t* const* masks,
                        const double* alpha1, const double* alpha2, const double* kx, const double* ky,
                        const double* dt, const double* eta, const rsfde_opts* opts);
@@ -253,6 +253,19 @@ int rsfde_profile_enable(rsfde_ctx* ctx, int on);
  * (HOST array of RSFDE_K_COUNT int64), then clears the accumulators. */
 int rsfde_profile_read(rsfde_ctx* ctx, double* ms, int64_t* launches);
 const char* rsfde_kernel_class_name(int k);
+
+/* Tile-shape autotuner.  The transform kernels process F vectors (rows or
+ * columns) per block; for the context's transform lengths and precisions
+ * this times every feasible F of each kernel family (reps calls each, CUDA
+ * events on the context's stream, on its own buffers) and records the
+ * fastest in a process-wide table that every later launch with the same
+ * length and precision uses (captured graphs are rebuilt).  chosen: HOST
+ * array of RSFDE_TUNE_COUNT int32 (the chosen F per family, 0 = not tuned)
+ * or NULL.  Overwrites the context's Krylov workspace. */
+#define RSFDE_TUNE_COUNT 6 /* Toeplitz rows, Toeplitz columns, sine rows, sine columns,
+                              preconditioner columns, preconditioner rows */
+int rsfde_autotune(rsfde_ctx* ctx, int32_t reps, int32_t* chosen);
+int rsfde_batch_autotune(rsfde_batch* b, int32_t reps);
 
 /* Number of this library's kernel launches since the context was made (host counter). */
 int64_t rsfde_kernel_launches(const rsfde_ctx* ctx);

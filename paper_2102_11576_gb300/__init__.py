@@ -107,6 +107,10 @@ def load_library(path=LIB_PATH):
     lib.rsfde_batch_kernel_launches.argtypes = [vp]
     lib.rsfde_batch_kernel_launches.restype = ctypes.c_int64
     lib.rsfde_batch_destroy.argtypes = [vp]
+    lib.rsfde_autotune.argtypes = [vp, i32, vp]
+    lib.rsfde_autotune.restype = ctypes.c_int
+    lib.rsfde_batch_autotune.argtypes = [vp, i32]
+    lib.rsfde_batch_autotune.restype = ctypes.c_int
     for name in ("rsfde_batch_create", "rsfde_batch_set", "rsfde_batch_run", "rsfde_batch_get"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("rsfde_setup", "rsfde_set_params", "rsfde_set_opts", "rsfde_set_stream",
@@ -321,6 +325,15 @@ class Solver:
     def kernel_launches(self):
         return int(self._lib.rsfde_kernel_launches(self._h))
 
+    TUNE_NAMES = ("toeplitz_rows", "toeplitz_cols", "dst_rows", "dst_cols", "precond_cols", "precond_rows")
+
+    def autotune(self, reps=5):
+        """Measures every feasible tile shape of this context's transform
+        kernels and records the fastest (rsfde_autotune); returns them."""
+        out = np.zeros(6, dtype=np.int32)
+        _check(self._lib.rsfde_autotune(self._h, int(reps), ctypes.c_void_p(out.ctypes.data)), "autotune")
+        return {n: int(f) for n, f in zip(self.TUNE_NAMES, out) if f}
+
 
 class Batch:
     """Many independent problems advanced together (rsfde_batch_*): each time
@@ -386,6 +399,9 @@ class Batch:
         rc = self._lib.rsfde_batch_run(self._h, int(steps), st)
         _check(rc, "batch_run")
         return [x.as_dict() for x in st]
+
+    def autotune(self, reps=3):
+        _check(self._lib.rsfde_batch_autotune(self._h, int(reps)), "batch_autotune")
 
     def get(self, i):
         out = self._torch.empty(self.shapes[i], dtype=self._torch.float64, device=self.dev)

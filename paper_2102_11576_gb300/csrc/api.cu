@@ -639,6 +639,97 @@ int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
   return h.status;
 }
 
+// ---- tile-shape autotuning ----------------------------------------------------
+template <typename Fn>
+float time_calls(rsfde_ctx* c, int reps, Fn fn) {
+  fn();  // warm-up (also sets the kernel's shared-memory attribute)
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, c->stream);
+  for (int r = 0; r < reps; ++r) fn();
+  cudaEventRecord(b, c->stream);
+  cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / reps;
+}
+
+int log2_of(int L) {
+  int k = 0;
+  while ((1 << k) < L) ++k;
+  return k;
+}
+
+// Tries every feasible tile shape F of one kernel family and records the fastest.
+template <typename T, typename Fn>
+int tune_one(rsfde_ctx* c, int kind, int L, int items, int reps, Fn run) {
+  const int Fmax = max_groups<T>(L, items);
+  int best = 1;
+  float best_ms = 1e30f;
+  for (int F = 1; F <= Fmax; F *= 2) {
+    tune_force_groups(F);
+    const float ms = time_calls(c, reps, run);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = F;
+    }
+  }
+  tune_force_groups(0);
+  tune_record(kind, log2_of(L), sizeof(T) == 8, best);
+  return best;
+}
+
+template <typename T>
+void tune_operator(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTables<T>& ty, int* chosen) {
+  double* z = c->V;
+  double* w = c->V + c->N;
+  chosen[TK_TOEP_ROWS] = tune_one<T>(c, TK_TOEP_ROWS, tx.L, (c->n2 + 1) / 2, reps, [&] {
+    launch_toeplitz_rows<T, double>(z, c->tmpx, c->n1, c->n2, tx, nullptr, c->stream);
+  });
+  chosen[TK_TOEP_COLS] = tune_one<T>(c, TK_TOEP_COLS, ty.L, (c->n1 + 1) / 2, reps, [&] {
+    launch_toeplitz_cols<T, double>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2, ty, nullptr,
+                                    nullptr, nullptr, c->stream);
+  });
+}
+
+template <typename T>
+void tune_precond(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTables<T>& ty, int* chosen) {
+  T* t1 = static_cast<T*>(c->T1);
+  T* t2a = static_cast<T*>(c->T2a);
+  T* t2b = static_cast<T*>(c->T2b);
+  chosen[TK_DST_ROWS] = tune_one<T>(c, TK_DST_ROWS, tx.L, c->n2, reps, [&] {
+    launch_dst_rows<T, T>(c->V, nullptr, t1, c->n1, c->n2, tx, nullptr, c->stream);
+  });
+  chosen[TK_PRE_COLS] = tune_one<T>(c, TK_PRE_COLS, ty.L, c->n1, reps, [&] {
+    launch_precond_cols<T>(t1, t2a, t2b, c->n1, c->n2, ty, tx.lam, c->pen, nullptr, c->stream);
+  });
+  chosen[TK_PRE_ROWS] = tune_one<T>(c, TK_PRE_ROWS, tx.L, c->n2, reps, [&] {
+    launch_precond_rows<T, double>(t2a, t2b, c->phi, c->V + c->N, c->n1, c->n2, tx, nullptr, c->stream);
+  });
+}
+
+int autotune_ctx(rsfde_ctx* c, int reps, int32_t* chosen_out) {
+  int chosen[TK_COUNT] = {0};
+  const size_t bytes = c->N * sizeof(double);
+  cudaMemsetAsync(c->V, 0, 2 * bytes, c->stream);  // defined inputs for the timing runs
+  cudaMemsetAsync(c->T1, 0, bytes, c->stream);
+  cudaMemsetAsync(c->T2a, 0, bytes, c->stream);
+  cudaMemsetAsync(c->T2b, 0, bytes, c->stream);
+  if (c->opts.matvec_prec == RSFDE_DF32) tune_operator<df>(c, reps, c->xdf.tab, c->ydf.tab, chosen);
+  else tune_operator<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
+  if (c->opts.precond_prec == RSFDE_FP32) tune_precond<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
+  else if (c->opts.precond_prec == RSFDE_FP64) tune_precond<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
+  c->graph_key = -1;  // captured launches carry the old shapes
+  if (chosen_out)
+    for (int k = 0; k < TK_COUNT; ++k) chosen_out[k] = chosen[k];
+  int rc = check_launch(c);
+  if (rc == RSFDE_OK) rc = cuda_fail(cudaStreamSynchronize(c->stream));
+  return rc;
+}
+
 // ---- batched instances: one CUDA graph advances every instance by a step ---
 
 // Captures fn(c) (work enqueued on c->stream) into a child-graph node of g.
@@ -1057,6 +1148,11 @@ int rsfde_get_params(rsfde_ctx* c, double* out5) {
 
 int64_t rsfde_kernel_launches(const rsfde_ctx* c) { return c ? c->launches : 0; }
 
+int rsfde_autotune(rsfde_ctx* c, int32_t reps, int32_t* chosen) {
+  if (!c || reps < 1) return RSFDE_EINVAL;
+  return autotune_ctx(c, reps, chosen);
+}
+
 int rsfde_profile_enable(rsfde_ctx* c, int on) {
   if (!c) return RSFDE_EINVAL;
   c->prof_on = on != 0;
@@ -1204,6 +1300,27 @@ int64_t rsfde_batch_kernel_launches(rsfde_batch* b) {
       n += (int64_t)runs * c->launches_per_body;
   }
   return n;
+}
+
+int rsfde_batch_autotune(rsfde_batch* b, int32_t reps) {
+  if (!b || reps < 1) return RSFDE_EINVAL;
+  // the recorded shapes are keyed by transform length: tune one instance per length pair
+  std::vector<std::pair<int, int>> seen;
+  for (rsfde_ctx* c : b->ctx) {
+    const std::pair<int, int> key(c->x64.tab.L, c->y64.tab.L);
+    bool done = false;
+    for (auto& k : seen) done |= (k == key);
+    if (done) continue;
+    seen.push_back(key);
+    int rc = autotune_ctx(c, reps, nullptr);
+    if (rc) return rc;
+  }
+  for (auto& x : b->exec)
+    if (x) {
+      cudaGraphExecDestroy(x);
+      x = nullptr;
+    }
+  return RSFDE_OK;
 }
 
 void rsfde_batch_destroy(rsfde_batch* b) {

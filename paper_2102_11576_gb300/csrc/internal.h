@@ -98,6 +98,14 @@ __device__ __forceinline__ void givens_step(SolverState* st, int j, double hnorm
     st->run_iter = 0;
 }
 
+// ---- tile-shape autotuning (transforms.cu) -----------------------------------
+enum TuneKind { TK_TOEP_ROWS, TK_TOEP_COLS, TK_DST_ROWS, TK_DST_COLS, TK_PRE_COLS, TK_PRE_ROWS, TK_COUNT };
+void tune_force_groups(int F);  // 0: use the recorded choice / heuristic
+void tune_record(int kind, int log2L, int wide, int F);
+int tune_lookup(int kind, int log2L, int wide);
+template <typename T>
+int max_groups(int L, int items);
+
 // ---- launchers (transforms.cu) ---------------------------------------------
 // tmpx: scratch of N values of the arithmetic type T (A_x z between the passes)
 template <typename T, typename Tin>

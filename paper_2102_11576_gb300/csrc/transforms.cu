@@ -365,13 +365,40 @@ static int group_stride(int L, int F, bool cols) {
   return base + ((target - base) % P + P) % P;
 }
 
+// Tile shape (F, the vectors one block transforms) per kernel family,
+// transform length and 4/8-byte arithmetic: chosen by measurement
+// (rsfde_autotune) when recorded, else by the occupancy heuristic below.
+static int g_tuned[TK_COUNT][16][2];
+static thread_local int g_force_groups = 0;
+
+void tune_force_groups(int F) { g_force_groups = F; }
+void tune_record(int kind, int log2L, int wide, int F) {
+  if (kind >= 0 && kind < TK_COUNT && log2L >= 0 && log2L < 16) g_tuned[kind][log2L][wide ? 1 : 0] = F;
+}
+int tune_lookup(int kind, int log2L, int wide) {
+  return (kind >= 0 && kind < TK_COUNT && log2L >= 0 && log2L < 16) ? g_tuned[kind][log2L][wide ? 1 : 0] : 0;
+}
+
+// Largest feasible F: the thread cap (512 for 8-byte arithmetic, else
+// RSFDE_FP32_THREADS), the shared-memory budget and the work available.
 template <typename T>
-static int pick_groups(int L, int items) {
+int max_groups(int L, int items) {
   const int G = L / 16;
   const int cap = sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS;
   const size_t per = (size_t)(L + L / 16 + lanes_per_phase<T>()) * 2 * sizeof(T);
   int F = 1;
   while (2 * F * G <= cap && per * 2 * F <= (size_t)kSmemBudget && 2 * F <= items) F *= 2;
+  return F;
+}
+
+template <typename T>
+static int pick_groups(int L, int items, int kind) {
+  const int Fmax = max_groups<T>(L, items);
+  int log2L = 0;
+  while ((1 << log2L) < L) ++log2L;
+  int F = g_force_groups ? g_force_groups : tune_lookup(kind, log2L, sizeof(T) == 8);
+  if (F > 0) return F < Fmax ? F : Fmax;
+  F = Fmax;  // heuristic: as wide as fits, but at least ~2 blocks per SM
   while (F > 1 && (items + F - 1) / F < 2 * kNumSMs) F /= 2;
   return F;
 }
@@ -390,7 +417,7 @@ template <typename T, typename Tin>
 void launch_toeplitz_rows(const Tin* z, void* tmpx, int n1, int n2, const AxisTables<T>& ax, const int* gate,
                           cudaStream_t s) {
   const int npairs = (n2 + 1) / 2;
-  const int F = pick_groups<T>(ax.L, npairs);
+  const int F = pick_groups<T>(ax.L, npairs, TK_TOEP_ROWS);
   const size_t sm = group_smem<T>(ax.L, F, false);
   auto k = toeplitz_kernel<T, Tin, MODE_APPLY, false>;
   set_smem(k, sm);
@@ -404,7 +431,7 @@ void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi
                           const double* b, double* out, int n1, int n2, const AxisTables<T>& ay,
                           const int* gate, double* partials, SolverState* st, cudaStream_t s) {
   const int npairs = (n1 + 1) / 2;
-  const int F = pick_groups<T>(ay.L, npairs);
+  const int F = pick_groups<T>(ay.L, npairs, TK_TOEP_COLS);
   const size_t sm = group_smem<T>(ay.L, F, true);
   const int gs = group_stride<T>(ay.L, F, true);
   int grid = (npairs + F - 1) / F;
@@ -435,7 +462,7 @@ void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi
 template <typename T, typename Tout>
 void launch_dst_rows(const double* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
                      const int* gate, cudaStream_t s) {
-  const int F = pick_groups<T>(ax.L, n2);
+  const int F = pick_groups<T>(ax.L, n2, TK_DST_ROWS);
   const size_t sm = group_smem<T>(ax.L, F, false);
   auto k = dst_kernel<T, double, Tout, false>;
   set_smem(k, sm);
@@ -445,7 +472,7 @@ void launch_dst_rows(const double* v, const double* vscale, Tout* out, int n1, i
 
 template <typename T, typename Tin, typename Tout>
 void launch_dst_cols(const Tin* in, Tout* out, int n1, int n2, const AxisTables<T>& ay, cudaStream_t s) {
-  const int F = pick_groups<T>(ay.L, n1);
+  const int F = pick_groups<T>(ay.L, n1, TK_DST_COLS);
   const size_t sm = group_smem<T>(ay.L, F, true);
   auto k = dst_kernel<T, Tin, Tout, true>;
   set_smem(k, sm);
@@ -456,7 +483,7 @@ void launch_dst_cols(const Tin* in, Tout* out, int n1, int n2, const AxisTables<
 template <typename T>
 void launch_precond_cols(const T* T1, T* T2a, T* T2b, int n1, int n2, const AxisTables<T>& ay, const T* lamx,
                          double pen, const int* gate, cudaStream_t s) {
-  const int F = pick_groups<T>(ay.L, n1);
+  const int F = pick_groups<T>(ay.L, n1, TK_PRE_COLS);
   const size_t sm = group_smem<T>(ay.L, F, true);
   auto k = precond_cols_kernel<T>;
   set_smem(k, sm);
@@ -467,7 +494,7 @@ void launch_precond_cols(const T* T1, T* T2a, T* T2b, int n1, int n2, const Axis
 template <typename T, typename Tz>
 void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, int n1, int n2,
                          const AxisTables<T>& ax, const int* gate, cudaStream_t s) {
-  const int F = pick_groups<T>(ax.L, n2);
+  const int F = pick_groups<T>(ax.L, n2, TK_PRE_ROWS);
   const size_t sm = group_smem<T>(ax.L, F, false);
   auto k = precond_rows_kernel<T, Tz>;
   set_smem(k, sm);
@@ -476,6 +503,9 @@ void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, 
 }
 
 // explicit instantiations used by the solver
+template int max_groups<double>(int, int);
+template int max_groups<float>(int, int);
+template int max_groups<df>(int, int);
 template void launch_toeplitz_rows<double, double>(const double*, void*, int, int, const AxisTables<double>&,
                                                    const int*, cudaStream_t);
 template void launch_toeplitz_rows<double, float>(const float*, void*, int, int, const AxisTables<double>&,

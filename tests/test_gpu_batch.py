@@ -47,3 +47,27 @@ def test_batch_equals_single_instances_and_meets_tolerance():
     st2 = b.run(1)
     assert all(s["converged"] for s in st2)
     b.close()
+
+
+def test_autotune_records_feasible_shapes_and_keeps_results():
+    w = workloads.make("polygon2048", n=300)
+    args = (w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"], w["dt"],
+            w["eta"])
+    s = Solver(*args, precond="fp32", matvec="df32")
+    u0 = torch.as_tensor(w["u0"]).cuda()
+    before, st0 = s.step(u0)
+    chosen = s.autotune(reps=2)
+    assert set(chosen) >= {"toeplitz_rows", "toeplitz_cols", "dst_rows", "precond_cols", "precond_rows"}
+    assert all(f >= 1 and (f & (f - 1)) == 0 for f in chosen.values())
+    after, st1 = s.step(u0)
+    assert st1["converged"]
+    # each vector's transform does not depend on how many vectors a block holds
+    rel = ((after - before).abs().max() / before.abs().max()).item()
+    assert rel <= 1e-13
+    probs = workloads.make_batch(seed=6, count=4, n_range=(40, 130), steps=10)
+    b = Batch(probs)
+    for i, p in enumerate(probs):
+        b.set(i, p["u0"])
+    b.autotune(reps=2)
+    st = b.run(2)
+    assert all(x["converged"] for x in st)
