@@ -258,8 +258,9 @@ def run_ours(args, rank, world, local_rank):
     # FP64 form, each marched from the same u0 over the same steps
     mixed = timed_form("fp32", "df32", args.steps, args.warmup, args.profile_steps, clocks)
     others = {}
-    others["bf16x3+df32"] = timed_form("bf16x3", "df32", args.steps, args.warmup, args.profile_steps)
-    if not args.no_fp64:
+    if not args.only_headline:
+        others["bf16x3+df32"] = timed_form("bf16x3", "df32", args.steps, args.warmup, args.profile_steps)
+    if not args.no_fp64 and not args.only_headline:
         others["fp32_op64"] = timed_form("fp32", "fp64", args.steps, args.warmup, args.profile_steps)
         others["fp64"] = timed_form("fp64", "fp64", args.fp64_steps, args.warmup, args.profile_steps)
     plain = others.get("fp64")
@@ -469,7 +470,7 @@ def run_op(args):
     import torch
     from paper_2102_11576_gb300 import Solver, workloads
     w = workloads.make(args.workload)
-    prec = "fp64" if args.op.endswith("fp64") else "fp32"
+    prec = "fp64" if args.op.endswith("fp64") else ("bf16x3" if args.op.endswith("bf16x3") else "fp32")
     matvec = "df32" if args.op.endswith("df32") else "fp64"
     s = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
                w["dt"], w["eta"], restart=w["restart"], precond=prec, matvec=matvec)
@@ -477,7 +478,7 @@ def run_op(args):
     v = torch.as_tensor(rng.standard_normal((w["n2"], w["n1"]))).cuda()
     out = torch.empty_like(v)
     fn = {"apply_M": s.apply_M, "apply_M_df32": s.apply_M, "precond_fp32": s.apply_precond,
-          "precond_fp64": s.apply_precond, "dst2": s.dst2}[args.op]
+          "precond_fp64": s.apply_precond, "precond_bf16x3": s.apply_precond, "dst2": s.dst2}[args.op]
     fn(v, out)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -575,7 +576,8 @@ def main():
     ap.add_argument("--batch-precond", default="fp32")
     ap.add_argument("--adjoint", action="store_true",
                     help="time one differentiable march of the 1024^2 differentiation workload")
-    ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "precond_fp32", "precond_fp64", "dst2"],
+    ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "precond_fp32", "precond_fp64", "precond_bf16x3",
+                                     "dst2"],
                     default=None,
                     help="time one operator entry point instead of the time march")
     ap.add_argument("--reps", type=int, default=5)
@@ -594,6 +596,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic tile shapes")
+    ap.add_argument("--only-headline", action="store_true", help="time the headline form only")
     ap.add_argument("--no-graph", action="store_true",
                     help="direct kernel launches instead of the graph loop (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")

@@ -6,9 +6,11 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "fft.cuh"  // host butterflies for the setup spectra
+
 #include "internal.h"
 
 using namespace rsfde;
@@ -229,7 +231,10 @@ int cuda_fail(cudaError_t e) {
   return RSFDE_ECUDA;
 }
 
-int check_launch(rsfde_ctx* c) { return cuda_fail(cudaGetLastError()); }
+int check_launch(rsfde_ctx* c) {
+  if (take_unsupported_launch()) return RSFDE_EINVAL;
+  return cuda_fail(cudaGetLastError());
+}
 
 cudaEvent_t prof_event(rsfde_ctx* c) {
   if (!c->ev_pool.empty()) {
@@ -326,17 +331,18 @@ int ensure_bf16(rsfde_ctx* c) {
 }
 
 // The tensor-core preconditioner z = P-hat^-1 (scale * v) (five launches).
-template <typename Tz>
-void enqueue_precond_bf16(rsfde_ctx* c, const double* v, const double* vscale, Tz* z, const int* gate) {
+template <typename Tz, typename Tin>
+void enqueue_precond_bf16(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate) {
   ProfScope ps(c, RSFDE_K_DST_GEMM);
   c->launches += 4;
-  bf16_precond<Tz>(c->bf16, v, vscale, z, c->phi, c->pen, gate, c->stream);
+  bf16_precond<Tz, Tin>(c->bf16, v, vscale, z, c->phi, c->pen, gate, c->stream);
 }
 
 // ---- enqueue helpers ---------------------------------------------------------
-// w = M z (Eq. 2.17), z in precision Tz, arithmetic T (double or df).
-template <typename T, typename Tz>
-void enqueue_apply_M_t(rsfde_ctx* c, const Tz* z, double* w, const int* gate, const AxisTables<T>& tx,
+// w = M z (Eq. 2.17), z in precision Tz, arithmetic T (double or df), w
+// stored as Tw (double, or df for a double-FP32 Krylov basis).
+template <typename T, typename Tz, typename Tw>
+void enqueue_apply_M_t(rsfde_ctx* c, const Tz* z, Tw* w, const int* gate, const AxisTables<T>& tx,
                        const AxisTables<T>& ty) {
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
@@ -344,31 +350,36 @@ void enqueue_apply_M_t(rsfde_ctx* c, const Tz* z, double* w, const int* gate, co
   }
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
-    launch_toeplitz_cols<T, Tz>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2, ty, gate,
-                                nullptr, nullptr, c->stream);
+    launch_toeplitz_cols<T, Tz, Tw>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2, ty, gate,
+                                    nullptr, nullptr, c->stream);
   }
 }
 
 template <typename Tz>
 void enqueue_apply_M(rsfde_ctx* c, const Tz* z, double* w, const int* gate) {
-  if (c->opts.matvec_prec == RSFDE_DF32) enqueue_apply_M_t<df, Tz>(c, z, w, gate, c->xdf.tab, c->ydf.tab);
-  else enqueue_apply_M_t<double, Tz>(c, z, w, gate, c->x64.tab, c->y64.tab);
+  if (c->opts.matvec_prec == RSFDE_DF32) enqueue_apply_M_t<df, Tz, double>(c, z, w, gate, c->xdf.tab, c->ydf.tab);
+  else enqueue_apply_M_t<double, Tz, double>(c, z, w, gate, c->x64.tab, c->y64.tab);
 }
 
 bool left_variant(const rsfde_ctx* c) { return c->opts.variant == RSFDE_GMRES_LEFT; }
 
-template <typename T, typename Tz>
-void enqueue_precond_t(rsfde_ctx* c, const double* v, const double* vscale, Tz* z, const int* gate,
+// The right-preconditioned FGMRES keeps its Krylov basis in double-FP32 when
+// the Arnoldi operator runs in double-FP32 (the operator's output is then
+// stored without rounding to FP64, and the Gram-Schmidt runs on the FP32 pipe).
+bool df_basis(const rsfde_ctx* c) { return c->opts.matvec_prec == RSFDE_DF32 && !left_variant(c); }
+
+template <typename T, typename Tz, typename Tin>
+void enqueue_precond_t(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate,
                        const AxisTables<T>& tx, const AxisTables<T>& ty);
 
 // z = P-hat^-1 (scale * v) into an FP64 vector, in the context's preconditioner precision.
-template <typename Tz>
-void enqueue_precond_bf16(rsfde_ctx* c, const double* v, const double* vscale, Tz* z, const int* gate);
+template <typename Tz, typename Tin>
+void enqueue_precond_bf16(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate);
 
 void enqueue_precond64(rsfde_ctx* c, const double* v, const double* vscale, double* z, const int* gate) {
-  if (bf16_precond_on(c)) enqueue_precond_bf16<double>(c, v, vscale, z, gate);
-  else if (fp32_precond(c)) enqueue_precond_t<float, double>(c, v, vscale, z, gate, c->x32.tab, c->y32.tab);
-  else enqueue_precond_t<double, double>(c, v, vscale, z, gate, c->x64.tab, c->y64.tab);
+  if (bf16_precond_on(c)) enqueue_precond_bf16<double, double>(c, v, vscale, z, gate);
+  else if (fp32_precond(c)) enqueue_precond_t<float, double, double>(c, v, vscale, z, gate, c->x32.tab, c->y32.tab);
+  else enqueue_precond_t<double, double, double>(c, v, vscale, z, gate, c->x64.tab, c->y64.tab);
 }
 
 // Left-preconditioned GMRES: V_0 = P^-1 (b - M x) (or b - M x without a
@@ -412,21 +423,26 @@ void enqueue_residual(rsfde_ctx* c, const int* gate) {
   }
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
-    launch_toeplitz_cols<double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1,
-                                         c->n2, c->y64.tab, gate, c->partials, c->st, c->stream);
+    if (df_basis(c))
+      launch_toeplitz_cols<double, double, df>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
+                                               reinterpret_cast<df*>(c->V), c->n1, c->n2, c->y64.tab, gate,
+                                               c->partials, c->st, c->stream);
+    else
+      launch_toeplitz_cols<double, double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1,
+                                                   c->n2, c->y64.tab, gate, c->partials, c->st, c->stream);
   }
 }
 
 // z = P-hat^-1 (scale * v) (Eq. 4.6) into z of precision Tz.
-template <typename T, typename Tz>
-void enqueue_precond_t(rsfde_ctx* c, const double* v, const double* vscale, Tz* z, const int* gate,
+template <typename T, typename Tz, typename Tin>
+void enqueue_precond_t(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate,
                        const AxisTables<T>& tx, const AxisTables<T>& ty) {
   T* t1 = static_cast<T*>(c->T1);
   T* t2a = static_cast<T*>(c->T2a);
   T* t2b = static_cast<T*>(c->T2b);
   {
     ProfScope ps(c, RSFDE_K_DST_ROWS);
-    launch_dst_rows<T, T>(v, vscale, t1, c->n1, c->n2, tx, gate, c->stream);
+    launch_dst_rows<T, Tin, T>(v, vscale, t1, c->n1, c->n2, tx, gate, c->stream);
   }
   {
     ProfScope ps(c, RSFDE_K_PRECOND_COLS);
@@ -450,36 +466,40 @@ void enqueue_rhs(rsfde_ctx* c, const double* u, const double* uu, const double* 
 
 // One FGMRES(m) cycle: m gated Arnoldi iterations, the solution update and
 // the true residual with the restart decision.  Nothing is read on the host.
-template <typename Tz>
+// Krylov basis element type Tv: double, or df (df_basis).
+template <typename Tz, typename Tv>
 void enqueue_cycle_t(rsfde_ctx* c) {
   const size_t N = c->N;
   const int m = c->opts.restart;
   const int* gi = &c->st->run_iter;
   const int* gc = &c->st->run_cycle;
   Tz* Z = static_cast<Tz*>(c->Z);
+  Tv* V = reinterpret_cast<Tv*>(c->V);
   for (int j = 0; j < m; ++j) {
-    const double* vj = c->V + (size_t)j * N;
+    const Tv* vj = V + (size_t)j * N;
     Tz* zj = Z + (size_t)j * N;
     if (c->opts.use_precond) {
       if (bf16_precond_on(c))
-        enqueue_precond_bf16<Tz>(c, vj, &c->st->s[j], zj, gi);
+        enqueue_precond_bf16<Tz, Tv>(c, vj, &c->st->s[j], zj, gi);
       else if (fp32_precond(c))
-        enqueue_precond_t<float, Tz>(c, vj, &c->st->s[j], zj, gi, c->x32.tab, c->y32.tab);
+        enqueue_precond_t<float, Tz, Tv>(c, vj, &c->st->s[j], zj, gi, c->x32.tab, c->y32.tab);
       else
-        enqueue_precond_t<double, Tz>(c, vj, &c->st->s[j], zj, gi, c->x64.tab, c->y64.tab);
+        enqueue_precond_t<double, Tz, Tv>(c, vj, &c->st->s[j], zj, gi, c->x64.tab, c->y64.tab);
     } else {
       ProfScope ps(c, RSFDE_K_OTHER);
-      launch_scale_copy<Tz>(vj, &c->st->s[j], zj, N, gi, c->stream);  // P = I: z_j = v_j
+      launch_scale_copy<Tv, Tz>(vj, &c->st->s[j], zj, N, gi, c->stream);  // P = I: z_j = v_j
     }
-    enqueue_apply_M<Tz>(c, zj, c->V + (size_t)(j + 1) * N, gi);
+    Tv* w = V + (size_t)(j + 1) * N;
+    if constexpr (std::is_same<Tv, df>::value) enqueue_apply_M_t<df, Tz, df>(c, zj, w, gi, c->xdf.tab, c->ydf.tab);
+    else enqueue_apply_M<Tz>(c, zj, w, gi);
     const bool cgs2 = c->opts.arnoldi == RSFDE_CGS2;
     for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
       {
         ProfScope ps(c, RSFDE_K_MULTIDOT);
-        launch_multidot(c->V, N, j, pass, c->partials, c->st, c->stream);
+        launch_multidot<Tv>(V, N, j, pass, c->partials, c->st, c->stream);
       }
       ProfScope ps(c, RSFDE_K_UPDATE);
-      launch_update(c->V, N, j, (!cgs2 || pass == 1) ? 1 : 0, c->partials, c->st, c->stream);
+      launch_update<Tv>(V, N, j, (!cgs2 || pass == 1) ? 1 : 0, c->partials, c->st, c->stream);
     }
   }
   {
@@ -509,7 +529,7 @@ void enqueue_cycle_left(rsfde_ctx* c) {
     } else {
       {
         ProfScope ps(c, RSFDE_K_OTHER);
-        launch_scale_copy<double>(vj, &c->st->s[j], tmp, N, gi, c->stream);
+        launch_scale_copy<double, double>(vj, &c->st->s[j], tmp, N, gi, c->stream);
       }
       enqueue_apply_M<double>(c, tmp, w, gi);
     }
@@ -517,10 +537,10 @@ void enqueue_cycle_left(rsfde_ctx* c) {
     for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
       {
         ProfScope ps(c, RSFDE_K_MULTIDOT);
-        launch_multidot(c->V, N, j, pass, c->partials, c->st, c->stream);
+        launch_multidot<double>(c->V, N, j, pass, c->partials, c->st, c->stream);
       }
       ProfScope ps(c, RSFDE_K_UPDATE);
-      launch_update(c->V, N, j, (!cgs2 || pass == 1) ? 1 : 0, c->partials, c->st, c->stream);
+      launch_update<double>(c->V, N, j, (!cgs2 || pass == 1) ? 1 : 0, c->partials, c->st, c->stream);
     }
   }
   {
@@ -536,8 +556,11 @@ void enqueue_cycle_left(rsfde_ctx* c) {
 
 void enqueue_cycle(rsfde_ctx* c) {
   if (left_variant(c)) enqueue_cycle_left(c);
-  else if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float>(c);
-  else enqueue_cycle_t<double>(c);
+  else if (df_basis(c)) {
+    if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float, df>(c);
+    else enqueue_cycle_t<double, df>(c);
+  } else if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float, double>(c);
+  else enqueue_cycle_t<double, double>(c);
 }
 
 int graph_key(const rsfde_ctx* c) {
@@ -682,15 +705,19 @@ int tune_one(rsfde_ctx* c, int kind, int L, int items, int reps, Fn run) {
   return best;
 }
 
+// Times the operator in the types the solver uses: FP64 z and w, or (double-
+// FP32 arithmetic) an FP32 z and a double-FP32 w.
 template <typename T>
 void tune_operator(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTables<T>& ty, int* chosen) {
-  double* z = c->V;
-  double* w = c->V + c->N;
+  using Tz = typename std::conditional<std::is_same<T, df>::value, float, double>::type;
+  using Tw = typename std::conditional<std::is_same<T, df>::value, df, double>::type;
+  const Tz* z = reinterpret_cast<const Tz*>(c->V);
+  Tw* w = reinterpret_cast<Tw*>(c->V + c->N);
   chosen[TK_TOEP_ROWS] = tune_one<T>(c, TK_TOEP_ROWS, tx.L, (c->n2 + 1) / 2, reps, [&] {
-    launch_toeplitz_rows<T, double>(z, c->tmpx, c->n1, c->n2, tx, nullptr, c->stream);
+    launch_toeplitz_rows<T, Tz>(z, c->tmpx, c->n1, c->n2, tx, nullptr, c->stream);
   });
   chosen[TK_TOEP_COLS] = tune_one<T>(c, TK_TOEP_COLS, ty.L, (c->n1 + 1) / 2, reps, [&] {
-    launch_toeplitz_cols<T, double>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2, ty, nullptr,
+    launch_toeplitz_cols<T, Tz, Tw>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2, ty, nullptr,
                                     nullptr, nullptr, c->stream);
   });
 }
@@ -701,7 +728,9 @@ void tune_precond(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTab
   T* t2a = static_cast<T*>(c->T2a);
   T* t2b = static_cast<T*>(c->T2b);
   chosen[TK_DST_ROWS] = tune_one<T>(c, TK_DST_ROWS, tx.L, c->n2, reps, [&] {
-    launch_dst_rows<T, T>(c->V, nullptr, t1, c->n1, c->n2, tx, nullptr, c->stream);
+    if (df_basis(c)) launch_dst_rows<T, df, T>(reinterpret_cast<const df*>(c->V), nullptr, t1, c->n1, c->n2, tx,
+                                               nullptr, c->stream);
+    else launch_dst_rows<T, double, T>(c->V, nullptr, t1, c->n1, c->n2, tx, nullptr, c->stream);
   });
   chosen[TK_PRE_COLS] = tune_one<T>(c, TK_PRE_COLS, ty.L, c->n1, reps, [&] {
     launch_precond_cols<T>(t1, t2a, t2b, c->n1, c->n2, ty, tx.lam, c->pen, nullptr, c->stream);
@@ -1105,12 +1134,12 @@ int rsfde_apply_precond(rsfde_ctx* c, const double* v, double* z) {
   if (bf16_precond_on(c)) {
     int rc = ensure_bf16(c);
     if (rc) return rc;
-    enqueue_precond_bf16<double>(c, v, nullptr, z, nullptr);
+    enqueue_precond_bf16<double, double>(c, v, nullptr, z, nullptr);
     if ((rc = check_launch(c))) return rc;
     return bf16_plan_error(c->bf16, c->stream);
   }
-  if (fp32_precond(c)) enqueue_precond_t<float, double>(c, v, nullptr, z, nullptr, c->x32.tab, c->y32.tab);
-  else enqueue_precond_t<double, double>(c, v, nullptr, z, nullptr, c->x64.tab, c->y64.tab);
+  if (fp32_precond(c)) enqueue_precond_t<float, double, double>(c, v, nullptr, z, nullptr, c->x32.tab, c->y32.tab);
+  else enqueue_precond_t<double, double, double>(c, v, nullptr, z, nullptr, c->x64.tab, c->y64.tab);
   return check_launch(c);
 }
 
@@ -1118,7 +1147,7 @@ int rsfde_dst2(rsfde_ctx* c, const double* v, double* out) {
   if (!c || !v || !out) return RSFDE_EINVAL;
   {
     ProfScope ps(c, RSFDE_K_DST_ROWS);
-    launch_dst_rows<double, double>(v, nullptr, c->tmpx, c->n1, c->n2, c->x64.tab, nullptr, c->stream);
+    launch_dst_rows<double, double, double>(v, nullptr, c->tmpx, c->n1, c->n2, c->x64.tab, nullptr, c->stream);
   }
   {
     ProfScope ps(c, RSFDE_K_PRECOND_COLS);

@@ -14,7 +14,7 @@
 
 namespace rsfde {
 
-struct df {
+struct __align__(8) df {
   float hi, lo;
   df() = default;
   __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
@@ -48,5 +48,45 @@ __device__ __forceinline__ df operator*(df a, df b) {
 
 __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
 __device__ __forceinline__ df& operator*=(df& a, df b) { return a = a * b; }
+
+// acc + a * b: the product's error term is carried into the sum without its
+// own renormalisation (a fused form of the two operators above).
+__device__ __forceinline__ df df_fma(df acc, df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(acc.hi, p);
+  const float bb = __fsub_rn(s, acc.hi);
+  const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  return df_fast_two_sum(s, __fadd_rn(err, __fadd_rn(acc.lo, e)));
+}
+
+// Conversions between the storage and arithmetic types (float, double, df);
+// float -> df is exact and needs no FP64 instruction.
+template <typename To, typename From>
+__device__ __forceinline__ To cvt(From x) {
+  return static_cast<To>(x);
+}
+template <>
+__device__ __forceinline__ df cvt<df, float>(float x) {
+  return df(x, 0.0f);
+}
+template <>
+__device__ __forceinline__ df cvt<df, double>(double x) {
+  return df(x);
+}
+template <>
+__device__ __forceinline__ df cvt<df, df>(df x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ double cvt<double, df>(df x) {
+  return double(x);
+}
+template <>
+__device__ __forceinline__ float cvt<float, df>(df x) {
+  return __fadd_rn(x.hi, x.lo);
+}
 
 }  // namespace rsfde

@@ -64,15 +64,21 @@ bool make_map(CUtensorMap* m, void* p, int rows, int cols, int ld) {
 }
 
 // A = scale * V split into a BF16 pair (rows y, columns x, leading dim ld).
-__global__ void __launch_bounds__(kBlock) split_kernel(const double* __restrict__ v, const double* scale,
+// FP64 input is scaled in FP64; double-FP32 input in FP32 (its leading part).
+__device__ __forceinline__ float scaled_f32(double sc, float, double v) { return (float)(sc * v); }
+__device__ __forceinline__ float scaled_f32(double, float scf, df v) { return __fmul_rn(scf, __fadd_rn(v.hi, v.lo)); }
+
+template <typename Tin>
+__global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v, const double* scale,
                                                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                                        int n1, int n2, int ld, const int* gate) {
   if (gate && *(volatile const int*)gate == 0) return;
   const double sc = scale ? *scale : 1.0;
+  const float scf = (float)sc;
   const size_t N = (size_t)n1 * n2;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
     const size_t j = p / n1, i = p - j * n1;
-    const float x = (float)(sc * v[p]);
+    const float x = scaled_f32(sc, scf, v[p]);
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     hi[j * ld + i] = h;
     lo[j * ld + i] = __float2bfloat16_rn(x - __bfloat162float(h));
@@ -190,12 +196,12 @@ static void launch_gemm(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K,
   k<<<grid, 128, kGemmSmem, s>>>(A.map_hi, A.map_lo, B.map_hi, B.map_lo, K, ep, err, gate);
 }
 
-template <typename Tz>
-int bf16_precond(Bf16Plan* p, const double* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
+template <typename Tz, typename Tin>
+int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
                  const int* gate, cudaStream_t s) {
   const int n1 = p->n1, n2 = p->n2;
   const size_t N = (size_t)n1 * n2;
-  split_kernel<<<vec_grid(N), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, gate);
+  split_kernel<Tin><<<vec_grid(N), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, gate);
   GemmEpiParams ep{};
   // 1. T1t = (A0 S_x)^T
   ep.M = n2;
@@ -240,9 +246,13 @@ int bf16_precond(Bf16Plan* p, const double* v, const double* vscale, Tz* z, cons
   return cudaGetLastError() == cudaSuccess ? RSFDE_OK : RSFDE_ECUDA;
 }
 
-template int bf16_precond<float>(Bf16Plan*, const double*, const double*, float*, const uint8_t*, double,
-                                 const int*, cudaStream_t);
-template int bf16_precond<double>(Bf16Plan*, const double*, const double*, double*, const uint8_t*, double,
-                                  const int*, cudaStream_t);
+template int bf16_precond<float, double>(Bf16Plan*, const double*, const double*, float*, const uint8_t*, double,
+                                         const int*, cudaStream_t);
+template int bf16_precond<double, double>(Bf16Plan*, const double*, const double*, double*, const uint8_t*,
+                                          double, const int*, cudaStream_t);
+template int bf16_precond<float, df>(Bf16Plan*, const df*, const double*, float*, const uint8_t*, double,
+                                     const int*, cudaStream_t);
+template int bf16_precond<double, df>(Bf16Plan*, const df*, const double*, double*, const uint8_t*, double,
+                                      const int*, cudaStream_t);
 
 }  // namespace rsfde

@@ -107,16 +107,21 @@ template <typename T>
 int max_groups(int L, int items);
 
 // ---- launchers (transforms.cu) ---------------------------------------------
+// A launcher asked for a (type, mode) pair it has no kernel for launches
+// nothing and raises a flag that the next launch check reports.
+void note_unsupported_launch();
+bool take_unsupported_launch();
 // tmpx: scratch of N values of the arithmetic type T (A_x z between the passes)
 template <typename T, typename Tin>
 void launch_toeplitz_rows(const Tin* z, void* tmpx, int n1, int n2, const AxisTables<T>& ax, const int* gate,
                           cudaStream_t s);
-template <typename T, typename Tin>
+// out: Tout = double, or df for a double-FP32 Krylov basis
+template <typename T, typename Tin, typename Tout>
 void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi, double pen,
-                          const double* b, double* out, int n1, int n2, const AxisTables<T>& ay,
+                          const double* b, Tout* out, int n1, int n2, const AxisTables<T>& ay,
                           const int* gate, double* partials, SolverState* st, cudaStream_t s);
-template <typename T, typename Tout>
-void launch_dst_rows(const double* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
+template <typename T, typename Tin, typename Tout>
+void launch_dst_rows(const Tin* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
                      const int* gate, cudaStream_t s);
 template <typename T, typename Tin, typename Tout>
 void launch_dst_cols(const Tin* in, Tout* out, int n1, int n2, const AxisTables<T>& ay, cudaStream_t s);
@@ -132,8 +137,8 @@ struct Bf16Plan;
 int bf16_plan_create(Bf16Plan** out, int n1, int n2, const float* lamx, const float* lamy, cudaStream_t s);
 void bf16_plan_destroy(Bf16Plan* p);
 int bf16_plan_error(Bf16Plan* p, cudaStream_t s);
-template <typename Tz>
-int bf16_precond(Bf16Plan* p, const double* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
+template <typename Tz, typename Tin>
+int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
                  const int* gate, cudaStream_t s);
 
 // ---- launchers (krylov.cu) -------------------------------------------------
@@ -143,9 +148,13 @@ void launch_mask_to_phi(const uint8_t* in_omega, uint8_t* phi, size_t N, cudaStr
 void launch_rhs(const double* u, const double* uu, const double* src, const uint8_t* phi, double dt, double* b,
                 double* x0, size_t N, double* partials, SolverState* st, cudaStream_t s);
 void launch_norm_b(const double* b, size_t N, double* partials, SolverState* st, cudaStream_t s);
-void launch_multidot(const double* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
+// Gram-Schmidt over the Krylov basis V (Tv = double, or df: double-FP32
+// storage and arithmetic)
+template <typename Tv>
+void launch_multidot(const Tv* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
                      cudaStream_t s);
-void launch_update(double* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s);
+template <typename Tv>
+void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s);
 void launch_solve_y(SolverState* st, cudaStream_t s);
 template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s);
@@ -158,7 +167,7 @@ void launch_adjoint_accum(const double* u_prev, const double* mu, const double* 
                           const uint8_t* phi, double dt, double ikx, double iky, double* lam_prev,
                           double* grad_src, double* grad_k, size_t N, double* partials, SolverState* st,
                           cudaStream_t s);
-template <typename Tz>
-void launch_scale_copy(const double* v, const double* scale, Tz* z, size_t N, const int* gate, cudaStream_t s);
+template <typename Tv, typename Tz>
+void launch_scale_copy(const Tv* v, const double* scale, Tz* z, size_t N, const int* gate, cudaStream_t s);
 
 }  // namespace rsfde

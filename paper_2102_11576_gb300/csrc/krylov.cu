@@ -1,7 +1,12 @@
-// krylov.cu -- grid-vector kernels of the flexible GMRES solve (FP64):
+// krylov.cu -- grid-vector kernels of the flexible GMRES solve:
 // right side of Eq. 2.17, fused multi-dot and update of the classical
 // Gram-Schmidt Arnoldi step, the Givens least squares (single thread, in the
 // last block of the norm reduction) and the solution update.
+//
+// The Krylov basis is FP64, or double-FP32 (df.cuh) when the Arnoldi
+// operator runs in double-FP32: then the Gram-Schmidt arithmetic runs on the
+// FP32 pipe as well (GB300 issues FP32 at 58x its FP64 rate) and only the
+// per-warp sums, the Hessenberg entries and the Givens step are FP64.
 //
 // Every reduction is two-level and deterministic: fixed grid, per-block
 // partials in block order, summed in a fixed order by the last block.
@@ -83,37 +88,111 @@ __global__ void __launch_bounds__(kBlock) norm_b_kernel(const double* __restrict
   }
 }
 
-// h_i = <w, v_i> = s_i <V_{j+1}, V_i> for i = 0..j  (w is stored in slot j+1).
-// blockIdx.y selects a chunk of kDotChunk basis vectors; w is re-read per
-// chunk (it stays in L2).  accumulate = 1 adds to H (second CGS pass).
-__global__ void __launch_bounds__(kBlock) multidot_kernel(const double* __restrict__ V, size_t N, int j,
-                                                          int accumulate, double* partials, SolverState* st) {
-  if (closed(&st->run_iter)) return;
-  __shared__ double red[32];
-  const int i0 = blockIdx.y * kDotChunk;
-  const int cnt = min(kDotChunk, j + 1 - i0);
-  const double* __restrict__ w = V + (size_t)(j + 1) * N;
-  double acc[kDotChunk];
+// ---- Gram-Schmidt over the Krylov basis ---------------------------------------
+// Element operations of the basis type: FP64, or double-FP32 (storage and
+// arithmetic; the sums leave each warp as FP64).
+template <typename Tv>
+struct VecOps;
+template <>
+struct VecOps<double> {
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double ld(const double* p) { return *p; }
+  static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+  static __device__ __forceinline__ double fma(double acc, double a, double b) { return __fma_rn(a, b, acc); }
+  static __device__ __forceinline__ double from(double x) { return x; }
+  static __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-  for (int k = 0; k < kDotChunk; ++k) acc[k] = 0.0;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    const double wp = w[p];
-#pragma unroll
-    for (int k = 0; k < kDotChunk; ++k)
-      if (k < cnt) acc[k] += wp * V[(size_t)(i0 + k) * N + p];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
   }
-  const int G = gridDim.x;
+};
+template <>
+struct VecOps<df> {
+  static __device__ __forceinline__ df zero() { return df(0.0f, 0.0f); }
+  static __device__ __forceinline__ df ld(const df* p) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    return df(v.x, v.y);
+  }
+  static __device__ __forceinline__ void st(df* p, df v) { *reinterpret_cast<float2*>(p) = make_float2(v.hi, v.lo); }
+  static __device__ __forceinline__ df fma(df acc, df a, df b) { return df_fma(acc, a, b); }
+  static __device__ __forceinline__ df from(double x) { return df(x); }
+  // fixed shuffle order; the result (lane 0) converted to FP64
+  static __device__ __forceinline__ double warp_sum(df v) {
 #pragma unroll
-  for (int k = 0; k < kDotChunk; ++k) {
-    if (k < cnt) {  // uniform over the block
-      const double bs = block_sum(acc[k], red);
-      if (threadIdx.x == 0) partials[(size_t)(i0 + k) * G + blockIdx.x] = bs;
+    for (int o = 16; o; o >>= 1) {
+      const df u(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+      v = v + u;
+    }
+    return double(v);
+  }
+};
+
+constexpr int kWarps = kBlock / 32;
+static_assert(kDotChunk <= kWarps, "one warp per multi-dot accumulator");
+
+// Block sums of cnt <= K accumulators: warp sums, then warp k adds the
+// per-warp FP64 sums of accumulator k (fixed order).  Thread 32k returns sum k.
+template <typename Tv, int K>
+__device__ __forceinline__ double block_sums(const Tv* acc, int cnt, double (*sh)[kWarps]) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (k < cnt) {
+      const double ws = VecOps<Tv>::warp_sum(acc[k]);
+      if (l == 0) sh[k][w] = ws;
     }
   }
+  __syncthreads();
+  double v = 0.0;
+  if (w < cnt) {
+    v = l < kWarps ? sh[w][l] : 0.0;
+    v = VecOps<double>::warp_sum(v);
+  }
+  return v;
+}
+
+// Sum of the G partials p[0..G) by one warp, fixed order (lane 0 returns it).
+__device__ __forceinline__ double warp_sum_partials(const double* p, int G) {
+  const int l = threadIdx.x & 31;
+  double v = 0.0;
+#pragma unroll 4
+  for (int q = l; q < G; q += 32) v += __ldcg(p + q);
+  return VecOps<double>::warp_sum(v);
+}
+
+// h_i = <w, v_i> = s_i <V_{j+1}, V_i> for i = 0..j  (w is stored in slot j+1).
+// blockIdx.y selects a chunk of kDotChunk basis vectors; w is re-read per
+// chunk (it stays in L2).  accumulate = 1 adds to H (second CGS pass).  The
+// last block finishes the j+1 sums, one warp per sum.
+template <typename Tv>
+__global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__ V, size_t N, int j, int accumulate,
+                                                          double* partials, SolverState* st) {
+  if (closed(&st->run_iter)) return;
+  using Op = VecOps<Tv>;
+  __shared__ double wsum[kDotChunk][kWarps];
+  const int i0 = blockIdx.y * kDotChunk;
+  const int cnt = min(kDotChunk, j + 1 - i0);
+  const Tv* __restrict__ w = V + (size_t)(j + 1) * N;
+  Tv acc[kDotChunk];
+#pragma unroll
+  for (int k = 0; k < kDotChunk; ++k) acc[k] = Op::zero();
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    const Tv wp = Op::ld(w + p);
+    Tv a[kDotChunk];  // all loads issued before the arithmetic
+#pragma unroll
+    for (int k = 0; k < kDotChunk; ++k) a[k] = k < cnt ? Op::ld(V + (size_t)(i0 + k) * N + p) : Op::zero();
+#pragma unroll
+    for (int k = 0; k < kDotChunk; ++k)
+      if (k < cnt) acc[k] = Op::fma(acc[k], wp, a[k]);
+  }
+  const int G = gridDim.x;
+  const double bs = block_sums<Tv, kDotChunk>(acc, cnt, wsum);
+  const int wk = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0 && wk < cnt) partials[(size_t)(i0 + wk) * G + blockIdx.x] = bs;
   if (arrive_last(&st->counter, gridDim.x * gridDim.y)) {
-    for (int i = 0; i <= j; ++i) {
-      const double tot = sum_partials(partials + (size_t)i * G, G, red);
-      if (threadIdx.x == 0) {
+    for (int i = wk; i <= j; i += kWarps) {
+      const double tot = warp_sum_partials(partials + (size_t)i * G, G);
+      if ((threadIdx.x & 31) == 0) {
         const double h = st->s[i] * tot;
         st->hcol[i] = h;
         if (accumulate) st->H[i * kMaxRestart + j] += h;
@@ -124,26 +203,37 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const double* __restri
 }
 
 // V_{j+1} <- V_{j+1} - sum_i (h_i s_i) V_i and ||V_{j+1}||; on the final pass
-// the last block runs the Givens step.
-__global__ void __launch_bounds__(kBlock) update_kernel(double* __restrict__ V, size_t N, int j, int final_pass,
+// the last block runs the Givens step.  The basis vectors are read in groups
+// of kUpdChunk independent loads ahead of the dependent update chain.
+constexpr int kUpdChunk = 8;
+template <typename Tv>
+__global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size_t N, int j, int final_pass,
                                                         double* partials, SolverState* st) {
   if (closed(&st->run_iter)) return;
-  __shared__ double red[32];
-  __shared__ double coef[kMaxRestart + 1];
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) coef[i] = st->hcol[i] * st->s[i];
+  using Op = VecOps<Tv>;
+  __shared__ double wsum[1][kWarps];
+  __shared__ Tv ncoef[kMaxRestart + 1];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) ncoef[i] = Op::from(-(st->hcol[i] * st->s[i]));
   __syncthreads();
-  double* __restrict__ w = V + (size_t)(j + 1) * N;
-  double acc = 0.0;
+  Tv* __restrict__ w = V + (size_t)(j + 1) * N;
+  Tv acc = Op::zero();
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    double val = w[p];
-    for (int i = 0; i <= j; ++i) val -= coef[i] * V[(size_t)i * N + p];
-    w[p] = val;
-    acc += val * val;
+    Tv val = Op::ld(w + p);
+    for (int i0 = 0; i0 <= j; i0 += kUpdChunk) {
+      Tv a[kUpdChunk];  // all loads issued before the dependent chain
+#pragma unroll
+      for (int k = 0; k < kUpdChunk; ++k) a[k] = i0 + k <= j ? Op::ld(V + (size_t)(i0 + k) * N + p) : Op::zero();
+#pragma unroll
+      for (int k = 0; k < kUpdChunk; ++k)
+        if (i0 + k <= j) val = Op::fma(val, ncoef[i0 + k], a[k]);
+    }
+    Op::st(w + p, val);
+    acc = Op::fma(acc, val, val);
   }
-  const double bs = block_sum(acc, red);
+  const double bs = block_sums<Tv, 1>(&acc, 1, wsum);
   if (threadIdx.x == 0) partials[blockIdx.x] = bs;
-  if (arrive_last(&st->counter, gridDim.x)) {
-    const double tot = sum_partials(partials, gridDim.x, red);
+  if (arrive_last(&st->counter, gridDim.x) && threadIdx.x < 32) {
+    const double tot = warp_sum_partials(partials, gridDim.x);
     if (threadIdx.x == 0 && final_pass) givens_step(st, j, sqrt(tot));
   }
 }
@@ -183,13 +273,13 @@ __global__ void finalize_kernel(double* __restrict__ x, size_t N, SolverState* s
 }
 
 // z = scale * v (the identity preconditioner of plain GMRES).
-template <typename Tz>
-__global__ void __launch_bounds__(kBlock) scale_copy_kernel(const double* __restrict__ v, const double* scale,
+template <typename Tv, typename Tz>
+__global__ void __launch_bounds__(kBlock) scale_copy_kernel(const Tv* __restrict__ v, const double* scale,
                                                             Tz* __restrict__ z, size_t N, const int* gate) {
   if (closed(gate)) return;
   const double sc = *scale;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
-    z[p] = Tz(sc * v[p]);
+    z[p] = Tz(sc * cvt<double>(v[p]));
 }
 
 // Condition of the device-side loop over FGMRES cycles (a CUDA graph WHILE
@@ -295,14 +385,36 @@ void launch_rhs(const double* u, const double* uu, const double* src, const uint
 void launch_norm_b(const double* b, size_t N, double* partials, SolverState* st, cudaStream_t s) {
   norm_b_kernel<<<vec_grid(N), kBlock, 0, s>>>(b, N, partials, st);
 }
-void launch_multidot(const double* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
+// Gram-Schmidt grid: the SMs times the resident blocks of the kernel (one
+// full wave), at most vec_grid(N) blocks (the partials buffer's width).
+static int wave_grid(int per_sm, size_t N) {
+  const int g = kNumSMs * per_sm;
+  const int cap = vec_grid(N);
+  return g < cap ? g : cap;
+}
+template <typename K>
+static int resident_blocks(K kernel) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, 0) != cudaSuccess || b < 1) b = 1;
+  return b;
+}
+
+template <typename Tv>
+void launch_multidot(const Tv* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
                      cudaStream_t s) {
-  dim3 grid(vec_grid(N), (j + 1 + kDotChunk - 1) / kDotChunk);
-  multidot_kernel<<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+  static const int per_sm = resident_blocks(multidot_kernel<Tv>);
+  dim3 grid(wave_grid(per_sm, N), (j + 1 + kDotChunk - 1) / kDotChunk);
+  multidot_kernel<Tv><<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
 }
-void launch_update(double* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s) {
-  update_kernel<<<vec_grid(N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st);
+template <typename Tv>
+void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s) {
+  static const int per_sm = resident_blocks(update_kernel<Tv>);
+  update_kernel<Tv><<<wave_grid(per_sm, N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st);
 }
+template void launch_multidot<double>(const double*, size_t, int, int, double*, SolverState*, cudaStream_t);
+template void launch_multidot<df>(const df*, size_t, int, int, double*, SolverState*, cudaStream_t);
+template void launch_update<double>(double*, size_t, int, int, double*, SolverState*, cudaStream_t);
+template void launch_update<df>(df*, size_t, int, int, double*, SolverState*, cudaStream_t);
 void launch_solve_y(SolverState* st, cudaStream_t s) { solve_y_kernel<<<1, 32, 0, s>>>(st); }
 template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s) {
@@ -331,11 +443,15 @@ void launch_finalize(double* x, size_t N, SolverState* st, cudaStream_t s) {
   finalize_kernel<<<vec_grid(N), kBlock, 0, s>>>(x, N, st);
 }
 
-template <typename Tz>
-void launch_scale_copy(const double* v, const double* scale, Tz* z, size_t N, const int* gate, cudaStream_t s) {
-  scale_copy_kernel<Tz><<<vec_grid(N), kBlock, 0, s>>>(v, scale, z, N, gate);
+template <typename Tv, typename Tz>
+void launch_scale_copy(const Tv* v, const double* scale, Tz* z, size_t N, const int* gate, cudaStream_t s) {
+  scale_copy_kernel<Tv, Tz><<<vec_grid(N), kBlock, 0, s>>>(v, scale, z, N, gate);
 }
-template void launch_scale_copy<double>(const double*, const double*, double*, size_t, const int*, cudaStream_t);
-template void launch_scale_copy<float>(const double*, const double*, float*, size_t, const int*, cudaStream_t);
+template void launch_scale_copy<double, double>(const double*, const double*, double*, size_t, const int*,
+                                                cudaStream_t);
+template void launch_scale_copy<double, float>(const double*, const double*, float*, size_t, const int*,
+                                               cudaStream_t);
+template void launch_scale_copy<df, double>(const df*, const double*, double*, size_t, const int*, cudaStream_t);
+template void launch_scale_copy<df, float>(const df*, const double*, float*, size_t, const int*, cudaStream_t);
 
 }  // namespace rsfde

@@ -21,6 +21,9 @@
 //    (S = S_{n2} (x) S_{n1}; proof of Lemma 4.2) in three passes: rows S_x;
 //    columns S_y, the two spectral divides and both inverse S_y; rows S_x
 //    of both channels with the masked combine.
+#include <atomic>
+#include <type_traits>
+
 #include "common.cuh"
 #include "df.cuh"
 #include "fft16.cuh"
@@ -85,6 +88,32 @@ __device__ __forceinline__ void bluestein(cx<T>* v, cx<T>* buf, int t, const Axi
   fft16_inverse<T>(v, buf, t, L, ax.log2L, tw);
 }
 
+// scale * x in the arithmetic type T: FP64 vectors are scaled in FP64 before
+// rounding; double-FP32 vectors feeding an FP32 transform are scaled in FP32,
+// with no FP64 instruction.
+template <typename T>
+__device__ __forceinline__ T scaled_load(double sc, float, double x) {
+  return cvt<T>(sc * x);
+}
+template <typename T>
+__device__ __forceinline__ T scaled_load(double sc, float scf, df x);
+template <>
+__device__ __forceinline__ float scaled_load<float>(double, float scf, df x) {
+  return __fmul_rn(scf, cvt<float>(x));
+}
+template <>
+__device__ __forceinline__ double scaled_load<double>(double sc, float, df x) {
+  return sc * double(x);
+}
+template <>
+__device__ __forceinline__ df scaled_load<df>(double sc, float, df x) {
+  return df(sc) * x;
+}
+template <typename T>
+__device__ __forceinline__ T scaled_load(double sc, float, float x) {
+  return cvt<T>(sc * (double)x);
+}
+
 // Im(c_out[pos] * y)
 template <typename T>
 __device__ __forceinline__ T dst_out(const AxisTables<T>& ax, int pos, cx<T> y) {
@@ -99,12 +128,13 @@ __device__ __forceinline__ T dst_out(const AxisTables<T>& ax, int pos, cx<T> y) 
 //   MODE_APPLY:    out = z - tmpx - A_y z + (dt/eta) phi z
 //   MODE_RESIDUAL: out = b - (z - tmpx - A_y z + (dt/eta) phi z), ||out||^2
 //                  reduced, and the last block restarts the solver.
-template <typename T, typename Tin, int MODE, bool COLS>
+template <typename T, typename Tin, int MODE, bool COLS, typename Tout>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
     toeplitz_kernel(const Tin* __restrict__ z, T* __restrict__ tmpx, const uint8_t* __restrict__ phi,
-                    double pen, const double* __restrict__ b, double* __restrict__ out, int n1, int n2,
+                    double pen, const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2,
                     AxisTables<T> ax, int F, int gstride, const int* gate, double* partials, SolverState* st) {
   if (gate_closed<T>(gate)) return;
+  const T tpen = cvt<T>(pen);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   const int L = ax.L, Lq = L >> 4, G = Lq;
@@ -125,8 +155,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
       const int pos = gi.t + k * Lq;
       T re = T(0), im = T(0);
       if (live && pos < len) {
-        re = T(z[vaddr<COLS>(a, pos, n1)]);
-        if (second) im = T(z[vaddr<COLS>(a + 1, pos, n1)]);
+        re = cvt<T>(z[vaddr<COLS>(a, pos, n1)]);
+        if (second) im = cvt<T>(z[vaddr<COLS>(a + 1, pos, n1)]);
       }
       v[k] = {re, im};
     }
@@ -152,19 +182,19 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
           if (!COLS) {
             tmpx[p] = az;  // A_x z, kept in the arithmetic type T
           } else {
-            // z - A_x z - A_y z + (dt/eta) phi z in T; only the result is rounded to FP64
-            const T zz = T(z[p]);
+            // z - A_x z - A_y z + (dt/eta) phi z in T; only the result is rounded to Tout
+            const T zz = cvt<T>(z[p]);
             T w = zz - tmpx[p] - az;
-            if (phi[p]) w = w + T(pen) * zz;
+            if (phi[p]) w = w + tpen * zz;
             if (MODE == MODE_RAW) {
-              out[p] = double(az);
+              out[p] = cvt<Tout>(az);
             } else if (MODE == MODE_APPLY) {
-              out[p] = double(w);
+              out[p] = cvt<Tout>(w);
             } else if (MODE == MODE_RESID_ONLY) {
-              out[p] = b[p] - double(w);
+              out[p] = cvt<Tout>(b[p] - cvt<double>(w));
             } else {
-              const double r = b[p] - double(w);
-              out[p] = r;
+              const double r = b[p] - cvt<double>(w);
+              out[p] = cvt<Tout>(r);
               acc += r * r;
             }
           }
@@ -194,6 +224,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
   const int nvec = COLS ? n1 : n2, len = COLS ? n2 : n1;
   const double sc = vscale ? *vscale : 1.0;
+  const float scf = (float)sc;
   const int ngroups = (nvec + F - 1) / F;
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const int vec = grp * F + gi.g;
@@ -204,7 +235,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
       const int pos = gi.t + k * Lq;
       cx<T> x = {T(0), T(0)};
       if (live && pos < len) {
-        const T xv = T(sc * double(in[vaddr<COLS>(vec, pos, n1)]));
+        const T xv = scaled_load<T>(sc, scf, in[vaddr<COLS>(vec, pos, n1)]);
         const cx<T> c = ldc(ax.chirp, pos);
         x = {xv * c.r, xv * c.i};
       }
@@ -419,52 +450,69 @@ void launch_toeplitz_rows(const Tin* z, void* tmpx, int n1, int n2, const AxisTa
   const int npairs = (n2 + 1) / 2;
   const int F = pick_groups<T>(ax.L, npairs, TK_TOEP_ROWS);
   const size_t sm = group_smem<T>(ax.L, F, false);
-  auto k = toeplitz_kernel<T, Tin, MODE_APPLY, false>;
+  auto k = toeplitz_kernel<T, Tin, MODE_APPLY, false, double>;
   set_smem(k, sm);
   k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), nullptr, 0.0, nullptr, nullptr,
                                                       n1, n2, ax, F, group_stride<T>(ax.L, F, false), gate,
                                                       nullptr, nullptr);
 }
 
-template <typename T, typename Tin>
+static std::atomic<int> g_unsupported{0};
+void note_unsupported_launch() { g_unsupported.store(1); }
+bool take_unsupported_launch() { return g_unsupported.exchange(0) != 0; }
+
+// Only the combinations the solver uses are instantiated: double-FP32
+// arithmetic runs the operator (MODE_APPLY) alone; residuals and the raw
+// Toeplitz products are FP64.
+template <typename T, typename Tin, typename Tout>
 void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi, double pen,
-                          const double* b, double* out, int n1, int n2, const AxisTables<T>& ay,
+                          const double* b, Tout* out, int n1, int n2, const AxisTables<T>& ay,
                           const int* gate, double* partials, SolverState* st, cudaStream_t s) {
   const int npairs = (n1 + 1) / 2;
   const int F = pick_groups<T>(ay.L, npairs, TK_TOEP_COLS);
   const size_t sm = group_smem<T>(ay.L, F, true);
   const int gs = group_stride<T>(ay.L, F, true);
   int grid = (npairs + F - 1) / F;
-  if (mode == MODE_RESID_ONLY) {
-    auto k = toeplitz_kernel<T, Tin, MODE_RESID_ONLY, true>;
-    set_smem(k, sm);
-    k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
-                                        partials, st);
-  } else if (mode == MODE_RAW) {
-    auto k = toeplitz_kernel<T, Tin, MODE_RAW, true>;
-    set_smem(k, sm);
-    k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
-                                        partials, st);
-  } else if (mode == MODE_APPLY) {
-    auto k = toeplitz_kernel<T, Tin, MODE_APPLY, true>;
-    set_smem(k, sm);
-    k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
-                                        partials, st);
-  } else {
-    if (grid > kMaxPartials) grid = kMaxPartials;
-    auto k = toeplitz_kernel<T, Tin, MODE_RESIDUAL, true>;
-    set_smem(k, sm);
-    k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
-                                        partials, st);
+  constexpr bool fp64_modes = std::is_same<T, double>::value && std::is_same<Tin, double>::value;
+  constexpr bool apply_mode = !std::is_same<T, double>::value || std::is_same<Tout, double>::value;
+  if constexpr (fp64_modes) {
+    if (mode == MODE_RESIDUAL) {
+      if (grid > kMaxPartials) grid = kMaxPartials;
+      auto k = toeplitz_kernel<T, Tin, MODE_RESIDUAL, true, Tout>;
+      set_smem(k, sm);
+      k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
+                                          partials, st);
+      return;
+    }
+    if constexpr (std::is_same<Tout, double>::value) {
+      if (mode == MODE_RESID_ONLY || mode == MODE_RAW) {
+        auto k = mode == MODE_RAW ? toeplitz_kernel<T, Tin, MODE_RAW, true, Tout>
+                                  : toeplitz_kernel<T, Tin, MODE_RESID_ONLY, true, Tout>;
+        set_smem(k, sm);
+        k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
+                                            partials, st);
+        return;
+      }
+    }
   }
+  if constexpr (apply_mode) {
+    if (mode == MODE_APPLY) {
+      auto k = toeplitz_kernel<T, Tin, MODE_APPLY, true, Tout>;
+      set_smem(k, sm);
+      k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
+                                          partials, st);
+      return;
+    }
+  }
+  note_unsupported_launch();  // no kernel for this combination: reported as RSFDE_EINVAL
 }
 
-template <typename T, typename Tout>
-void launch_dst_rows(const double* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
+template <typename T, typename Tin, typename Tout>
+void launch_dst_rows(const Tin* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
                      const int* gate, cudaStream_t s) {
   const int F = pick_groups<T>(ax.L, n2, TK_DST_ROWS);
   const size_t sm = group_smem<T>(ax.L, F, false);
-  auto k = dst_kernel<T, double, Tout, false>;
+  auto k = dst_kernel<T, Tin, Tout, false>;
   set_smem(k, sm);
   k<<<(n2 + F - 1) / F, F * (ax.L / 16), sm, s>>>(v, vscale, out, n1, n2, ax, F, group_stride<T>(ax.L, F, false),
                                                   gate);
@@ -510,28 +558,31 @@ template void launch_toeplitz_rows<double, double>(const double*, void*, int, in
                                                    const int*, cudaStream_t);
 template void launch_toeplitz_rows<double, float>(const float*, void*, int, int, const AxisTables<double>&,
                                                   const int*, cudaStream_t);
-template void launch_toeplitz_cols<double, double>(int, const double*, void*, const uint8_t*, double,
-                                                   const double*, double*, int, int, const AxisTables<double>&,
-                                                   const int*, double*, SolverState*, cudaStream_t);
-template void launch_toeplitz_cols<double, float>(int, const float*, void*, const uint8_t*, double,
-                                                  const double*, double*, int, int, const AxisTables<double>&,
-                                                  const int*, double*, SolverState*, cudaStream_t);
+#define RSFDE_TOEP_COLS(T, Tin, Tout)                                                                  \
+  template void launch_toeplitz_cols<T, Tin, Tout>(int, const Tin*, void*, const uint8_t*, double, const double*, \
+                                                   Tout*, int, int, const AxisTables<T>&, const int*, double*,    \
+                                                   SolverState*, cudaStream_t);
+RSFDE_TOEP_COLS(double, double, double)
+RSFDE_TOEP_COLS(double, float, double)
+RSFDE_TOEP_COLS(double, double, df)
+RSFDE_TOEP_COLS(df, double, double)
+RSFDE_TOEP_COLS(df, float, double)
+RSFDE_TOEP_COLS(df, double, df)
+RSFDE_TOEP_COLS(df, float, df)
+#undef RSFDE_TOEP_COLS
 template void launch_toeplitz_rows<df, double>(const double*, void*, int, int, const AxisTables<df>&,
                                                const int*, cudaStream_t);
 template void launch_toeplitz_rows<df, float>(const float*, void*, int, int, const AxisTables<df>&,
                                               const int*, cudaStream_t);
-template void launch_toeplitz_cols<df, double>(int, const double*, void*, const uint8_t*, double,
-                                               const double*, double*, int, int, const AxisTables<df>&,
-                                               const int*, double*, SolverState*, cudaStream_t);
-template void launch_toeplitz_cols<df, float>(int, const float*, void*, const uint8_t*, double,
-                                              const double*, double*, int, int, const AxisTables<df>&,
-                                              const int*, double*, SolverState*, cudaStream_t);
-template void launch_dst_rows<double, double>(const double*, const double*, double*, int, int,
-                                              const AxisTables<double>&, const int*, cudaStream_t);
-template void launch_dst_rows<float, float>(const double*, const double*, float*, int, int,
-                                            const AxisTables<float>&, const int*, cudaStream_t);
-template void launch_dst_rows<double, float>(const double*, const double*, float*, int, int,
-                                             const AxisTables<double>&, const int*, cudaStream_t);
+#define RSFDE_DST_ROWS(T, Tin, Tout)                                                                        \
+  template void launch_dst_rows<T, Tin, Tout>(const Tin*, const double*, Tout*, int, int, const AxisTables<T>&, \
+                                              const int*, cudaStream_t);
+RSFDE_DST_ROWS(double, double, double)
+RSFDE_DST_ROWS(float, double, float)
+RSFDE_DST_ROWS(double, double, float)
+RSFDE_DST_ROWS(double, df, double)
+RSFDE_DST_ROWS(float, df, float)
+#undef RSFDE_DST_ROWS
 template void launch_dst_cols<double, double, double>(const double*, double*, int, int, const AxisTables<double>&,
                                                       cudaStream_t);
 template void launch_precond_cols<double>(const double*, double*, double*, int, int, const AxisTables<double>&,
