@@ -34,6 +34,16 @@ sys.path.insert(0, ROOT)
 METRIC = "implicit steps/s at 2048² grid, rel.res 1e-10: mixed vs FP64; % HBM roofline"
 UNIT = "steps/s"
 WORKLOAD = "polygon2048"
+FORM_TEXT = {
+    ("fp32", "df32"): "mixed: preconditioner FP32, Arnoldi operator and Krylov basis double-FP32; true "
+                      "residual, Hessenberg and Givens FP64",
+    ("fp32", "fp32"): "mixed: preconditioner, Arnoldi operator and Krylov basis FP32; true residual, "
+                      "Hessenberg and Givens FP64",
+    ("bf16x3", "fp32"): "mixed: preconditioner split-BF16 on tensor cores, Arnoldi operator and Krylov basis "
+                        "FP32; true residual, Hessenberg and Givens FP64",
+    ("bf16", "fp32"): "mixed: preconditioner BF16 on tensor cores (FP32 accumulation), Arnoldi operator and "
+                      "Krylov basis FP32; true residual, Hessenberg and Givens FP64",
+}
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
 # the kernel classes, with the hash of the CUDA sources they were taken from;
@@ -120,16 +130,17 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ our arm ------
-def algorithmic_bytes_per_iter(N, m, ez):
+def algorithmic_bytes_per_iter(N, m, ez, ev=8):
     """Minimal HBM bytes of one FGMRES(m) iteration, averaged over a cycle:
     precond read v / write z, matvec read z / write w, CGS dots and update over
-    the j+1 basis vectors (8N(2j+4)), the mask, and the per-cycle x update
-    and true residual spread over m iterations."""
-    cgs = 8 * N * (m - 1 + 4)           # mean over j = 0..m-1 of 8N(2j+4)
-    pre = (8 + ez) * N
-    mv = (ez + 8) * N
+    the j+1 basis vectors (ev N (2j+4), ev = bytes per basis element), the
+    mask, and the per-cycle x update and true residual spread over m
+    iterations."""
+    cgs = ev * N * (m - 1 + 4)          # mean over j = 0..m-1 of ev N (2j+4)
+    pre = (ev + ez) * N
+    mv = (ez + ev) * N
     mask = N / 8
-    cyc = ((ez * m + 16) * N + 32 * N) / m
+    cyc = ((ez * m + 16) * N + (24 + ev) * N) / m
     return pre + mv + cgs + mask + cyc
 
 
@@ -154,6 +165,9 @@ def kernel_units(name, n1, n2, L1, L2):
         return n1 * 3 * dst(n2)
     if name == "precond_rows":
         return n2 * 2 * dst(n1)
+    if name.startswith("dst_gemm"):  # one preconditioner apply: the six GEMM-equivalents of Eq. 4.6
+        nt = 3 if name.endswith("bf16x3") else 1
+        return nt * 2.0 * 3 * (n1 * n1 * n2 + n1 * n2 * n2)
     return None
 
 
@@ -259,10 +273,13 @@ def run_ours(args, rank, world, local_rank):
     # headline: the mixed form (FP32 preconditioner) with the double-FP32
     # Arnoldi operator; beside it the same with an FP64 operator and the plain
     # FP64 form, each marched from the same u0 over the same steps
-    mixed = timed_form("fp32", "df32", args.steps, args.warmup, args.profile_steps, clocks)
+    mixed = timed_form(args.precond, args.matvec, args.steps, args.warmup, args.profile_steps, clocks)
+    head = f"{args.precond}+{args.matvec}"
     others = {}
     if not args.only_headline:
-        others["bf16x3+df32"] = timed_form("bf16x3", "df32", args.steps, args.warmup, args.profile_steps)
+        for pre, mv in (("bf16", args.matvec), ("bf16x3", args.matvec), ("fp32", args.matvec), ("fp32", "df32")):
+            if f"{pre}+{mv}" != head and f"{pre}+{mv}" not in others:
+                others[f"{pre}+{mv}"] = timed_form(pre, mv, args.steps, args.warmup, args.profile_steps)
     if not args.no_fp64 and not args.only_headline:
         others["fp32_op64"] = timed_form("fp32", "fp64", args.steps, args.warmup, args.profile_steps)
         others["fp64"] = timed_form("fp64", "fp64", args.fp64_steps, args.warmup, args.profile_steps)
@@ -288,9 +305,19 @@ def run_ours(args, rank, world, local_rank):
         # convergence are counted in the time (a few microseconds each)
         work = iters_p + (cycles_p + mixed["prof"]["steps"] if dom.startswith("toeplitz") else 0)
         avg_ms = tot_ms / max(work, 1)
-        flops = kernel_units(dom, n1, n2, L1, L2)
+        flops = kernel_units(dom if dom != "dst_gemm" else f"dst_gemm_{mixed['precond']}", n1, n2, L1, L2)
         sm_max = peaks.get("sm_max_mhz", 2070.0)
-        if dom.startswith("toeplitz") and mixed["matvec"] == "df32":
+        bound = "alu"
+        if dom == "dst_gemm":
+            # tensor cores, timed inside a long step: the sustained measured BF16 rate
+            bound, prec_name = "tensor", mixed["precond"]
+            peak = 1e3 * peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+            kpeak_src = ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16 GEMM back to back)"
+                         if "bf16_tflops_sustained" in peaks else "MEASURED_PEAKS.json bf16_tflops")
+        elif dom.startswith("toeplitz") and mixed["matvec"] == "fp32":
+            prec_name, peak = "fp32", fp32_peak_gflops(sm_max)
+            kpeak_src = "152 SMs x 128 FFMA/clk x 2 x sm_max_mhz (derived)"
+        elif dom.startswith("toeplitz") and mixed["matvec"] == "df32":
             # double-FP32: each algorithmic flop costs ~10 FP32 operations
             # (df.cuh: sloppy add 10, product 6, the FFT is mostly additions)
             prec_name, peak = "df32", fp32_peak_gflops(sm_max) / 10.0
@@ -304,8 +331,8 @@ def run_ours(args, rank, world, local_rank):
         achieved = flops / (avg_ms / 1e3) / 1e9 if flops else None
         tr = TRAFFIC.get(dom)
         traffic = tr["bytes_per_launch"] if tr and tr.get("src") == src_hash() else None
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 2) if achieved else None,
-                "peak": round(peak, 1), "unit": "GFLOP/s",
+        roof = {"kernel": dom, "bound": bound, "achieved": round(achieved / 1e3, 3) if achieved else None,
+                "peak": round(peak / 1e3, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,
                 "precision": prec_name, "peak_source": kpeak_src,
                 "avg_launch_ms": round(avg_ms, 4), "launches_with_work": work,
@@ -313,8 +340,9 @@ def run_ours(args, rank, world, local_rank):
                 "per_kernel_ms": {k: round(v[0], 3) for k, v in kern.items()},
                 "per_kernel_launches": {k: v[1] for k, v in kern.items()}}
     # whole-step HBM roofline (the metric's "% HBM roofline")
-    ez = 4
-    bpi = algorithmic_bytes_per_iter(N, w["restart"], ez)
+    ez = 4 if mixed["precond"] != "fp64" else 8
+    ev = {"fp32": 4, "df32": 8, "fp64": 8}[mixed["matvec"]]
+    bpi = algorithmic_bytes_per_iter(N, w["restart"], ez, ev)
     bytes_step = mixed["iters_per_step"] * bpi + 40 * N
     ach_gbs = bytes_step / (mixed["ms"] / mixed["steps"] / 1e3) / 1e9
     hbm = {"algorithmic_bytes_per_step": bytes_step, "achieved_GBs": round(ach_gbs, 1),
@@ -359,13 +387,13 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded 12-gon domain, bump initial field)",
         "config": {"workload": f"{WORKLOAD}: {n1}x{n2} grid, convex 12-gon, alpha=(1.3,1.6), k=(1,1), "
                                f"dt=0.02, eta=1e-8, FGMRES({w['restart']}), tol 1e-10",
-                   "form": "mixed: preconditioner FP32, Arnoldi operator double-FP32; true residual, "
-                           "Arnoldi orthogonalisation, Givens FP64",
+                   "form": FORM_TEXT.get((args.precond, args.matvec), f"{args.precond}+{args.matvec}"),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "working set > L2 (Krylov basis 41 vectors x 33.5 MB)"},
+                   "l2": f"working set > L2 (Krylov basis {w['restart'] + 1} and preconditioned basis "
+                         f"{w['restart']} vectors of {N / 1e6:.1f} M values)"},
         "iters_per_step": round(mixed["iters_per_step"], 2),
         "max_rel_res": mixed["max_rel_res"], "all_converged": mixed["all_converged"],
-        "forms": {"fp32+df32": {"steps_per_s": round(value / world, 4),
+        "forms": {head: {"steps_per_s": round(value / world, 4),
                                 "iters_per_step": round(mixed["iters_per_step"], 2),
                                 "ms_per_step": round(mixed["ms"] / args.steps, 3)}},
         "hbm_roofline_step": hbm,
@@ -389,7 +417,7 @@ def run_ours(args, rank, world, local_rank):
                 (a - b).abs().max() / b.abs().max())
     if plain is not None:
         res["forms"]["speedup_headline_over_fp64"] = round(
-            res["forms"]["fp32+df32"]["steps_per_s"] / res["forms"]["fp64"]["steps_per_s"], 3)
+            res["forms"][head]["steps_per_s"] / res["forms"]["fp64"]["steps_per_s"], 3)
     return res
 
 
@@ -473,15 +501,14 @@ def run_op(args):
     import torch
     from paper_2102_11576_gb300 import Solver, workloads
     w = workloads.make(args.workload)
-    prec = "fp64" if args.op.endswith("fp64") else ("bf16x3" if args.op.endswith("bf16x3") else "fp32")
-    matvec = "df32" if args.op.endswith("df32") else "fp64"
+    prec = args.op.split("_")[1] if args.op.startswith("precond_") else "fp64"
+    matvec = args.op.split("_")[2] if args.op.startswith("apply_M_") else "fp64"
     s = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
                w["dt"], w["eta"], restart=w["restart"], precond=prec, matvec=matvec)
     rng = np.random.default_rng(0)
     v = torch.as_tensor(rng.standard_normal((w["n2"], w["n1"]))).cuda()
     out = torch.empty_like(v)
-    fn = {"apply_M": s.apply_M, "apply_M_df32": s.apply_M, "precond_fp32": s.apply_precond,
-          "precond_fp64": s.apply_precond, "precond_bf16x3": s.apply_precond, "dst2": s.dst2}[args.op]
+    fn = s.dst2 if args.op == "dst2" else (s.apply_M if args.op.startswith("apply_M") else s.apply_precond)
     fn(v, out)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -579,8 +606,8 @@ def main():
     ap.add_argument("--batch-precond", default="fp32")
     ap.add_argument("--adjoint", action="store_true",
                     help="time one differentiable march of the 1024^2 differentiation workload")
-    ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "precond_fp32", "precond_fp64", "precond_bf16x3",
-                                     "dst2"],
+    ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "apply_M_fp32", "precond_fp32", "precond_fp64",
+                                     "precond_bf16x3", "precond_bf16", "dst2"],
                     default=None,
                     help="time one operator entry point instead of the time march")
     ap.add_argument("--reps", type=int, default=5)
@@ -600,6 +627,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the heuristic tile shapes")
     ap.add_argument("--only-headline", action="store_true", help="time the headline form only")
+    ap.add_argument("--precond", choices=["fp32", "bf16", "bf16x3", "fp64"], default="bf16",
+                    help="preconditioner precision of the headline form")
+    ap.add_argument("--matvec", choices=["fp32", "df32", "fp64"], default="fp32",
+                    help="Arnoldi operator (and Krylov basis) precision of the headline form")
     ap.add_argument("--no-graph", action="store_true",
                     help="direct kernel launches instead of the graph loop (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")

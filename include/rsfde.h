@@ -46,14 +46,20 @@ extern "C" {
 #define RSFDE_ETIMEOUT (-6)    /* a bounded device-side wait gave up */
 
 /* Precisions.  The preconditioner apply (Eq. 4.6) runs in RSFDE_FP64,
- * RSFDE_FP32 or RSFDE_BF16X3; the operator applied to the Arnoldi vectors in RSFDE_FP64 or
- * RSFDE_DF32.  The true residual, the Arnoldi orthogonalisation and the
- * Givens least squares are FP64 in every mode. */
+ * RSFDE_FP32, RSFDE_BF16X3 or RSFDE_BF16; the operator applied to the Arnoldi
+ * vectors (and, in right-preconditioned FGMRES, the Krylov basis) in
+ * RSFDE_FP64, RSFDE_DF32 or RSFDE_FP32.  The true residual, the Hessenberg
+ * matrix and the Givens least squares are FP64 in every mode; flexible GMRES
+ * tolerates the inexact preconditioner, and convergence is always decided by
+ * the FP64 true residual. */
 #define RSFDE_FP64 0
 #define RSFDE_FP32 1
 /* Preconditioner sine transforms as tensor-core GEMMs in split BF16
  * (X = X_hi + X_lo; X_hi S_hi + X_hi S_lo + X_lo S_hi with FP32 accumulation). */
 #define RSFDE_BF16X3 3
+/* Preconditioner sine transforms as tensor-core GEMMs in plain BF16 (one
+ * product X_hi S_hi with FP32 accumulation; about 3 significant digits). */
+#define RSFDE_BF16 4
 /* Operator M applied to the Arnoldi vectors in double-FP32 arithmetic (pairs
  * of FP32 numbers, ~48-bit significand, error-free transforms of Dekker and
  * Knuth).  The true residual b - M x is always computed in FP64. */
@@ -85,10 +91,12 @@ typedef struct {
   int32_t restart;      /* m of FGMRES(m); Section 5 uses 20.  1..64 */
   int32_t max_iter;     /* cap on inner iterations per solve */
   double tol;           /* stop when ||b - M x||_2 <= tol ||b||_2 */
-  int32_t precond_prec; /* RSFDE_FP64 | RSFDE_FP32 | RSFDE_BF16X3 */
+  int32_t precond_prec; /* RSFDE_FP64 | RSFDE_FP32 | RSFDE_BF16X3 | RSFDE_BF16 */
   int32_t arnoldi;      /* RSFDE_CGS | RSFDE_CGS2 */
   int32_t use_precond;  /* 1: P-hat of Eq. 4.6; 0: unpreconditioned GMRES */
-  int32_t matvec_prec;  /* RSFDE_FP64 | RSFDE_DF32: M applied to the Arnoldi vectors */
+  int32_t matvec_prec;  /* RSFDE_FP64 | RSFDE_DF32 | RSFDE_FP32: M applied to the Arnoldi vectors, and
+                           (right-preconditioned FGMRES) the Krylov basis's storage and Gram-Schmidt
+                           arithmetic.  The true residual that decides convergence is always FP64. */
   int32_t variant;      /* RSFDE_FGMRES_RIGHT | RSFDE_GMRES_LEFT */
   int32_t use_graph;    /* 1: the cycles of a solve replay as one CUDA graph with a device-side
                            loop (one host synchronisation per solve); 0: direct launches with

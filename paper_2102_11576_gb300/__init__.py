@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(_HERE, "librsfde.so")
 
 FP64, FP32, DF32 = 0, 1, 2
 _VARIANTS = {"fgmres_right": 0, "gmres_left": 1}
-_PRECONDS = {"fp64": 0, "fp32": 1, "bf16x3": 3}
+_PRECONDS = {"fp64": 0, "fp32": 1, "bf16x3": 3, "bf16": 4}
+_MATVECS = {"fp64": FP64, "df32": DF32, "fp32": FP32}
 CGS, CGS2 = 0, 1
 _ERR = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV", -5: "ENONFINITE",
         -6: "ETIMEOUT"}
@@ -158,7 +159,7 @@ class Solver:
         o.precond_prec = _PRECONDS[precond]
         o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
         o.use_precond = int(bool(use_precond))
-        o.matvec_prec = {"fp64": FP64, "df32": DF32}[matvec]
+        o.matvec_prec = _MATVECS[matvec]
         o.variant = _VARIANTS[variant]
         o.use_graph = int(bool(use_graph))
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
@@ -207,7 +208,7 @@ class Solver:
             elif k == "use_precond":
                 o.use_precond = int(bool(v))
             elif k == "matvec":
-                o.matvec_prec = {"fp64": FP64, "df32": DF32}[v]
+                o.matvec_prec = _MATVECS[v]
             elif k == "use_graph":
                 o.use_graph = int(bool(v))
             elif k == "variant":
@@ -365,7 +366,7 @@ class Batch:
         lib.rsfde_opts_default(ctypes.byref(o))
         o.restart, o.max_iter, o.tol = int(restart), int(max_iter), float(tol)
         o.precond_prec = _PRECONDS[precond]
-        o.matvec_prec = {"fp64": FP64, "df32": DF32}[matvec]
+        o.matvec_prec = _MATVECS[matvec]
         o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         h = ctypes.c_void_p()

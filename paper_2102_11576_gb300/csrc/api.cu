@@ -321,20 +321,32 @@ void free_ctx(rsfde_ctx* c) {
 
 // Z (the preconditioned vectors) is FP32 for the FP32 and split-BF16 preconditioners.
 bool fp32_precond(const rsfde_ctx* c) {
-  return c->opts.precond_prec == RSFDE_FP32 || c->opts.precond_prec == RSFDE_BF16X3;
+  const int p = c->opts.precond_prec;
+  return p == RSFDE_FP32 || p == RSFDE_BF16X3 || p == RSFDE_BF16;
 }
-bool bf16_precond_on(const rsfde_ctx* c) { return c->opts.precond_prec == RSFDE_BF16X3; }
+bool bf16_precond_on(const rsfde_ctx* c) {
+  return c->opts.precond_prec == RSFDE_BF16X3 || c->opts.precond_prec == RSFDE_BF16;
+}
 
+// The tensor-core plan of the current preconditioner precision (three BF16
+// products per GEMM for BF16X3, one for BF16).
 int ensure_bf16(rsfde_ctx* c) {
-  if (c->bf16 || !bf16_precond_on(c)) return RSFDE_OK;
-  return bf16_plan_create(&c->bf16, c->n1, c->n2, c->x32.tab.lam, c->y32.tab.lam, c->stream);
+  if (!bf16_precond_on(c)) return RSFDE_OK;
+  const int nt = c->opts.precond_prec == RSFDE_BF16X3 ? 3 : 1;
+  if (c->bf16 && bf16_plan_nt(c->bf16) == nt) return RSFDE_OK;
+  if (c->bf16) {
+    cudaStreamSynchronize(c->stream);
+    bf16_plan_destroy(c->bf16);
+    c->bf16 = nullptr;
+  }
+  return bf16_plan_create(&c->bf16, c->n1, c->n2, nt, c->x32.tab.lam, c->y32.tab.lam, c->stream);
 }
 
 // The tensor-core preconditioner z = P-hat^-1 (scale * v) (five launches).
 template <typename Tz, typename Tin>
 void enqueue_precond_bf16(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate) {
   ProfScope ps(c, RSFDE_K_DST_GEMM);
-  c->launches += 4;
+  c->launches += 5;
   bf16_precond<Tz, Tin>(c->bf16, v, vscale, z, c->phi, c->pen, gate, c->stream);
 }
 
@@ -358,15 +370,25 @@ void enqueue_apply_M_t(rsfde_ctx* c, const Tz* z, Tw* w, const int* gate, const 
 template <typename Tz>
 void enqueue_apply_M(rsfde_ctx* c, const Tz* z, double* w, const int* gate) {
   if (c->opts.matvec_prec == RSFDE_DF32) enqueue_apply_M_t<df, Tz, double>(c, z, w, gate, c->xdf.tab, c->ydf.tab);
+  else if (c->opts.matvec_prec == RSFDE_FP32)
+    enqueue_apply_M_t<float, Tz, double>(c, z, w, gate, c->x32.tab, c->y32.tab);
   else enqueue_apply_M_t<double, Tz, double>(c, z, w, gate, c->x64.tab, c->y64.tab);
 }
 
 bool left_variant(const rsfde_ctx* c) { return c->opts.variant == RSFDE_GMRES_LEFT; }
 
-// The right-preconditioned FGMRES keeps its Krylov basis in double-FP32 when
-// the Arnoldi operator runs in double-FP32 (the operator's output is then
-// stored without rounding to FP64, and the Gram-Schmidt runs on the FP32 pipe).
-bool df_basis(const rsfde_ctx* c) { return c->opts.matvec_prec == RSFDE_DF32 && !left_variant(c); }
+// The right-preconditioned FGMRES keeps its Krylov basis in the Arnoldi
+// operator's precision (FP64, double-FP32 or FP32): the operator's output is
+// stored without a conversion, and with 4- or 8-byte FP32-pipe arithmetic the
+// Gram-Schmidt needs no FP64 instruction per element.  Paper mode keeps FP64.
+enum BasisKind { BASIS_FP64, BASIS_DF32, BASIS_FP32 };
+BasisKind basis_kind(const rsfde_ctx* c) {
+  if (left_variant(c)) return BASIS_FP64;
+  if (c->opts.matvec_prec == RSFDE_DF32) return BASIS_DF32;
+  if (c->opts.matvec_prec == RSFDE_FP32) return BASIS_FP32;
+  return BASIS_FP64;
+}
+bool df_basis(const rsfde_ctx* c) { return basis_kind(c) == BASIS_DF32; }
 
 template <typename T, typename Tz, typename Tin>
 void enqueue_precond_t(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate,
@@ -423,10 +445,14 @@ void enqueue_residual(rsfde_ctx* c, const int* gate) {
   }
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
-    if (df_basis(c))
+    if (basis_kind(c) == BASIS_DF32)
       launch_toeplitz_cols<double, double, df>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
                                                reinterpret_cast<df*>(c->V), c->n1, c->n2, c->y64.tab, gate,
                                                c->partials, c->st, c->stream);
+    else if (basis_kind(c) == BASIS_FP32)
+      launch_toeplitz_cols<double, double, float>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
+                                                  reinterpret_cast<float*>(c->V), c->n1, c->n2, c->y64.tab, gate,
+                                                  c->partials, c->st, c->stream);
     else
       launch_toeplitz_cols<double, double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1,
                                                    c->n2, c->y64.tab, gate, c->partials, c->st, c->stream);
@@ -491,6 +517,8 @@ void enqueue_cycle_t(rsfde_ctx* c) {
     }
     Tv* w = V + (size_t)(j + 1) * N;
     if constexpr (std::is_same<Tv, df>::value) enqueue_apply_M_t<df, Tz, df>(c, zj, w, gi, c->xdf.tab, c->ydf.tab);
+    else if constexpr (std::is_same<Tv, float>::value)
+      enqueue_apply_M_t<float, Tz, float>(c, zj, w, gi, c->x32.tab, c->y32.tab);
     else enqueue_apply_M<Tz>(c, zj, w, gi);
     const bool cgs2 = c->opts.arnoldi == RSFDE_CGS2;
     for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
@@ -556,9 +584,12 @@ void enqueue_cycle_left(rsfde_ctx* c) {
 
 void enqueue_cycle(rsfde_ctx* c) {
   if (left_variant(c)) enqueue_cycle_left(c);
-  else if (df_basis(c)) {
+  else if (basis_kind(c) == BASIS_DF32) {
     if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float, df>(c);
     else enqueue_cycle_t<double, df>(c);
+  } else if (basis_kind(c) == BASIS_FP32) {
+    if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float, float>(c);
+    else enqueue_cycle_t<double, float>(c);
   } else if (fp32_precond(c) && c->opts.use_precond) enqueue_cycle_t<float, double>(c);
   else enqueue_cycle_t<double, double>(c);
 }
@@ -705,12 +736,12 @@ int tune_one(rsfde_ctx* c, int kind, int L, int items, int reps, Fn run) {
   return best;
 }
 
-// Times the operator in the types the solver uses: FP64 z and w, or (double-
-// FP32 arithmetic) an FP32 z and a double-FP32 w.
+// Times the operator in the types the solver uses: FP64 z and w, or (FP32 or
+// double-FP32 arithmetic) an FP32 z and a w of the arithmetic type.
 template <typename T>
 void tune_operator(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTables<T>& ty, int* chosen) {
-  using Tz = typename std::conditional<std::is_same<T, df>::value, float, double>::type;
-  using Tw = typename std::conditional<std::is_same<T, df>::value, df, double>::type;
+  using Tz = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  using Tw = T;
   const Tz* z = reinterpret_cast<const Tz*>(c->V);
   Tw* w = reinterpret_cast<Tw*>(c->V + c->N);
   chosen[TK_TOEP_ROWS] = tune_one<T>(c, TK_TOEP_ROWS, tx.L, (c->n2 + 1) / 2, reps, [&] {
@@ -728,8 +759,12 @@ void tune_precond(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTab
   T* t2a = static_cast<T*>(c->T2a);
   T* t2b = static_cast<T*>(c->T2b);
   chosen[TK_DST_ROWS] = tune_one<T>(c, TK_DST_ROWS, tx.L, c->n2, reps, [&] {
-    if (df_basis(c)) launch_dst_rows<T, df, T>(reinterpret_cast<const df*>(c->V), nullptr, t1, c->n1, c->n2, tx,
-                                               nullptr, c->stream);
+    if (basis_kind(c) == BASIS_DF32)
+      launch_dst_rows<T, df, T>(reinterpret_cast<const df*>(c->V), nullptr, t1, c->n1, c->n2, tx, nullptr,
+                                c->stream);
+    else if (basis_kind(c) == BASIS_FP32)
+      launch_dst_rows<T, float, T>(reinterpret_cast<const float*>(c->V), nullptr, t1, c->n1, c->n2, tx, nullptr,
+                                   c->stream);
     else launch_dst_rows<T, double, T>(c->V, nullptr, t1, c->n1, c->n2, tx, nullptr, c->stream);
   });
   chosen[TK_PRE_COLS] = tune_one<T>(c, TK_PRE_COLS, ty.L, c->n1, reps, [&] {
@@ -748,6 +783,7 @@ int autotune_ctx(rsfde_ctx* c, int reps, int32_t* chosen_out) {
   cudaMemsetAsync(c->T2a, 0, bytes, c->stream);
   cudaMemsetAsync(c->T2b, 0, bytes, c->stream);
   if (c->opts.matvec_prec == RSFDE_DF32) tune_operator<df>(c, reps, c->xdf.tab, c->ydf.tab, chosen);
+  else if (c->opts.matvec_prec == RSFDE_FP32) tune_operator<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
   else tune_operator<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
   if (c->opts.precond_prec == RSFDE_FP32) tune_precond<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
   else if (c->opts.precond_prec == RSFDE_FP64) tune_precond<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
@@ -925,9 +961,11 @@ const char* rsfde_strerror(int code) {
 
 static int valid_opts(const rsfde_opts* o) {
   if (o->restart < 1 || o->restart > kMaxRestart || o->max_iter < 1 || !(o->tol > 0.0)) return 0;
-  if (o->precond_prec != RSFDE_FP64 && o->precond_prec != RSFDE_FP32 && o->precond_prec != RSFDE_BF16X3) return 0;
+  if (o->precond_prec != RSFDE_FP64 && o->precond_prec != RSFDE_FP32 && o->precond_prec != RSFDE_BF16X3 &&
+      o->precond_prec != RSFDE_BF16)
+    return 0;
   if (o->arnoldi != RSFDE_CGS && o->arnoldi != RSFDE_CGS2) return 0;
-  if (o->matvec_prec != RSFDE_FP64 && o->matvec_prec != RSFDE_DF32) return 0;
+  if (o->matvec_prec != RSFDE_FP64 && o->matvec_prec != RSFDE_DF32 && o->matvec_prec != RSFDE_FP32) return 0;
   if (o->variant != RSFDE_FGMRES_RIGHT && o->variant != RSFDE_GMRES_LEFT) return 0;
   return 1;
 }

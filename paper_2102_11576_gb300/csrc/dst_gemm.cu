@@ -1,5 +1,6 @@
 // dst_gemm.cu -- the preconditioner of Eq. 4.6 with every sine transform done
-// as a split-BF16 tensor-core GEMM (dst_gemm.cuh).
+// as a tensor-core GEMM (dst_gemm.cuh) in split BF16 (three products) or
+// plain BF16 (one product).
 //
 // P-hat^-1 v = (1-Phi) S W1 + Phi S W2 with S = S_{n2} (x) S_{n1}, W = S v,
 // W1 = W / (1 - Lx - Ly), W2 = W / (1 + dt/eta - Lx - Ly).  As matrices
@@ -13,7 +14,8 @@
 //   4. GEMM x2:  (S_y W_c S_x)^T = Yt_c S_y; the epilogue writes z where the
 //                mask selects channel c.
 // All BF16 matrices have a leading dimension padded to a multiple of 64 and
-// are zeroed once, so tile reads past the valid extent see zeros.
+// are zeroed once, so tile reads past the valid extent see zeros.  Plain BF16
+// keeps only the leading matrix of every pair.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -64,11 +66,12 @@ bool make_map(CUtensorMap* m, void* p, int rows, int cols, int ld) {
 }
 
 // A = scale * V split into a BF16 pair (rows y, columns x, leading dim ld).
-// FP64 input is scaled in FP64; double-FP32 input in FP32 (its leading part).
+// FP64 input is scaled in FP64; FP32 and double-FP32 input in FP32.
 __device__ __forceinline__ float scaled_f32(double sc, float, double v) { return (float)(sc * v); }
 __device__ __forceinline__ float scaled_f32(double, float scf, df v) { return __fmul_rn(scf, __fadd_rn(v.hi, v.lo)); }
+__device__ __forceinline__ float scaled_f32(double, float scf, float v) { return __fmul_rn(scf, v); }
 
-template <typename Tin>
+template <typename Tin, int NT>
 __global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v, const double* scale,
                                                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                                        int n1, int n2, int ld, const int* gate) {
@@ -81,7 +84,7 @@ __global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v
     const float x = scaled_f32(sc, scf, v[p]);
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     hi[j * ld + i] = h;
-    lo[j * ld + i] = __float2bfloat16_rn(x - __bfloat162float(h));
+    if (NT == 3) lo[j * ld + i] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
 }
 
@@ -89,6 +92,7 @@ __global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v
 
 struct Bf16Plan {
   int n1 = 0, n2 = 0, ld1 = 0, ld2 = 0;
+  int nt = 3;  // BF16 products per GEMM: 3 (split) or 1 (plain)
   Bf16Mat Sx, Sy, A0, T1t, Wst, Yt;
   const float* lamx = nullptr;
   const float* lamy = nullptr;
@@ -113,10 +117,13 @@ static void host_sine_matrix(int n, int ld, std::vector<__nv_bfloat16>& hi, std:
     }
 }
 
-int bf16_plan_create(Bf16Plan** out, int n1, int n2, const float* lamx, const float* lamy, cudaStream_t s) {
+int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, const float* lamy,
+                     cudaStream_t s) {
   *out = nullptr;
   if (!encode_fn()) return RSFDE_ECUDA;
+  if (nt != 1 && nt != 3) return RSFDE_EINVAL;
   Bf16Plan* p = new Bf16Plan();
+  p->nt = nt;
   p->n1 = n1;
   p->n2 = n2;
   p->ld1 = pad64(n1);
@@ -128,8 +135,9 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, const float* lamx, const fl
     int rows, cols, ld;
   } specs[] = {{&p->Sx, n1, n1, p->ld1},     {&p->Sy, n2, n2, p->ld2},      {&p->A0, n2, n1, p->ld1},
                {&p->T1t, n1, n2, p->ld2},    {&p->Wst, 2 * n2, n1, p->ld1}, {&p->Yt, n1, 2 * p->ld2, 2 * p->ld2}};
+  const int parts = nt == 3 ? 2 : 1;
   size_t total = 256;
-  for (auto& sp : specs) total += 2 * (size_t)sp.rows * sp.ld * sizeof(__nv_bfloat16) + 256;
+  for (auto& sp : specs) total += parts * ((size_t)sp.rows * sp.ld * sizeof(__nv_bfloat16) + 256);
   cudaError_t e = cudaMalloc(&p->mem, total);
   if (e != cudaSuccess) {
     delete p;
@@ -147,8 +155,11 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, const float* lamx, const fl
     sp.m->ld = sp.ld;
     sp.m->hi = reinterpret_cast<__nv_bfloat16*>(base + off);
     off += (bytes + 255) / 256 * 256;
-    sp.m->lo = reinterpret_cast<__nv_bfloat16*>(base + off);
-    off += (bytes + 255) / 256 * 256;
+    sp.m->lo = sp.m->hi;  // plain BF16: no second matrix (the kernels never touch it)
+    if (nt == 3) {
+      sp.m->lo = reinterpret_cast<__nv_bfloat16*>(base + off);
+      off += (bytes + 255) / 256 * 256;
+    }
     if (!make_map(&sp.m->map_hi, sp.m->hi, sp.rows, sp.cols, sp.ld) ||
         !make_map(&sp.m->map_lo, sp.m->lo, sp.rows, sp.cols, sp.ld)) {
       cudaFree(p->mem);
@@ -159,11 +170,11 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, const float* lamx, const fl
   std::vector<__nv_bfloat16> hi, lo;
   host_sine_matrix(n1, p->ld1, hi, lo);
   cudaMemcpyAsync(p->Sx.hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(p->Sx.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
+  if (nt == 3) cudaMemcpyAsync(p->Sx.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
   cudaStreamSynchronize(s);
   host_sine_matrix(n2, p->ld2, hi, lo);
   cudaMemcpyAsync(p->Sy.hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(p->Sy.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
+  if (nt == 3) cudaMemcpyAsync(p->Sy.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     cudaFree(p->mem);
@@ -173,6 +184,8 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, const float* lamx, const fl
   *out = p;
   return RSFDE_OK;
 }
+
+int bf16_plan_nt(const Bf16Plan* p) { return p ? p->nt : 0; }
 
 void bf16_plan_destroy(Bf16Plan* p) {
   if (!p) return;
@@ -187,13 +200,19 @@ int bf16_plan_error(Bf16Plan* p, cudaStream_t s) {
   return h ? RSFDE_ETIMEOUT : RSFDE_OK;
 }
 
-template <int EPI>
-static void launch_gemm(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
-                        const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
-  auto k = dst_gemm_kernel<EPI>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+template <int EPI, int NT>
+static void launch_gemm_nt(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
+                           const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
+  auto k = dst_gemm_kernel<EPI, NT>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem(NT));
   dim3 grid((N + kGemmBN - 1) / kGemmBN, (M + kGemmBM - 1) / kGemmBM, channels);
-  k<<<grid, 128, kGemmSmem, s>>>(A.map_hi, A.map_lo, B.map_hi, B.map_lo, K, ep, err, gate);
+  k<<<grid, 128, gemm_smem(NT), s>>>(A.map_hi, A.map_lo, B.map_hi, B.map_lo, K, ep, err, gate);
+}
+template <int EPI>
+static void launch_gemm(int nt, const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
+                        const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
+  if (nt == 3) launch_gemm_nt<EPI, 3>(A, B, M, N, K, channels, ep, err, gate, s);
+  else launch_gemm_nt<EPI, 1>(A, B, M, N, K, channels, ep, err, gate, s);
 }
 
 template <typename Tz, typename Tin>
@@ -201,7 +220,10 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
                  const int* gate, cudaStream_t s) {
   const int n1 = p->n1, n2 = p->n2;
   const size_t N = (size_t)n1 * n2;
-  split_kernel<Tin><<<vec_grid(N), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, gate);
+  if (p->nt == 3)
+    split_kernel<Tin, 3><<<vec_grid(N), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, gate);
+  else
+    split_kernel<Tin, 1><<<vec_grid(N), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, gate);
   GemmEpiParams ep{};
   // 1. T1t = (A0 S_x)^T
   ep.M = n2;
@@ -210,7 +232,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.out_lo = p->T1t.lo;
   ep.ldo = p->ld2;
   ep.row_b = 1 << 30;
-  launch_gemm<EPI_SPLIT_T>(p->A0, p->Sx, n2, n1, n1, 1, ep, p->err, gate, s);
+  launch_gemm<EPI_SPLIT_T>(p->nt, p->A0, p->Sx, n2, n1, n1, 1, ep, p->err, gate, s);
   // 2. W^T = T1t S_y; both tau divides (Eq. 4.6), stacked [W1; W2]
   ep = GemmEpiParams{};
   ep.M = n1;
@@ -222,7 +244,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.lam_n = p->lamy;
   ep.pen = (float)pen;
   ep.chb_rows = n2;
-  launch_gemm<EPI_DIVIDE_T>(p->T1t, p->Sy, n1, n2, n2, 1, ep, p->err, gate, s);
+  launch_gemm<EPI_DIVIDE_T>(p->nt, p->T1t, p->Sy, n1, n2, n2, 1, ep, p->err, gate, s);
   // 3. Yt = ([W1; W2] S_x)^T, the channels side by side (column offset ld2)
   ep = GemmEpiParams{};
   ep.M = 2 * n2;
@@ -232,7 +254,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.ldo = 2 * p->ld2;
   ep.row_b = n2;
   ep.col_b = p->ld2;
-  launch_gemm<EPI_SPLIT_T>(p->Wst, p->Sx, 2 * n2, n1, n1, 1, ep, p->err, gate, s);
+  launch_gemm<EPI_SPLIT_T>(p->nt, p->Wst, p->Sx, 2 * n2, n1, n1, 1, ep, p->err, gate, s);
   // 4. z = (1-Phi) S_y W1 S_x + Phi S_y W2 S_x (channel = blockIdx.z)
   ep = GemmEpiParams{};
   ep.M = n1;
@@ -242,7 +264,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.phi = phi;
   ep.ldz = n1;
   ep.a_koff = p->ld2;
-  launch_gemm<EPI_COMBINE_T>(p->Yt, p->Sy, n1, n2, n2, 2, ep, p->err, gate, s);
+  launch_gemm<EPI_COMBINE_T>(p->nt, p->Yt, p->Sy, n1, n2, n2, 2, ep, p->err, gate, s);
   return cudaGetLastError() == cudaSuccess ? RSFDE_OK : RSFDE_ECUDA;
 }
 
@@ -254,5 +276,9 @@ template int bf16_precond<float, df>(Bf16Plan*, const df*, const double*, float*
                                      const int*, cudaStream_t);
 template int bf16_precond<double, df>(Bf16Plan*, const df*, const double*, double*, const uint8_t*, double,
                                       const int*, cudaStream_t);
+template int bf16_precond<float, float>(Bf16Plan*, const float*, const double*, float*, const uint8_t*, double,
+                                        const int*, cudaStream_t);
+template int bf16_precond<double, float>(Bf16Plan*, const float*, const double*, double*, const uint8_t*, double,
+                                         const int*, cudaStream_t);
 
 }  // namespace rsfde

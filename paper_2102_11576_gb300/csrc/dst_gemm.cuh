@@ -1,19 +1,23 @@
 // dst_gemm.cuh -- the sine transform as a tensor-core GEMM in split BF16.
 //
 // D = A * S with S = S_n (Section 4.1) symmetric, so both operands are
-// K-major rows: D[m][n] = sum_k A[m][k] S[n][k].  Every operand X is held as
-// a pair of BF16 matrices X = X_hi + X_lo (X_lo = bf16(X - X_hi)), and the
-// product is accumulated in FP32 tensor memory as
+// K-major rows: D[m][n] = sum_k A[m][k] S[n][k].  NT = 3 (split BF16): every
+// operand X is held as a pair of BF16 matrices X = X_hi + X_lo
+// (X_lo = bf16(X - X_hi)), and the product is accumulated in FP32 tensor
+// memory as
 //     A_hi S_hi + A_hi S_lo + A_lo S_hi
 // (the split-BF16 product of Henry, Tang & Heinecke, 2019: about 16
-// significant bits per operand, the A_lo S_lo term dropped).
+// significant bits per operand, the A_lo S_lo term dropped).  NT = 1 (plain
+// BF16): only A_hi S_hi, about 8 significant bits per operand.
 //
 // One CTA computes a 128 x 128 tile of D: a TMA producer thread streams
-// 64-wide K slices of the four operand tiles through a 3-stage shared-memory
-// ring (128-byte swizzle), one MMA thread issues tcgen05.mma (M=128, N=128,
-// K=16) into a TMEM accumulator, and all four warps run the epilogue from
-// TMEM.  The epilogue always stores D transposed: TMEM lanes are rows m, so
-// a warp's 32 lanes write 32 consecutive addresses of a row of D^T.
+// 64-wide K slices of the operand tiles (four for NT = 3, two for NT = 1)
+// through a 3-stage shared-memory ring (128-byte swizzle), one MMA thread
+// issues tcgen05.mma (M=128, N=128, K=16) into a TMEM accumulator, and all
+// four warps run the epilogue from TMEM.  NT = 1 needs 97 KB of shared
+// memory, so two CTAs share an SM and one's epilogue overlaps the other's
+// MMAs.  The epilogue always stores D transposed: TMEM lanes are rows m, so a
+// warp's 32 lanes write 32 consecutive addresses of a row of D^T.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -23,8 +27,11 @@ namespace rsfde {
 
 constexpr int kGemmBM = 128, kGemmBN = 128, kGemmBK = 64, kGemmStages = 3;
 constexpr int kGemmTileBytes = kGemmBM * kGemmBK * 2;  // 16 KB (BM == BN)
-constexpr int kGemmStageBytes = 4 * kGemmTileBytes;    // A_hi, A_lo, B_hi, B_lo
-constexpr int kGemmSmem = kGemmStages * kGemmStageBytes + 1024;  // + alignment slack
+// per stage: A_hi, A_lo, B_hi, B_lo (NT = 3) or A_hi, B_hi (NT = 1)
+__host__ __device__ constexpr int gemm_stage_bytes(int NT) { return (NT == 3 ? 4 : 2) * kGemmTileBytes; }
+__host__ __device__ constexpr int gemm_smem(int NT) {
+  return kGemmStages * gemm_stage_bytes(NT) + 1024;  // + alignment slack
+}
 
 enum GemmEpi {
   EPI_SPLIT_T = 0,   // out^T (split BF16 pair); rows m >= row_b go to column (m - row_b + col_b)
@@ -49,17 +56,20 @@ struct GemmEpiParams {
   int a_koff;           // K offset of channel 1's A operand (EPI_COMBINE_T, blockIdx.z = 1)
 };
 
+template <int NT>
 __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo, size_t idx, float v) {
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   hi[idx] = h;
-  lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+  if (NT == 3) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(128, 1)
+template <int EPI, int NT>
+__global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
     dst_gemm_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                     const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, int K,
                     GemmEpiParams ep, int* err, const int* gate) {
+  static_assert(NT == 1 || NT == 3, "one or three BF16 products");
+  constexpr int kStageBytes = gemm_stage_bytes(NT);
   if (gate && *(volatile const int*)gate == 0) return;
   extern __shared__ __align__(1024) uint8_t gemm_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -85,18 +95,23 @@ __global__ void __launch_bounds__(128, 1)
   const int m0 = blockIdx.y * kGemmBM, n0 = blockIdx.x * kGemmBN, ch = blockIdx.z;
   const int a_koff = ch * ep.a_koff;
   const int KB = (K + kGemmBK - 1) / kGemmBK;
-  auto tile = [&](int s, int which) { return smem + s * kGemmStageBytes + which * kGemmTileBytes; };
+  auto tile = [&](int s, int which) { return smem + s * kStageBytes + which * kGemmTileBytes; };
 
   if (warp == 0 && lane == 0) {  // TMA producer
     int issued = 0;
     for (int kb = 0; kb < KB; ++kb) {
       const int s = kb % kGemmStages, it = kb / kGemmStages;
       if (kb >= kGemmStages && !mbar_wait(&empty[s], (it - 1) & 1, err)) break;
-      mbar_expect_tx(&full[s], kGemmStageBytes);
-      tma_load_2d(tile(s, 0), &tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
-      tma_load_2d(tile(s, 1), &tA_lo, a_koff + kb * kGemmBK, m0, &full[s]);
-      tma_load_2d(tile(s, 2), &tB_hi, kb * kGemmBK, n0, &full[s]);
-      tma_load_2d(tile(s, 3), &tB_lo, kb * kGemmBK, n0, &full[s]);
+      mbar_expect_tx(&full[s], kStageBytes);
+      if (NT == 3) {
+        tma_load_2d(tile(s, 0), &tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
+        tma_load_2d(tile(s, 1), &tA_lo, a_koff + kb * kGemmBK, m0, &full[s]);
+        tma_load_2d(tile(s, 2), &tB_hi, kb * kGemmBK, n0, &full[s]);
+        tma_load_2d(tile(s, 3), &tB_lo, kb * kGemmBK, n0, &full[s]);
+      } else {
+        tma_load_2d(tile(s, 0), &tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
+        tma_load_2d(tile(s, 1), &tB_hi, kb * kGemmBK, n0, &full[s]);
+      }
       issued = kb + 1;
     }
     if (*(volatile int*)err) {  // give up: let the loads in flight land before the block exits
@@ -110,15 +125,17 @@ __global__ void __launch_bounds__(128, 1)
       if (!mbar_wait(&full[s], it & 1, err)) break;
       tc_fence_after();
       const uint64_t a_hi = umma_desc_sw128(smem_u32(tile(s, 0)));
-      const uint64_t a_lo = umma_desc_sw128(smem_u32(tile(s, 1)));
-      const uint64_t b_hi = umma_desc_sw128(smem_u32(tile(s, 2)));
-      const uint64_t b_lo = umma_desc_sw128(smem_u32(tile(s, 3)));
+      const uint64_t a_lo = umma_desc_sw128(smem_u32(tile(s, 1)));  // NT = 1: B_hi
+      const uint64_t b_hi = NT == 3 ? umma_desc_sw128(smem_u32(tile(s, 2))) : a_lo;
+      const uint64_t b_lo = NT == 3 ? umma_desc_sw128(smem_u32(tile(s, 3))) : 0;
 #pragma unroll
       for (int k = 0; k < kGemmBK / 16; ++k) {  // 16 BF16 = 32 bytes per MMA: start address + 2
         const uint64_t dk = (uint64_t)(2 * k);
         umma_bf16(taddr, a_hi + dk, b_hi + dk, idesc, (kb > 0 || k > 0) ? 1u : 0u);
-        umma_bf16(taddr, a_hi + dk, b_lo + dk, idesc, 1u);
-        umma_bf16(taddr, a_lo + dk, b_hi + dk, idesc, 1u);
+        if (NT == 3) {
+          umma_bf16(taddr, a_hi + dk, b_lo + dk, idesc, 1u);
+          umma_bf16(taddr, a_lo + dk, b_hi + dk, idesc, 1u);
+        }
       }
       umma_commit(&empty[s]);
     }
@@ -141,12 +158,12 @@ __global__ void __launch_bounds__(128, 1)
         const float val = v[q];
         if (EPI == EPI_SPLIT_T) {
           const int col = m < ep.row_b ? m : m - ep.row_b + ep.col_b;
-          split_store(ep.out_hi, ep.out_lo, (size_t)n * ep.ldo + col, val);
+          split_store<NT>(ep.out_hi, ep.out_lo, (size_t)n * ep.ldo + col, val);
         } else if (EPI == EPI_DIVIDE_T) {
           // rows m: x-frequency i, columns n: y-frequency l (Eq. 4.6 divides)
           const float base = 1.0f - ep.lam_m[m] - ep.lam_n[n];
-          split_store(ep.out_hi, ep.out_lo, (size_t)n * ep.ldo + m, val / base);
-          split_store(ep.out_hi, ep.out_lo, (size_t)(ep.chb_rows + n) * ep.ldo + m, val / (base + ep.pen));
+          split_store<NT>(ep.out_hi, ep.out_lo, (size_t)n * ep.ldo + m, val / base);
+          split_store<NT>(ep.out_hi, ep.out_lo, (size_t)(ep.chb_rows + n) * ep.ldo + m, val / (base + ep.pen));
         } else {  // EPI_COMBINE_T: z[y][x] from channel ch where phi == ch
           const size_t p = (size_t)n * ep.ldz + m;
           if ((int)ep.phi[p] == ch) {

@@ -3,8 +3,8 @@
 // Gram-Schmidt Arnoldi step, the Givens least squares (single thread, in the
 // last block of the norm reduction) and the solution update.
 //
-// The Krylov basis is FP64, or double-FP32 (df.cuh) when the Arnoldi
-// operator runs in double-FP32: then the Gram-Schmidt arithmetic runs on the
+// The Krylov basis has the Arnoldi operator's precision: FP64, double-FP32
+// (df.cuh) or FP32.  In the last two the Gram-Schmidt arithmetic runs on the
 // FP32 pipe as well (GB300 issues FP32 at 58x its FP64 rate) and only the
 // per-warp sums, the Hessenberg entries and the Givens step are FP64.
 //
@@ -104,6 +104,20 @@ struct VecOps<double> {
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+  }
+};
+template <>
+struct VecOps<float> {
+  static __device__ __forceinline__ float zero() { return 0.0f; }
+  static __device__ __forceinline__ float ld(const float* p) { return *p; }
+  static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+  static __device__ __forceinline__ float fma(float acc, float a, float b) { return __fmaf_rn(a, b, acc); }
+  static __device__ __forceinline__ float from(double x) { return (float)x; }
+  // FP32 within the warp (the basis itself carries FP32 accuracy), FP64 after
+  static __device__ __forceinline__ double warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return (double)v;
   }
 };
 template <>
@@ -415,6 +429,8 @@ template void launch_multidot<double>(const double*, size_t, int, int, double*, 
 template void launch_multidot<df>(const df*, size_t, int, int, double*, SolverState*, cudaStream_t);
 template void launch_update<double>(double*, size_t, int, int, double*, SolverState*, cudaStream_t);
 template void launch_update<df>(df*, size_t, int, int, double*, SolverState*, cudaStream_t);
+template void launch_multidot<float>(const float*, size_t, int, int, double*, SolverState*, cudaStream_t);
+template void launch_update<float>(float*, size_t, int, int, double*, SolverState*, cudaStream_t);
 void launch_solve_y(SolverState* st, cudaStream_t s) { solve_y_kernel<<<1, 32, 0, s>>>(st); }
 template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s) {
@@ -453,5 +469,9 @@ template void launch_scale_copy<double, float>(const double*, const double*, flo
                                                cudaStream_t);
 template void launch_scale_copy<df, double>(const df*, const double*, double*, size_t, const int*, cudaStream_t);
 template void launch_scale_copy<df, float>(const df*, const double*, float*, size_t, const int*, cudaStream_t);
+template void launch_scale_copy<float, double>(const float*, const double*, double*, size_t, const int*,
+                                               cudaStream_t);
+template void launch_scale_copy<float, float>(const float*, const double*, float*, size_t, const int*,
+                                              cudaStream_t);
 
 }  // namespace rsfde

@@ -8,8 +8,7 @@
 // positions (coalesced rows); column kernels interleave the F groups across
 // the lanes of a warp so each access touches F (or 2F) adjacent columns.
 //
-//  * Arithmetic: T = double, float, or df (double-FP32, df.cuh) for the
-//    operator applied to the Arnoldi vectors.
+//  * Arithmetic: T = double, float, or df (double-FP32, df.cuh).
 //  * Toeplitz product along an axis: two real vectors are packed as the real
 //    and imaginary parts of one complex sequence (the circulant spectrum is
 //    real because the Toeplitz matrix of Eq. 2.16 is symmetric), zero padded
@@ -89,8 +88,8 @@ __device__ __forceinline__ void bluestein(cx<T>* v, cx<T>* buf, int t, const Axi
 }
 
 // scale * x in the arithmetic type T: FP64 vectors are scaled in FP64 before
-// rounding; double-FP32 vectors feeding an FP32 transform are scaled in FP32,
-// with no FP64 instruction.
+// rounding; FP32 and double-FP32 vectors feeding an FP32 transform are scaled
+// in FP32, with no FP64 instruction.
 template <typename T>
 __device__ __forceinline__ T scaled_load(double sc, float, double x) {
   return cvt<T>(sc * x);
@@ -110,8 +109,18 @@ __device__ __forceinline__ df scaled_load<df>(double sc, float, df x) {
   return df(sc) * x;
 }
 template <typename T>
-__device__ __forceinline__ T scaled_load(double sc, float, float x) {
-  return cvt<T>(sc * (double)x);
+__device__ __forceinline__ T scaled_load(double sc, float scf, float x);
+template <>
+__device__ __forceinline__ float scaled_load<float>(double, float scf, float x) {
+  return __fmul_rn(scf, x);
+}
+template <>
+__device__ __forceinline__ double scaled_load<double>(double sc, float, float x) {
+  return sc * (double)x;
+}
+template <>
+__device__ __forceinline__ df scaled_load<df>(double sc, float, float x) {
+  return df(sc) * df(x, 0.0f);
 }
 
 // Im(c_out[pos] * y)
@@ -569,7 +578,16 @@ RSFDE_TOEP_COLS(df, double, double)
 RSFDE_TOEP_COLS(df, float, double)
 RSFDE_TOEP_COLS(df, double, df)
 RSFDE_TOEP_COLS(df, float, df)
+RSFDE_TOEP_COLS(double, double, float)
+RSFDE_TOEP_COLS(float, float, float)
+RSFDE_TOEP_COLS(float, double, float)
+RSFDE_TOEP_COLS(float, float, double)
+RSFDE_TOEP_COLS(float, double, double)
 #undef RSFDE_TOEP_COLS
+template void launch_toeplitz_rows<float, double>(const double*, void*, int, int, const AxisTables<float>&,
+                                                  const int*, cudaStream_t);
+template void launch_toeplitz_rows<float, float>(const float*, void*, int, int, const AxisTables<float>&,
+                                                 const int*, cudaStream_t);
 template void launch_toeplitz_rows<df, double>(const double*, void*, int, int, const AxisTables<df>&,
                                                const int*, cudaStream_t);
 template void launch_toeplitz_rows<df, float>(const float*, void*, int, int, const AxisTables<df>&,
@@ -582,6 +600,8 @@ RSFDE_DST_ROWS(float, double, float)
 RSFDE_DST_ROWS(double, double, float)
 RSFDE_DST_ROWS(double, df, double)
 RSFDE_DST_ROWS(float, df, float)
+RSFDE_DST_ROWS(float, float, float)
+RSFDE_DST_ROWS(double, float, double)
 #undef RSFDE_DST_ROWS
 template void launch_dst_cols<double, double, double>(const double*, double*, int, int, const AxisTables<double>&,
                                                       cudaStream_t);

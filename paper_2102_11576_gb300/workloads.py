@@ -88,10 +88,10 @@ def make(name, seed=0, n=None):
         mask = convex_polygon_mask(X, Y, polygon_vertices(rng, 12))
         w = dict(alpha1=1.3, alpha2=1.6, kx=1.0, ky=1.0, eta=1e-8, T=1.0, steps=50, restart=20,
                  u0=bump(X, Y) * mask, src=None,
-                 # mean FGMRES(20) iterations per step over the default timed region
-                 # of the benchmark (steps 4-13 of the march from the bump; every
-                 # precision form gives the same count), used to scale the CPU
-                 # oracle's sampled per-iteration time to steps/s
+                 # mean FGMRES(20) iterations per step of the FP64 form over the
+                 # default timed region of the benchmark (steps 4-13 of the march
+                 # from the bump), used to scale the CPU oracle's sampled
+                 # per-iteration time (FP64 arithmetic) to steps/s
                  iters_per_step_recorded=59.4)
     elif name == "disk1024":
         n = n or 1024

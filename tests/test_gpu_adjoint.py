@@ -42,7 +42,7 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32")])
+@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32"), ("bf16", "fp32")])
 def test_adjoint_matches_oracle(prec, matvec):
     w = workloads.random_problem(31, 20, 16)
     rng = np.random.default_rng(1)

@@ -17,12 +17,13 @@ if not torch.cuda.is_available():
 from paper_2102_11576_gb300 import Batch, Solver  # noqa: E402
 
 
-def test_batch_equals_single_instances_and_meets_tolerance():
+@pytest.mark.parametrize("precond,matvec", [("fp32", "df32"), ("bf16", "fp32")])
+def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec):
     probs = workloads.make_batch(seed=5, count=7, n_range=(9, 96), steps=10)
     steps = 3
     rng = np.random.default_rng(0)
     srcs = [rng.standard_normal(p["u0"].shape) if i % 2 else None for i, p in enumerate(probs)]
-    b = Batch(probs, precond="fp32", matvec="df32")
+    b = Batch(probs, precond=precond, matvec=matvec)
     for i, p in enumerate(probs):
         b.set(i, p["u0"], srcs[i])
     st = b.run(steps)
@@ -31,7 +32,7 @@ def test_batch_equals_single_instances_and_meets_tolerance():
     for i, p in enumerate(probs):
         args = (p["n1"], p["n2"], p["box"], p["in_omega"], p["alpha1"], p["alpha2"], p["kx"], p["ky"],
                 p["dt"], p["eta"])
-        single = Solver(*args, precond="fp32", matvec="df32")
+        single = Solver(*args, precond=precond, matvec=matvec)
         src = None if srcs[i] is None else torch.as_tensor(srcs[i]).cuda()
         prev, prevprev = torch.as_tensor(p["u0"]).cuda(), None
         orc = oracle.Problem(*args)

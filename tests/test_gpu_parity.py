@@ -63,7 +63,7 @@ def test_tables_match_oracle(n1, n2):
 
 
 @pytest.mark.parametrize("n1,n2", SIZES)
-@pytest.mark.parametrize("matvec,tol", [("fp64", 1e-13), ("df32", 2e-12)])
+@pytest.mark.parametrize("matvec,tol", [("fp64", 1e-13), ("df32", 2e-12), ("fp32", 2e-6)])
 def test_apply_M(n1, n2, matvec, tol):
     w = workloads.random_problem(2, n1, n2)
     orc, gpu = pair(w, matvec=matvec)
@@ -90,7 +90,7 @@ def test_dst2(n1, n2):
 
 
 @pytest.mark.parametrize("n1,n2", SIZES)
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5), ("bf16x3", 2e-4)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5), ("bf16x3", 2e-4), ("bf16", 2e-2)])
 def test_apply_precond(n1, n2, prec, tol):
     w = workloads.random_problem(4, n1, n2)
     orc, gpu = pair(w, precond=prec)
@@ -101,9 +101,9 @@ def test_apply_precond(n1, n2, prec, tol):
 
 
 @pytest.mark.parametrize("n1,n2", [(1, 1), (5, 7), (33, 20), (64, 64), (65, 127)])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16"])
 @pytest.mark.parametrize("arnoldi", ["cgs", "cgs2"])
-@pytest.mark.parametrize("matvec", ["fp64", "df32"])
+@pytest.mark.parametrize("matvec", ["fp64", "df32", "fp32"])
 def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec):
     w = workloads.random_problem(5, n1, n2)
     orc, gpu = pair(w, precond=prec, arnoldi=arnoldi, tol=1e-11, restart=10, matvec=matvec)
@@ -120,7 +120,7 @@ def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec):
     assert rel(x, x_ref) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32")])
+@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32"), ("fp32", "fp32"), ("bf16", "fp32")])
 def test_graph_loop_equals_direct_launches(prec, matvec):
     """The device-side graph loop and the host-driven loop run the same
     kernels in the same order with deterministic reductions: identical bits."""
@@ -146,7 +146,8 @@ def test_unpreconditioned_and_dense_lu():
     assert st["converged"] and rel(host(x), x_lu) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32"), ("bf16x3", "df32")])
+@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32"), ("bf16x3", "df32"), ("fp32", "fp32"),
+                                         ("bf16x3", "fp32"), ("bf16", "fp32")])
 def test_march_disk64_matches_oracle(prec, matvec):
     w = workloads.make("disk64")
     orc, gpu = pair(w, tol=1e-12, restart=w["restart"], precond=prec, matvec=matvec)
@@ -158,7 +159,12 @@ def test_march_disk64_matches_oracle(prec, matvec):
     assert rel(u, u_ref) <= 1e-9
     it_gpu = np.mean([s["iters"] for s in st])
     it_ref = np.mean([s["iters"] for s in st_ref])
-    assert abs(it_gpu - it_ref) <= 0.1 * it_ref + 1  # same method, different Gram-Schmidt
+    if matvec == "fp32":
+        # an FP32 Arnoldi operator bounds each restart cycle's residual reduction
+        # near its rounding level: at this 1e-12 tolerance it takes extra cycles
+        assert it_ref <= it_gpu + 1 and it_gpu <= 1.5 * it_ref + 1
+    else:
+        assert abs(it_gpu - it_ref) <= 0.1 * it_ref + 1  # same method, different Gram-Schmidt
 
 
 def test_step_host_equals_step():
@@ -226,7 +232,8 @@ def test_full_size_polygon2048_sampled():
     rng = np.random.default_rng(0)
     idx = rng.choice(w["n1"] * w["n2"], size=256, replace=False)
     u0 = w["u0"]
-    for prec, matvec in (("fp32", "df32"), ("bf16x3", "df32"), ("fp32", "fp64"), ("fp64", "fp64")):
+    for prec, matvec in (("bf16", "fp32"), ("fp32", "fp32"), ("fp32", "df32"), ("bf16x3", "fp32"), ("fp32", "fp64"),
+                         ("fp64", "fp64")):
         gpu = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"],
                      w["ky"], w["dt"], w["eta"], restart=w["restart"], precond=prec, matvec=matvec)
         z = rng.standard_normal((w["n2"], w["n1"]))
@@ -234,7 +241,9 @@ def test_full_size_polygon2048_sampled():
         ref = orc.apply_M_points(z, idx)
         scale = np.abs(z).max() * (1 + 2 * np.abs(orc.toeplitz()[0]).sum()
                                    + 2 * np.abs(orc.toeplitz()[1]).sum())
-        assert np.abs(mz - ref).max() <= (2e-12 if matvec == "df32" else 1e-13) * scale
+        if matvec == "fp32":  # FP32 rounds the penalty term (dt/eta) phi z too
+            scale += np.abs(z).max() * orc.pen
+        assert np.abs(mz - ref).max() <= {"df32": 2e-12, "fp32": 2e-6, "fp64": 1e-13}[matvec] * scale
         u1, st = gpu.step(dev(u0))
         u1 = host(u1)
         assert st["converged"] and st["rel_res"] <= 1e-10
