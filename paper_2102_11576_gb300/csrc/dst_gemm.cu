@@ -71,28 +71,41 @@ __device__ __forceinline__ float scaled_f32(double sc, float, double v) { return
 __device__ __forceinline__ float scaled_f32(double, float scf, df v) { return __fmul_rn(scf, __fadd_rn(v.hi, v.lo)); }
 __device__ __forceinline__ float scaled_f32(double, float scf, float v) { return __fmul_rn(scf, v); }
 
+// Column x goes to column sym_perm(x, hk) (the symmetric GEMM's K layout;
+// hk = 0: natural order).
 template <typename Tin, int NT>
 __global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v, const double* scale,
                                                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
-                                                       int n1, int n2, int ld, const int* gate) {
+                                                       int n1, int n2, int ld, int hk, const int* gate) {
   if (gate && *(volatile const int*)gate == 0) return;
   const double sc = scale ? *scale : 1.0;
   const float scf = (float)sc;
-  const size_t N = (size_t)n1 * n2;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = p / n1, i = p - j * n1;
-    const float x = scaled_f32(sc, scf, v[p]);
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    hi[j * ld + i] = h;
-    if (NT == 3) lo[j * ld + i] = __float2bfloat16_rn(x - __bfloat162float(h));
-  }
+  for (int j = blockIdx.y; j < n2; j += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
+      const float x = scaled_f32(sc, scf, v[(size_t)j * n1 + i]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      const size_t o = (size_t)j * ld + sym_perm(i, hk);
+      hi[o] = h;
+      if (NT == 3) lo[o] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+}
+
+// Rows over blockIdx.y, columns over blockIdx.x: about 4096 blocks of 256.
+static dim3 split_grid(int n1, int n2) {
+  const int gx = (n1 + kBlock - 1) / kBlock;
+  int gy = 4096 / gx;
+  if (gy < 1) gy = 1;
+  if (gy > n2) gy = n2;
+  return dim3(gx, gy);
 }
 
 }  // namespace
 
 struct Bf16Plan {
-  int n1 = 0, n2 = 0, ld1 = 0, ld2 = 0;
-  int nt = 3;  // BF16 products per GEMM: 3 (split) or 1 (plain)
+  int n1 = 0, n2 = 0;
+  int ld1 = 0, ld2 = 0;  // K extent (and leading dimension) of an x- and a y-transform operand
+  int h1 = 0, h2 = 0;    // symmetric form: half of that extent (0: natural layout, full GEMMs)
+  int nt = 3;            // BF16 products per GEMM: 3 (split) or 1 (plain)
   Bf16Mat Sx, Sy, A0, T1t, Wst, Yt;
   const float* lamx = nullptr;
   const float* lamy = nullptr;
@@ -101,19 +114,23 @@ struct Bf16Plan {
 };
 
 // S_n as a split BF16 pair: [S_n]_{ij} = sqrt(2/(n+1)) sin(pi i j/(n+1)), FP64 on the host.
-static void host_sine_matrix(int n, int ld, std::vector<__nv_bfloat16>& hi, std::vector<__nv_bfloat16>& lo) {
-  hi.assign((size_t)n * ld, __float2bfloat16(0.0f));
-  lo.assign((size_t)n * ld, __float2bfloat16(0.0f));
+// Symmetric form (hk > 0): only the rows i <= n/2, columns in sym_perm order.
+static void host_sine_matrix(int n, int ld, int hk, std::vector<__nv_bfloat16>& hi,
+                             std::vector<__nv_bfloat16>& lo) {
+  const int rows = hk ? n / 2 : n;
+  hi.assign((size_t)rows * ld, __float2bfloat16(0.0f));
+  lo.assign((size_t)rows * ld, __float2bfloat16(0.0f));
   const long per = 2L * (n + 1);
   const double sc = std::sqrt(2.0 / (n + 1));
   std::vector<double> sn(per);
   for (long m = 0; m < per; ++m) sn[m] = sc * std::sin(M_PI * (double)m / (double)(n + 1));
-  for (int i = 1; i <= n; ++i)
+  for (int i = 1; i <= rows; ++i)
     for (int j = 1; j <= n; ++j) {
       const float x = (float)sn[((long)i * j) % per];
       const __nv_bfloat16 h = __float2bfloat16(x);
-      hi[(size_t)(i - 1) * ld + (j - 1)] = h;
-      lo[(size_t)(i - 1) * ld + (j - 1)] = __float2bfloat16(x - __bfloat162float(h));
+      const size_t o = (size_t)(i - 1) * ld + sym_perm(j - 1, hk);
+      hi[o] = h;
+      lo[o] = __float2bfloat16(x - __bfloat162float(h));
     }
 }
 
@@ -126,15 +143,21 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
   p->nt = nt;
   p->n1 = n1;
   p->n2 = n2;
-  p->ld1 = pad64(n1);
-  p->ld2 = pad64(n2);
+  // even n1 and n2: the symmetric form (half the MMAs)
+  const bool sym = n1 % 2 == 0 && n2 % 2 == 0;
+  p->h1 = sym ? pad64(n1 / 2) : 0;
+  p->h2 = sym ? pad64(n2 / 2) : 0;
+  p->ld1 = sym ? 2 * p->h1 : pad64(n1);
+  p->ld2 = sym ? 2 * p->h2 : pad64(n2);
+  const int c1 = sym ? p->ld1 : n1, c2 = sym ? p->ld2 : n2;  // K extents of the tensor maps
   p->lamx = lamx;
   p->lamy = lamy;
   struct Spec {
     Bf16Mat* m;
     int rows, cols, ld;
-  } specs[] = {{&p->Sx, n1, n1, p->ld1},     {&p->Sy, n2, n2, p->ld2},      {&p->A0, n2, n1, p->ld1},
-               {&p->T1t, n1, n2, p->ld2},    {&p->Wst, 2 * n2, n1, p->ld1}, {&p->Yt, n1, 2 * p->ld2, 2 * p->ld2}};
+  } specs[] = {{&p->Sx, sym ? n1 / 2 : n1, c1, p->ld1}, {&p->Sy, sym ? n2 / 2 : n2, c2, p->ld2},
+               {&p->A0, n2, c1, p->ld1},                {&p->T1t, n1, c2, p->ld2},
+               {&p->Wst, 2 * n2, c1, p->ld1},           {&p->Yt, n1, 2 * p->ld2, 2 * p->ld2}};
   const int parts = nt == 3 ? 2 : 1;
   size_t total = 256;
   for (auto& sp : specs) total += parts * ((size_t)sp.rows * sp.ld * sizeof(__nv_bfloat16) + 256);
@@ -168,11 +191,11 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
     }
   }
   std::vector<__nv_bfloat16> hi, lo;
-  host_sine_matrix(n1, p->ld1, hi, lo);
+  host_sine_matrix(n1, p->ld1, p->h1, hi, lo);
   cudaMemcpyAsync(p->Sx.hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s);
   if (nt == 3) cudaMemcpyAsync(p->Sx.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
   cudaStreamSynchronize(s);
-  host_sine_matrix(n2, p->ld2, hi, lo);
+  host_sine_matrix(n2, p->ld2, p->h2, hi, lo);
   cudaMemcpyAsync(p->Sy.hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s);
   if (nt == 3) cudaMemcpyAsync(p->Sy.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
   e = cudaStreamSynchronize(s);
@@ -200,43 +223,52 @@ int bf16_plan_error(Bf16Plan* p, cudaStream_t s) {
   return h ? RSFDE_ETIMEOUT : RSFDE_OK;
 }
 
-template <int EPI, int NT>
-static void launch_gemm_nt(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
-                           const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
-  auto k = dst_gemm_kernel<EPI, NT>;
+template <int EPI, int NT, bool SYM>
+static void launch_gemm_t(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
+                          const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
+  auto k = dst_gemm_kernel<EPI, NT, SYM>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem(NT));
   dim3 grid((N + kGemmBN - 1) / kGemmBN, (M + kGemmBM - 1) / kGemmBM, channels);
   k<<<grid, 128, gemm_smem(NT), s>>>(A.map_hi, A.map_lo, B.map_hi, B.map_lo, K, ep, err, gate);
 }
+// D = A S for a transform of length n along K; the symmetric form (hk > 0)
+// computes the n/2 output pairs from the K operand's two halves.
 template <int EPI>
-static void launch_gemm(int nt, const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
-                        const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
-  if (nt == 3) launch_gemm_nt<EPI, 3>(A, B, M, N, K, channels, ep, err, gate, s);
-  else launch_gemm_nt<EPI, 1>(A, B, M, N, K, channels, ep, err, gate, s);
+static void launch_gemm(const Bf16Plan* p, int hk, const Bf16Mat& A, const Bf16Mat& B, int M, int n, int channels,
+                        GemmEpiParams ep, const int* gate, cudaStream_t s) {
+  ep.M = M;
+  ep.N = hk ? n / 2 : n;
+  ep.n_full = hk ? n : 0;
+  const int K = hk ? 2 * hk : n;
+  if (p->nt == 3) {
+    if (hk) launch_gemm_t<EPI, 3, true>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+    else launch_gemm_t<EPI, 3, false>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+  } else {
+    if (hk) launch_gemm_t<EPI, 1, true>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+    else launch_gemm_t<EPI, 1, false>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+  }
 }
 
 template <typename Tz, typename Tin>
 int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
                  const int* gate, cudaStream_t s) {
   const int n1 = p->n1, n2 = p->n2;
-  const size_t N = (size_t)n1 * n2;
   if (p->nt == 3)
-    split_kernel<Tin, 3><<<vec_grid(N), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, gate);
+    split_kernel<Tin, 3><<<split_grid(n1, n2), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, p->h1,
+                                                               gate);
   else
-    split_kernel<Tin, 1><<<vec_grid(N), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, gate);
+    split_kernel<Tin, 1><<<split_grid(n1, n2), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, p->h1,
+                                                               gate);
   GemmEpiParams ep{};
-  // 1. T1t = (A0 S_x)^T
-  ep.M = n2;
-  ep.N = n1;
+  // 1. T1t = (A0 S_x)^T, columns y in the layout of GEMM 2's K
   ep.out_hi = p->T1t.hi;
   ep.out_lo = p->T1t.lo;
   ep.ldo = p->ld2;
   ep.row_b = 1 << 30;
-  launch_gemm<EPI_SPLIT_T>(p->nt, p->A0, p->Sx, n2, n1, n1, 1, ep, p->err, gate, s);
+  ep.hk = p->h2;
+  launch_gemm<EPI_SPLIT_T>(p, p->h1, p->A0, p->Sx, n2, n1, 1, ep, gate, s);
   // 2. W^T = T1t S_y; both tau divides (Eq. 4.6), stacked [W1; W2]
   ep = GemmEpiParams{};
-  ep.M = n1;
-  ep.N = n2;
   ep.out_hi = p->Wst.hi;
   ep.out_lo = p->Wst.lo;
   ep.ldo = p->ld1;
@@ -244,27 +276,25 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.lam_n = p->lamy;
   ep.pen = (float)pen;
   ep.chb_rows = n2;
-  launch_gemm<EPI_DIVIDE_T>(p->nt, p->T1t, p->Sy, n1, n2, n2, 1, ep, p->err, gate, s);
+  ep.hk = p->h1;
+  launch_gemm<EPI_DIVIDE_T>(p, p->h2, p->T1t, p->Sy, n1, n2, 1, ep, gate, s);
   // 3. Yt = ([W1; W2] S_x)^T, the channels side by side (column offset ld2)
   ep = GemmEpiParams{};
-  ep.M = 2 * n2;
-  ep.N = n1;
   ep.out_hi = p->Yt.hi;
   ep.out_lo = p->Yt.lo;
   ep.ldo = 2 * p->ld2;
   ep.row_b = n2;
   ep.col_b = p->ld2;
-  launch_gemm<EPI_SPLIT_T>(p->nt, p->Wst, p->Sx, 2 * n2, n1, n1, 1, ep, p->err, gate, s);
+  ep.hk = p->h2;
+  launch_gemm<EPI_SPLIT_T>(p, p->h1, p->Wst, p->Sx, 2 * n2, n1, 1, ep, gate, s);
   // 4. z = (1-Phi) S_y W1 S_x + Phi S_y W2 S_x (channel = blockIdx.z)
   ep = GemmEpiParams{};
-  ep.M = n1;
-  ep.N = n2;
   ep.z = z;
   ep.z_double = sizeof(Tz) == 8;
   ep.phi = phi;
   ep.ldz = n1;
   ep.a_koff = p->ld2;
-  launch_gemm<EPI_COMBINE_T>(p->nt, p->Yt, p->Sy, n1, n2, n2, 2, ep, p->err, gate, s);
+  launch_gemm<EPI_COMBINE_T>(p, p->h2, p->Yt, p->Sy, n1, n2, 2, ep, gate, s);
   return cudaGetLastError() == cudaSuccess ? RSFDE_OK : RSFDE_ECUDA;
 }
 

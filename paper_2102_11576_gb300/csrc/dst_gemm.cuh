@@ -34,17 +34,28 @@ __host__ __device__ constexpr int gemm_smem(int NT) {
 }
 
 enum GemmEpi {
-  EPI_SPLIT_T = 0,   // out^T (split BF16 pair); rows m >= row_b go to column (m - row_b + col_b)
-  EPI_DIVIDE_T = 1,  // two tau divides (Eq. 4.6), both channels out^T as split BF16 pairs
+  EPI_SPLIT_T = 0,   // out^T (BF16, or split BF16 pair); rows m >= row_b go to the second channel's columns
+  EPI_DIVIDE_T = 1,  // two tau divides (Eq. 4.6), both channels out^T
   EPI_COMBINE_T = 2  // masked combine of Eq. 4.6 into z (channel = blockIdx.z)
 };
 
+// Symmetric form (SYM): for even n the sine matrix satisfies
+//     S[n-1-i][j] = (-1)^j S[i][j]        (0-based i, j),
+// so with u_i = sum over even j and e_i = sum over odd j of S[i][j] x_j the
+// two outputs i and n-1-i are u_i + e_i and u_i - e_i (i < n/2).  The K
+// operand then holds the even-j entries in columns [0, hk) and the odd-j
+// entries in [hk, 2 hk) (hk = n/2 rounded up to 64, zero padded), the GEMM
+// has n/2 output columns and two TMEM accumulators, and half the MMAs.
+__host__ __device__ __forceinline__ int sym_perm(int x, int hk) { return hk ? (x & 1) * hk + (x >> 1) : x; }
+
 struct GemmEpiParams {
-  int M, N;  // valid extent of D
+  int M, N;       // valid extent of D (N: n/2 in the symmetric form)
+  int n_full;     // symmetric form: the transform length n (outputs i and n-1-i); 0 otherwise
+  int hk;         // K layout the epilogue writes for the next GEMM: 0 natural, else symmetric halves of hk
   __nv_bfloat16* out_hi;
   __nv_bfloat16* out_lo;
   int ldo;
-  int row_b, col_b;     // EPI_SPLIT_T: second-channel rows and their column offset
+  int row_b, col_b;     // EPI_SPLIT_T: rows m >= row_b are channel 2, written from column col_b on
   const float* lam_m;   // EPI_DIVIDE_T: tau eigenvalues along D rows (x) and columns (y)
   const float* lam_n;
   float pen;            // dt / eta
@@ -63,13 +74,14 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
   if (NT == 3) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-template <int EPI, int NT>
+template <int EPI, int NT, bool SYM>
 __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
     dst_gemm_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                     const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, int K,
                     GemmEpiParams ep, int* err, const int* gate) {
   static_assert(NT == 1 || NT == 3, "one or three BF16 products");
   constexpr int kStageBytes = gemm_stage_bytes(NT);
+  constexpr uint32_t kCols = SYM ? 2 * kGemmBN : kGemmBN;  // TMEM columns: one or two accumulators
   if (gate && *(volatile const int*)gate == 0) return;
   extern __shared__ __align__(1024) uint8_t gemm_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -85,7 +97,7 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
     mbar_fence_init();
   }
   if (warp == 0) {
-    tmem_alloc(&tmem_base, kGemmBN);
+    tmem_alloc(&tmem_base, kCols);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -94,7 +106,8 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
   const uint32_t taddr = tmem_base;
   const int m0 = blockIdx.y * kGemmBM, n0 = blockIdx.x * kGemmBN, ch = blockIdx.z;
   const int a_koff = ch * ep.a_koff;
-  const int KB = (K + kGemmBK - 1) / kGemmBK;
+  const int KB = (K + kGemmBK - 1) / kGemmBK;  // SYM: K = 2 hk, KB even
+  const int KBh = SYM ? KB / 2 : KB;
   auto tile = [&](int s, int which) { return smem + s * kStageBytes + which * kGemmTileBytes; };
 
   if (warp == 0 && lane == 0) {  // TMA producer
@@ -124,6 +137,9 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
       const int s = kb % kGemmStages, it = kb / kGemmStages;
       if (!mbar_wait(&full[s], it & 1, err)) break;
       tc_fence_after();
+      // SYM: even-j half into the first accumulator, odd-j half into the second
+      const uint32_t acc = (SYM && kb >= KBh) ? taddr + kGemmBN : taddr;
+      const bool first = SYM ? (kb == 0 || kb == KBh) : (kb == 0);
       const uint64_t a_hi = umma_desc_sw128(smem_u32(tile(s, 0)));
       const uint64_t a_lo = umma_desc_sw128(smem_u32(tile(s, 1)));  // NT = 1: B_hi
       const uint64_t b_hi = NT == 3 ? umma_desc_sw128(smem_u32(tile(s, 2))) : a_lo;
@@ -131,10 +147,10 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
 #pragma unroll
       for (int k = 0; k < kGemmBK / 16; ++k) {  // 16 BF16 = 32 bytes per MMA: start address + 2
         const uint64_t dk = (uint64_t)(2 * k);
-        umma_bf16(taddr, a_hi + dk, b_hi + dk, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+        umma_bf16(acc, a_hi + dk, b_hi + dk, idesc, (!first || k > 0) ? 1u : 0u);
         if (NT == 3) {
-          umma_bf16(taddr, a_hi + dk, b_lo + dk, idesc, 1u);
-          umma_bf16(taddr, a_lo + dk, b_hi + dk, idesc, 1u);
+          umma_bf16(acc, a_hi + dk, b_lo + dk, idesc, 1u);
+          umma_bf16(acc, a_lo + dk, b_hi + dk, idesc, 1u);
         }
       }
       umma_commit(&empty[s]);
@@ -147,28 +163,70 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
   if (ok && !*(volatile int*)err) {
     const int mloc = warp * 32 + lane;  // TMEM lane = row of the tile
     const int m = m0 + mloc;
+    const bool mvalid = m < ep.M;
+    const float lm = (EPI == EPI_DIVIDE_T && mvalid) ? __ldg(ep.lam_m + m) : 0.0f;
+    // column of D^T that row m goes to, in the next GEMM's K layout
+    const int col = (EPI == EPI_SPLIT_T && m >= ep.row_b) ? ep.col_b + sym_perm(m - ep.row_b, ep.hk)
+                                                           : sym_perm(m, ep.hk);
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
     for (int c = 0; c < kGemmBN / 32; ++c) {
-      float v[32];
-      tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      if (m >= ep.M) continue;
-#pragma unroll 4
-      for (int q = 0; q < 32; ++q) {
-        const int n = n0 + c * 32 + q;
-        if (n >= ep.N) break;
-        const float val = v[q];
-        if (EPI == EPI_SPLIT_T) {
-          const int col = m < ep.row_b ? m : m - ep.row_b + ep.col_b;
-          split_store<NT>(ep.out_hi, ep.out_lo, (size_t)n * ep.ldo + col, val);
-        } else if (EPI == EPI_DIVIDE_T) {
-          // rows m: x-frequency i, columns n: y-frequency l (Eq. 4.6 divides)
-          const float base = 1.0f - ep.lam_m[m] - ep.lam_n[n];
-          split_store<NT>(ep.out_hi, ep.out_lo, (size_t)n * ep.ldo + m, val / base);
-          split_store<NT>(ep.out_hi, ep.out_lo, (size_t)(ep.chb_rows + n) * ep.ldo + m, val / (base + ep.pen));
-        } else {  // EPI_COMBINE_T: z[y][x] from channel ch where phi == ch
-          const size_t p = (size_t)n * ep.ldz + m;
-          if ((int)ep.phi[p] == ch) {
-            if (ep.z_double) static_cast<double*>(ep.z)[p] = (double)val;
-            else static_cast<float*>(ep.z)[p] = val;
+      float u[32], e[32];
+      tmem_ld32(taddr + lane_off + (uint32_t)(c * 32), u);  // whole warp
+      if constexpr (SYM) tmem_ld32(taddr + lane_off + (uint32_t)(kGemmBN + c * 32), e);
+      const int nb = n0 + c * 32;
+      if (nb >= ep.N) continue;  // uniform over the block
+      const int nq = min(32, ep.N - nb);
+      if (EPI == EPI_SPLIT_T) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          if (q < nq && mvalid) {
+            const size_t n = (size_t)(nb + q);
+            split_store<NT>(ep.out_hi, ep.out_lo, n * ep.ldo + col, SYM ? u[q] + e[q] : u[q]);
+            if constexpr (SYM) split_store<NT>(ep.out_hi, ep.out_lo, (size_t)(ep.n_full - 1 - (nb + q)) * ep.ldo + col,
+                                     u[q] - e[q]);
+          }
+        }
+      } else if (EPI == EPI_DIVIDE_T) {
+        // rows m: x-frequency i, columns n: y-frequency l (Eq. 4.6 divides);
+        // lane l fetches lam_n at its output columns once, the warp shares them
+        const float ln0 = lane < nq ? __ldg(ep.lam_n + nb + lane) : 0.0f;
+        const float ln1 = (SYM && lane < nq) ? __ldg(ep.lam_n + ep.n_full - 1 - (nb + lane)) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const float base0 = 1.0f - lm - __shfl_sync(0xffffffffu, ln0, q);
+          const float base1 = SYM ? 1.0f - lm - __shfl_sync(0xffffffffu, ln1, q) : 0.0f;
+          if (q < nq && mvalid) {
+            const size_t n = (size_t)(nb + q);
+            const float y0 = SYM ? u[q] + e[q] : u[q];
+            split_store<NT>(ep.out_hi, ep.out_lo, n * ep.ldo + col, y0 / base0);
+            split_store<NT>(ep.out_hi, ep.out_lo, (ep.chb_rows + n) * ep.ldo + col, y0 / (base0 + ep.pen));
+            if constexpr (SYM) {
+              const size_t n1 = (size_t)(ep.n_full - 1 - (nb + q));
+              const float y1 = u[q] - e[q];
+              split_store<NT>(ep.out_hi, ep.out_lo, n1 * ep.ldo + col, y1 / base1);
+              split_store<NT>(ep.out_hi, ep.out_lo, (ep.chb_rows + n1) * ep.ldo + col, y1 / (base1 + ep.pen));
+            }
+          }
+        }
+      } else {  // EPI_COMBINE_T: z[y][x] from channel ch where phi == ch
+#pragma unroll
+        for (int h = 0; h < (SYM ? 2 : 1); ++h) {
+          // the 32 mask bytes of this half are loaded before the first store
+          uint32_t ph[32];
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int n = h ? ep.n_full - 1 - (nb + q) : nb + q;
+            ph[q] = (q < nq && mvalid) ? (uint32_t)__ldg(ep.phi + (size_t)n * ep.ldz + m) : 255u;
+          }
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            if (ph[q] == (uint32_t)ch) {
+              const int n = h ? ep.n_full - 1 - (nb + q) : nb + q;
+              const size_t p = (size_t)n * ep.ldz + m;
+              const float y = SYM ? (h ? u[q] - e[q] : u[q] + e[q]) : u[q];
+              if (ep.z_double) static_cast<double*>(ep.z)[p] = (double)y;
+              else static_cast<float*>(ep.z)[p] = y;
+            }
           }
         }
       }
@@ -176,7 +234,7 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(taddr, kGemmBN);
+  if (warp == 0) tmem_dealloc(taddr, kCols);
 }
 
 }  // namespace rsfde
