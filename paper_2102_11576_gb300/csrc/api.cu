@@ -339,7 +339,7 @@ int ensure_bf16(rsfde_ctx* c) {
     bf16_plan_destroy(c->bf16);
     c->bf16 = nullptr;
   }
-  return bf16_plan_create(&c->bf16, c->n1, c->n2, nt, c->x32.tab.lam, c->y32.tab.lam, c->stream);
+  return bf16_plan_create(&c->bf16, c->n1, c->n2, nt, c->x32.tab.lam, c->y32.tab.lam, c->phi, c->stream);
 }
 
 // The tensor-core preconditioner z = P-hat^-1 (scale * v) (five launches).

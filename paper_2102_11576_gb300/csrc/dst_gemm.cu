@@ -90,6 +90,21 @@ __global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v
     }
 }
 
+// The mask for the combine epilogue: bits[x * wpc + y / 32] bit y % 32 = phi[y][x] != 0.
+__global__ void __launch_bounds__(kBlock) mask_bits_kernel(const uint8_t* __restrict__ phi, uint32_t* bits, int n1,
+                                                           int n2, int wpc) {
+  const long total = (long)n1 * wpc;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int x = (int)(t / wpc), w = (int)(t - (long)x * wpc);
+    uint32_t b = 0;
+    for (int k = 0; k < 32; ++k) {
+      const int y = 32 * w + k;
+      if (y < n2 && phi[(size_t)y * n1 + x]) b |= 1u << k;
+    }
+    bits[t] = b;
+  }
+}
+
 // Rows over blockIdx.y, columns over blockIdx.x: about 4096 blocks of 256.
 static dim3 split_grid(int n1, int n2) {
   const int gx = (n1 + kBlock - 1) / kBlock;
@@ -106,6 +121,8 @@ struct Bf16Plan {
   int ld1 = 0, ld2 = 0;  // K extent (and leading dimension) of an x- and a y-transform operand
   int h1 = 0, h2 = 0;    // symmetric form: half of that extent (0: natural layout, full GEMMs)
   int nt = 3;            // BF16 products per GEMM: 3 (split) or 1 (plain)
+  uint32_t* phibits = nullptr;  // the mask, transposed and bit-packed (wpc words per column x)
+  int wpc = 0;
   Bf16Mat Sx, Sy, A0, T1t, Wst, Yt;
   const float* lamx = nullptr;
   const float* lamy = nullptr;
@@ -135,7 +152,7 @@ static void host_sine_matrix(int n, int ld, int hk, std::vector<__nv_bfloat16>& 
 }
 
 int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, const float* lamy,
-                     cudaStream_t s) {
+                     const uint8_t* phi, cudaStream_t s) {
   *out = nullptr;
   if (!encode_fn()) return RSFDE_ECUDA;
   if (nt != 1 && nt != 3) return RSFDE_EINVAL;
@@ -159,7 +176,9 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
                {&p->A0, n2, c1, p->ld1},                {&p->T1t, n1, c2, p->ld2},
                {&p->Wst, 2 * n2, c1, p->ld1},           {&p->Yt, n1, 2 * p->ld2, 2 * p->ld2}};
   const int parts = nt == 3 ? 2 : 1;
-  size_t total = 256;
+  p->wpc = (n2 + 31) / 32;
+  const size_t bits_bytes = ((size_t)n1 * p->wpc * sizeof(uint32_t) + 255) / 256 * 256;
+  size_t total = 256 + bits_bytes;
   for (auto& sp : specs) total += parts * ((size_t)sp.rows * sp.ld * sizeof(__nv_bfloat16) + 256);
   cudaError_t e = cudaMalloc(&p->mem, total);
   if (e != cudaSuccess) {
@@ -171,6 +190,8 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
   size_t off = 0;
   p->err = reinterpret_cast<int*>(base);
   off += 256;
+  p->phibits = reinterpret_cast<uint32_t*>(base + off);
+  off += bits_bytes;
   for (auto& sp : specs) {
     const size_t bytes = (size_t)sp.rows * sp.ld * sizeof(__nv_bfloat16);
     sp.m->rows = sp.rows;
@@ -195,6 +216,7 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
   cudaMemcpyAsync(p->Sx.hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s);
   if (nt == 3) cudaMemcpyAsync(p->Sx.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
   cudaStreamSynchronize(s);
+  mask_bits_kernel<<<vec_grid((size_t)n1 * p->wpc), kBlock, 0, s>>>(phi, p->phibits, n1, n2, p->wpc);
   host_sine_matrix(n2, p->ld2, p->h2, hi, lo);
   cudaMemcpyAsync(p->Sy.hi, hi.data(), hi.size() * 2, cudaMemcpyHostToDevice, s);
   if (nt == 3) cudaMemcpyAsync(p->Sy.lo, lo.data(), lo.size() * 2, cudaMemcpyHostToDevice, s);
@@ -291,7 +313,8 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep = GemmEpiParams{};
   ep.z = z;
   ep.z_double = sizeof(Tz) == 8;
-  ep.phi = phi;
+  ep.phibits = p->phibits;
+  ep.wpc = p->wpc;
   ep.ldz = n1;
   ep.a_koff = p->ld2;
   launch_gemm<EPI_COMBINE_T>(p, p->h2, p->Yt, p->Sy, n1, n2, 2, ep, gate, s);

@@ -62,7 +62,8 @@ struct GemmEpiParams {
   int chb_rows;         // EPI_DIVIDE_T: row offset of channel b in out
   void* z;              // EPI_COMBINE_T: output vector (n2 x n1, x fastest)
   int z_double;
-  const uint8_t* phi;   // 1 outside Omega
+  const uint32_t* phibits;  // EPI_COMBINE_T: Phi transposed and bit-packed, bit y%32 of word
+  int wpc;                  //   [x * wpc + y/32] is 1 where (x, y) lies outside Omega
   int ldz;
   int a_koff;           // K offset of channel 1's A operand (EPI_COMBINE_T, blockIdx.z = 1)
 };
@@ -198,34 +199,48 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
           if (q < nq && mvalid) {
             const size_t n = (size_t)(nb + q);
             const float y0 = SYM ? u[q] + e[q] : u[q];
-            split_store<NT>(ep.out_hi, ep.out_lo, n * ep.ldo + col, y0 / base0);
-            split_store<NT>(ep.out_hi, ep.out_lo, (ep.chb_rows + n) * ep.ldo + col, y0 / (base0 + ep.pen));
+            // approximate divides (2 ulp): the results are stored in BF16 precision
+            split_store<NT>(ep.out_hi, ep.out_lo, n * ep.ldo + col, __fdividef(y0, base0));
+            split_store<NT>(ep.out_hi, ep.out_lo, (ep.chb_rows + n) * ep.ldo + col, __fdividef(y0, base0 + ep.pen));
             if constexpr (SYM) {
               const size_t n1 = (size_t)(ep.n_full - 1 - (nb + q));
               const float y1 = u[q] - e[q];
-              split_store<NT>(ep.out_hi, ep.out_lo, n1 * ep.ldo + col, y1 / base1);
-              split_store<NT>(ep.out_hi, ep.out_lo, (ep.chb_rows + n1) * ep.ldo + col, y1 / (base1 + ep.pen));
+              split_store<NT>(ep.out_hi, ep.out_lo, n1 * ep.ldo + col, __fdividef(y1, base1));
+              split_store<NT>(ep.out_hi, ep.out_lo, (ep.chb_rows + n1) * ep.ldo + col, __fdividef(y1, base1 + ep.pen));
             }
           }
         }
       } else {  // EPI_COMBINE_T: z[y][x] from channel ch where phi == ch
+        // one mask word holds the 32 y of this chunk for column x = m (nb is a
+        // multiple of 32); the mirrored y = n - 1 - nb - q span at most two words
+        const uint32_t* colbits = ep.phibits + (size_t)(mvalid ? m : 0) * ep.wpc;
+        const uint32_t b0 = mvalid ? __ldg(colbits + (nb >> 5)) : 0u;
+        uint32_t bt = 0u, bb = 0u;
+        int ytop = 0;
+        if constexpr (SYM) {
+          ytop = ep.n_full - 1 - nb;
+          const int wt = ytop >> 5, wb = max(ytop - 31, 0) >> 5;
+          bt = mvalid ? __ldg(colbits + wt) : 0u;
+          bb = (mvalid && wb != wt) ? __ldg(colbits + wb) : bt;
+        }
+        const uint32_t want = (uint32_t)ch;
 #pragma unroll
-        for (int h = 0; h < (SYM ? 2 : 1); ++h) {
-          // the 32 mask bytes of this half are loaded before the first store
-          uint32_t ph[32];
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            const int n = h ? ep.n_full - 1 - (nb + q) : nb + q;
-            ph[q] = (q < nq && mvalid) ? (uint32_t)__ldg(ep.phi + (size_t)n * ep.ldz + m) : 255u;
-          }
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            if (ph[q] == (uint32_t)ch) {
-              const int n = h ? ep.n_full - 1 - (nb + q) : nb + q;
-              const size_t p = (size_t)n * ep.ldz + m;
-              const float y = SYM ? (h ? u[q] - e[q] : u[q] + e[q]) : u[q];
+        for (int q = 0; q < 32; ++q) {
+          if (q < nq && mvalid) {
+            if (((b0 >> q) & 1u) == want) {
+              const int p = (nb + q) * ep.ldz + m;
+              const float y = SYM ? u[q] + e[q] : u[q];
               if (ep.z_double) static_cast<double*>(ep.z)[p] = (double)y;
               else static_cast<float*>(ep.z)[p] = y;
+            }
+            if constexpr (SYM) {
+              const int yy = ytop - q;
+              const uint32_t word = ((yy >> 5) == (ytop >> 5)) ? bt : bb;
+              if (((word >> (yy & 31)) & 1u) == want) {
+                const int p = yy * ep.ldz + m;
+                if (ep.z_double) static_cast<double*>(ep.z)[p] = (double)(u[q] - e[q]);
+                else static_cast<float*>(ep.z)[p] = u[q] - e[q];
+              }
             }
           }
         }

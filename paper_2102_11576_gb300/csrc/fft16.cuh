@@ -136,7 +136,9 @@ __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
 
 // Twiddle w^q for q = 1..R-1 with w = tw[step].  FP64 reads every power from
 // the table (the FP64 units are the scarce resource); FP32 reads w, w^2, w^4,
-// w^8 and forms the others with at most three products (a few ulp).
+// w^8 and forms each other power, as it is applied, from the factors of q's
+// binary digits (at most three products, a few ulp) -- four table values and
+// one power live at a time, which keeps the pass within 64 registers.
 template <typename T, bool INV, int R>
 __device__ __forceinline__ void twiddle_apply(cx<T>* v, int i, int step, const cx<T>* __restrict__ tw) {
   constexpr int S = 16 / R;
@@ -148,25 +150,26 @@ __device__ __forceinline__ void twiddle_apply(cx<T>* v, int i, int step, const c
       v[i + q * S] = c_mul(v[i + q * S], w);
     }
   } else {
-    cx<T> p[16];
-    p[1] = tw[step];
-    if (R > 2) p[2] = tw[2 * step];
-    if (R > 4) p[4] = tw[4 * step];
-    if (R > 8) p[8] = tw[8 * step];
-    if (R > 2) p[3] = c_mul(p[1], p[2]);
-    if (R > 4) {
-      p[5] = c_mul(p[1], p[4]);
-      p[6] = c_mul(p[2], p[4]);
-      p[7] = c_mul(p[3], p[4]);
-    }
-    if (R > 8) {
+    cx<T> b[4];  // w^1, w^2, w^4, w^8
+    b[0] = tw[step];
+    if (R > 2) b[1] = tw[2 * step];
+    if (R > 4) b[2] = tw[4 * step];
+    if (R > 8) b[3] = tw[8 * step];
+    if (INV) {
 #pragma unroll
-      for (int q = 9; q < 16; ++q) p[q] = c_mul(p[q - 8], p[8]);
+      for (int k = 0; k < 4; ++k) b[k].i = -b[k].i;
     }
 #pragma unroll
     for (int q = 1; q < R; ++q) {
-      cx<T> w = p[q];
-      if (INV) w.i = -w.i;
+      cx<T> w;
+      bool have = false;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (q & (1 << k)) {
+          w = have ? c_mul(w, b[k]) : b[k];
+          have = true;
+        }
+      }
       v[i + q * S] = c_mul(v[i + q * S], w);
     }
   }

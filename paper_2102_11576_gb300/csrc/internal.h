@@ -135,8 +135,9 @@ void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, 
 // ---- split-BF16 tensor-core preconditioner (dst_gemm.cu) --------------------
 struct Bf16Plan;
 // nt: BF16 products per GEMM, 3 (split BF16) or 1 (plain BF16)
+// phi: the context's mask (device, n2 x n1, 1 outside Omega), fixed for the plan's life
 int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, const float* lamy,
-                     cudaStream_t s);
+                     const uint8_t* phi, cudaStream_t s);
 int bf16_plan_nt(const Bf16Plan* p);
 void bf16_plan_destroy(Bf16Plan* p);
 int bf16_plan_error(Bf16Plan* p, cudaStream_t s);
