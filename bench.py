@@ -35,15 +35,14 @@ METRIC = "implicit steps/s at 2048² grid, rel.res 1e-10: mixed vs FP64; % HBM r
 UNIT = "steps/s"
 WORKLOAD = "polygon2048"
 FORM_TEXT = {
-    ("fp32", "df32"): "mixed: preconditioner FP32, Arnoldi operator and Krylov basis double-FP32; true "
-                      "residual, Hessenberg and Givens FP64",
-    ("fp32", "fp32"): "mixed: preconditioner, Arnoldi operator and Krylov basis FP32; true residual, "
-                      "Hessenberg and Givens FP64",
-    ("bf16x3", "fp32"): "mixed: preconditioner split-BF16 on tensor cores, Arnoldi operator and Krylov basis "
-                        "FP32; true residual, Hessenberg and Givens FP64",
+    ("fp32", "df32"): "mixed: preconditioner FP32, Arnoldi operator and Krylov basis double-FP32",
+    ("fp32", "fp32"): "mixed: preconditioner, Arnoldi operator and Krylov basis FP32",
+    ("bf16x3", "fp32"): "mixed: preconditioner split-BF16 on tensor cores, Arnoldi operator and Krylov basis FP32",
     ("bf16", "fp32"): "mixed: preconditioner BF16 on tensor cores (FP32 accumulation), Arnoldi operator and "
-                      "Krylov basis FP32; true residual, Hessenberg and Givens FP64",
+                      "Krylov basis FP32",
 }
+RESID_TEXT = {"df32": "; true residual b - Mx double-FP32 (M x) and FP64 (b - Mx, norm); Hessenberg and Givens FP64",
+              "fp64": "; true residual, Hessenberg and Givens FP64"}
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
 # the kernel classes, with the hash of the CUDA sources they were taken from;
@@ -222,8 +221,9 @@ def run_ours(args, rank, world, local_rank):
 
     tiles = {}
 
-    def timed_form(precond, matvec, steps, warmup, profile_steps, clocks=None):
-        solver = Solver(*solver_args, precond=precond, matvec=matvec, use_graph=not args.no_graph, **mk)
+    def timed_form(precond, matvec, steps, warmup, profile_steps, clocks=None, resid="fp64"):
+        solver = Solver(*solver_args, precond=precond, matvec=matvec, use_graph=not args.no_graph, resid=resid,
+                        **mk)
         if not args.no_autotune:  # tile shapes by measurement (setup, outside the timed region)
             tiles[f"{precond}+{matvec}"] = solver.autotune(reps=3)
         bufs = [u0.clone(), torch.empty_like(u0), torch.empty_like(u0)]
@@ -258,7 +258,7 @@ def run_ours(args, rank, world, local_rank):
                     "cycles": sum(s["restarts"] + 1 for s in pstats)}
         iters = [s["iters"] for s in stats]
         out = {"ms": ms, "steps": steps, "launches": launches, "clocks": clk, "prof": prof,
-               "precond": precond, "matvec": matvec,
+               "precond": precond, "matvec": matvec, "resid": resid,
                "iters_per_step": float(np.mean(iters)), "max_rel_res": max(s["rel_res"] for s in stats),
                "all_converged": all(s["converged"] for s in stats), "u": bufs[state[0]].clone()}
         solver.close()
@@ -273,13 +273,14 @@ def run_ours(args, rank, world, local_rank):
     # headline: the mixed form (FP32 preconditioner) with the double-FP32
     # Arnoldi operator; beside it the same with an FP64 operator and the plain
     # FP64 form, each marched from the same u0 over the same steps
-    mixed = timed_form(args.precond, args.matvec, args.steps, args.warmup, args.profile_steps, clocks)
+    mixed = timed_form(args.precond, args.matvec, args.steps, args.warmup, args.profile_steps, clocks, args.resid)
     head = f"{args.precond}+{args.matvec}"
     others = {}
     if not args.only_headline:
         for pre, mv in (("bf16", args.matvec), ("bf16x3", args.matvec), ("fp32", args.matvec), ("fp32", "df32")):
             if f"{pre}+{mv}" != head and f"{pre}+{mv}" not in others:
-                others[f"{pre}+{mv}"] = timed_form(pre, mv, args.steps, args.warmup, args.profile_steps)
+                others[f"{pre}+{mv}"] = timed_form(pre, mv, args.steps, args.warmup, args.profile_steps,
+                                                   resid=args.resid)
     if not args.no_fp64 and not args.only_headline:
         others["fp32_op64"] = timed_form("fp32", "fp64", args.steps, args.warmup, args.profile_steps)
         others["fp64"] = timed_form("fp64", "fp64", args.fp64_steps, args.warmup, args.profile_steps)
@@ -352,7 +353,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- end to end through the C ABI with host arrays ----
     e2e = None
     if not args.no_e2e:
-        solver = Solver(*solver_args, precond=mixed["precond"], matvec=mixed["matvec"], **mk)
+        solver = Solver(*solver_args, precond=mixed["precond"], matvec=mixed["matvec"], resid=mixed["resid"], **mk)
         h = [torch.empty((n2, n1), dtype=torch.float64).pin_memory() for _ in range(3)]
         h[0].copy_(torch.as_tensor(w["u0"]))
         hn = [t.numpy() for t in h]
@@ -387,7 +388,8 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded 12-gon domain, bump initial field)",
         "config": {"workload": f"{WORKLOAD}: {n1}x{n2} grid, convex 12-gon, alpha=(1.3,1.6), k=(1,1), "
                                f"dt=0.02, eta=1e-8, FGMRES({w['restart']}), tol 1e-10",
-                   "form": FORM_TEXT.get((args.precond, args.matvec), f"{args.precond}+{args.matvec}"),
+                   "form": FORM_TEXT.get((args.precond, args.matvec), f"{args.precond}+{args.matvec}")
+                   + RESID_TEXT[args.resid],
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": f"working set > L2 (Krylov basis {w['restart'] + 1} and preconditioned basis "
                          f"{w['restart']} vectors of {N / 1e6:.1f} M values)"},
@@ -631,6 +633,8 @@ def main():
                     help="preconditioner precision of the headline form")
     ap.add_argument("--matvec", choices=["fp32", "df32", "fp64"], default="fp32",
                     help="Arnoldi operator (and Krylov basis) precision of the headline form")
+    ap.add_argument("--resid", choices=["df32", "fp64"], default="df32",
+                    help="arithmetic of the true residual in the mixed forms (the FP64 forms use FP64)")
     ap.add_argument("--no-graph", action="store_true",
                     help="direct kernel launches instead of the graph loop (ncu cannot profile "
                          "kernels inside graphs with conditional nodes)")

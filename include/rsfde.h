@@ -102,6 +102,11 @@ typedef struct {
                            loop (one host synchronisation per solve); 0: direct launches with
                            one host check per cycle.  Profiling always uses direct launches. */
   void* stream;         /* cudaStream_t; NULL = the legacy default stream */
+  int32_t resid_prec;   /* RSFDE_FP64 (default) | RSFDE_DF32: arithmetic of the true residual
+                           b - M x that decides convergence (right-preconditioned FGMRES; paper
+                           mode always FP64).  Double-FP32 carries ~48 significant bits: its
+                           rounding error is a few units of 1e-14 times |M||x|, far below a 1e-10
+                           tolerance. */
 } rsfde_opts;
 
 typedef struct {

@@ -25,6 +25,7 @@ FP64, FP32, DF32 = 0, 1, 2
 _VARIANTS = {"fgmres_right": 0, "gmres_left": 1}
 _PRECONDS = {"fp64": 0, "fp32": 1, "bf16x3": 3, "bf16": 4}
 _MATVECS = {"fp64": FP64, "df32": DF32, "fp32": FP32}
+_RESIDS = {"fp64": FP64, "df32": DF32}
 CGS, CGS2 = 0, 1
 _ERR = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV", -5: "ENONFINITE",
         -6: "ETIMEOUT"}
@@ -47,7 +48,7 @@ class _Opts(ctypes.Structure):
                 ("precond_prec", ctypes.c_int32), ("arnoldi", ctypes.c_int32),
                 ("use_precond", ctypes.c_int32), ("matvec_prec", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("resid_prec", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
@@ -139,7 +140,7 @@ class Solver:
 
     def __init__(self, n1, n2, box, in_omega, alpha1, alpha2, kx, ky, dt, eta, restart=20,
                  max_iter=10000, tol=1e-10, precond="fp64", arnoldi="cgs", use_precond=True,
-                 matvec="fp64", variant="fgmres_right", use_graph=True, stream=None):
+                 matvec="fp64", variant="fgmres_right", use_graph=True, stream=None, resid="fp64"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
@@ -163,6 +164,7 @@ class Solver:
         o.variant = _VARIANTS[variant]
         o.use_graph = int(bool(use_graph))
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        o.resid_prec = _RESIDS[resid]
         self._opts = o
         g = _Grid(self.n1, self.n2, *map(float, box))
         h = ctypes.c_void_p()
@@ -213,6 +215,8 @@ class Solver:
                 o.use_graph = int(bool(v))
             elif k == "variant":
                 o.variant = _VARIANTS[v]
+            elif k == "resid":
+                o.resid_prec = _RESIDS[v]
             else:
                 setattr(o, k, v)
         _check(self._lib.rsfde_set_opts(self._h, ctypes.byref(o)), "set_opts")
@@ -344,7 +348,7 @@ class Batch:
     ky, dt, eta; solver options as for Solver apply to all instances."""
 
     def __init__(self, problems, restart=20, max_iter=10000, tol=1e-10, precond="fp32", matvec="df32",
-                 arnoldi="cgs", stream=None):
+                 arnoldi="cgs", stream=None, resid="fp64"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
@@ -369,6 +373,7 @@ class Batch:
         o.matvec_prec = _MATVECS[matvec]
         o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        o.resid_prec = _RESIDS[resid]
         h = ctypes.c_void_p()
         pp = lambda a: ctypes.c_void_p(a.ctypes.data)
         _check(lib.rsfde_batch_create(ctypes.byref(h), self.count, grids, masks,

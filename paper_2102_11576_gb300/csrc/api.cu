@@ -433,30 +433,35 @@ void enqueue_bnorm(rsfde_ctx* c) {
   launch_norm_b(v, c->N, c->partials, c->st, c->stream);
 }
 
-// V_0 = b - M x, beta = ||V_0||, then restart_prep (device).
+// V_0 = b - M x, beta = ||V_0||, then restart_prep (device); M x in FP64 or
+// (resid_prec = RSFDE_DF32) double-FP32, b - M x and its norm in FP64.
+template <typename T>
+void enqueue_residual_t(rsfde_ctx* c, const int* gate, const AxisTables<T>& tx, const AxisTables<T>& ty) {
+  {
+    ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
+    launch_toeplitz_rows<T, double>(c->x, c->tmpx, c->n1, c->n2, tx, gate, c->stream);
+  }
+  ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
+  if (basis_kind(c) == BASIS_DF32)
+    launch_toeplitz_cols<T, double, df>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
+                                        reinterpret_cast<df*>(c->V), c->n1, c->n2, ty, gate, c->partials, c->st,
+                                        c->stream);
+  else if (basis_kind(c) == BASIS_FP32)
+    launch_toeplitz_cols<T, double, float>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
+                                           reinterpret_cast<float*>(c->V), c->n1, c->n2, ty, gate, c->partials,
+                                           c->st, c->stream);
+  else
+    launch_toeplitz_cols<T, double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1, c->n2,
+                                            ty, gate, c->partials, c->st, c->stream);
+}
+
 void enqueue_residual(rsfde_ctx* c, const int* gate) {
   if (left_variant(c)) {
     enqueue_residual_left(c, gate);
     return;
   }
-  {
-    ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
-    launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
-  }
-  {
-    ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
-    if (basis_kind(c) == BASIS_DF32)
-      launch_toeplitz_cols<double, double, df>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
-                                               reinterpret_cast<df*>(c->V), c->n1, c->n2, c->y64.tab, gate,
-                                               c->partials, c->st, c->stream);
-    else if (basis_kind(c) == BASIS_FP32)
-      launch_toeplitz_cols<double, double, float>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
-                                                  reinterpret_cast<float*>(c->V), c->n1, c->n2, c->y64.tab, gate,
-                                                  c->partials, c->st, c->stream);
-    else
-      launch_toeplitz_cols<double, double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1,
-                                                   c->n2, c->y64.tab, gate, c->partials, c->st, c->stream);
-  }
+  if (c->opts.resid_prec == RSFDE_DF32) enqueue_residual_t<df>(c, gate, c->xdf.tab, c->ydf.tab);
+  else enqueue_residual_t<double>(c, gate, c->x64.tab, c->y64.tab);
 }
 
 // z = P-hat^-1 (scale * v) (Eq. 4.6) into z of precision Tz.
@@ -596,8 +601,13 @@ void enqueue_cycle(rsfde_ctx* c) {
 
 int graph_key(const rsfde_ctx* c) {
   const rsfde_opts& o = c->opts;
-  return (((((o.restart * 4 + o.precond_prec) * 4 + o.matvec_prec) * 2 + o.arnoldi) * 2 + o.use_precond) * 2 +
-          o.variant);
+  int k = o.resid_prec == RSFDE_DF32 ? 1 : 0;
+  k = k * 65 + o.restart;
+  k = k * 5 + o.precond_prec;
+  k = k * 4 + o.matvec_prec;
+  k = k * 2 + o.arnoldi;
+  k = k * 2 + o.use_precond;
+  return k * 2 + o.variant;
 }
 
 // Captures one FGMRES cycle into the body of a CUDA graph WHILE node whose
@@ -944,6 +954,7 @@ void rsfde_opts_default(rsfde_opts* o) {
   o->variant = RSFDE_FGMRES_RIGHT;
   o->use_graph = 1;
   o->stream = nullptr;
+  o->resid_prec = RSFDE_FP64;
 }
 
 const char* rsfde_strerror(int code) {
@@ -967,6 +978,7 @@ static int valid_opts(const rsfde_opts* o) {
   if (o->arnoldi != RSFDE_CGS && o->arnoldi != RSFDE_CGS2) return 0;
   if (o->matvec_prec != RSFDE_FP64 && o->matvec_prec != RSFDE_DF32 && o->matvec_prec != RSFDE_FP32) return 0;
   if (o->variant != RSFDE_FGMRES_RIGHT && o->variant != RSFDE_GMRES_LEFT) return 0;
+  if (o->resid_prec != RSFDE_FP64 && o->resid_prec != RSFDE_DF32) return 0;
   return 1;
 }
 

@@ -263,20 +263,51 @@ __global__ void solve_y_kernel(SolverState* st) {
   }
 }
 
-// x <- x + sum_{i < jlast} y_i z_i  (flexible GMRES keeps the z_i).
+// x <- x + sum_{i < jlast} y_i z_i  (flexible GMRES keeps the z_i).  With FP32
+// z_i the correction sum_i y_i z_i is accumulated in double-FP32 (FP32 pipe;
+// FP64 products per basis vector would make the pass FP64-bound on GB300) and
+// added to the FP64 x once.  The basis vectors are read in groups of eight
+// independent loads.
+template <typename Tz>
+struct XAcc;
+template <>
+struct XAcc<double> {
+  using C = double;  // coefficient and accumulator type
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double coef(double y) { return y; }
+  static __device__ __forceinline__ double fma(double acc, double y, double z) { return __fma_rn(y, z, acc); }
+  static __device__ __forceinline__ double value(double acc) { return acc; }
+};
+template <>
+struct XAcc<float> {
+  using C = df;
+  static __device__ __forceinline__ df zero() { return df(0.0f, 0.0f); }
+  static __device__ __forceinline__ df coef(double y) { return df(y); }
+  static __device__ __forceinline__ df fma(df acc, df y, float z) { return df_fma(acc, y, df(z, 0.0f)); }
+  static __device__ __forceinline__ double value(df acc) { return double(acc); }
+};
+
 template <typename Tz>
 __global__ void __launch_bounds__(kBlock) xupdate_kernel(double* __restrict__ x, const Tz* __restrict__ Z, size_t N,
                                                          SolverState* st) {
   if (closed(&st->run_cycle)) return;
   const int J = st->jlast;
   if (J == 0) return;
-  __shared__ double y[kMaxRestart];
-  for (int i = threadIdx.x; i < J; i += blockDim.x) y[i] = st->y[i];
+  using A = XAcc<Tz>;
+  __shared__ typename A::C y[kMaxRestart];
+  for (int i = threadIdx.x; i < J; i += blockDim.x) y[i] = A::coef(st->y[i]);
   __syncthreads();
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    double v = x[p];
-    for (int i = 0; i < J; ++i) v += y[i] * double(Z[(size_t)i * N + p]);
-    x[p] = v;
+    typename A::C acc = A::zero();
+    for (int i0 = 0; i0 < J; i0 += 8) {
+      Tz a[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a[k] = i0 + k < J ? Z[(size_t)(i0 + k) * N + p] : Tz(0);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (i0 + k < J) acc = A::fma(acc, y[i0 + k], a[k]);
+    }
+    x[p] += A::value(acc);
   }
 }
 

@@ -470,9 +470,9 @@ static std::atomic<int> g_unsupported{0};
 void note_unsupported_launch() { g_unsupported.store(1); }
 bool take_unsupported_launch() { return g_unsupported.exchange(0) != 0; }
 
-// Only the combinations the solver uses are instantiated: double-FP32
-// arithmetic runs the operator (MODE_APPLY) alone; residuals and the raw
-// Toeplitz products are FP64.
+// Only the combinations the solver uses are instantiated: FP32 arithmetic
+// runs the operator (MODE_APPLY) alone, double-FP32 the operator and the true
+// residual; the raw Toeplitz products and the left variant's residual are FP64.
 template <typename T, typename Tin, typename Tout>
 void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi, double pen,
                           const double* b, Tout* out, int n1, int n2, const AxisTables<T>& ay,
@@ -482,9 +482,12 @@ void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi
   const size_t sm = group_smem<T>(ay.L, F, true);
   const int gs = group_stride<T>(ay.L, F, true);
   int grid = (npairs + F - 1) / F;
-  constexpr bool fp64_modes = std::is_same<T, double>::value && std::is_same<Tin, double>::value;
+  // the true residual: FP64 or double-FP32 arithmetic on an FP64 x
+  constexpr bool resid_mode = std::is_same<Tin, double>::value && !std::is_same<T, float>::value;
+  constexpr bool fp64_modes = std::is_same<T, double>::value && std::is_same<Tin, double>::value &&
+                              std::is_same<Tout, double>::value;
   constexpr bool apply_mode = !std::is_same<T, double>::value || std::is_same<Tout, double>::value;
-  if constexpr (fp64_modes) {
+  if constexpr (resid_mode) {
     if (mode == MODE_RESIDUAL) {
       if (grid > kMaxPartials) grid = kMaxPartials;
       auto k = toeplitz_kernel<T, Tin, MODE_RESIDUAL, true, Tout>;
@@ -493,15 +496,15 @@ void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi
                                           partials, st);
       return;
     }
-    if constexpr (std::is_same<Tout, double>::value) {
-      if (mode == MODE_RESID_ONLY || mode == MODE_RAW) {
-        auto k = mode == MODE_RAW ? toeplitz_kernel<T, Tin, MODE_RAW, true, Tout>
-                                  : toeplitz_kernel<T, Tin, MODE_RESID_ONLY, true, Tout>;
-        set_smem(k, sm);
-        k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
-                                            partials, st);
-        return;
-      }
+  }
+  if constexpr (fp64_modes) {
+    if (mode == MODE_RESID_ONLY || mode == MODE_RAW) {
+      auto k = mode == MODE_RAW ? toeplitz_kernel<T, Tin, MODE_RAW, true, Tout>
+                                : toeplitz_kernel<T, Tin, MODE_RESID_ONLY, true, Tout>;
+      set_smem(k, sm);
+      k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
+                                          partials, st);
+      return;
     }
   }
   if constexpr (apply_mode) {
@@ -578,6 +581,7 @@ RSFDE_TOEP_COLS(df, double, double)
 RSFDE_TOEP_COLS(df, float, double)
 RSFDE_TOEP_COLS(df, double, df)
 RSFDE_TOEP_COLS(df, float, df)
+RSFDE_TOEP_COLS(df, double, float)
 RSFDE_TOEP_COLS(double, double, float)
 RSFDE_TOEP_COLS(float, float, float)
 RSFDE_TOEP_COLS(float, double, float)

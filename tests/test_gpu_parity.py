@@ -103,10 +103,11 @@ def test_apply_precond(n1, n2, prec, tol):
 @pytest.mark.parametrize("n1,n2", [(1, 1), (5, 7), (33, 20), (64, 64), (65, 127)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16"])
 @pytest.mark.parametrize("arnoldi", ["cgs", "cgs2"])
-@pytest.mark.parametrize("matvec", ["fp64", "df32", "fp32"])
-def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec):
+@pytest.mark.parametrize("matvec,resid", [("fp64", "fp64"), ("df32", "fp64"), ("fp32", "fp64"), ("fp32", "df32"),
+                                          ("df32", "df32")])
+def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec, resid):
     w = workloads.random_problem(5, n1, n2)
-    orc, gpu = pair(w, precond=prec, arnoldi=arnoldi, tol=1e-11, restart=10, matvec=matvec)
+    orc, gpu = pair(w, precond=prec, arnoldi=arnoldi, tol=1e-11, restart=10, matvec=matvec, resid=resid)
     rng = np.random.default_rng(0)
     b = rng.standard_normal((n2, n1))
     x_ref, st_ref = orc.fgmres(b, restart=10, tol=1e-12)
@@ -120,8 +121,9 @@ def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec):
     assert rel(x, x_ref) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32"), ("fp32", "fp32"), ("bf16", "fp32")])
-def test_graph_loop_equals_direct_launches(prec, matvec):
+@pytest.mark.parametrize("prec,matvec,resid", [("fp64", "fp64", "fp64"), ("fp32", "df32", "fp64"),
+                                               ("fp32", "fp32", "fp64"), ("bf16", "fp32", "df32")])
+def test_graph_loop_equals_direct_launches(prec, matvec, resid):
     """The device-side graph loop and the host-driven loop run the same
     kernels in the same order with deterministic reductions: identical bits."""
     w = workloads.random_problem(8, 70, 45)
@@ -129,7 +131,7 @@ def test_graph_loop_equals_direct_launches(prec, matvec):
     b = dev(rng.standard_normal((45, 70)))
     res = []
     for use_graph in (True, False):
-        _, gpu = pair(w, precond=prec, matvec=matvec, restart=6, tol=1e-12, use_graph=use_graph)
+        _, gpu = pair(w, precond=prec, matvec=matvec, restart=6, tol=1e-12, use_graph=use_graph, resid=resid)
         for _ in range(2):  # the second solve replays the captured graph
             x, st = gpu.solve(b)
         res.append((host(x), st))
@@ -146,11 +148,12 @@ def test_unpreconditioned_and_dense_lu():
     assert st["converged"] and rel(host(x), x_lu) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32"), ("bf16x3", "df32"), ("fp32", "fp32"),
-                                         ("bf16x3", "fp32"), ("bf16", "fp32")])
-def test_march_disk64_matches_oracle(prec, matvec):
+@pytest.mark.parametrize("prec,matvec,resid", [("fp64", "fp64", "fp64"), ("fp32", "df32", "fp64"),
+                                               ("bf16x3", "df32", "fp64"), ("fp32", "fp32", "fp64"),
+                                               ("bf16x3", "fp32", "fp64"), ("bf16", "fp32", "df32")])
+def test_march_disk64_matches_oracle(prec, matvec, resid):
     w = workloads.make("disk64")
-    orc, gpu = pair(w, tol=1e-12, restart=w["restart"], precond=prec, matvec=matvec)
+    orc, gpu = pair(w, tol=1e-12, restart=w["restart"], precond=prec, matvec=matvec, resid=resid)
     steps = 16
     u_ref, st_ref = orc.march(w["u0"], steps, restart=w["restart"], tol=1e-12)
     u, st = gpu.march(dev(w["u0"]), steps)
@@ -232,10 +235,10 @@ def test_full_size_polygon2048_sampled():
     rng = np.random.default_rng(0)
     idx = rng.choice(w["n1"] * w["n2"], size=256, replace=False)
     u0 = w["u0"]
-    for prec, matvec in (("bf16", "fp32"), ("fp32", "fp32"), ("fp32", "df32"), ("bf16x3", "fp32"), ("fp32", "fp64"),
-                         ("fp64", "fp64")):
+    for prec, matvec, resid in (("bf16", "fp32", "df32"), ("fp32", "fp32", "fp64"), ("fp32", "df32", "fp64"),
+                                ("bf16x3", "fp32", "df32"), ("fp32", "fp64", "fp64"), ("fp64", "fp64", "fp64")):
         gpu = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"],
-                     w["ky"], w["dt"], w["eta"], restart=w["restart"], precond=prec, matvec=matvec)
+                     w["ky"], w["dt"], w["eta"], restart=w["restart"], precond=prec, matvec=matvec, resid=resid)
         z = rng.standard_normal((w["n2"], w["n1"]))
         mz = host(gpu.apply_M(dev(z))).reshape(-1)[idx]
         ref = orc.apply_M_points(z, idx)
