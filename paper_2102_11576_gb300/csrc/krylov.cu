@@ -10,6 +10,8 @@
 //
 // Every reduction is two-level and deterministic: fixed grid, per-block
 // partials in block order, summed in a fixed order by the last block.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace rsfde {
@@ -142,7 +144,42 @@ struct VecOps<df> {
 };
 
 constexpr int kWarps = kBlock / 32;
-static_assert(kDotChunk <= kWarps, "one warp per multi-dot accumulator");
+
+// VEC consecutive elements moved as one 16-byte access (VEC = 16 / sizeof(Tv));
+// VEC = 1: one element.  The 16-byte form needs every basis vector 16-byte
+// aligned, i.e. N * sizeof(Tv) a multiple of 16.
+template <typename Tv, int VEC>
+__device__ __forceinline__ void ld_vec(const Tv* p, Tv* o) {
+  if constexpr (VEC == 1) {
+    o[0] = VecOps<Tv>::ld(p);
+  } else if constexpr (std::is_same<Tv, double>::value) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    o[0] = t.x;
+    o[1] = t.y;
+  } else if constexpr (std::is_same<Tv, df>::value) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = df(t.x, t.y);
+    o[1] = df(t.z, t.w);
+  } else {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x;
+    o[1] = t.y;
+    o[2] = t.z;
+    o[3] = t.w;
+  }
+}
+template <typename Tv, int VEC>
+__device__ __forceinline__ void st_vec(Tv* p, const Tv* v) {
+  if constexpr (VEC == 1) {
+    VecOps<Tv>::st(p, v[0]);
+  } else if constexpr (std::is_same<Tv, double>::value) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else if constexpr (std::is_same<Tv, df>::value) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
 
 // Block sums of cnt <= K accumulators: warp sums, then warp k adds the
 // per-warp FP64 sums of accumulator k (fixed order).  Thread 32k returns sum k.
@@ -178,7 +215,7 @@ __device__ __forceinline__ double warp_sum_partials(const double* p, int G) {
 // blockIdx.y selects a chunk of kDotChunk basis vectors; w is re-read per
 // chunk (it stays in L2).  accumulate = 1 adds to H (second CGS pass).  The
 // last block finishes the j+1 sums, one warp per sum.
-template <typename Tv>
+template <typename Tv, int VEC>
 __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__ V, size_t N, int j, int accumulate,
                                                           double* partials, SolverState* st) {
   if (closed(&st->run_iter)) return;
@@ -190,14 +227,27 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
   Tv acc[kDotChunk];
 #pragma unroll
   for (int k = 0; k < kDotChunk; ++k) acc[k] = Op::zero();
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    const Tv wp = Op::ld(w + p);
-    Tv a[kDotChunk];  // all loads issued before the arithmetic
+  const size_t NP = N / VEC;  // VEC divides N (launcher)
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NP; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = q * VEC;
+    Tv wv[VEC];
+    ld_vec<Tv, VEC>(w + p, wv);
+    Tv a[kDotChunk][VEC];  // all loads issued before the arithmetic
 #pragma unroll
-    for (int k = 0; k < kDotChunk; ++k) a[k] = k < cnt ? Op::ld(V + (size_t)(i0 + k) * N + p) : Op::zero();
+    for (int k = 0; k < kDotChunk; ++k) {
+      if (k < cnt) {
+        ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + p, a[k]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) a[k][e] = Op::zero();
+      }
+    }
 #pragma unroll
     for (int k = 0; k < kDotChunk; ++k)
-      if (k < cnt) acc[k] = Op::fma(acc[k], wp, a[k]);
+      if (k < cnt) {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[k] = Op::fma(acc[k], wv[e], a[k][e]);
+      }
   }
   const int G = gridDim.x;
   const double bs = block_sums<Tv, kDotChunk>(acc, cnt, wsum);
@@ -220,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
 // the last block runs the Givens step.  The basis vectors are read in groups
 // of kUpdChunk independent loads ahead of the dependent update chain.
 constexpr int kUpdChunk = 8;
-template <typename Tv>
+template <typename Tv, int VEC>
 __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size_t N, int j, int final_pass,
                                                         double* partials, SolverState* st) {
   if (closed(&st->run_iter)) return;
@@ -231,18 +281,32 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size
   __syncthreads();
   Tv* __restrict__ w = V + (size_t)(j + 1) * N;
   Tv acc = Op::zero();
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    Tv val = Op::ld(w + p);
+  const size_t NP = N / VEC;  // VEC divides N (launcher)
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NP; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = q * VEC;
+    Tv val[VEC];
+    ld_vec<Tv, VEC>(w + p, val);
     for (int i0 = 0; i0 <= j; i0 += kUpdChunk) {
-      Tv a[kUpdChunk];  // all loads issued before the dependent chain
+      Tv a[kUpdChunk][VEC];  // all loads issued before the dependent chains
 #pragma unroll
-      for (int k = 0; k < kUpdChunk; ++k) a[k] = i0 + k <= j ? Op::ld(V + (size_t)(i0 + k) * N + p) : Op::zero();
+      for (int k = 0; k < kUpdChunk; ++k) {
+        if (i0 + k <= j) {
+          ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + p, a[k]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) a[k][e] = Op::zero();
+        }
+      }
 #pragma unroll
       for (int k = 0; k < kUpdChunk; ++k)
-        if (i0 + k <= j) val = Op::fma(val, ncoef[i0 + k], a[k]);
+        if (i0 + k <= j) {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) val[e] = Op::fma(val[e], ncoef[i0 + k], a[k][e]);
+        }
     }
-    Op::st(w + p, val);
-    acc = Op::fma(acc, val, val);
+    st_vec<Tv, VEC>(w + p, val);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc = Op::fma(acc, val[e], val[e]);
   }
   const double bs = block_sums<Tv, 1>(&acc, 1, wsum);
   if (threadIdx.x == 0) partials[blockIdx.x] = bs;
@@ -444,17 +508,32 @@ static int resident_blocks(K kernel) {
   return b;
 }
 
+// 16-byte accesses when every basis vector is 16-byte aligned, else one element.
 template <typename Tv>
 void launch_multidot(const Tv* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
                      cudaStream_t s) {
-  static const int per_sm = resident_blocks(multidot_kernel<Tv>);
-  dim3 grid(wave_grid(per_sm, N), (j + 1 + kDotChunk - 1) / kDotChunk);
-  multidot_kernel<Tv><<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+  constexpr int VEC = 16 / sizeof(Tv);
+  const dim3 chunks(1, (j + 1 + kDotChunk - 1) / kDotChunk);
+  if (N % VEC == 0) {
+    static const int per_sm = resident_blocks(multidot_kernel<Tv, VEC>);
+    dim3 grid(wave_grid(per_sm, N / VEC), chunks.y);
+    multidot_kernel<Tv, VEC><<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+  } else {
+    static const int per_sm = resident_blocks(multidot_kernel<Tv, 1>);
+    dim3 grid(wave_grid(per_sm, N), chunks.y);
+    multidot_kernel<Tv, 1><<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+  }
 }
 template <typename Tv>
 void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s) {
-  static const int per_sm = resident_blocks(update_kernel<Tv>);
-  update_kernel<Tv><<<wave_grid(per_sm, N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st);
+  constexpr int VEC = 16 / sizeof(Tv);
+  if (N % VEC == 0) {
+    static const int per_sm = resident_blocks(update_kernel<Tv, VEC>);
+    update_kernel<Tv, VEC><<<wave_grid(per_sm, N / VEC), kBlock, 0, s>>>(V, N, j, final_pass, partials, st);
+  } else {
+    static const int per_sm = resident_blocks(update_kernel<Tv, 1>);
+    update_kernel<Tv, 1><<<wave_grid(per_sm, N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st);
+  }
 }
 template void launch_multidot<double>(const double*, size_t, int, int, double*, SolverState*, cudaStream_t);
 template void launch_multidot<df>(const df*, size_t, int, int, double*, SolverState*, cudaStream_t);
