@@ -18,6 +18,7 @@
 // keeps only the leading matrix of every pair.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "dst_gemm.cuh"
@@ -50,15 +51,16 @@ struct Bf16Mat {
   __nv_bfloat16* hi = nullptr;
   __nv_bfloat16* lo = nullptr;
   int rows = 0, cols = 0, ld = 0;
-  CUtensorMap map_hi, map_lo;
+  CUtensorMap map_hi, map_lo;      // tiles of 128 rows (A operands, 128-wide B)
+  CUtensorMap map64_hi, map64_lo;  // tiles of 64 rows (64-wide B)
 };
 
-bool make_map(CUtensorMap* m, void* p, int rows, int cols, int ld) {
+bool make_map(CUtensorMap* m, void* p, int rows, int cols, int ld, int box_rows = kGemmBM) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t stride[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kGemmBK, (cuuint32_t)kGemmBM};
+  cuuint32_t box[2] = {(cuuint32_t)kGemmBK, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p, dim, stride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -72,7 +74,9 @@ __device__ __forceinline__ float scaled_f32(double, float scf, df v) { return __
 __device__ __forceinline__ float scaled_f32(double, float scf, float v) { return __fmul_rn(scf, v); }
 
 // Column x goes to column sym_perm(x, hk) (the symmetric GEMM's K layout;
-// hk = 0: natural order).
+// hk = 0: natural order).  FP32 rows whose length is a multiple of 4 move four
+// values per thread (one 16-byte load; in the symmetric layout the even and
+// the odd pair each land as one 4-byte store).
 template <typename Tin, int NT>
 __global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v, const double* scale,
                                                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
@@ -80,6 +84,21 @@ __global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v
   if (gate && *(volatile const int*)gate == 0) return;
   const double sc = scale ? *scale : 1.0;
   const float scf = (float)sc;
+  if constexpr (std::is_same<Tin, float>::value && NT == 1) {
+    if (hk && (n1 & 3) == 0) {
+      const int q1 = n1 >> 2;
+      for (int j = blockIdx.y; j < n2; j += gridDim.y)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < q1; i += gridDim.x * blockDim.x) {
+          const float4 t = *reinterpret_cast<const float4*>(v + (size_t)j * n1 + 4 * i);
+          // x = 4i, 4i+2 (even) -> columns 2i, 2i+1; x = 4i+1, 4i+3 (odd) -> hk + 2i, hk + 2i + 1
+          const __nv_bfloat162 ev = __floats2bfloat162_rn(__fmul_rn(scf, t.x), __fmul_rn(scf, t.z));
+          const __nv_bfloat162 od = __floats2bfloat162_rn(__fmul_rn(scf, t.y), __fmul_rn(scf, t.w));
+          *reinterpret_cast<__nv_bfloat162*>(hi + (size_t)j * ld + 2 * i) = ev;
+          *reinterpret_cast<__nv_bfloat162*>(hi + (size_t)j * ld + hk + 2 * i) = od;
+        }
+      return;
+    }
+  }
   for (int j = blockIdx.y; j < n2; j += gridDim.y)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
       const float x = scaled_f32(sc, scf, v[(size_t)j * n1 + i]);
@@ -205,7 +224,9 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
       off += (bytes + 255) / 256 * 256;
     }
     if (!make_map(&sp.m->map_hi, sp.m->hi, sp.rows, sp.cols, sp.ld) ||
-        !make_map(&sp.m->map_lo, sp.m->lo, sp.rows, sp.cols, sp.ld)) {
+        !make_map(&sp.m->map_lo, sp.m->lo, sp.rows, sp.cols, sp.ld) ||
+        !make_map(&sp.m->map64_hi, sp.m->hi, sp.rows, sp.cols, sp.ld, 64) ||
+        !make_map(&sp.m->map64_lo, sp.m->lo, sp.rows, sp.cols, sp.ld, 64)) {
       cudaFree(p->mem);
       delete p;
       return RSFDE_ECUDA;
@@ -245,13 +266,25 @@ int bf16_plan_error(Bf16Plan* p, cudaStream_t s) {
   return h ? RSFDE_ETIMEOUT : RSFDE_OK;
 }
 
-template <int EPI, int NT, bool SYM>
+template <int EPI, int NT, bool SYM, int BN>
 static void launch_gemm_t(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
                           const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
-  auto k = dst_gemm_kernel<EPI, NT, SYM>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem(NT));
-  dim3 grid((N + kGemmBN - 1) / kGemmBN, (M + kGemmBM - 1) / kGemmBM, channels);
-  k<<<grid, 128, gemm_smem(NT), s>>>(A.map_hi, A.map_lo, B.map_hi, B.map_lo, K, ep, err, gate);
+  auto k = dst_gemm_kernel<EPI, NT, SYM, BN>;
+  constexpr int smem = gemm_smem(NT, BN);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  dim3 grid((N + BN - 1) / BN, (M + kGemmBM - 1) / kGemmBM, channels);
+  const CUtensorMap& bh = BN == 64 ? B.map64_hi : B.map_hi;
+  const CUtensorMap& bl = BN == 64 ? B.map64_lo : B.map_lo;
+  k<<<grid, 128, smem, s>>>(A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
+}
+template <int EPI, int NT, bool SYM>
+static void launch_gemm_bn(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
+                           const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
+  // 64-wide tiles while 128-wide ones would leave SMs idle (measured: with
+  // at least one 128-wide tile per SM the wider tiles are faster)
+  const long tiles128 = (long)((N + 127) / 128) * ((M + kGemmBM - 1) / kGemmBM) * channels;
+  if (tiles128 < kNumSMs) launch_gemm_t<EPI, NT, SYM, 64>(A, B, M, N, K, channels, ep, err, gate, s);
+  else launch_gemm_t<EPI, NT, SYM, 128>(A, B, M, N, K, channels, ep, err, gate, s);
 }
 // D = A S for a transform of length n along K; the symmetric form (hk > 0)
 // computes the n/2 output pairs from the K operand's two halves.
@@ -263,11 +296,11 @@ static void launch_gemm(const Bf16Plan* p, int hk, const Bf16Mat& A, const Bf16M
   ep.n_full = hk ? n : 0;
   const int K = hk ? 2 * hk : n;
   if (p->nt == 3) {
-    if (hk) launch_gemm_t<EPI, 3, true>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
-    else launch_gemm_t<EPI, 3, false>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+    if (hk) launch_gemm_bn<EPI, 3, true>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+    else launch_gemm_bn<EPI, 3, false>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
   } else {
-    if (hk) launch_gemm_t<EPI, 1, true>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
-    else launch_gemm_t<EPI, 1, false>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+    if (hk) launch_gemm_bn<EPI, 1, true>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+    else launch_gemm_bn<EPI, 1, false>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
   }
 }
 

@@ -25,13 +25,19 @@
 
 namespace rsfde {
 
-constexpr int kGemmBM = 128, kGemmBN = 128, kGemmBK = 64, kGemmStages = 3;
-constexpr int kGemmTileBytes = kGemmBM * kGemmBK * 2;  // 16 KB (BM == BN)
+constexpr int kGemmBM = 128, kGemmBK = 64, kGemmStages = 3;
+constexpr int kGemmATileBytes = kGemmBM * kGemmBK * 2;  // 16 KB
+// B tile: BN rows (64 or 128) of 64 BF16
+__host__ __device__ constexpr int gemm_btile_bytes(int BN) { return BN * kGemmBK * 2; }
 // per stage: A_hi, A_lo, B_hi, B_lo (NT = 3) or A_hi, B_hi (NT = 1)
-__host__ __device__ constexpr int gemm_stage_bytes(int NT) { return (NT == 3 ? 4 : 2) * kGemmTileBytes; }
-__host__ __device__ constexpr int gemm_smem(int NT) {
-  return kGemmStages * gemm_stage_bytes(NT) + 1024;  // + alignment slack
+__host__ __device__ constexpr int gemm_stage_bytes(int NT, int BN) {
+  return (NT == 3 ? 2 : 1) * (kGemmATileBytes + gemm_btile_bytes(BN));
 }
+__host__ __device__ constexpr int gemm_smem(int NT, int BN) {
+  return kGemmStages * gemm_stage_bytes(NT, BN) + 1024;  // + alignment slack
+}
+// CTAs that share an SM: shared memory (and TMEM: at most 2 x 128 or 3 x 128 columns)
+__host__ __device__ constexpr int gemm_ctas_per_sm(int NT, int BN) { return NT == 3 ? 1 : (BN == 64 ? 3 : 2); }
 
 enum GemmEpi {
   EPI_SPLIT_T = 0,   // out^T (BF16, or split BF16 pair); rows m >= row_b go to the second channel's columns
@@ -75,14 +81,16 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
   if (NT == 3) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-template <int EPI, int NT, bool SYM>
-__global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
+template <int EPI, int NT, bool SYM, int BN>
+__global__ void __launch_bounds__(128, gemm_ctas_per_sm(NT, BN))
     dst_gemm_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                     const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, int K,
                     GemmEpiParams ep, int* err, const int* gate) {
   static_assert(NT == 1 || NT == 3, "one or three BF16 products");
-  constexpr int kStageBytes = gemm_stage_bytes(NT);
-  constexpr uint32_t kCols = SYM ? 2 * kGemmBN : kGemmBN;  // TMEM columns: one or two accumulators
+  static_assert(BN == 64 || BN == 128, "64- or 128-wide tiles");
+  constexpr int kStageBytes = gemm_stage_bytes(NT, BN);
+  constexpr int kB = gemm_btile_bytes(BN);
+  constexpr uint32_t kCols = SYM ? 2 * BN : BN;  // TMEM columns: one or two accumulators
   if (gate && *(volatile const int*)gate == 0) return;
   extern __shared__ __align__(1024) uint8_t gemm_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -105,11 +113,15 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = tmem_base;
-  const int m0 = blockIdx.y * kGemmBM, n0 = blockIdx.x * kGemmBN, ch = blockIdx.z;
+  const int m0 = blockIdx.y * kGemmBM, n0 = blockIdx.x * BN, ch = blockIdx.z;
   const int a_koff = ch * ep.a_koff;
   const int KB = (K + kGemmBK - 1) / kGemmBK;  // SYM: K = 2 hk, KB even
   const int KBh = SYM ? KB / 2 : KB;
-  auto tile = [&](int s, int which) { return smem + s * kStageBytes + which * kGemmTileBytes; };
+  // stage layout: A_hi, [A_lo], B_hi, [B_lo] (all 1024-byte aligned)
+  auto a_tile = [&](int s, int lo) { return smem + s * kStageBytes + lo * kGemmATileBytes; };
+  auto b_tile = [&](int s, int lo) {
+    return smem + s * kStageBytes + (NT == 3 ? 2 : 1) * kGemmATileBytes + lo * kB;
+  };
 
   if (warp == 0 && lane == 0) {  // TMA producer
     int issued = 0;
@@ -117,14 +129,11 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
       const int s = kb % kGemmStages, it = kb / kGemmStages;
       if (kb >= kGemmStages && !mbar_wait(&empty[s], (it - 1) & 1, err)) break;
       mbar_expect_tx(&full[s], kStageBytes);
+      tma_load_2d(a_tile(s, 0), &tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
+      tma_load_2d(b_tile(s, 0), &tB_hi, kb * kGemmBK, n0, &full[s]);
       if (NT == 3) {
-        tma_load_2d(tile(s, 0), &tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
-        tma_load_2d(tile(s, 1), &tA_lo, a_koff + kb * kGemmBK, m0, &full[s]);
-        tma_load_2d(tile(s, 2), &tB_hi, kb * kGemmBK, n0, &full[s]);
-        tma_load_2d(tile(s, 3), &tB_lo, kb * kGemmBK, n0, &full[s]);
-      } else {
-        tma_load_2d(tile(s, 0), &tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
-        tma_load_2d(tile(s, 1), &tB_hi, kb * kGemmBK, n0, &full[s]);
+        tma_load_2d(a_tile(s, 1), &tA_lo, a_koff + kb * kGemmBK, m0, &full[s]);
+        tma_load_2d(b_tile(s, 1), &tB_lo, kb * kGemmBK, n0, &full[s]);
       }
       issued = kb + 1;
     }
@@ -133,18 +142,18 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
         mbar_wait(&full[kb % kGemmStages], (kb / kGemmStages) & 1, err);
     }
   } else if (warp == 1 && lane == 0) {  // MMA issuer
-    constexpr uint32_t idesc = umma_idesc_bf16(kGemmBM, kGemmBN);
+    constexpr uint32_t idesc = umma_idesc_bf16(kGemmBM, BN);
     for (int kb = 0; kb < KB; ++kb) {
       const int s = kb % kGemmStages, it = kb / kGemmStages;
       if (!mbar_wait(&full[s], it & 1, err)) break;
       tc_fence_after();
       // SYM: even-j half into the first accumulator, odd-j half into the second
-      const uint32_t acc = (SYM && kb >= KBh) ? taddr + kGemmBN : taddr;
+      const uint32_t acc = (SYM && kb >= KBh) ? taddr + BN : taddr;
       const bool first = SYM ? (kb == 0 || kb == KBh) : (kb == 0);
-      const uint64_t a_hi = umma_desc_sw128(smem_u32(tile(s, 0)));
-      const uint64_t a_lo = umma_desc_sw128(smem_u32(tile(s, 1)));  // NT = 1: B_hi
-      const uint64_t b_hi = NT == 3 ? umma_desc_sw128(smem_u32(tile(s, 2))) : a_lo;
-      const uint64_t b_lo = NT == 3 ? umma_desc_sw128(smem_u32(tile(s, 3))) : 0;
+      const uint64_t a_hi = umma_desc_sw128(smem_u32(a_tile(s, 0)));
+      const uint64_t b_hi = umma_desc_sw128(smem_u32(b_tile(s, 0)));
+      const uint64_t a_lo = NT == 3 ? umma_desc_sw128(smem_u32(a_tile(s, 1))) : 0;
+      const uint64_t b_lo = NT == 3 ? umma_desc_sw128(smem_u32(b_tile(s, 1))) : 0;
 #pragma unroll
       for (int k = 0; k < kGemmBK / 16; ++k) {  // 16 BF16 = 32 bytes per MMA: start address + 2
         const uint64_t dk = (uint64_t)(2 * k);
@@ -170,10 +179,10 @@ __global__ void __launch_bounds__(128, NT == 3 ? 1 : 2)
     const int col = (EPI == EPI_SPLIT_T && m >= ep.row_b) ? ep.col_b + sym_perm(m - ep.row_b, ep.hk)
                                                            : sym_perm(m, ep.hk);
     const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    for (int c = 0; c < kGemmBN / 32; ++c) {
+    for (int c = 0; c < BN / 32; ++c) {
       float u[32], e[32];
       tmem_ld32(taddr + lane_off + (uint32_t)(c * 32), u);  // whole warp
-      if constexpr (SYM) tmem_ld32(taddr + lane_off + (uint32_t)(kGemmBN + c * 32), e);
+      if constexpr (SYM) tmem_ld32(taddr + lane_off + (uint32_t)(BN + c * 32), e);
       const int nb = n0 + c * 32;
       if (nb >= ep.N) continue;  // uniform over the block
       const int nq = min(32, ep.N - nb);

@@ -351,7 +351,7 @@ struct XAcc<float> {
   static __device__ __forceinline__ double value(df acc) { return double(acc); }
 };
 
-template <typename Tz>
+template <typename Tz, int VEC>
 __global__ void __launch_bounds__(kBlock) xupdate_kernel(double* __restrict__ x, const Tz* __restrict__ Z, size_t N,
                                                          SolverState* st) {
   if (closed(&st->run_cycle)) return;
@@ -361,17 +361,32 @@ __global__ void __launch_bounds__(kBlock) xupdate_kernel(double* __restrict__ x,
   __shared__ typename A::C y[kMaxRestart];
   for (int i = threadIdx.x; i < J; i += blockDim.x) y[i] = A::coef(st->y[i]);
   __syncthreads();
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
-    typename A::C acc = A::zero();
-    for (int i0 = 0; i0 < J; i0 += 8) {
-      Tz a[8];
+  const size_t NP = N / VEC;  // VEC divides N (launcher)
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NP; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t p = q * VEC;
+    typename A::C acc[VEC];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) a[k] = i0 + k < J ? Z[(size_t)(i0 + k) * N + p] : Tz(0);
+    for (int e = 0; e < VEC; ++e) acc[e] = A::zero();
+    for (int i0 = 0; i0 < J; i0 += 8) {
+      Tz a[8][VEC];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (i0 + k < J) {
+          ld_vec<Tz, VEC>(Z + (size_t)(i0 + k) * N + p, a[k]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) a[k][e] = Tz(0);
+        }
+      }
 #pragma unroll
       for (int k = 0; k < 8; ++k)
-        if (i0 + k < J) acc = A::fma(acc, y[i0 + k], a[k]);
+        if (i0 + k < J) {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) acc[e] = A::fma(acc[e], y[i0 + k], a[k][e]);
+        }
     }
-    x[p] += A::value(acc);
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) x[p + e] += A::value(acc[e]);
   }
 }
 
@@ -544,7 +559,9 @@ template void launch_update<float>(float*, size_t, int, int, double*, SolverStat
 void launch_solve_y(SolverState* st, cudaStream_t s) { solve_y_kernel<<<1, 32, 0, s>>>(st); }
 template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s) {
-  xupdate_kernel<Tz><<<vec_grid(N), kBlock, 0, s>>>(x, Z, N, st);
+  constexpr int VEC = 16 / sizeof(Tz);
+  if (N % VEC == 0) xupdate_kernel<Tz, VEC><<<vec_grid(N / VEC), kBlock, 0, s>>>(x, Z, N, st);
+  else xupdate_kernel<Tz, 1><<<vec_grid(N), kBlock, 0, s>>>(x, Z, N, st);
 }
 template void launch_xupdate<double>(double*, const double*, size_t, SolverState*, cudaStream_t);
 template void launch_xupdate<float>(double*, const float*, size_t, SolverState*, cudaStream_t);
