@@ -526,13 +526,13 @@ def run_op(args):
 def run_batched(args):
     """Times the batched workload: 256 independent instances (grid side
     uniform in 64..512, random alpha, k, ellipse or polygon domain), each
-    advanced by one CUDA graph launch per time step, FP32 preconditioner,
-    double-FP32 Arnoldi operator, FP64 residual to 1e-10."""
+    advanced by one CUDA graph launch per time step (--batch-precond,
+    --matvec, --resid select the precisions), residual to 1e-10."""
     import torch
     from paper_2102_11576_gb300 import Batch, workloads
     probs = workloads.make_batch(seed=0, count=args.batch_count)
     t0 = time.perf_counter()
-    b = Batch(probs, precond=args.batch_precond, matvec="df32")
+    b = Batch(probs, precond=args.batch_precond, matvec=args.matvec, resid=args.resid)
     for i, p in enumerate(probs):
         b.set(i, p["u0"])
     if not args.no_autotune:
@@ -551,7 +551,8 @@ def run_batched(args):
     iters = [s["iters"] for s in st]
     print(json.dumps({"workload": f"batched: {len(probs)} instances, n in 64..512 (sum N = {unknowns}), "
                                   "random alpha/k/domain, FGMRES(20), tol 1e-10",
-                      "form": f"{args.batch_precond} preconditioner, double-FP32 Arnoldi operator",
+                      "form": f"{args.batch_precond} preconditioner, {args.matvec} Arnoldi operator and basis, "
+                              f"{args.resid} true residual",
                       "steps": args.steps, "ms_per_batch_step": ms / args.steps,
                       "instance_steps_per_s": len(probs) * args.steps / (ms / 1e3),
                       "unknown_steps_per_s": unknowns * args.steps / (ms / 1e3),
@@ -572,7 +573,8 @@ def run_adjoint(args):
     w = workloads.make("disk1024")
     steps = args.steps if args.steps != 10 else w["steps"]
     s = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
-               w["dt"], w["eta"], restart=w["restart"], tol=w["tol"], precond="fp32", matvec="df32")
+               w["dt"], w["eta"], restart=w["restart"], tol=w["tol"], precond=args.precond, matvec=args.matvec,
+               resid=args.resid)
     dev = torch.device("cuda")
     u0 = torch.as_tensor(w["u0"]).to(dev).requires_grad_(True)
     src = torch.zeros_like(u0).requires_grad_(True)
@@ -590,7 +592,8 @@ def run_adjoint(args):
     t2 = time.perf_counter()
     print(json.dumps({"workload": f"disk1024: 1024x1024 unit disk, alpha=(1.5,1.5), {steps} steps, "
                                   f"checkpoint every {math.ceil(math.sqrt(steps))}",
-                      "form": "FP32 preconditioner, double-FP32 Arnoldi operator, FP64 residual",
+                      "form": f"{args.precond} preconditioner, {args.matvec} Arnoldi operator and basis, "
+                              f"{args.resid} true residual",
                       "loss": loss.item(), "forward_s": t1 - t0, "backward_s": t2 - t1,
                       "gradient_evals_per_s": 1.0 / (t2 - t0),
                       "forward_steps_per_s": steps / (t1 - t0),
@@ -605,7 +608,7 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="time the batched workload (256 instances of uneven size)")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--batch-precond", default="fp32")
+    ap.add_argument("--batch-precond", default="bf16")
     ap.add_argument("--adjoint", action="store_true",
                     help="time one differentiable march of the 1024^2 differentiation workload")
     ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "apply_M_fp32", "precond_fp32", "precond_fp64",
