@@ -344,10 +344,11 @@ int ensure_bf16(rsfde_ctx* c) {
 
 // The tensor-core preconditioner z = P-hat^-1 (scale * v) (five launches).
 template <typename Tz, typename Tin>
-void enqueue_precond_bf16(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate) {
+void enqueue_precond_bf16(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate,
+                          bool first_operand_ready = false) {
   ProfScope ps(c, RSFDE_K_DST_GEMM);
-  c->launches += 5;
-  bf16_precond<Tz, Tin>(c->bf16, v, vscale, z, c->phi, c->pen, gate, c->stream);
+  c->launches += first_operand_ready ? 4 : 5;
+  bf16_precond<Tz, Tin>(c->bf16, v, vscale, z, c->phi, c->pen, gate, c->stream, first_operand_ready, vscale);
 }
 
 // ---- enqueue helpers ---------------------------------------------------------
@@ -396,7 +397,8 @@ void enqueue_precond_t(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, 
 
 // z = P-hat^-1 (scale * v) into an FP64 vector, in the context's preconditioner precision.
 template <typename Tz, typename Tin>
-void enqueue_precond_bf16(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate);
+void enqueue_precond_bf16(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate,
+                          bool first_operand_ready);
 
 void enqueue_precond64(rsfde_ctx* c, const double* v, const double* vscale, double* z, const int* gate) {
   if (bf16_precond_on(c)) enqueue_precond_bf16<double, double>(c, v, vscale, z, gate);
@@ -506,12 +508,18 @@ void enqueue_cycle_t(rsfde_ctx* c) {
   const int* gc = &c->st->run_cycle;
   Tz* Z = static_cast<Tz*>(c->Z);
   Tv* V = reinterpret_cast<Tv*>(c->V);
+  // Plain-BF16 preconditioner with an FP32 basis: the final update pass of
+  // iteration j also writes V_{j+1} rounded to BF16 as the first GEMM operand
+  // of iteration j+1, whose split pass is then skipped.
+  Bf16Out bo{};
+  const bool fused = std::is_same<Tv, float>::value && c->opts.use_precond && bf16_precond_on(c) &&
+                     bf16_plan_a0(c->bf16, &bo);
   for (int j = 0; j < m; ++j) {
     const Tv* vj = V + (size_t)j * N;
     Tz* zj = Z + (size_t)j * N;
     if (c->opts.use_precond) {
       if (bf16_precond_on(c))
-        enqueue_precond_bf16<Tz, Tv>(c, vj, &c->st->s[j], zj, gi);
+        enqueue_precond_bf16<Tz, Tv>(c, vj, &c->st->s[j], zj, gi, fused && j > 0);
       else if (fp32_precond(c))
         enqueue_precond_t<float, Tz, Tv>(c, vj, &c->st->s[j], zj, gi, c->x32.tab, c->y32.tab);
       else
@@ -532,7 +540,8 @@ void enqueue_cycle_t(rsfde_ctx* c) {
         launch_multidot<Tv>(V, N, j, pass, c->partials, c->st, c->stream);
       }
       ProfScope ps(c, RSFDE_K_UPDATE);
-      launch_update<Tv>(V, N, j, (!cgs2 || pass == 1) ? 1 : 0, c->partials, c->st, c->stream);
+      launch_update<Tv>(V, N, j, (!cgs2 || pass == 1) ? 1 : 0, c->partials, c->st, c->stream,
+                        fused && j + 1 < m ? &bo : nullptr);
     }
   }
   {

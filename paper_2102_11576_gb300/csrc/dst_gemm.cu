@@ -304,11 +304,19 @@ static void launch_gemm(const Bf16Plan* p, int hk, const Bf16Mat& A, const Bf16M
   }
 }
 
+bool bf16_plan_a0(const Bf16Plan* p, Bf16Out* out) {
+  if (!p || p->nt != 1 || p->h1 == 0 || p->n1 % 4 != 0) return false;
+  *out = Bf16Out{p->A0.hi, p->n1, p->ld1, p->h1};
+  return true;
+}
+
 template <typename Tz, typename Tin>
 int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
-                 const int* gate, cudaStream_t s) {
+                 const int* gate, cudaStream_t s, bool skip_split, const double* zscale) {
   const int n1 = p->n1, n2 = p->n2;
-  if (p->nt == 3)
+  if (skip_split) {
+    // A0 already holds the unscaled vector (update_kernel); scale at the end
+  } else if (p->nt == 3)
     split_kernel<Tin, 3><<<split_grid(n1, n2), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, p->h1,
                                                                gate);
   else
@@ -349,22 +357,23 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.phibits = p->phibits;
   ep.wpc = p->wpc;
   ep.ldz = n1;
+  ep.zscale = skip_split ? zscale : nullptr;
   ep.a_koff = p->ld2;
   launch_gemm<EPI_COMBINE_T>(p, p->h2, p->Yt, p->Sy, n1, n2, 2, ep, gate, s);
   return cudaGetLastError() == cudaSuccess ? RSFDE_OK : RSFDE_ECUDA;
 }
 
 template int bf16_precond<float, double>(Bf16Plan*, const double*, const double*, float*, const uint8_t*, double,
-                                         const int*, cudaStream_t);
+                                         const int*, cudaStream_t, bool, const double*);
 template int bf16_precond<double, double>(Bf16Plan*, const double*, const double*, double*, const uint8_t*,
-                                          double, const int*, cudaStream_t);
+                                          double, const int*, cudaStream_t, bool, const double*);
 template int bf16_precond<float, df>(Bf16Plan*, const df*, const double*, float*, const uint8_t*, double,
-                                     const int*, cudaStream_t);
+                                     const int*, cudaStream_t, bool, const double*);
 template int bf16_precond<double, df>(Bf16Plan*, const df*, const double*, double*, const uint8_t*, double,
-                                      const int*, cudaStream_t);
+                                      const int*, cudaStream_t, bool, const double*);
 template int bf16_precond<float, float>(Bf16Plan*, const float*, const double*, float*, const uint8_t*, double,
-                                        const int*, cudaStream_t);
+                                        const int*, cudaStream_t, bool, const double*);
 template int bf16_precond<double, float>(Bf16Plan*, const float*, const double*, double*, const uint8_t*, double,
-                                         const int*, cudaStream_t);
+                                         const int*, cudaStream_t, bool, const double*);
 
 }  // namespace rsfde

@@ -71,6 +71,7 @@ struct GemmEpiParams {
   const uint32_t* phibits;  // EPI_COMBINE_T: Phi transposed and bit-packed, bit y%32 of word
   int wpc;                  //   [x * wpc + y/32] is 1 where (x, y) lies outside Omega
   int ldz;
+  const double* zscale;  // EPI_COMBINE_T: if set, z is scaled by *zscale (unscaled first operand)
   int a_koff;           // K offset of channel 1's A operand (EPI_COMBINE_T, blockIdx.z = 1)
 };
 
@@ -233,12 +234,13 @@ __global__ void __launch_bounds__(128, gemm_ctas_per_sm(NT, BN))
           bb = (mvalid && wb != wt) ? __ldg(colbits + wb) : bt;
         }
         const uint32_t want = (uint32_t)ch;
+        const float zs = ep.zscale ? (float)*ep.zscale : 1.0f;
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
           if (q < nq && mvalid) {
             if (((b0 >> q) & 1u) == want) {
               const int p = (nb + q) * ep.ldz + m;
-              const float y = SYM ? u[q] + e[q] : u[q];
+              const float y = zs * (SYM ? u[q] + e[q] : u[q]);
               if (ep.z_double) static_cast<double*>(ep.z)[p] = (double)y;
               else static_cast<float*>(ep.z)[p] = y;
             }
@@ -247,8 +249,8 @@ __global__ void __launch_bounds__(128, gemm_ctas_per_sm(NT, BN))
               const uint32_t word = ((yy >> 5) == (ytop >> 5)) ? bt : bb;
               if (((word >> (yy & 31)) & 1u) == want) {
                 const int p = yy * ep.ldz + m;
-                if (ep.z_double) static_cast<double*>(ep.z)[p] = (double)(u[q] - e[q]);
-                else static_cast<float*>(ep.z)[p] = u[q] - e[q];
+                if (ep.z_double) static_cast<double*>(ep.z)[p] = (double)(zs * (u[q] - e[q]));
+                else static_cast<float*>(ep.z)[p] = zs * (u[q] - e[q]);
               }
             }
           }

@@ -1,5 +1,6 @@
 // internal.h -- declarations shared by the library's translation units.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -132,6 +133,14 @@ template <typename T, typename Tz>
 void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, int n1, int n2,
                          const AxisTables<T>& ax, const int* gate, cudaStream_t s);
 
+// Optional second output of the final update pass (FP32 basis): the new
+// vector rounded to BF16 in the symmetric GEMM's K layout (row y at a0 + y*ld,
+// even x at x/2, odd x at hk + x/2), the next preconditioner's first operand.
+struct Bf16Out {
+  __nv_bfloat16* a0;
+  int n1, ld, hk;
+};
+
 // ---- split-BF16 tensor-core preconditioner (dst_gemm.cu) --------------------
 struct Bf16Plan;
 // nt: BF16 products per GEMM, 3 (split BF16) or 1 (plain BF16)
@@ -141,9 +150,14 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
 int bf16_plan_nt(const Bf16Plan* p);
 void bf16_plan_destroy(Bf16Plan* p);
 int bf16_plan_error(Bf16Plan* p, cudaStream_t s);
+// skip_split: the first operand was already written (update_kernel's Bf16Out,
+// unscaled), and zscale multiplies the result instead.
 template <typename Tz, typename Tin>
 int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
-                 const int* gate, cudaStream_t s);
+                 const int* gate, cudaStream_t s, bool skip_split = false, const double* zscale = nullptr);
+// The Bf16Out target of the plan's first operand, if the plan can take it
+// (plain BF16, symmetric layout, n1 a multiple of 4); returns false otherwise.
+bool bf16_plan_a0(const Bf16Plan* p, Bf16Out* out);
 
 // ---- launchers (krylov.cu) -------------------------------------------------
 int vec_grid(size_t N);
@@ -158,7 +172,8 @@ template <typename Tv>
 void launch_multidot(const Tv* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
                      cudaStream_t s);
 template <typename Tv>
-void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s);
+void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s,
+                   const Bf16Out* bo = nullptr);
 void launch_solve_y(SolverState* st, cudaStream_t s);
 template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s);

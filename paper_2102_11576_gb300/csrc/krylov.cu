@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
 constexpr int kUpdChunk = 8;
 template <typename Tv, int VEC>
 __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size_t N, int j, int final_pass,
-                                                        double* partials, SolverState* st) {
+                                                        double* partials, SolverState* st, Bf16Out bo) {
   if (closed(&st->run_iter)) return;
   using Op = VecOps<Tv>;
   __shared__ double wsum[1][kWarps];
@@ -305,6 +305,14 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size
         }
     }
     st_vec<Tv, VEC>(w + p, val);
+    if constexpr (std::is_same<Tv, float>::value && VEC == 4) {
+      if (bo.a0 && final_pass) {  // x = p mod n1 is a multiple of 4 (n1 is)
+        const int y = (int)(p / (size_t)bo.n1), x = (int)(p - (size_t)y * bo.n1);
+        __nv_bfloat16* row = bo.a0 + (size_t)y * bo.ld + (x >> 1);
+        *reinterpret_cast<__nv_bfloat162*>(row) = __floats2bfloat162_rn(val[0], val[2]);
+        *reinterpret_cast<__nv_bfloat162*>(row + bo.hk) = __floats2bfloat162_rn(val[1], val[3]);
+      }
+    }
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc = Op::fma(acc, val[e], val[e]);
   }
@@ -540,22 +548,27 @@ void launch_multidot(const Tv* V, size_t N, int j, int accumulate, double* parti
   }
 }
 template <typename Tv>
-void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s) {
+void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s,
+                   const Bf16Out* bo) {
   constexpr int VEC = 16 / sizeof(Tv);
+  const Bf16Out none{nullptr, 1, 0, 0};
   if (N % VEC == 0) {
     static const int per_sm = resident_blocks(update_kernel<Tv, VEC>);
-    update_kernel<Tv, VEC><<<wave_grid(per_sm, N / VEC), kBlock, 0, s>>>(V, N, j, final_pass, partials, st);
-  } else {
+    update_kernel<Tv, VEC><<<wave_grid(per_sm, N / VEC), kBlock, 0, s>>>(V, N, j, final_pass, partials, st,
+                                                                        bo ? *bo : none);
+  } else {  // (the BF16 copy is only taken with 16-byte packs)
     static const int per_sm = resident_blocks(update_kernel<Tv, 1>);
-    update_kernel<Tv, 1><<<wave_grid(per_sm, N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st);
+    update_kernel<Tv, 1><<<wave_grid(per_sm, N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st, none);
   }
 }
 template void launch_multidot<double>(const double*, size_t, int, int, double*, SolverState*, cudaStream_t);
 template void launch_multidot<df>(const df*, size_t, int, int, double*, SolverState*, cudaStream_t);
-template void launch_update<double>(double*, size_t, int, int, double*, SolverState*, cudaStream_t);
-template void launch_update<df>(df*, size_t, int, int, double*, SolverState*, cudaStream_t);
+template void launch_update<double>(double*, size_t, int, int, double*, SolverState*, cudaStream_t,
+                                    const Bf16Out*);
+template void launch_update<df>(df*, size_t, int, int, double*, SolverState*, cudaStream_t, const Bf16Out*);
 template void launch_multidot<float>(const float*, size_t, int, int, double*, SolverState*, cudaStream_t);
-template void launch_update<float>(float*, size_t, int, int, double*, SolverState*, cudaStream_t);
+template void launch_update<float>(float*, size_t, int, int, double*, SolverState*, cudaStream_t,
+                                   const Bf16Out*);
 void launch_solve_y(SolverState* st, cudaStream_t s) { solve_y_kernel<<<1, 32, 0, s>>>(st); }
 template <typename Tz>
 void launch_xupdate(double* x, const Tz* Z, size_t N, SolverState* st, cudaStream_t s) {
