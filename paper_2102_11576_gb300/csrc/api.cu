@@ -804,6 +804,12 @@ int autotune_ctx(rsfde_ctx* c, int reps, int32_t* chosen_out) {
   if (c->opts.matvec_prec == RSFDE_DF32) tune_operator<df>(c, reps, c->xdf.tab, c->ydf.tab, chosen);
   else if (c->opts.matvec_prec == RSFDE_FP32) tune_operator<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
   else tune_operator<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
+  // the double-FP32 true residual runs the same transform families in 8-byte
+  // arithmetic (recorded separately from the 4-byte shapes)
+  if (c->opts.resid_prec == RSFDE_DF32 && c->opts.matvec_prec != RSFDE_DF32) {
+    int unused[TK_COUNT] = {0};
+    tune_operator<df>(c, reps, c->xdf.tab, c->ydf.tab, unused);
+  }
   if (c->opts.precond_prec == RSFDE_FP32) tune_precond<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
   else if (c->opts.precond_prec == RSFDE_FP64) tune_precond<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
   c->graph_key = -1;  // captured launches carry the old shapes

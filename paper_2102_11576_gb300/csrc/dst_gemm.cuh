@@ -25,7 +25,10 @@
 
 namespace rsfde {
 
-constexpr int kGemmBM = 128, kGemmBK = 64, kGemmStages = 3;
+constexpr int kGemmBM = 128, kGemmBK = 64;
+// Ring depth: as many stages as fit beside a second CTA on the SM (the TMA
+// round trip, not bandwidth, bounds these short-K GEMMs).
+__host__ __device__ constexpr int gemm_stages(int NT, int BN) { return (NT == 1 && BN == 64) ? 4 : 3; }
 constexpr int kGemmATileBytes = kGemmBM * kGemmBK * 2;  // 16 KB
 // B tile: BN rows (64 or 128) of 64 BF16
 __host__ __device__ constexpr int gemm_btile_bytes(int BN) { return BN * kGemmBK * 2; }
@@ -34,10 +37,10 @@ __host__ __device__ constexpr int gemm_stage_bytes(int NT, int BN) {
   return (NT == 3 ? 2 : 1) * (kGemmATileBytes + gemm_btile_bytes(BN));
 }
 __host__ __device__ constexpr int gemm_smem(int NT, int BN) {
-  return kGemmStages * gemm_stage_bytes(NT, BN) + 1024;  // + alignment slack
+  return gemm_stages(NT, BN) * gemm_stage_bytes(NT, BN) + 1024;  // + alignment slack
 }
-// CTAs that share an SM: shared memory (and TMEM: at most 2 x 128 or 3 x 128 columns)
-__host__ __device__ constexpr int gemm_ctas_per_sm(int NT, int BN) { return NT == 3 ? 1 : (BN == 64 ? 3 : 2); }
+// CTAs that share an SM: shared memory (and TMEM: at most 2 x 256 columns)
+__host__ __device__ constexpr int gemm_ctas_per_sm(int NT, int BN) { return NT == 3 ? 1 : 2; }
 
 enum GemmEpi {
   EPI_SPLIT_T = 0,   // out^T (BF16, or split BF16 pair); rows m >= row_b go to the second channel's columns
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(128, gemm_ctas_per_sm(NT, BN))
   static_assert(BN == 64 || BN == 128, "64- or 128-wide tiles");
   constexpr int kStageBytes = gemm_stage_bytes(NT, BN);
   constexpr int kB = gemm_btile_bytes(BN);
+  constexpr int kGemmStages = gemm_stages(NT, BN);
   constexpr uint32_t kCols = SYM ? 2 * BN : BN;  // TMEM columns: one or two accumulators
   if (gate && *(volatile const int*)gate == 0) return;
   extern __shared__ __align__(1024) uint8_t gemm_smem_raw[];
