@@ -203,12 +203,22 @@ __device__ __forceinline__ double block_sums(const Tv* acc, int cnt, double (*sh
 }
 
 // Sum of the G partials p[0..G) by one warp, fixed order (lane 0 returns it).
+// Sixteen loads per lane are issued before they are added, in four fixed
+// accumulators (the tail of every reduction waits on these L2 round trips).
 __device__ __forceinline__ double warp_sum_partials(const double* p, int G) {
   const int l = threadIdx.x & 31;
-  double v = 0.0;
-#pragma unroll 4
-  for (int q = l; q < G; q += 32) v += __ldcg(p + q);
-  return VecOps<double>::warp_sum(v);
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q0 = l; q0 < G; q0 += 16 * 32) {
+    double t[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int q = q0 + 32 * k;
+      t[k] = q < G ? __ldcg(p + q) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k & 3] += t[k];
+  }
+  return VecOps<double>::warp_sum((a[0] + a[1]) + (a[2] + a[3]));
 }
 
 // h_i = <w, v_i> = s_i <V_{j+1}, V_i> for i = 0..j  (w is stored in slot j+1).

@@ -152,6 +152,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
   const int nvec = COLS ? n1 : n2, len = COLS ? n2 : n1;
   const int npairs = (nvec + 1) >> 1;
   const int ngroups = (npairs + F - 1) / F;
+  // FP32 column pass of the operator with even n1: the pair of columns a, a+1
+  // a group transforms is adjacent in memory, so z, A_x z, the mask and w
+  // move as 8-byte (2-byte for the mask) pairs.
+  constexpr bool kPairIO = COLS && MODE == MODE_APPLY && std::is_same<T, float>::value &&
+                           std::is_same<Tin, float>::value && std::is_same<Tout, float>::value;
+  const bool pair_io = kPairIO && (n1 & 1) == 0;
   double acc = 0.0;
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
     const int pr = grp * F + gi.g;
@@ -164,8 +170,19 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
       const int pos = gi.t + k * Lq;
       T re = T(0), im = T(0);
       if (live && pos < len) {
-        re = cvt<T>(z[vaddr<COLS>(a, pos, n1)]);
-        if (second) im = cvt<T>(z[vaddr<COLS>(a + 1, pos, n1)]);
+        if constexpr (kPairIO) {
+          if (pair_io) {
+            const float2 t2 = *reinterpret_cast<const float2*>(z + vaddr<COLS>(a, pos, n1));
+            re = t2.x;
+            im = t2.y;
+          } else {
+            re = cvt<T>(z[vaddr<COLS>(a, pos, n1)]);
+            if (second) im = cvt<T>(z[vaddr<COLS>(a + 1, pos, n1)]);
+          }
+        } else {
+          re = cvt<T>(z[vaddr<COLS>(a, pos, n1)]);
+          if (second) im = cvt<T>(z[vaddr<COLS>(a + 1, pos, n1)]);
+        }
       }
       v[k] = {re, im};
     }
@@ -178,6 +195,26 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
       v[k].i *= sg;
     }
     fft16_inverse<T>(v, buf, gi.t, L, ax.log2L, tw);
+    if constexpr (kPairIO) {
+      if (pair_io) {
+        if (live) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int pos = gi.t + k * Lq;
+            if (pos >= len) continue;
+            const size_t p = vaddr<COLS>(a, pos, n1);
+            const float2 z2 = *reinterpret_cast<const float2*>(z + p);
+            const float2 t2 = *reinterpret_cast<const float2*>(tmpx + p);
+            const uchar2 f2 = *reinterpret_cast<const uchar2*>(phi + p);
+            float w0 = z2.x - t2.x - v[k].r, w1 = z2.y - t2.y - v[k].i;
+            if (f2.x) w0 = w0 + tpen * z2.x;
+            if (f2.y) w1 = w1 + tpen * z2.y;
+            *reinterpret_cast<float2*>(out + p) = make_float2(w0, w1);
+          }
+        }
+        continue;
+      }
+    }
     if (live) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
