@@ -130,6 +130,35 @@ __device__ __forceinline__ T dst_out(const AxisTables<T>& ax, int pos, cx<T> y) 
   return c.r * y.i + c.i * y.r;
 }
 
+// Two adjacent elements as one access (8 or 16 bytes; the address is aligned
+// to the pair's size).
+template <typename X>
+struct Pair {
+  X x, y;
+};
+template <typename X>
+__device__ __forceinline__ Pair<X> ld_pair(const X* p) {
+  if constexpr (std::is_same<X, float>::value) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    return {t.x, t.y};
+  } else if constexpr (std::is_same<X, double>::value) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    return {t.x, t.y};
+  } else if constexpr (std::is_same<X, df>::value) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    return {df(t.x, t.y), df(t.z, t.w)};
+  } else {  // uint8_t
+    const uchar2 t = *reinterpret_cast<const uchar2*>(p);
+    return {t.x, t.y};
+  }
+}
+template <typename X>
+__device__ __forceinline__ void st_pair(X* p, X a, X b) {
+  if constexpr (std::is_same<X, float>::value) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  else if constexpr (std::is_same<X, double>::value) *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  else *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
 // ---------------------------------------------------------------------------
 // Toeplitz product along rows (COLS = false: tmpx = A_x z, MODE_APPLY only) or
 // columns (COLS = true), two vectors per group; tmpx holds A_x z in the
@@ -152,11 +181,13 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
   const int nvec = COLS ? n1 : n2, len = COLS ? n2 : n1;
   const int npairs = (nvec + 1) >> 1;
   const int ngroups = (npairs + F - 1) / F;
-  // FP32 column pass of the operator with even n1: the pair of columns a, a+1
-  // a group transforms is adjacent in memory, so z, A_x z, the mask and w
-  // move as 8-byte (2-byte for the mask) pairs.
-  constexpr bool kPairIO = COLS && MODE == MODE_APPLY && std::is_same<T, float>::value &&
-                           std::is_same<Tin, float>::value && std::is_same<Tout, float>::value;
+  // Column passes with even n1: the pair of columns a, a+1 a group transforms
+  // is adjacent in memory, so z, A_x z, the mask, b and the output move as
+  // pairs (the FP32 operator and the double-FP32 true residual).
+  constexpr bool kPairIO =
+      COLS && ((MODE == MODE_APPLY && std::is_same<T, float>::value && std::is_same<Tin, float>::value &&
+                std::is_same<Tout, float>::value) ||
+               (MODE == MODE_RESIDUAL && std::is_same<T, df>::value && std::is_same<Tin, double>::value));
   const bool pair_io = kPairIO && (n1 & 1) == 0;
   double acc = 0.0;
   for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
@@ -172,9 +203,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
       if (live && pos < len) {
         if constexpr (kPairIO) {
           if (pair_io) {
-            const float2 t2 = *reinterpret_cast<const float2*>(z + vaddr<COLS>(a, pos, n1));
-            re = t2.x;
-            im = t2.y;
+            const Pair<Tin> t2 = ld_pair(z + vaddr<COLS>(a, pos, n1));
+            re = cvt<T>(t2.x);
+            im = cvt<T>(t2.y);
           } else {
             re = cvt<T>(z[vaddr<COLS>(a, pos, n1)]);
             if (second) im = cvt<T>(z[vaddr<COLS>(a + 1, pos, n1)]);
@@ -203,13 +234,22 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
             const int pos = gi.t + k * Lq;
             if (pos >= len) continue;
             const size_t p = vaddr<COLS>(a, pos, n1);
-            const float2 z2 = *reinterpret_cast<const float2*>(z + p);
-            const float2 t2 = *reinterpret_cast<const float2*>(tmpx + p);
-            const uchar2 f2 = *reinterpret_cast<const uchar2*>(phi + p);
-            float w0 = z2.x - t2.x - v[k].r, w1 = z2.y - t2.y - v[k].i;
-            if (f2.x) w0 = w0 + tpen * z2.x;
-            if (f2.y) w1 = w1 + tpen * z2.y;
-            *reinterpret_cast<float2*>(out + p) = make_float2(w0, w1);
+            const Pair<Tin> z2 = ld_pair(z + p);
+            const Pair<T> t2 = ld_pair(tmpx + p);
+            const Pair<uint8_t> f2 = ld_pair(phi + p);
+            const T zz0 = cvt<T>(z2.x), zz1 = cvt<T>(z2.y);
+            T w0 = zz0 - t2.x - v[k].r, w1 = zz1 - t2.y - v[k].i;
+            if (f2.x) w0 = w0 + tpen * zz0;
+            if (f2.y) w1 = w1 + tpen * zz1;
+            if constexpr (MODE == MODE_APPLY) {
+              st_pair(out + p, cvt<Tout>(w0), cvt<Tout>(w1));
+            } else {
+              const Pair<double> b2 = ld_pair(b + p);
+              const double r0 = b2.x - cvt<double>(w0), r1 = b2.y - cvt<double>(w1);
+              st_pair(out + p, cvt<Tout>(r0), cvt<Tout>(r1));
+              acc += r0 * r0;
+              acc += r1 * r1;
+            }
           }
         }
         continue;
