@@ -135,11 +135,12 @@ __device__ __forceinline__ void dft_r(cx<T>* v) {
 __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
 
 // Twiddle w^q for q = 1..R-1 with w = tw[step].  FP64 reads every power from
-// the table (the FP64 units are the scarce resource); FP32 reads w and w^4
-// (read-only path), squares them into w^2 and w^8, and forms each other power,
-// as it is applied, from the factors of q's binary digits (at most three
-// products, a few ulp) -- the FP32 transforms wait on loads, not arithmetic,
-// and four base powers and one product live at a time (64 registers).
+// the table (the FP64 units are the scarce resource); FP32 reads w (read-only
+// path), squares it into w^2, w^4, w^8, and forms each other power, as it is
+// applied, from the factors of q's binary digits (at most three products;
+// ~15 ulp at worst, inside the FP32 transforms' error) -- the FP32 transforms
+// wait on loads, not arithmetic, and four base powers and one product live at
+// a time (64 registers).
 template <typename T, bool INV, int R>
 __device__ __forceinline__ void twiddle_apply(cx<T>* v, int i, int step, const cx<T>* __restrict__ tw) {
   constexpr int S = 16 / R;
@@ -157,8 +158,8 @@ __device__ __forceinline__ void twiddle_apply(cx<T>* v, int i, int step, const c
       return cx<T>{t.x, t.y};
     };
     b[0] = ld(step);
-    if (R > 4) b[2] = ld(4 * step);
     if (R > 2) b[1] = c_mul(b[0], b[0]);
+    if (R > 4) b[2] = c_mul(b[1], b[1]);
     if (R > 8) b[3] = c_mul(b[2], b[2]);
     if (INV) {
 #pragma unroll
