@@ -275,7 +275,7 @@ static void launch_gemm_t(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int 
   dim3 grid((N + BN - 1) / BN, (M + kGemmBM - 1) / kGemmBM, channels);
   const CUtensorMap& bh = BN == 64 ? B.map64_hi : B.map_hi;
   const CUtensorMap& bl = BN == 64 ? B.map64_lo : B.map_lo;
-  k<<<grid, 128, smem, s>>>(A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
+  k<<<grid, kGemmThreads, smem, s>>>(A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
 }
 template <int EPI, int NT, bool SYM>
 static void launch_gemm_bn(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,

@@ -85,8 +85,12 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
   if (NT == 3) lo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
+// Threads of a CTA: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs,
+// and all eight warps run the epilogue (two per TMEM lane quarter, alternate
+// 32-column chunks), which is latency-bound with fewer warps.
+constexpr int kGemmThreads = 256;
 template <int EPI, int NT, bool SYM, int BN>
-__global__ void __launch_bounds__(128, gemm_ctas_per_sm(NT, BN))
+__global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
     dst_gemm_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                     const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, int K,
                     GemmEpiParams ep, int* err, const int* gate) {
@@ -176,15 +180,16 @@ __global__ void __launch_bounds__(128, gemm_ctas_per_sm(NT, BN))
   const bool ok = mbar_wait(&done, 0, err);
   tc_fence_after();
   if (ok && !*(volatile int*)err) {
-    const int mloc = warp * 32 + lane;  // TMEM lane = row of the tile
+    const int q4 = warp & 3, half = warp >> 2;  // TMEM lane quarter, chunk parity
+    const int mloc = q4 * 32 + lane;            // TMEM lane = row of the tile
     const int m = m0 + mloc;
     const bool mvalid = m < ep.M;
     const float lm = (EPI == EPI_DIVIDE_T && mvalid) ? __ldg(ep.lam_m + m) : 0.0f;
     // column of D^T that row m goes to, in the next GEMM's K layout
     const int col = (EPI == EPI_SPLIT_T && m >= ep.row_b) ? ep.col_b + sym_perm(m - ep.row_b, ep.hk)
                                                            : sym_perm(m, ep.hk);
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-    for (int c = 0; c < BN / 32; ++c) {
+    const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
+    for (int c = half; c < BN / 32; c += 2) {
       float u[32], e[32];
       tmem_ld32(taddr + lane_off + (uint32_t)(c * 32), u);  // whole warp
       if constexpr (SYM) tmem_ld32(taddr + lane_off + (uint32_t)(BN + c * 32), e);
