@@ -48,8 +48,9 @@ RESID_TEXT = {"df32": "; true residual b - Mx double-FP32 (M x) and FP64 (b - Mx
 # the kernel classes, with the hash of the CUDA sources they were taken from;
 # reported as null once the sources change.
 TRAFFIC = {
-    # profiles/toeplitz_cols_df32_polygon2048.md: 54.78 MB read + 8.76 MB write
-    "toeplitz_cols": {"bytes_per_launch": 63541504, "src": "07ca9be2100923e0"},
+    # profiles/dst_gemm_bf16_polygon2048.md: one preconditioner application
+    # (four GEMM launches) 67.80 MB read + 0.015 MB written
+    "dst_gemm": {"bytes_per_launch": 67819264, "src": "a70aa50b73e212f0"},
 }
 
 
