@@ -179,7 +179,76 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
   __syncwarp();
   const bool ok = mbar_wait(&done, 0, err);
   tc_fence_after();
-  if (ok && !*(volatile int*)err) {
+  // Staged transposed stores (symmetric plain-BF16 split and divide epilogues):
+  // the ring's shared memory, idle once the MMAs are done, holds the tile's
+  // output rows (each: the tile's 128 rows m as two runs of 64 columns, even
+  // and odd m, in the next GEMM's K layout), then the block writes them out as
+  // 16-byte vectors.  Runs sit 160 B apart in a 288-B row, so the two halves
+  // of a warp's 2-byte writes fall in different banks.  Tiles that straddle
+  // the channel boundary or the end of M take the per-element path below.
+  constexpr int kStPitch = 144, kStRun = 80;  // BF16 elements
+  constexpr int kStRows = (EPI == EPI_DIVIDE_T ? 4 : 2) * BN;
+  constexpr bool kCanStage = SYM && NT == 1 && EPI != EPI_COMBINE_T &&
+                             kStRows * kStPitch * 2 <= gemm_stages(NT, BN) * kStageBytes;
+  bool staged = false;
+  if constexpr (kCanStage) {
+    const bool regular =
+        m0 + kGemmBM <= ep.M && (ep.ldo & 7) == 0 && (ep.hk & 7) == 0 &&
+        (reinterpret_cast<uintptr_t>(ep.out_hi) & 15) == 0 &&
+        (EPI != EPI_SPLIT_T || m0 + kGemmBM <= ep.row_b ||
+         (m0 >= ep.row_b && ((m0 - ep.row_b) & 15) == 0 && (ep.col_b & 7) == 0));
+    staged = __syncthreads_and(regular && ok && !*(volatile int*)err) != 0;  // uniform over the block
+  }
+  if (staged) {
+    const int q4 = warp & 3, half = warp >> 2;
+    const int lc = (lane & 1) * kStRun + q4 * 16 + (lane >> 1);  // this lane's m within a staged row
+    __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(smem);
+    const float lm = EPI == EPI_DIVIDE_T ? __ldg(ep.lam_m + m0 + q4 * 32 + lane) : 0.0f;
+    const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
+    for (int c = half; c < BN / 32; c += 2) {
+      float u[32], e[32];
+      tmem_ld32x2(taddr + lane_off + (uint32_t)(c * 32), taddr + lane_off + (uint32_t)(BN + c * 32), u, e);
+      const int nb = n0 + c * 32;
+      if (nb >= ep.N) continue;  // uniform over the warp
+      const int nq = min(32, ep.N - nb);
+      if constexpr (EPI == EPI_SPLIT_T) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          if (q < nq) {
+            const int r = c * 32 + q;  // staged rows: [n | n_full - 1 - n]
+            st[r * kStPitch + lc] = __float2bfloat16_rn(u[q] + e[q]);
+            st[(BN + r) * kStPitch + lc] = __float2bfloat16_rn(u[q] - e[q]);
+          }
+        }
+      } else {
+        const float ln0 = lane < nq ? __ldg(ep.lam_n + nb + lane) : 0.0f;
+        const float ln1 = lane < nq ? __ldg(ep.lam_n + ep.n_full - 1 - (nb + lane)) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const float base0 = 1.0f - lm - __shfl_sync(0xffffffffu, ln0, q);
+          const float base1 = 1.0f - lm - __shfl_sync(0xffffffffu, ln1, q);
+          if (q < nq) {
+            const int r = c * 32 + q;  // staged rows: [n | mirror | n, penalised | mirror, penalised]
+            const float y0 = u[q] + e[q], y1 = u[q] - e[q];
+            st[r * kStPitch + lc] = __float2bfloat16_rn(__fdividef(y0, base0));
+            st[(BN + r) * kStPitch + lc] = __float2bfloat16_rn(__fdividef(y1, base1));
+            st[(2 * BN + r) * kStPitch + lc] = __float2bfloat16_rn(__fdividef(y0, base0 + ep.pen));
+            st[(3 * BN + r) * kStPitch + lc] = __float2bfloat16_rn(__fdividef(y1, base1 + ep.pen));
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int colbase = (EPI == EPI_SPLIT_T && m0 >= ep.row_b) ? ep.col_b + ((m0 - ep.row_b) >> 1) : (m0 >> 1);
+    for (int v = threadIdx.x; v < kStRows * 16; v += kGemmThreads) {
+      const int r = v >> 4, part = v & 15, run = part >> 3, off = (part & 7) * 8;
+      const int sub = r / BN, n = n0 + (r - sub * BN);
+      if (n >= ep.N) continue;
+      const int grow = ((sub & 1) ? ep.n_full - 1 - n : n) + (sub >= 2 ? ep.chb_rows : 0);
+      const uint4 val = *reinterpret_cast<const uint4*>(st + r * kStPitch + run * kStRun + off);
+      *reinterpret_cast<uint4*>(ep.out_hi + (size_t)grow * ep.ldo + colbase + run * ep.hk + off) = val;
+    }
+  } else if (ok && !*(volatile int*)err) {
     const int q4 = warp & 3, half = warp >> 2;  // TMEM lane quarter, chunk parity
     const int mloc = q4 * 32 + lane;            // TMEM lane = row of the tile
     const int m = m0 + mloc;
@@ -191,8 +260,8 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
     for (int c = half; c < BN / 32; c += 2) {
       float u[32], e[32];
-      tmem_ld32(taddr + lane_off + (uint32_t)(c * 32), u);  // whole warp
-      if constexpr (SYM) tmem_ld32(taddr + lane_off + (uint32_t)(BN + c * 32), e);
+      if constexpr (SYM) tmem_ld32x2(taddr + lane_off + (uint32_t)(c * 32), taddr + lane_off + (uint32_t)(BN + c * 32), u, e);
+      else tmem_ld32(taddr + lane_off + (uint32_t)(c * 32), u);  // whole warp
       const int nb = n0 + c * 32;
       if (nb >= ep.N) continue;  // uniform over the block
       const int nq = min(32, ep.N - nb);
