@@ -389,7 +389,6 @@ BasisKind basis_kind(const rsfde_ctx* c) {
   if (c->opts.matvec_prec == RSFDE_FP32) return BASIS_FP32;
   return BASIS_FP64;
 }
-bool df_basis(const rsfde_ctx* c) { return basis_kind(c) == BASIS_DF32; }
 
 template <typename T, typename Tz, typename Tin>
 void enqueue_precond_t(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, const int* gate,
@@ -499,7 +498,7 @@ void enqueue_rhs(rsfde_ctx* c, const double* u, const double* uu, const double* 
 
 // One FGMRES(m) cycle: m gated Arnoldi iterations, the solution update and
 // the true residual with the restart decision.  Nothing is read on the host.
-// Krylov basis element type Tv: double, or df (df_basis).
+// Krylov basis element type Tv: double, df or float (basis_kind).
 template <typename Tz, typename Tv>
 void enqueue_cycle_t(rsfde_ctx* c) {
   const size_t N = c->N;

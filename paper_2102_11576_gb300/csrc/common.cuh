@@ -6,6 +6,32 @@
 namespace rsfde {
 
 constexpr int kMaxRestart = 64;  // largest m of FGMRES(m)
+
+// Programmatic dependent launch (the BF16 preconditioner's split and GEMM
+// chain).  A kernel launched by launch_pdl may be scheduled while the previous
+// kernel in the stream (or graph) still runs; it must call pdl_wait() before
+// touching memory, which returns once that grid has completed and its writes
+// are visible (a no-op after an ordinary launch).  pdl_trigger() lets the next
+// kernel be scheduled as soon as every block of this grid has issued it (all of
+// them are then resident).  Measured: it hides the launch gaps of the GEMM
+// chain; issued by the transform and Gram-Schmidt kernels too, the early
+// trigger made the graph-replayed step ~4 % slower, so those launch normally.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, args...);  // errors surface through cudaGetLastError
+}
 constexpr int kBlock = 256;      // threads per block of the grid-vector kernels
 
 // Device-resident control state of one FGMRES solve.  Every kernel of an

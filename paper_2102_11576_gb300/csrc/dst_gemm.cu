@@ -81,6 +81,8 @@ template <typename Tin, int NT>
 __global__ void __launch_bounds__(kBlock) split_kernel(const Tin* __restrict__ v, const double* scale,
                                                        __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
                                                        int n1, int n2, int ld, int hk, const int* gate) {
+  pdl_wait();
+  pdl_trigger();
   if (gate && *(volatile const int*)gate == 0) return;
   const double sc = scale ? *scale : 1.0;
   const float scf = (float)sc;
@@ -275,7 +277,7 @@ static void launch_gemm_t(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int 
   dim3 grid((N + BN - 1) / BN, (M + kGemmBM - 1) / kGemmBM, channels);
   const CUtensorMap& bh = BN == 64 ? B.map64_hi : B.map_hi;
   const CUtensorMap& bl = BN == 64 ? B.map64_lo : B.map_lo;
-  k<<<grid, kGemmThreads, smem, s>>>(A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
+  launch_pdl(k, grid, dim3(kGemmThreads), smem, s, A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
 }
 template <int EPI, int NT, bool SYM>
 static void launch_gemm_bn(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
@@ -317,11 +319,11 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   if (skip_split) {
     // A0 already holds the unscaled vector (update_kernel); scale at the end
   } else if (p->nt == 3)
-    split_kernel<Tin, 3><<<split_grid(n1, n2), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, p->h1,
-                                                               gate);
+    launch_pdl(split_kernel<Tin, 3>, split_grid(n1, n2), dim3(kBlock), 0, s, v, vscale, p->A0.hi, p->A0.lo, n1, n2,
+               p->ld1, p->h1, gate);
   else
-    split_kernel<Tin, 1><<<split_grid(n1, n2), kBlock, 0, s>>>(v, vscale, p->A0.hi, p->A0.lo, n1, n2, p->ld1, p->h1,
-                                                               gate);
+    launch_pdl(split_kernel<Tin, 1>, split_grid(n1, n2), dim3(kBlock), 0, s, v, vscale, p->A0.hi, p->A0.lo, n1, n2,
+               p->ld1, p->h1, gate);
   GemmEpiParams ep{};
   // 1. T1t = (A0 S_x)^T, columns y in the layout of GEMM 2's K
   ep.out_hi = p->T1t.hi;

@@ -21,6 +21,7 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include "common.cuh"
 #include "umma.cuh"
 
 namespace rsfde {
@@ -100,6 +101,8 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
   constexpr int kB = gemm_btile_bytes(BN);
   constexpr int kGemmStages = gemm_stages(NT, BN);
   constexpr uint32_t kCols = SYM ? 2 * BN : BN;  // TMEM columns: one or two accumulators
+  pdl_wait();
+  pdl_trigger();
   if (gate && *(volatile const int*)gate == 0) return;
   extern __shared__ __align__(1024) uint8_t gemm_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~(uintptr_t)1023);
