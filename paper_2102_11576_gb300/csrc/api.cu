@@ -771,6 +771,27 @@ void tune_operator(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTa
   });
 }
 
+// Times the true residual's two passes (FP64 x and b; the residual written
+// into the first basis vector) in arithmetic T.  x, b, the basis and the
+// solver state are scratch here: every solve re-initialises them.
+template <typename T>
+void tune_residual(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTables<T>& ty, int* chosen) {
+  cudaMemsetAsync(c->x, 0, c->N * sizeof(double), c->stream);
+  cudaMemsetAsync(c->b, 0, c->N * sizeof(double), c->stream);
+  chosen[TK_TOEP_ROWS] = tune_one<T>(c, TK_TOEP_ROWS, tx.L, (c->n2 + 1) / 2, reps, [&] {
+    launch_toeplitz_rows<T, double>(c->x, c->tmpx, c->n1, c->n2, tx, nullptr, c->stream);
+  });
+  chosen[TK_TOEP_COLS] = tune_one<T>(c, TK_TOEP_COLS, ty.L, (c->n1 + 1) / 2, reps, [&] {
+    if (basis_kind(c) == BASIS_FP32)
+      launch_toeplitz_cols<T, double, float>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
+                                             reinterpret_cast<float*>(c->V), c->n1, c->n2, ty, nullptr, c->partials,
+                                             c->st, c->stream);
+    else
+      launch_toeplitz_cols<T, double, double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1,
+                                              c->n2, ty, nullptr, c->partials, c->st, c->stream);
+  });
+}
+
 template <typename T>
 void tune_precond(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTables<T>& ty, int* chosen) {
   T* t1 = static_cast<T*>(c->T1);
@@ -804,10 +825,10 @@ int autotune_ctx(rsfde_ctx* c, int reps, int32_t* chosen_out) {
   else if (c->opts.matvec_prec == RSFDE_FP32) tune_operator<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
   else tune_operator<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
   // the double-FP32 true residual runs the same transform families in 8-byte
-  // arithmetic (recorded separately from the 4-byte shapes)
-  if (c->opts.resid_prec == RSFDE_DF32 && c->opts.matvec_prec != RSFDE_DF32) {
+  // arithmetic (recorded separately from the 4-byte shapes): timed as itself
+  if (c->opts.resid_prec == RSFDE_DF32 && c->opts.matvec_prec != RSFDE_DF32 && !left_variant(c)) {
     int unused[TK_COUNT] = {0};
-    tune_operator<df>(c, reps, c->xdf.tab, c->ydf.tab, unused);
+    tune_residual<df>(c, reps, c->xdf.tab, c->ydf.tab, unused);
   }
   if (c->opts.precond_prec == RSFDE_FP32) tune_precond<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
   else if (c->opts.precond_prec == RSFDE_FP64) tune_precond<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
