@@ -49,8 +49,8 @@ RESID_TEXT = {"df32": "; true residual b - Mx double-FP32 (M x) and FP64 (b - Mx
 # reported as null once the sources change.
 TRAFFIC = {
     # profiles/dst_gemm_bf16_polygon2048.md: one preconditioner application
-    # (four GEMM launches) 67.80 MB read + 0.015 MB written
-    "dst_gemm": {"bytes_per_launch": 67819264, "src": "a70aa50b73e212f0"},
+    # (four GEMM launches) 67.82 MB read, nothing written back within them
+    "dst_gemm": {"bytes_per_launch": 67821824, "src": "d9daba0dcb9da861"},
 }
 
 
