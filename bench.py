@@ -45,19 +45,21 @@ RESID_TEXT = {"df32": "; true residual b - Mx double-FP32 (M x) and FP64 (b - Mx
               "fp64": "; true residual, Hessenberg and Givens FP64"}
 
 # ncu DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# the kernel classes, with the hash of the CUDA sources they were taken from;
-# reported as null once the sources change.
+# the kernel classes, with the hash of the CUDA sources that define those
+# kernels; reported as null once any of them changes.
 TRAFFIC = {
     # profiles/dst_gemm_bf16_polygon2048.md: one preconditioner application
     # (four GEMM launches) 67.82 MB read, nothing written back within them
-    "dst_gemm": {"bytes_per_launch": 67821824, "src": "d9daba0dcb9da861"},
+    "dst_gemm": {"bytes_per_launch": 67821824, "src": "ec2aabe5563973c1",
+                 "files": ["common.cuh", "dst_gemm.cu", "dst_gemm.cuh", "umma.cuh"]},
 }
 
 
-def src_hash():
+def src_hash(files=None):
+    """Hash of the CUDA sources `files` (default: every file of csrc/)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2102_11576_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files or os.listdir(d)):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -332,7 +334,7 @@ def run_ours(args, rank, world, local_rank):
             kpeak_src = "152 SMs x 128 FFMA/clk x 2 x sm_max_mhz (derived)"
         achieved = flops / (avg_ms / 1e3) / 1e9 if flops else None
         tr = TRAFFIC.get(dom)
-        traffic = tr["bytes_per_launch"] if tr and tr.get("src") == src_hash() else None
+        traffic = tr["bytes_per_launch"] if tr and tr.get("src") == src_hash(tr.get("files")) else None
         roof = {"kernel": dom, "bound": bound, "achieved": round(achieved / 1e3, 3) if achieved else None,
                 "peak": round(peak / 1e3, 2), "unit": "TFLOP/s",
                 "frac": round(achieved / peak, 4) if achieved else None, "traffic": traffic,

@@ -222,45 +222,62 @@ __device__ __forceinline__ double warp_sum_partials(const double* p, int G) {
 }
 
 // h_i = <w, v_i> = s_i <V_{j+1}, V_i> for i = 0..j  (w is stored in slot j+1).
-// blockIdx.y selects a chunk of kDotChunk basis vectors; w is re-read per
-// chunk (it stays in L2).  accumulate = 1 adds to H (second CGS pass).  The
-// last block finishes the j+1 sums, one warp per sum.
-template <typename Tv, int VEC>
+// blockIdx.y selects a chunk of at most CH basis vectors (the j+1 vectors
+// spread evenly over gridDim.y chunks); w is re-read per chunk (it stays in
+// L2).  A thread takes kDotChunk / CH packs per round, so about eight loads
+// are in flight whatever j is; the packs are still visited in grid-stride
+// order.  accumulate = 1 adds to H (second CGS pass).  The last block
+// finishes the j+1 sums, one warp per sum.
+template <typename Tv, int VEC, int CH>
 __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__ V, size_t N, int j, int accumulate,
                                                           double* partials, SolverState* st) {
   if (closed(&st->run_iter)) return;
   using Op = VecOps<Tv>;
-  __shared__ double wsum[kDotChunk][kWarps];
-  const int i0 = blockIdx.y * kDotChunk;
-  const int cnt = min(kDotChunk, j + 1 - i0);
+  constexpr int UNR = kDotChunk / CH;
+  __shared__ double wsum[CH][kWarps];
+  const int per = (j + 1 + gridDim.y - 1) / gridDim.y;  // <= CH (launcher)
+  const int i0 = blockIdx.y * per;
+  const int cnt = min(per, j + 1 - i0);
   const Tv* __restrict__ w = V + (size_t)(j + 1) * N;
-  Tv acc[kDotChunk];
+  Tv acc[CH];
 #pragma unroll
-  for (int k = 0; k < kDotChunk; ++k) acc[k] = Op::zero();
+  for (int k = 0; k < CH; ++k) acc[k] = Op::zero();
   const size_t NP = N / VEC;  // VEC divides N (launcher)
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NP; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = q * VEC;
-    Tv wv[VEC];
-    ld_vec<Tv, VEC>(w + p, wv);
-    Tv a[kDotChunk][VEC];  // all loads issued before the arithmetic
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q0 < NP; q0 += UNR * stride) {
+    Tv wv[UNR][VEC];
+    Tv a[UNR][CH][VEC];  // all loads issued before the arithmetic
 #pragma unroll
-    for (int k = 0; k < kDotChunk; ++k) {
-      if (k < cnt) {
-        ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + p, a[k]);
+    for (int u = 0; u < UNR; ++u) {
+      const size_t q = q0 + u * stride;
+      const bool in = q < NP;
+      if (in) {
+        ld_vec<Tv, VEC>(w + q * VEC, wv[u]);
       } else {
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) a[k][e] = Op::zero();
+        for (int e = 0; e < VEC; ++e) wv[u][e] = Op::zero();
+      }
+#pragma unroll
+      for (int k = 0; k < CH; ++k) {
+        if (in && k < cnt) {
+          ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + q * VEC, a[u][k]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) a[u][k][e] = Op::zero();
+        }
       }
     }
 #pragma unroll
-    for (int k = 0; k < kDotChunk; ++k)
-      if (k < cnt) {
+    for (int u = 0; u < UNR; ++u)
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) acc[k] = Op::fma(acc[k], wv[e], a[k][e]);
-      }
+      for (int k = 0; k < CH; ++k)
+        if (k < cnt) {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) acc[k] = Op::fma(acc[k], wv[u][e], a[u][k][e]);
+        }
   }
   const int G = gridDim.x;
-  const double bs = block_sums<Tv, kDotChunk>(acc, cnt, wsum);
+  const double bs = block_sums<Tv, CH>(acc, cnt, wsum);
   const int wk = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0 && wk < cnt) partials[(size_t)(i0 + wk) * G + blockIdx.x] = bs;
   if (arrive_last(&st->counter, gridDim.x * gridDim.y)) {
@@ -278,13 +295,15 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
 
 // V_{j+1} <- V_{j+1} - sum_i (h_i s_i) V_i and ||V_{j+1}||; on the final pass
 // the last block runs the Givens step.  The basis vectors are read in groups
-// of kUpdChunk independent loads ahead of the dependent update chain.
-constexpr int kUpdChunk = 8;
-template <typename Tv, int VEC>
+// of CH independent loads for each of kDotChunk / CH packs ahead of the
+// dependent update chains (about eight loads in flight for every j); each
+// element still takes the terms in the order i = 0..j.
+template <typename Tv, int VEC, int CH>
 __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size_t N, int j, int final_pass,
                                                         double* partials, SolverState* st, Bf16Out bo) {
   if (closed(&st->run_iter)) return;
   using Op = VecOps<Tv>;
+  constexpr int UNR = kDotChunk / CH;
   __shared__ double wsum[1][kWarps];
   __shared__ Tv ncoef[kMaxRestart + 1];
   for (int i = threadIdx.x; i <= j; i += blockDim.x) ncoef[i] = Op::from(-(st->hcol[i] * st->s[i]));
@@ -292,39 +311,58 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size
   Tv* __restrict__ w = V + (size_t)(j + 1) * N;
   Tv acc = Op::zero();
   const size_t NP = N / VEC;  // VEC divides N (launcher)
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NP; q += (size_t)gridDim.x * blockDim.x) {
-    const size_t p = q * VEC;
-    Tv val[VEC];
-    ld_vec<Tv, VEC>(w + p, val);
-    for (int i0 = 0; i0 <= j; i0 += kUpdChunk) {
-      Tv a[kUpdChunk][VEC];  // all loads issued before the dependent chains
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q0 < NP; q0 += UNR * stride) {
+    Tv val[UNR][VEC];
 #pragma unroll
-      for (int k = 0; k < kUpdChunk; ++k) {
-        if (i0 + k <= j) {
-          ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + p, a[k]);
-        } else {
+    for (int u = 0; u < UNR; ++u) {
+      if (q0 + u * stride < NP) {
+        ld_vec<Tv, VEC>(w + (q0 + u * stride) * VEC, val[u]);
+      } else {
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) a[k][e] = Op::zero();
+        for (int e = 0; e < VEC; ++e) val[u][e] = Op::zero();
+      }
+    }
+    for (int i0 = 0; i0 <= j; i0 += CH) {
+      Tv a[UNR][CH][VEC];  // all loads issued before the dependent chains
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+          if (i0 + k <= j && q0 + u * stride < NP) {
+            ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + (q0 + u * stride) * VEC, a[u][k]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) a[u][k][e] = Op::zero();
+          }
         }
       }
 #pragma unroll
-      for (int k = 0; k < kUpdChunk; ++k)
-        if (i0 + k <= j) {
+      for (int u = 0; u < UNR; ++u)
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) val[e] = Op::fma(val[e], ncoef[i0 + k], a[k][e]);
+        for (int k = 0; k < CH; ++k)
+          if (i0 + k <= j) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) val[u][e] = Op::fma(val[u][e], ncoef[i0 + k], a[u][k][e]);
+          }
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const size_t q = q0 + u * stride;
+      if (q >= NP) break;
+      const size_t p = q * VEC;
+      st_vec<Tv, VEC>(w + p, val[u]);
+      if constexpr (std::is_same<Tv, float>::value && VEC == 4) {
+        if (bo.a0 && final_pass) {  // x = p mod n1 is a multiple of 4 (n1 is)
+          const int y = (int)(p / (size_t)bo.n1), x = (int)(p - (size_t)y * bo.n1);
+          __nv_bfloat16* row = bo.a0 + (size_t)y * bo.ld + (x >> 1);
+          *reinterpret_cast<__nv_bfloat162*>(row) = __floats2bfloat162_rn(val[u][0], val[u][2]);
+          *reinterpret_cast<__nv_bfloat162*>(row + bo.hk) = __floats2bfloat162_rn(val[u][1], val[u][3]);
         }
-    }
-    st_vec<Tv, VEC>(w + p, val);
-    if constexpr (std::is_same<Tv, float>::value && VEC == 4) {
-      if (bo.a0 && final_pass) {  // x = p mod n1 is a multiple of 4 (n1 is)
-        const int y = (int)(p / (size_t)bo.n1), x = (int)(p - (size_t)y * bo.n1);
-        __nv_bfloat16* row = bo.a0 + (size_t)y * bo.ld + (x >> 1);
-        *reinterpret_cast<__nv_bfloat162*>(row) = __floats2bfloat162_rn(val[0], val[2]);
-        *reinterpret_cast<__nv_bfloat162*>(row + bo.hk) = __floats2bfloat162_rn(val[1], val[3]);
       }
-    }
 #pragma unroll
-    for (int e = 0; e < VEC; ++e) acc = Op::fma(acc, val[e], val[e]);
+      for (int e = 0; e < VEC; ++e) acc = Op::fma(acc, val[u][e], val[u][e]);
+    }
   }
   const double bs = block_sums<Tv, 1>(&acc, 1, wsum);
   if (threadIdx.x == 0) partials[blockIdx.x] = bs;
@@ -541,34 +579,57 @@ static int resident_blocks(K kernel) {
   return b;
 }
 
+// Vectors per chunk for the j+1 basis vectors: 2 or 4 while that is enough
+// (the kernels then take 4 or 2 packs per round), else 8.
+static int dot_chunk(int j) { return j + 1 <= 2 ? 2 : j + 1 <= 4 ? 4 : kDotChunk; }
+
+template <typename Tv, int VEC, int CH>
+static void launch_multidot_t(const Tv* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
+                              cudaStream_t s) {
+  static const int per_sm = resident_blocks(multidot_kernel<Tv, VEC, CH>);
+  // the chunks share one wave: each takes 1/chunks of the resident blocks
+  const int chunks = (j + 1 + CH - 1) / CH;
+  const int gx = wave_grid(per_sm, N / VEC);
+  dim3 grid(gx / chunks > kNumSMs ? gx / chunks : (gx < kNumSMs ? gx : kNumSMs), chunks);
+  multidot_kernel<Tv, VEC, CH><<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+}
 // 16-byte accesses when every basis vector is 16-byte aligned, else one element.
 template <typename Tv>
 void launch_multidot(const Tv* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
                      cudaStream_t s) {
   constexpr int VEC = 16 / sizeof(Tv);
-  const dim3 chunks(1, (j + 1 + kDotChunk - 1) / kDotChunk);
+  const int ch = dot_chunk(j);
   if (N % VEC == 0) {
-    static const int per_sm = resident_blocks(multidot_kernel<Tv, VEC>);
-    dim3 grid(wave_grid(per_sm, N / VEC), chunks.y);
-    multidot_kernel<Tv, VEC><<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+    if (ch == 2) launch_multidot_t<Tv, VEC, 2>(V, N, j, accumulate, partials, st, s);
+    else if (ch == 4) launch_multidot_t<Tv, VEC, 4>(V, N, j, accumulate, partials, st, s);
+    else launch_multidot_t<Tv, VEC, kDotChunk>(V, N, j, accumulate, partials, st, s);
   } else {
-    static const int per_sm = resident_blocks(multidot_kernel<Tv, 1>);
-    dim3 grid(wave_grid(per_sm, N), chunks.y);
-    multidot_kernel<Tv, 1><<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+    if (ch == 2) launch_multidot_t<Tv, 1, 2>(V, N, j, accumulate, partials, st, s);
+    else if (ch == 4) launch_multidot_t<Tv, 1, 4>(V, N, j, accumulate, partials, st, s);
+    else launch_multidot_t<Tv, 1, kDotChunk>(V, N, j, accumulate, partials, st, s);
   }
+}
+template <typename Tv, int VEC, int CH>
+static void launch_update_t(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st,
+                            cudaStream_t s, const Bf16Out& bo) {
+  static const int per_sm = resident_blocks(update_kernel<Tv, VEC, CH>);
+  update_kernel<Tv, VEC, CH><<<wave_grid(per_sm, N / VEC), kBlock, 0, s>>>(V, N, j, final_pass, partials, st, bo);
 }
 template <typename Tv>
 void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s,
                    const Bf16Out* bo) {
   constexpr int VEC = 16 / sizeof(Tv);
   const Bf16Out none{nullptr, 1, 0, 0};
+  const int ch = dot_chunk(j);
   if (N % VEC == 0) {
-    static const int per_sm = resident_blocks(update_kernel<Tv, VEC>);
-    update_kernel<Tv, VEC><<<wave_grid(per_sm, N / VEC), kBlock, 0, s>>>(V, N, j, final_pass, partials, st,
-                                                                        bo ? *bo : none);
+    const Bf16Out& b = bo ? *bo : none;
+    if (ch == 2) launch_update_t<Tv, VEC, 2>(V, N, j, final_pass, partials, st, s, b);
+    else if (ch == 4) launch_update_t<Tv, VEC, 4>(V, N, j, final_pass, partials, st, s, b);
+    else launch_update_t<Tv, VEC, kDotChunk>(V, N, j, final_pass, partials, st, s, b);
   } else {  // (the BF16 copy is only taken with 16-byte packs)
-    static const int per_sm = resident_blocks(update_kernel<Tv, 1>);
-    update_kernel<Tv, 1><<<wave_grid(per_sm, N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st, none);
+    if (ch == 2) launch_update_t<Tv, 1, 2>(V, N, j, final_pass, partials, st, s, none);
+    else if (ch == 4) launch_update_t<Tv, 1, 4>(V, N, j, final_pass, partials, st, s, none);
+    else launch_update_t<Tv, 1, kDotChunk>(V, N, j, final_pass, partials, st, s, none);
   }
 }
 template void launch_multidot<double>(const double*, size_t, int, int, double*, SolverState*, cudaStream_t);
