@@ -2,7 +2,7 @@
 solution on an ellipse, used to pin the oracle against Tables 1-3.
 
 The printed example is garbled; this module takes the following reading
-(each item is listed with its reason in the design doc):
+(each item below states the fix to the printed text):
   * the ellipse x^2/a^2 + y^2/b^2 <= 1 is centred in the box (-a,a) x (-b,b);
   * exact solution u_e = exp(-t) (x^2/a^2 + y^2/b^2 - 1)^2 on Omega, 0 outside;
   * the source follows from u_t = k_x R_x u + k_y R_y u + f with R the Riesz
