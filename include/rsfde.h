@@ -274,7 +274,10 @@ const char* rsfde_kernel_class_name(int k);
  * fastest in a process-wide table that every later launch with the same
  * length and precision uses (captured graphs are rebuilt).  chosen: HOST
  * array of RSFDE_TUNE_COUNT int32 (the chosen F per family, 0 = not tuned)
- * or NULL.  Overwrites the context's Krylov workspace. */
+ * or NULL.  With a double-FP32 true residual and an operator in another
+ * precision, the 8-byte shapes are timed on the residual's own two passes.
+ * Overwrites the context's Krylov workspace, its internal right-hand side and
+ * iterate, and its solver state (every solve and step re-initialises them). */
 #define RSFDE_TUNE_COUNT 6 /* Toeplitz rows, Toeplitz columns, sine rows, sine columns,
                               preconditioner columns, preconditioner rows */
 int rsfde_autotune(rsfde_ctx* ctx, int32_t reps, int32_t* chosen);
