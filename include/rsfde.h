@@ -45,13 +45,22 @@ extern "C" {
 #define RSFDE_ENONFINITE (-5)  /* NaN or Inf met in the right side or in the Arnoldi process */
 #define RSFDE_ETIMEOUT (-6)    /* a bounded device-side wait gave up */
 
-/* Precisions.  The preconditioner apply (Eq. 4.6) runs in RSFDE_FP64,
- * RSFDE_FP32, RSFDE_BF16X3 or RSFDE_BF16; the operator applied to the Arnoldi
- * vectors (and, in right-preconditioned FGMRES, the Krylov basis) in
- * RSFDE_FP64, RSFDE_DF32 or RSFDE_FP32.  The true residual, the Hessenberg
- * matrix and the Givens least squares are FP64 in every mode; flexible GMRES
- * tolerates the inexact preconditioner, and convergence is always decided by
- * the FP64 true residual. */
+/* Precisions.  Four choices are independent:
+ *  - precond_prec: the preconditioner apply (Eq. 4.6) in RSFDE_FP64,
+ *    RSFDE_FP32, RSFDE_BF16X3 or RSFDE_BF16;
+ *  - matvec_prec: the arithmetic of the operator M applied to the Arnoldi
+ *    vectors (Eq. 2.14-2.17), RSFDE_FP64, RSFDE_DF32 or RSFDE_FP32;
+ *  - basis_prec: the storage of the Krylov basis and the arithmetic of the
+ *    Gram-Schmidt orthogonalisation, RSFDE_FP64 (any operator), RSFDE_DF32
+ *    (with the double-FP32 operator) or RSFDE_FP32 (with the FP32 operator);
+ *  - resid_prec: the arithmetic of M x in the true residual b - M x that
+ *    decides convergence, RSFDE_FP64 or RSFDE_DF32.
+ * The Hessenberg matrix, the Givens least squares, the solution x and the
+ * subtraction b - M x and its norm are FP64 in every mode.  Flexible GMRES
+ * tolerates the inexact preconditioner.  With every choice FP64 except the
+ * preconditioner (FP32 or BF16X3) and, optionally, the operator's FFT
+ * arithmetic, the orthogonalisation, the least squares and the true residual
+ * are FP64 arithmetic throughout. */
 #define RSFDE_FP64 0
 #define RSFDE_FP32 1
 /* Preconditioner sine transforms as tensor-core GEMMs in split BF16
@@ -60,9 +69,9 @@ extern "C" {
 /* Preconditioner sine transforms as tensor-core GEMMs in plain BF16 (one
  * product X_hi S_hi with FP32 accumulation; about 3 significant digits). */
 #define RSFDE_BF16 4
-/* Operator M applied to the Arnoldi vectors in double-FP32 arithmetic (pairs
- * of FP32 numbers, ~48-bit significand, error-free transforms of Dekker and
- * Knuth).  The true residual b - M x is always computed in FP64. */
+/* Double-FP32 arithmetic (pairs of FP32 numbers, ~48-bit significand,
+ * error-free transforms of Dekker and Knuth) for the operator, the Krylov
+ * basis or the M x of the true residual. */
 #define RSFDE_DF32 2
 
 /* Krylov variant.  RSFDE_FGMRES_RIGHT (default): right-preconditioned flexible
@@ -94,19 +103,23 @@ typedef struct {
   int32_t precond_prec; /* RSFDE_FP64 | RSFDE_FP32 | RSFDE_BF16X3 | RSFDE_BF16 */
   int32_t arnoldi;      /* RSFDE_CGS | RSFDE_CGS2 */
   int32_t use_precond;  /* 1: P-hat of Eq. 4.6; 0: unpreconditioned GMRES */
-  int32_t matvec_prec;  /* RSFDE_FP64 | RSFDE_DF32 | RSFDE_FP32: M applied to the Arnoldi vectors, and
-                           (right-preconditioned FGMRES) the Krylov basis's storage and Gram-Schmidt
-                           arithmetic.  The true residual that decides convergence is always FP64. */
+  int32_t matvec_prec;  /* RSFDE_FP64 | RSFDE_DF32 | RSFDE_FP32: arithmetic of M applied to the
+                           Arnoldi vectors (its output is stored in basis_prec) */
   int32_t variant;      /* RSFDE_FGMRES_RIGHT | RSFDE_GMRES_LEFT */
   int32_t use_graph;    /* 1: the cycles of a solve replay as one CUDA graph with a device-side
                            loop (one host synchronisation per solve); 0: direct launches with
                            one host check per cycle.  Profiling always uses direct launches. */
   void* stream;         /* cudaStream_t; NULL = the legacy default stream */
-  int32_t resid_prec;   /* RSFDE_FP64 (default) | RSFDE_DF32: arithmetic of the true residual
-                           b - M x that decides convergence (right-preconditioned FGMRES; paper
-                           mode always FP64).  Double-FP32 carries ~48 significant bits: its
-                           rounding error is a few units of 1e-14 times |M||x|, far below a 1e-10
-                           tolerance. */
+  int32_t resid_prec;   /* RSFDE_FP64 (default) | RSFDE_DF32: arithmetic of M x in the true
+                           residual b - M x that decides convergence (right-preconditioned
+                           FGMRES; paper mode always FP64).  b - M x and its norm are FP64 either
+                           way.  Double-FP32 carries ~48 significant bits: its rounding error is
+                           a few units of 1e-14 times |M||x|, far below a 1e-10 tolerance, but it
+                           is not FP64 arithmetic. */
+  int32_t basis_prec;   /* RSFDE_FP64 (default) | RSFDE_DF32 | RSFDE_FP32: Krylov basis storage and
+                           Gram-Schmidt arithmetic (right-preconditioned FGMRES; paper mode always
+                           FP64).  RSFDE_DF32 needs matvec_prec RSFDE_DF32, RSFDE_FP32 needs
+                           matvec_prec RSFDE_FP32 (else RSFDE_EINVAL). */
 } rsfde_opts;
 
 typedef struct {
@@ -116,17 +129,29 @@ typedef struct {
   int32_t status;    /* RSFDE_OK, RSFDE_ENOTCONV or RSFDE_ENONFINITE */
   double rel_res;    /* final true ||b - M x||_2 / ||b||_2 */
   double bnorm;      /* ||b||_2 */
+  double t_ms[6];    /* device time of the last call per hot-path phase, measured only while the
+                        profiler is on (rsfde_profile_enable), else 0:
+                        [0] right side, norms and loop control, [1] operator M on the Arnoldi
+                        vectors, [2] preconditioner, [3] Gram-Schmidt with the Givens step,
+                        [4] least-squares back substitution, [5] solution update and true
+                        residual */
+  double bytes;      /* algorithmic HBM bytes of the last call: every grid vector the method must
+                        read or write once per use (the operands of each preconditioner apply,
+                        operator apply, Gram-Schmidt pass, solution update and true residual, the
+                        mask bits), in the precisions configured; excludes the transforms'
+                        intermediates and any re-read */
 } rsfde_stats;
 
 /* Defaults: restart 20, max_iter 10000, tol 1e-10, FP64 preconditioner, CGS,
- * preconditioned, FP64 operator, right-preconditioned FGMRES, CUDA graph,
- * default stream. */
+ * preconditioned, FP64 operator, basis and residual, right-preconditioned
+ * FGMRES, CUDA graph, default stream. */
 void rsfde_opts_default(rsfde_opts* o);
 
 /* Section 2 / Eq. 2.16 / Section 4.1 (setup of one linear system).
  * mask: DEVICE pointer to N uint8, 1 where the grid point lies in Omega,
  * 0 in the extension region (copied; the caller keeps ownership).
- * alpha1, alpha2 in (1,2); kx, ky, dt, eta > 0.  opts may be NULL (defaults).
+ * n1, n2 in 1..4096; alpha1, alpha2 in (1,2); kx, ky, dt, eta > 0.  opts may
+ * be NULL (defaults).
  * Builds the Toeplitz and tau tables on the host in FP64 and uploads them.
  * Returns RSFDE_EINVAL, RSFDE_ENOMEM or RSFDE_ECUDA on failure (*out = NULL). */
 int rsfde_setup(rsfde_ctx** out, const rsfde_grid* grid, const uint8_t* mask, double alpha1,
@@ -150,7 +175,11 @@ int rsfde_solve(rsfde_ctx* ctx, const double* b, double* x, rsfde_stats* stats);
  * zero outside Omega (Section 2):  b = u^{k-1} + dt (1-Phi)(u^{k-1} - (u^{k-1})^3 + src),
  * initial guess u^{k-1} if u_prevprev is NULL, else 2u^{k-1} - u^{k-2} (Section 5).
  * u_prev: device N doubles; u_prevprev, src: device N doubles or NULL;
- * u_next: device N doubles (may alias neither input).  Synchronises the stream. */
+ * u_next: device N doubles (may alias neither input).  Synchronises the stream.
+ * The built-in f does not depend on t, so the step takes no time argument; a
+ * time-dependent source is passed as this step's src (its values at t_{k-1}),
+ * and any other f(u, x, y, t) goes through rsfde_solve with a right side the
+ * caller builds. */
 int rsfde_step(rsfde_ctx* ctx, const double* u_prev, const double* u_prevprev, const double* src,
                double* u_next, rsfde_stats* stats);
 
@@ -222,10 +251,11 @@ int rsfde_get_params(rsfde_ctx* ctx, double* out5);
 /* ---- allocation-free variant ------------------------------------------------ */
 /* The paper has no counterpart to this entry point: it exists for callers
  * that cannot call cudaMalloc, such as an application or framework that owns
- * every device allocation through its own memory pool, or code that must not
- * allocate while it builds a CUDA graph.  They cannot make an rsfde_ctx
- * (rsfde_setup allocates), so this call computes out = (S_{n2} (x) S_{n1}) v
- * -- the same transform and kernels as rsfde_dst2 -- with no context.
+ * every device allocation through its own memory pool (a stray cudaMalloc
+ * would bypass its accounting or fragment the memory it manages).  They
+ * cannot make an rsfde_ctx (rsfde_setup allocates), so this call computes
+ * out = (S_{n2} (x) S_{n1}) v -- the same transform and kernels as
+ * rsfde_dst2 -- with no context.
  *
  * v, out: caller-owned DEVICE arrays of n1*n2 doubles, x fastest, distinct.
  * stream: cudaStream_t or NULL.  The intermediate between the row and column
@@ -236,11 +266,16 @@ int rsfde_get_params(rsfde_ctx* ctx, double* out5);
  *
  * The first call on each device looks up the static arrays' device
  * addresses (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  Every call uses the same static
- * arrays and overwrites all of it that the kernels read, so nothing carries
- * over from one call to the next; but calls whose work overlaps on the GPU
- * (two streams, or two host threads) race on the arrays and must be
- * serialised by the caller. */
+ * first call before any stream capture.  A call whose (n1, n2) or stream
+ * differs from the previous call's on that device copies the tables from
+ * host memory, which makes the host wait for the stream's earlier work; a
+ * repeat with the same sizes and stream reuses them.  Every call uses the
+ * same static arrays and overwrites all of them that its kernels read, so
+ * nothing carries over from one call to the next; calls whose work overlaps
+ * on the GPU (two streams, or two devices' work racing on one device's
+ * arrays from several host threads) race on the arrays and must be
+ * serialised by the caller.  The host side of the call is serialised
+ * internally. */
 #define RSFDE_NOALLOC_MAX_N 512
 int rsfde_dst2_noalloc(int32_t n1, int32_t n2, const double* v, double* out, void* stream);
 
@@ -255,8 +290,13 @@ int rsfde_dst2_noalloc(int32_t n1, int32_t n2, const double* v, double* out, voi
 #define RSFDE_K_UPDATE 6        /* Arnoldi update, norm and Givens step */
 #define RSFDE_K_XUPDATE 7       /* solution update x += Z y */
 #define RSFDE_K_OTHER 8         /* right side, norms, scalar kernels */
-#define RSFDE_K_DST_GEMM 9      /* preconditioner as split-BF16 tensor-core GEMMs (all 5 launches) */
-#define RSFDE_K_COUNT 10
+#define RSFDE_K_DST_GEMM 9      /* preconditioner as tensor-core GEMMs (split-BF16 or BF16): the four
+                                   GEMMs and, when the previous Gram-Schmidt update did not write the
+                                   first operand, the split */
+#define RSFDE_K_RESID_ROWS 10   /* row pass of M x in the true residual (Eq. 2.15) */
+#define RSFDE_K_RESID_COLS 11   /* column pass of the true residual b - M x and its norm */
+#define RSFDE_K_SOLVE_Y 12      /* back substitution of the Givens-rotated least squares */
+#define RSFDE_K_COUNT 13
 
 /* While on, every kernel launch of the context is bracketed by a pair of CUDA
  * events on the context's stream (adds one event record per launch). */
@@ -282,6 +322,17 @@ const char* rsfde_kernel_class_name(int k);
                               preconditioner columns, preconditioner rows */
 int rsfde_autotune(rsfde_ctx* ctx, int32_t reps, int32_t* chosen);
 int rsfde_batch_autotune(rsfde_batch* b, int32_t reps);
+
+/* Failure detection.  Every wait of the tensor-core preconditioner's
+ * pipeline (a TMA copy landing in a ring slot, a slot freed by the MMAs) is
+ * bounded; a wait that runs out makes that launch give up and the call
+ * return RSFDE_ETIMEOUT, after every copy and MMA the launch had issued has
+ * completed, so the context stays usable.  cycles: the bound of each such
+ * wait in SM clock cycles; 0 restores the default (4e9, about 2 s at
+ * 2.07 GHz).  A small bound makes the waits give up on purpose, which is how
+ * the timeout path is tested.  The waits that let issued work complete
+ * before a block frees its memory keep the default bound. */
+int rsfde_set_wait_cycles(rsfde_ctx* ctx, int64_t cycles);
 
 /* Number of this library's kernel launches since the context was made (host counter). */
 int64_t rsfde_kernel_launches(const rsfde_ctx* ctx);

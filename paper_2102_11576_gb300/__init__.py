@@ -26,6 +26,7 @@ _VARIANTS = {"fgmres_right": 0, "gmres_left": 1}
 _PRECONDS = {"fp64": 0, "fp32": 1, "bf16x3": 3, "bf16": 4}
 _MATVECS = {"fp64": FP64, "df32": DF32, "fp32": FP32}
 _RESIDS = {"fp64": FP64, "df32": DF32}
+_BASES = {"fp64": FP64, "df32": DF32, "fp32": FP32}
 CGS, CGS2 = 0, 1
 _ERR = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV", -5: "ENONFINITE",
         -6: "ETIMEOUT"}
@@ -48,18 +49,24 @@ class _Opts(ctypes.Structure):
                 ("precond_prec", ctypes.c_int32), ("arnoldi", ctypes.c_int32),
                 ("use_precond", ctypes.c_int32), ("matvec_prec", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("stream", ctypes.c_void_p), ("resid_prec", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("resid_prec", ctypes.c_int32),
+                ("basis_prec", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("rel_res", ctypes.c_double), ("bnorm", ctypes.c_double)]
+                ("rel_res", ctypes.c_double), ("bnorm", ctypes.c_double),
+                ("t_ms", ctypes.c_double * 6), ("bytes", ctypes.c_double)]
+
+    PHASES = ("rhs_and_control", "operator", "precond", "gram_schmidt", "least_squares",
+              "update_and_residual")
 
     def as_dict(self):
         return {"iters": self.iters, "restarts": self.restarts, "converged": bool(self.converged),
                 "status": _ERR.get(self.status, self.status), "rel_res": self.rel_res,
-                "bnorm": self.bnorm}
+                "bnorm": self.bnorm, "t_ms": dict(zip(self.PHASES, list(self.t_ms))),
+                "bytes": self.bytes}
 
 
 _lib = None
@@ -96,6 +103,8 @@ def load_library(path=LIB_PATH):
     lib.rsfde_profile_read.restype = ctypes.c_int
     lib.rsfde_kernel_class_name.argtypes = [i32]
     lib.rsfde_kernel_class_name.restype = ctypes.c_char_p
+    lib.rsfde_set_wait_cycles.argtypes = [vp, ctypes.c_int64]
+    lib.rsfde_set_wait_cycles.restype = ctypes.c_int
     lib.rsfde_kernel_launches.argtypes = [vp]
     lib.rsfde_kernel_launches.restype = ctypes.c_int64
     lib.rsfde_destroy.argtypes = [vp]
@@ -140,7 +149,8 @@ class Solver:
 
     def __init__(self, n1, n2, box, in_omega, alpha1, alpha2, kx, ky, dt, eta, restart=20,
                  max_iter=10000, tol=1e-10, precond="fp64", arnoldi="cgs", use_precond=True,
-                 matvec="fp64", variant="fgmres_right", use_graph=True, stream=None, resid="fp64"):
+                 matvec="fp64", variant="fgmres_right", use_graph=True, stream=None, resid="fp64",
+                 basis="fp64"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
@@ -165,6 +175,7 @@ class Solver:
         o.use_graph = int(bool(use_graph))
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         o.resid_prec = _RESIDS[resid]
+        o.basis_prec = _BASES[basis]
         self._opts = o
         g = _Grid(self.n1, self.n2, *map(float, box))
         h = ctypes.c_void_p()
@@ -217,6 +228,8 @@ class Solver:
                 o.variant = _VARIANTS[v]
             elif k == "resid":
                 o.resid_prec = _RESIDS[v]
+            elif k == "basis":
+                o.basis_prec = _BASES[v]
             else:
                 setattr(o, k, v)
         _check(self._lib.rsfde_set_opts(self._h, ctypes.byref(o)), "set_opts")
@@ -318,7 +331,7 @@ class Solver:
 
     def profile_read(self):
         """{kernel class: (device ms, launches)} since the last read."""
-        K = 10
+        K = 13
         ms = np.zeros(K)
         n = np.zeros(K, dtype=np.int64)
         _check(self._lib.rsfde_profile_read(self._h, ctypes.c_void_p(ms.ctypes.data),
@@ -329,6 +342,10 @@ class Solver:
     @property
     def kernel_launches(self):
         return int(self._lib.rsfde_kernel_launches(self._h))
+
+    def set_wait_cycles(self, cycles=0):
+        """Bound of each tensor-core pipeline wait in SM clock cycles (0: the default, ~2 s)."""
+        _check(self._lib.rsfde_set_wait_cycles(self._h, int(cycles)), "set_wait_cycles")
 
     TUNE_NAMES = ("toeplitz_rows", "toeplitz_cols", "dst_rows", "dst_cols", "precond_cols", "precond_rows")
 
@@ -348,7 +365,7 @@ class Batch:
     ky, dt, eta; solver options as for Solver apply to all instances."""
 
     def __init__(self, problems, restart=20, max_iter=10000, tol=1e-10, precond="fp32", matvec="df32",
-                 arnoldi="cgs", stream=None, resid="fp64"):
+                 arnoldi="cgs", stream=None, resid="fp64", basis=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
@@ -374,6 +391,7 @@ class Batch:
         o.arnoldi = {"cgs": CGS, "cgs2": CGS2}[arnoldi]
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         o.resid_prec = _RESIDS[resid]
+        o.basis_prec = _BASES[basis if basis is not None else matvec]
         h = ctypes.c_void_p()
         pp = lambda a: ctypes.c_void_p(a.ctypes.data)
         _check(lib.rsfde_batch_create(ctypes.byref(h), self.count, grids, masks,

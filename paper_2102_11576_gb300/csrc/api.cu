@@ -207,6 +207,7 @@ struct rsfde_ctx {
   SolverState* st_host = nullptr;  // pinned
   int64_t launches = 0;
   Bf16Plan* bf16 = nullptr;  // tensor-core preconditioner, made when first needed
+  long long wait_cycles = 0;  // its pipeline wait bound (0: the default)
   // one FGMRES cycle captured as the body of a device-side WHILE loop
   cudaStream_t cap_stream = nullptr;  // private stream used only for capture
   cudaGraph_t graph = nullptr;
@@ -219,11 +220,17 @@ struct rsfde_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double prof_ms[RSFDE_K_COUNT] = {0};
   int64_t prof_n[RSFDE_K_COUNT] = {0};
+  double prof_call0[RSFDE_K_COUNT] = {0};  // prof_ms when the current public call began
+  double call_bytes = 0;                   // right side bytes of the current call (rsfde_step)
 };
 
 namespace {
 
 bool bad_alpha(double a) { return !(a > 1.0 && a < 2.0); }
+
+// Largest grid side: the transform kernels take convolution lengths up to
+// 8192 (a group of L/16 = 512 threads, the FP64 and double-FP32 block cap).
+constexpr int kMaxN = 4096;
 
 int cuda_fail(cudaError_t e) {
   if (e == cudaSuccess) return RSFDE_OK;
@@ -339,7 +346,9 @@ int ensure_bf16(rsfde_ctx* c) {
     bf16_plan_destroy(c->bf16);
     c->bf16 = nullptr;
   }
-  return bf16_plan_create(&c->bf16, c->n1, c->n2, nt, c->x32.tab.lam, c->y32.tab.lam, c->phi, c->stream);
+  const int rc = bf16_plan_create(&c->bf16, c->n1, c->n2, nt, c->x32.tab.lam, c->y32.tab.lam, c->phi, c->stream);
+  if (rc == RSFDE_OK) bf16_plan_set_wait(c->bf16, c->wait_cycles);
+  return rc;
 }
 
 // The tensor-core preconditioner z = P-hat^-1 (scale * v) (five launches).
@@ -378,15 +387,16 @@ void enqueue_apply_M(rsfde_ctx* c, const Tz* z, double* w, const int* gate) {
 
 bool left_variant(const rsfde_ctx* c) { return c->opts.variant == RSFDE_GMRES_LEFT; }
 
-// The right-preconditioned FGMRES keeps its Krylov basis in the Arnoldi
-// operator's precision (FP64, double-FP32 or FP32): the operator's output is
-// stored without a conversion, and with 4- or 8-byte FP32-pipe arithmetic the
-// Gram-Schmidt needs no FP64 instruction per element.  Paper mode keeps FP64.
+// The right-preconditioned FGMRES keeps its Krylov basis, and runs its
+// Gram-Schmidt, in basis_prec: FP64 (FP64 arithmetic, whatever the operator's
+// arithmetic), or -- with an operator of the same precision, whose output is
+// then stored without a conversion -- double-FP32 or FP32 on the FP32 pipe.
+// Paper mode keeps FP64.
 enum BasisKind { BASIS_FP64, BASIS_DF32, BASIS_FP32 };
 BasisKind basis_kind(const rsfde_ctx* c) {
   if (left_variant(c)) return BASIS_FP64;
-  if (c->opts.matvec_prec == RSFDE_DF32) return BASIS_DF32;
-  if (c->opts.matvec_prec == RSFDE_FP32) return BASIS_FP32;
+  if (c->opts.basis_prec == RSFDE_DF32) return BASIS_DF32;
+  if (c->opts.basis_prec == RSFDE_FP32) return BASIS_FP32;
   return BASIS_FP64;
 }
 
@@ -410,11 +420,11 @@ void enqueue_precond64(rsfde_ctx* c, const double* v, const double* vscale, doub
 void enqueue_residual_left(rsfde_ctx* c, const int* gate) {
   double* r = c->opts.use_precond ? static_cast<double*>(c->Z) : c->V;
   {
-    ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
+    ProfScope ps(c, RSFDE_K_RESID_ROWS);
     launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
   }
   {
-    ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
+    ProfScope ps(c, RSFDE_K_RESID_COLS);
     launch_toeplitz_cols<double, double>(MODE_RESID_ONLY, c->x, c->tmpx, c->phi, c->pen, c->b, r, c->n1, c->n2,
                                          c->y64.tab, gate, nullptr, nullptr, c->stream);
   }
@@ -439,10 +449,10 @@ void enqueue_bnorm(rsfde_ctx* c) {
 template <typename T>
 void enqueue_residual_t(rsfde_ctx* c, const int* gate, const AxisTables<T>& tx, const AxisTables<T>& ty) {
   {
-    ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
+    ProfScope ps(c, RSFDE_K_RESID_ROWS);
     launch_toeplitz_rows<T, double>(c->x, c->tmpx, c->n1, c->n2, tx, gate, c->stream);
   }
-  ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
+  ProfScope ps(c, RSFDE_K_RESID_COLS);
   if (basis_kind(c) == BASIS_DF32)
     launch_toeplitz_cols<T, double, df>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b,
                                         reinterpret_cast<df*>(c->V), c->n1, c->n2, ty, gate, c->partials, c->st,
@@ -486,6 +496,13 @@ void enqueue_precond_t(rsfde_ctx* c, const Tin* v, const double* vscale, Tz* z, 
   }
 }
 
+// The right side and guess of a step (a1): read u^{k-1}, u^{k-2} and s when
+// given, the mask bits; write b and x0.
+double rhs_bytes(const rsfde_ctx* c, bool has_uu, bool has_src) {
+  const double N = (double)c->N;
+  return (8.0 + (has_uu ? 8.0 : 0.0) + (has_src ? 8.0 : 0.0) + 16.0) * N + N / 8.0;
+}
+
 void enqueue_init(rsfde_ctx* c) {
   ProfScope ps(c, RSFDE_K_OTHER);
   launch_init_state(c->st, c->opts.restart, c->opts.max_iter, c->opts.tol, c->stream);
@@ -507,12 +524,15 @@ void enqueue_cycle_t(rsfde_ctx* c) {
   const int* gc = &c->st->run_cycle;
   Tz* Z = static_cast<Tz*>(c->Z);
   Tv* V = reinterpret_cast<Tv*>(c->V);
-  // Plain-BF16 preconditioner with an FP32 basis: the final update pass of
-  // iteration j also writes V_{j+1} rounded to BF16 as the first GEMM operand
-  // of iteration j+1, whose split pass is then skipped.
+  // Tensor-core preconditioner with an FP32 or FP64 basis: the final update
+  // pass of iteration j also writes V_{j+1} rounded to BF16 (split BF16: the
+  // pair hi, lo) as the first GEMM operand of iteration j+1, whose split pass
+  // is then skipped.
   Bf16Out bo{};
-  const bool fused = std::is_same<Tv, float>::value && c->opts.use_precond && bf16_precond_on(c) &&
-                     bf16_plan_a0(c->bf16, &bo);
+  constexpr int kVec = 16 / sizeof(Tv);
+  const bool fused = (std::is_same<Tv, float>::value || std::is_same<Tv, double>::value) &&
+                     c->opts.use_precond && bf16_precond_on(c) && N % kVec == 0 &&
+                     bf16_plan_a0(c->bf16, kVec, &bo);
   for (int j = 0; j < m; ++j) {
     const Tv* vj = V + (size_t)j * N;
     Tz* zj = Z + (size_t)j * N;
@@ -544,7 +564,7 @@ void enqueue_cycle_t(rsfde_ctx* c) {
     }
   }
   {
-    ProfScope ps(c, RSFDE_K_OTHER);
+    ProfScope ps(c, RSFDE_K_SOLVE_Y);
     launch_solve_y(c->st, c->stream);
   }
   {
@@ -585,7 +605,7 @@ void enqueue_cycle_left(rsfde_ctx* c) {
     }
   }
   {
-    ProfScope ps(c, RSFDE_K_OTHER);
+    ProfScope ps(c, RSFDE_K_SOLVE_Y);
     launch_solve_y(c->st, c->stream);
   }
   {
@@ -609,7 +629,8 @@ void enqueue_cycle(rsfde_ctx* c) {
 
 int graph_key(const rsfde_ctx* c) {
   const rsfde_opts& o = c->opts;
-  int k = o.resid_prec == RSFDE_DF32 ? 1 : 0;
+  int k = o.basis_prec;
+  k = k * 2 + (o.resid_prec == RSFDE_DF32 ? 1 : 0);
   k = k * 65 + o.restart;
   k = k * 5 + o.precond_prec;
   k = k * 4 + o.matvec_prec;
@@ -665,6 +686,38 @@ int build_cycle_graph(rsfde_ctx* c) {
   return RSFDE_OK;
 }
 
+// Start of a public solve or step: with the profiler on, every earlier launch
+// is harvested so that the call's phase times are its own.
+void begin_call(rsfde_ctx* c) {
+  c->call_bytes = 0;
+  if (!c->prof_on) return;
+  cudaStreamSynchronize(c->stream);
+  prof_harvest(c);
+  for (int k = 0; k < RSFDE_K_COUNT; ++k) c->prof_call0[k] = c->prof_ms[k];
+}
+
+// Algorithmic HBM bytes of a solve (each grid vector the method reads or
+// writes once per use, in the configured precisions): per Arnoldi iteration j
+// the preconditioner (read v, write z), the operator (read z, write w, the
+// mask bits) and Gram-Schmidt (e_v N (2j + 4) per pass: the j+1 basis vectors
+// and w read by the dots and again by the update, the new vector written);
+// per cycle the solution update (read the z of the cycle, read and write x);
+// per true residual read x and b and the mask bits, write r.
+double solve_bytes(const rsfde_ctx* c, const SolverState& h) {
+  const double N = (double)c->N;
+  const double ev = left_variant(c) ? 8.0 : (basis_kind(c) == BASIS_FP32 ? 4.0 : 8.0);
+  const double ez = (left_variant(c) || !fp32_precond(c)) ? 8.0 : 4.0;
+  const double it = (double)h.iters, sj = (double)h.sum_j, cyc = (double)h.cycles;
+  const double passes = c->opts.arnoldi == RSFDE_CGS2 ? 2.0 : 1.0;
+  double b = 0.0;
+  if (c->opts.use_precond) b += it * (ev + ez) * N;
+  b += it * ((ez + ev) * N + N / 8.0);
+  b += passes * ev * N * (2.0 * sj + 4.0 * it);
+  b += ez * it * N + 16.0 * N * cyc;
+  b += (cyc + 1.0) * ((16.0 + ev) * N + N / 8.0);
+  return b;
+}
+
 // Solve M x = b with b = c->b, x = c->x (initial guess), st->bnorm set.
 int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
   int rc = ensure_bf16(c);
@@ -707,6 +760,16 @@ int run_solver(rsfde_ctx* c, rsfde_stats* stats) {
     stats->status = h.status;
     stats->rel_res = h.rel_res;
     stats->bnorm = h.bnorm;
+    stats->bytes = c->call_bytes + solve_bytes(c, h);
+    // phases: [0] right side, norms, loop control; [1] operator; [2]
+    // preconditioner; [3] Gram-Schmidt and Givens; [4] back substitution;
+    // [5] solution update and true residual
+    static const int phase[RSFDE_K_COUNT] = {1, 1, 2, 2, 2, 3, 3, 5, 0, 2, 5, 5, 4};
+    for (int k = 0; k < 6; ++k) stats->t_ms[k] = 0.0;
+    if (c->prof_on) {
+      prof_harvest(c);
+      for (int k = 0; k < RSFDE_K_COUNT; ++k) stats->t_ms[phase[k]] += c->prof_ms[k] - c->prof_call0[k];
+    }
   }
   return h.status;
 }
@@ -755,11 +818,10 @@ int tune_one(rsfde_ctx* c, int kind, int L, int items, int reps, Fn run) {
 }
 
 // Times the operator in the types the solver uses: FP64 z and w, or (FP32 or
-// double-FP32 arithmetic) an FP32 z and a w of the arithmetic type.
-template <typename T>
+// double-FP32 arithmetic) an FP32 z and a w of the basis type Tw.
+template <typename T, typename Tw>
 void tune_operator(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTables<T>& ty, int* chosen) {
   using Tz = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
-  using Tw = T;
   const Tz* z = reinterpret_cast<const Tz*>(c->V);
   Tw* w = reinterpret_cast<Tw*>(c->V + c->N);
   chosen[TK_TOEP_ROWS] = tune_one<T>(c, TK_TOEP_ROWS, tx.L, (c->n2 + 1) / 2, reps, [&] {
@@ -821,9 +883,16 @@ int autotune_ctx(rsfde_ctx* c, int reps, int32_t* chosen_out) {
   cudaMemsetAsync(c->T1, 0, bytes, c->stream);
   cudaMemsetAsync(c->T2a, 0, bytes, c->stream);
   cudaMemsetAsync(c->T2b, 0, bytes, c->stream);
-  if (c->opts.matvec_prec == RSFDE_DF32) tune_operator<df>(c, reps, c->xdf.tab, c->ydf.tab, chosen);
-  else if (c->opts.matvec_prec == RSFDE_FP32) tune_operator<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
-  else tune_operator<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
+  const bool b64 = basis_kind(c) == BASIS_FP64;
+  if (c->opts.matvec_prec == RSFDE_DF32) {
+    if (b64) tune_operator<df, double>(c, reps, c->xdf.tab, c->ydf.tab, chosen);
+    else tune_operator<df, df>(c, reps, c->xdf.tab, c->ydf.tab, chosen);
+  } else if (c->opts.matvec_prec == RSFDE_FP32) {
+    if (b64) tune_operator<float, double>(c, reps, c->x32.tab, c->y32.tab, chosen);
+    else tune_operator<float, float>(c, reps, c->x32.tab, c->y32.tab, chosen);
+  } else {
+    tune_operator<double, double>(c, reps, c->x64.tab, c->y64.tab, chosen);
+  }
   // the double-FP32 true residual runs the same transform families in 8-byte
   // arithmetic (recorded separately from the 4-byte shapes): timed as itself
   if (c->opts.resid_prec == RSFDE_DF32 && c->opts.matvec_prec != RSFDE_DF32 && !left_variant(c)) {
@@ -990,6 +1059,7 @@ void rsfde_opts_default(rsfde_opts* o) {
   o->use_graph = 1;
   o->stream = nullptr;
   o->resid_prec = RSFDE_FP64;
+  o->basis_prec = RSFDE_FP64;
 }
 
 const char* rsfde_strerror(int code) {
@@ -1014,6 +1084,10 @@ static int valid_opts(const rsfde_opts* o) {
   if (o->matvec_prec != RSFDE_FP64 && o->matvec_prec != RSFDE_DF32 && o->matvec_prec != RSFDE_FP32) return 0;
   if (o->variant != RSFDE_FGMRES_RIGHT && o->variant != RSFDE_GMRES_LEFT) return 0;
   if (o->resid_prec != RSFDE_FP64 && o->resid_prec != RSFDE_DF32) return 0;
+  // the basis stores the operator's output: FP64 takes any operator, the
+  // double-FP32 and FP32 bases only their own
+  if (o->basis_prec != RSFDE_FP64 && o->basis_prec != o->matvec_prec) return 0;
+  if (o->basis_prec != RSFDE_FP64 && o->basis_prec != RSFDE_DF32 && o->basis_prec != RSFDE_FP32) return 0;
   return 1;
 }
 
@@ -1022,7 +1096,7 @@ int rsfde_setup(rsfde_ctx** out, const rsfde_grid* g, const uint8_t* mask, doubl
   if (!out) return RSFDE_EINVAL;
   *out = nullptr;
   if (!g || !mask || bad_alpha(alpha1) || bad_alpha(alpha2) || !(kx > 0) || !(ky > 0) || !(dt > 0) ||
-      !(eta > 0) || g->n1 < 1 || g->n2 < 1 || g->n1 > 2048 || g->n2 > 2048 || !(g->bx > g->ax) ||
+      !(eta > 0) || g->n1 < 1 || g->n2 < 1 || g->n1 > kMaxN || g->n2 > kMaxN || !(g->bx > g->ax) ||
       !(g->by > g->ay))
     return RSFDE_EINVAL;
   rsfde_opts o;
@@ -1113,8 +1187,10 @@ int rsfde_set_stream(rsfde_ctx* c, void* stream) {
 int rsfde_solve(rsfde_ctx* c, const double* b, double* x, rsfde_stats* stats) {
   if (!c || !b || !x) return RSFDE_EINVAL;
   const size_t bytes = c->N * sizeof(double);
+  begin_call(c);
   cudaMemcpyAsync(c->b, b, bytes, cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  c->call_bytes = 8.0 * c->N;  // ||b||
   enqueue_init(c);
   enqueue_bnorm(c);
   int rc = check_launch(c);
@@ -1138,6 +1214,8 @@ int rsfde_rhs(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, cons
 int rsfde_step(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, const double* src, double* u_next,
                rsfde_stats* stats) {
   if (!c || !u_prev || !u_next) return RSFDE_EINVAL;
+  begin_call(c);
+  c->call_bytes = rhs_bytes(c, u_prevprev != nullptr, src != nullptr);
   enqueue_init(c);
   enqueue_rhs(c, u_prev, u_prevprev, src, c->b, c->x);
   if (left_variant(c)) enqueue_bnorm(c);
@@ -1165,6 +1243,8 @@ int rsfde_step_host(rsfde_ctx* c, const double* u_prev_h, const double* u_prevpr
   cudaMemcpyAsync(d_u, u_prev_h, bytes, cudaMemcpyHostToDevice, c->stream);
   if (d_uu) cudaMemcpyAsync(d_uu, u_prevprev_h, bytes, cudaMemcpyHostToDevice, c->stream);
   if (d_src) cudaMemcpyAsync(d_src, src_h, bytes, cudaMemcpyHostToDevice, c->stream);
+  begin_call(c);
+  c->call_bytes = rhs_bytes(c, d_uu != nullptr, d_src != nullptr);
   enqueue_init(c);
   enqueue_rhs(c, d_u, d_uu, d_src, c->b, c->x);
   if (left_variant(c)) enqueue_bnorm(c);
@@ -1262,6 +1342,13 @@ int rsfde_get_params(rsfde_ctx* c, double* out5) {
 
 int64_t rsfde_kernel_launches(const rsfde_ctx* c) { return c ? c->launches : 0; }
 
+int rsfde_set_wait_cycles(rsfde_ctx* c, int64_t cycles) {
+  if (!c || cycles < 0) return RSFDE_EINVAL;
+  c->wait_cycles = cycles;
+  bf16_plan_set_wait(c->bf16, cycles);
+  return RSFDE_OK;
+}
+
 int rsfde_autotune(rsfde_ctx* c, int32_t reps, int32_t* chosen) {
   if (!c || reps < 1) return RSFDE_EINVAL;
   return autotune_ctx(c, reps, chosen);
@@ -1288,9 +1375,10 @@ int rsfde_profile_read(rsfde_ctx* c, double* ms, int64_t* launches) {
 }
 
 const char* rsfde_kernel_class_name(int k) {
-  static const char* names[RSFDE_K_COUNT] = {"toeplitz_rows", "toeplitz_cols", "dst_rows", "precond_cols",
-                                             "precond_rows",  "multidot",      "update",   "xupdate",
-                                             "other",         "dst_gemm"};
+  static const char* names[RSFDE_K_COUNT] = {"toeplitz_rows", "toeplitz_cols", "dst_rows",   "precond_cols",
+                                             "precond_rows",  "multidot",      "update",     "xupdate",
+                                             "other",         "dst_gemm",      "resid_rows", "resid_cols",
+                                             "solve_y"};
   return (k >= 0 && k < RSFDE_K_COUNT) ? names[k] : "unknown";
 }
 
@@ -1380,6 +1468,8 @@ int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats) {
       stats[i].status = h.status;
       stats[i].rel_res = 0.0;
       stats[i].bnorm = 0.0;
+      for (int k = 0; k < 6; ++k) stats[i].t_ms[k] = 0.0;
+      stats[i].bytes = rhs_bytes(c, b->steps_done > 1, b->has_src[i] != 0) + solve_bytes(c, h);
     }
     if (h.status != RSFDE_OK && worst == RSFDE_OK) worst = h.status;
   }

@@ -48,6 +48,7 @@ struct SolverState {
   int zero_solution;  // b == 0: x must be zeroed
   int body_runs;      // FGMRES cycles replayed by the device-side graph loop (this solve)
   long long total_body_runs;  // the same over the context's lifetime (never reset)
+  long long sum_j;            // sum of the Arnoldi column index j over the solve's iterations
   unsigned int counter;  // arrivals for the last-block reductions
   unsigned int pad;
   double tol, bnorm, beta, rel_res;

@@ -149,6 +149,7 @@ struct Bf16Plan {
   const float* lamy = nullptr;
   int* err = nullptr;
   void* mem = nullptr;
+  long long wait_cycles = kWaitCycles;  // bound of each pipeline wait of the GEMM launches
 };
 
 // S_n as a split BF16 pair: [S_n]_{ij} = sqrt(2/(n+1)) sin(pi i j/(n+1)), FP64 on the host.
@@ -261,11 +262,20 @@ void bf16_plan_destroy(Bf16Plan* p) {
   delete p;
 }
 
+// Reads and clears the give-up flag of the plan's GEMM launches: a wait that
+// gave up left that launch's output incomplete (RSFDE_ETIMEOUT), but every
+// copy and MMA it had issued completed before it exited, so the plan stays
+// usable.
 int bf16_plan_error(Bf16Plan* p, cudaStream_t s) {
   int h = 0;
   if (cudaMemcpyAsync(&h, p->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RSFDE_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return RSFDE_ECUDA;
+  if (h && cudaMemsetAsync(p->err, 0, sizeof(int), s) != cudaSuccess) return RSFDE_ECUDA;
   return h ? RSFDE_ETIMEOUT : RSFDE_OK;
+}
+
+void bf16_plan_set_wait(Bf16Plan* p, long long cycles) {
+  if (p) p->wait_cycles = cycles > 0 ? cycles : kWaitCycles;
 }
 
 template <int EPI, int NT, bool SYM, int BN>
@@ -306,9 +316,9 @@ static void launch_gemm(const Bf16Plan* p, int hk, const Bf16Mat& A, const Bf16M
   }
 }
 
-bool bf16_plan_a0(const Bf16Plan* p, Bf16Out* out) {
-  if (!p || p->nt != 1 || p->h1 == 0 || p->n1 % 4 != 0) return false;
-  *out = Bf16Out{p->A0.hi, p->n1, p->ld1, p->h1};
+bool bf16_plan_a0(const Bf16Plan* p, int vec, Bf16Out* out) {
+  if (!p || p->h1 == 0 || vec < 1 || p->n1 % vec != 0) return false;
+  *out = Bf16Out{p->A0.hi, p->nt == 3 ? p->A0.lo : nullptr, p->n1, p->ld1, p->h1};
   return true;
 }
 
@@ -326,6 +336,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
                p->ld1, p->h1, gate);
   GemmEpiParams ep{};
   // 1. T1t = (A0 S_x)^T, columns y in the layout of GEMM 2's K
+  ep.wait_cycles = p->wait_cycles;
   ep.out_hi = p->T1t.hi;
   ep.out_lo = p->T1t.lo;
   ep.ldo = p->ld2;
@@ -334,6 +345,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   launch_gemm<EPI_SPLIT_T>(p, p->h1, p->A0, p->Sx, n2, n1, 1, ep, gate, s);
   // 2. W^T = T1t S_y; both tau divides (Eq. 4.6), stacked [W1; W2]
   ep = GemmEpiParams{};
+  ep.wait_cycles = p->wait_cycles;
   ep.out_hi = p->Wst.hi;
   ep.out_lo = p->Wst.lo;
   ep.ldo = p->ld1;
@@ -345,6 +357,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   launch_gemm<EPI_DIVIDE_T>(p, p->h2, p->T1t, p->Sy, n1, n2, 1, ep, gate, s);
   // 3. Yt = ([W1; W2] S_x)^T, the channels side by side (column offset ld2)
   ep = GemmEpiParams{};
+  ep.wait_cycles = p->wait_cycles;
   ep.out_hi = p->Yt.hi;
   ep.out_lo = p->Yt.lo;
   ep.ldo = 2 * p->ld2;
@@ -354,6 +367,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   launch_gemm<EPI_SPLIT_T>(p, p->h1, p->Wst, p->Sx, 2 * n2, n1, 1, ep, gate, s);
   // 4. z = (1-Phi) S_y W1 S_x + Phi S_y W2 S_x (channel = blockIdx.z)
   ep = GemmEpiParams{};
+  ep.wait_cycles = p->wait_cycles;
   ep.z = z;
   ep.z_double = sizeof(Tz) == 8;
   ep.phibits = p->phibits;

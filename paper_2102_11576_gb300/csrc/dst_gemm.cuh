@@ -77,6 +77,7 @@ struct GemmEpiParams {
   int ldz;
   const double* zscale;  // EPI_COMBINE_T: if set, z is scaled by *zscale (unscaled first operand)
   int a_koff;           // K offset of channel 1's A operand (EPI_COMBINE_T, blockIdx.z = 1)
+  long long wait_cycles;  // bound of each pipeline wait (ring slots, accumulator) in SM clock cycles
 };
 
 template <int NT>
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
     int issued = 0;
     for (int kb = 0; kb < KB; ++kb) {
       const int s = kb % kGemmStages, it = kb / kGemmStages;
-      if (kb >= kGemmStages && !mbar_wait(&empty[s], (it - 1) & 1, err)) break;
+      if (kb >= kGemmStages && !mbar_wait(&empty[s], (it - 1) & 1, err, ep.wait_cycles)) break;
       mbar_expect_tx(&full[s], kStageBytes);
       tma_load_2d(a_tile(s, 0), &tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
       tma_load_2d(b_tile(s, 0), &tB_hi, kb * kGemmBK, n0, &full[s]);
@@ -149,15 +150,17 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
       }
       issued = kb + 1;
     }
-    if (*(volatile int*)err) {  // give up: let the loads in flight land before the block exits
-      for (int kb = issued > kGemmStages ? issued - kGemmStages : 0; kb < issued; ++kb)
-        mbar_wait(&full[kb % kGemmStages], (kb / kGemmStages) & 1, err);
-    }
+    // Drain (default bound): load kb was issued only after load kb - stages
+    // had landed and been consumed, so at most the last `stages` loads can
+    // still be in flight; they land before the block exits, whether the
+    // pipeline ran through or a wait gave up.  (Completed phases return at once.)
+    for (int kb = issued > kGemmStages ? issued - kGemmStages : 0; kb < issued; ++kb)
+      mbar_wait(&full[kb % kGemmStages], (kb / kGemmStages) & 1, err);
   } else if (warp == 1 && lane == 0) {  // MMA issuer
     constexpr uint32_t idesc = umma_idesc_bf16(kGemmBM, BN);
     for (int kb = 0; kb < KB; ++kb) {
       const int s = kb % kGemmStages, it = kb / kGemmStages;
-      if (!mbar_wait(&full[s], it & 1, err)) break;
+      if (!mbar_wait(&full[s], it & 1, err, ep.wait_cycles)) break;
       tc_fence_after();
       // SYM: even-j half into the first accumulator, odd-j half into the second
       const uint32_t acc = (SYM && kb >= KBh) ? taddr + BN : taddr;
@@ -180,6 +183,9 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
     umma_commit(&done);
   }
   __syncwarp();
+  // done: every MMA this block issued has completed (the MMA thread commits it
+  // after its last issue, also when it gave up early); waited with the
+  // default bound, as the tensor memory is freed after it
   const bool ok = mbar_wait(&done, 0, err);
   tc_fence_after();
   // Staged transposed stores (symmetric plain-BF16 split and divide epilogues):

@@ -85,6 +85,7 @@ __device__ __forceinline__ void givens_step(SolverState* st, int j, double hnorm
   st->g[j + 1] = -s * st->g[j];
   st->g[j] = c * st->g[j];
   st->iters += 1;
+  st->sum_j += j;
   st->jlast = j + 1;
   st->s[j + 1] = hnorm > 0.0 ? 1.0 / hnorm : 0.0;
   if (!isfinite(hnorm) || !isfinite(st->g[j + 1]) || !isfinite(H[j * KM + j])) {
@@ -102,6 +103,7 @@ __device__ __forceinline__ void givens_step(SolverState* st, int j, double hnorm
 // ---- tile-shape autotuning (transforms.cu) -----------------------------------
 enum TuneKind { TK_TOEP_ROWS, TK_TOEP_COLS, TK_DST_ROWS, TK_DST_COLS, TK_PRE_COLS, TK_PRE_ROWS, TK_COUNT };
 void tune_force_groups(int F);  // 0: use the recorded choice / heuristic
+int tune_forced();              // the shape tune_force_groups set (0: none)
 void tune_record(int kind, int log2L, int wide, int F);
 int tune_lookup(int kind, int log2L, int wide);
 template <typename T>
@@ -133,11 +135,14 @@ template <typename T, typename Tz>
 void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, int n1, int n2,
                          const AxisTables<T>& ax, const int* gate, cudaStream_t s);
 
-// Optional second output of the final update pass (FP32 basis): the new
-// vector rounded to BF16 in the symmetric GEMM's K layout (row y at a0 + y*ld,
-// even x at x/2, odd x at hk + x/2), the next preconditioner's first operand.
+// Optional second output of the final update pass (FP32 or FP64 basis): the
+// new vector rounded to BF16 in the symmetric GEMM's K layout (row y at
+// a0 + y*ld, even x at x/2, odd x at hk + x/2), the next preconditioner's first
+// operand; with lo set (split BF16) also the remainder bf16(x - hi) at the
+// same place of lo.
 struct Bf16Out {
   __nv_bfloat16* a0;
+  __nv_bfloat16* lo;
   int n1, ld, hk;
 };
 
@@ -149,15 +154,16 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
                      const uint8_t* phi, cudaStream_t s);
 int bf16_plan_nt(const Bf16Plan* p);
 void bf16_plan_destroy(Bf16Plan* p);
-int bf16_plan_error(Bf16Plan* p, cudaStream_t s);
+int bf16_plan_error(Bf16Plan* p, cudaStream_t s);  // reads and clears the give-up flag
+void bf16_plan_set_wait(Bf16Plan* p, long long cycles);  // <= 0: the default bound
 // skip_split: the first operand was already written (update_kernel's Bf16Out,
 // unscaled), and zscale multiplies the result instead.
 template <typename Tz, typename Tin>
 int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
                  const int* gate, cudaStream_t s, bool skip_split = false, const double* zscale = nullptr);
 // The Bf16Out target of the plan's first operand, if the plan can take it
-// (plain BF16, symmetric layout, n1 a multiple of 4); returns false otherwise.
-bool bf16_plan_a0(const Bf16Plan* p, Bf16Out* out);
+// (symmetric layout, n1 a multiple of vec); returns false otherwise.
+bool bf16_plan_a0(const Bf16Plan* p, int vec, Bf16Out* out);
 
 // ---- launchers (krylov.cu) -------------------------------------------------
 int vec_grid(size_t N);

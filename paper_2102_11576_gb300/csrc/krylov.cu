@@ -38,6 +38,7 @@ __global__ void init_state_kernel(SolverState* st, int m, int max_iter, double t
   st->m = m;
   st->zero_solution = 0;
   st->body_runs = 0;
+  st->sum_j = 0;
   st->counter = 0;
   st->tol = tol;
   st->bnorm = 0.0;
@@ -355,9 +356,31 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size
       if constexpr (std::is_same<Tv, float>::value && VEC == 4) {
         if (bo.a0 && final_pass) {  // x = p mod n1 is a multiple of 4 (n1 is)
           const int y = (int)(p / (size_t)bo.n1), x = (int)(p - (size_t)y * bo.n1);
-          __nv_bfloat16* row = bo.a0 + (size_t)y * bo.ld + (x >> 1);
-          *reinterpret_cast<__nv_bfloat162*>(row) = __floats2bfloat162_rn(val[u][0], val[u][2]);
-          *reinterpret_cast<__nv_bfloat162*>(row + bo.hk) = __floats2bfloat162_rn(val[u][1], val[u][3]);
+          const size_t o = (size_t)y * bo.ld + (x >> 1);
+          const __nv_bfloat162 ev = __floats2bfloat162_rn(val[u][0], val[u][2]);
+          const __nv_bfloat162 od = __floats2bfloat162_rn(val[u][1], val[u][3]);
+          *reinterpret_cast<__nv_bfloat162*>(bo.a0 + o) = ev;
+          *reinterpret_cast<__nv_bfloat162*>(bo.a0 + o + bo.hk) = od;
+          if (bo.lo) {
+            const float2 e = __bfloat1622float2(ev), d = __bfloat1622float2(od);
+            *reinterpret_cast<__nv_bfloat162*>(bo.lo + o) =
+                __floats2bfloat162_rn(val[u][0] - e.x, val[u][2] - e.y);
+            *reinterpret_cast<__nv_bfloat162*>(bo.lo + o + bo.hk) =
+                __floats2bfloat162_rn(val[u][1] - d.x, val[u][3] - d.y);
+          }
+        }
+      } else if constexpr (std::is_same<Tv, double>::value && VEC == 2) {
+        if (bo.a0 && final_pass) {  // x = p mod n1 is even (n1 is): x to column x/2, x+1 to hk + x/2
+          const int y = (int)(p / (size_t)bo.n1), x = (int)(p - (size_t)y * bo.n1);
+          const size_t o = (size_t)y * bo.ld + (x >> 1);
+          const float f0 = (float)val[u][0], f1 = (float)val[u][1];
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
+          bo.a0[o] = h0;
+          bo.a0[o + bo.hk] = h1;
+          if (bo.lo) {
+            bo.lo[o] = __float2bfloat16_rn(f0 - __bfloat162float(h0));
+            bo.lo[o + bo.hk] = __float2bfloat16_rn(f1 - __bfloat162float(h1));
+          }
         }
       }
 #pragma unroll
@@ -619,7 +642,7 @@ template <typename Tv>
 void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s,
                    const Bf16Out* bo) {
   constexpr int VEC = 16 / sizeof(Tv);
-  const Bf16Out none{nullptr, 1, 0, 0};
+  const Bf16Out none{nullptr, nullptr, 1, 0, 0};
   const int ch = dot_chunk(j);
   if (N % VEC == 0) {
     const Bf16Out& b = bo ? *bo : none;

@@ -3,9 +3,8 @@
 //
 // Who needs it: code that must not call cudaMalloc -- for example a host
 // application or framework that owns every device allocation through its own
-// pool (a stray cudaMalloc would bypass its accounting or fragment it), or a
-// caller that is building a CUDA graph around this call and must not
-// allocate while doing so.  Such callers cannot create an rsfde_ctx, because
+// pool, where a stray cudaMalloc would bypass its accounting or fragment the
+// memory it manages.  Such callers cannot create an rsfde_ctx, because
 // rsfde_setup allocates the context's workspace and tables.
 //
 // Instead, the intermediate of the two passes (rows, then columns) and the
@@ -14,6 +13,7 @@
 // library's module, so every GPU that loads the library holds them
 // (about 2.1 MB) until the process exits.
 #include <cmath>
+#include <mutex>
 
 #include "fft.cuh"
 #include "internal.h"
@@ -31,16 +31,22 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_noalloc_scratch[(size_t)kMaxN * kMaxN];
 static __device__ __align__(256) double g_noalloc_tables[2 * kTableDoubles];
 
-// Host-side device addresses of the two arrays, looked up once per device.
+// Host-side device addresses of the two arrays, looked up once per device,
+// and the sizes and stream of the tables last copied to each device.
 static double* s_scratch_addr[kMaxDevices];
 static double* s_tables_addr[kMaxDevices];
 static bool s_ready[kMaxDevices];
+static int s_last_n1[kMaxDevices], s_last_n2[kMaxDevices];
+static cudaStream_t s_last_stream[kMaxDevices];
 
 // Host staging of the tables: fixed-size, so the call allocates nothing on
 // the host either.  cudaMemcpyAsync from pageable memory returns once the
-// bytes are staged, so the buffers may be refilled by the next call.
+// bytes are staged, so the buffers may be refilled by the next call.  One
+// mutex serialises the host side of all calls (the staging buffers and the
+// per-device records are process-wide).
 static double h_tables[2 * kTableDoubles];
 static double h_re[kMaxL], h_im[kMaxL];
+static std::mutex s_host_mutex;
 
 int pow2_at_least(int v, int* log2v) {
   int L = 16, lg = 4;
@@ -123,6 +129,7 @@ extern "C" int rsfde_dst2_noalloc(int32_t n1, int32_t n2, const double* v, doubl
   if (n1 < 1 || n2 < 1 || n1 > kMaxN || n2 > kMaxN || !v || !out || v == out) return RSFDE_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RSFDE_ECUDA;
+  std::lock_guard<std::mutex> lock(s_host_mutex);
   if (!s_ready[dev]) {
     // once per device, with that device current: the arrays' device addresses
     if (cudaGetSymbolAddress((void**)&s_scratch_addr[dev], g_noalloc_scratch) != cudaSuccess) return RSFDE_ECUDA;
@@ -133,12 +140,21 @@ extern "C" int rsfde_dst2_noalloc(int32_t n1, int32_t n2, const double* v, doubl
   int lg1 = 0, lg2 = 0;
   const int L1 = pow2_at_least(2 * n1 - 1, &lg1);
   const int L2 = pow2_at_least(2 * n2 - 1, &lg2);
-  fill_axis(0, n1, L1, lg1);
-  fill_axis(1, n2, L2, lg2);
-  // every value the kernels read is rewritten here, so nothing from an
-  // earlier call (the arrays keep the last call's contents) is used
-  if (cudaMemcpyAsync(s_tables_addr[dev], h_tables, sizeof(h_tables), cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return RSFDE_ECUDA;
+  // The tables depend only on (n1, n2).  When the previous call on this
+  // device had the same sizes and the same stream, the copy it enqueued
+  // before its kernels still holds them (stream order); otherwise they are
+  // rebuilt and every value the kernels read is rewritten, so nothing else
+  // from an earlier call (the arrays keep the last call's contents) is used.
+  if (s_last_n1[dev] != n1 || s_last_n2[dev] != n2 || s_last_stream[dev] != s) {
+    fill_axis(0, n1, L1, lg1);
+    fill_axis(1, n2, L2, lg2);
+    s_last_n1[dev] = 0;  // unknown until the copy is enqueued
+    if (cudaMemcpyAsync(s_tables_addr[dev], h_tables, sizeof(h_tables), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return RSFDE_ECUDA;
+    s_last_n1[dev] = n1;
+    s_last_n2[dev] = n2;
+    s_last_stream[dev] = s;
+  }
   const AxisTables<double> tx = device_axis(s_tables_addr[dev], 0, n1, L1, lg1);
   const AxisTables<double> ty = device_axis(s_tables_addr[dev], 1, n2, L2, lg2);
   launch_dst_rows<double, double>(v, nullptr, s_scratch_addr[dev], n1, n2, tx, nullptr, s);

@@ -1,702 +1,31 @@
-// transforms.cu -- the operator M (Eq. 2.14-2.17) and the preconditioner
-// P-hat^-1 (Eq. 4.6) as register-Stockham FFT kernels for sm_103a.
-//
-// Grid functions are x-fastest (u[j*n1 + i]).  A "vector" is a row (x
-// direction, contiguous) or a column (y direction, stride n1).  Each vector
-// (or pair of vectors) is transformed by a group of L/16 threads (fft16.cuh);
-// a block runs F groups.  Row kernels map a group's threads to consecutive
-// positions (coalesced rows); column kernels interleave the F groups across
-// the lanes of a warp so each access touches F (or 2F) adjacent columns.
-//
-//  * Arithmetic: T = double, float, or df (double-FP32, df.cuh).
-//  * Toeplitz product along an axis: two real vectors are packed as the real
-//    and imaginary parts of one complex sequence (the circulant spectrum is
-//    real because the Toeplitz matrix of Eq. 2.16 is symmetric), zero padded
-//    to L >= 2n-1, transformed, scaled by the spectrum and transformed back.
-//  * Sine transform S_n (Section 4.1): with c_k = exp(i pi k^2/(2(n+1))) and
-//    jk = (j^2 + k^2 - (k-j)^2)/2,  (S x)_k = sqrt(2/(n+1)) Im(c_k sum_j x_j c_j conj(c_{k-j})),
-//    a convolution of length L >= 2n-1 (Bluestein).
-//  * P-hat^-1 v = (I-Phi) S (I - Lx - Ly)^-1 S v + Phi S ((1+dt/eta) I - Lx - Ly)^-1 S v
-//    (S = S_{n2} (x) S_{n1}; proof of Lemma 4.2) in three passes: rows S_x;
-//    columns S_y, the two spectral divides and both inverse S_y; rows S_x
-//    of both channels with the masked combine.
+// transforms.cu -- process-wide state of the transform launchers: the
+// tile-shape table the autotuner records, the shape it forces while timing,
+// and the flag of a launch with no kernel for its (type, mode) pair.  The
+// kernels and launchers are in transforms.cuh, instantiated per arithmetic
+// type in transforms_f64.cu, transforms_f32.cu and transforms_df_*.cu.
 #include <atomic>
-#include <type_traits>
 
-#include "common.cuh"
-#include "df.cuh"
-#include "fft16.cuh"
-#include "internal.h"
-
-// Thread cap of one block of the FP32 transform kernels (their register
-// budget is 65536 / cap per thread); FP64 and double-FP32 blocks (8-byte
-// reals) are capped at 512.
-#ifndef RSFDE_FP32_THREADS
-#define RSFDE_FP32_THREADS 1024
-#endif
+#include "transforms.cuh"
 
 namespace rsfde {
 
-template <typename T>
-__device__ __forceinline__ bool gate_closed(const int* gate) {
-  return gate != nullptr && *(volatile const int*)gate == 0;
-}
-
-// Read-only loads of table entries, including double-FP32 pairs.
-template <typename T>
-__device__ __forceinline__ T ldg_t(const T* p) {
-  return __ldg(p);
-}
-template <>
-__device__ __forceinline__ df ldg_t<df>(const df* p) {
-  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-  return {v.x, v.y};
-}
-template <typename T>
-__device__ __forceinline__ cx<T> ldc(const T* p, int k) {
-  return {ldg_t(p + 2 * k), ldg_t(p + 2 * k + 1)};
-}
-
-// Thread geometry of one block: F groups of G = L/16 threads.
-struct GroupIdx {
-  int g, t;
-};
-template <bool COLS>
-__device__ __forceinline__ GroupIdx group_idx(int G, int F) {
-  // rows: each group's threads consecutive; columns: groups interleaved over lanes
-  if (COLS) return {(int)threadIdx.x & (F - 1), (int)threadIdx.x / F};
-  return {(int)threadIdx.x / G, (int)threadIdx.x & (G - 1)};
-}
-
-// Address of element `pos` of vector `vec`.
-template <bool COLS>
-__device__ __forceinline__ size_t vaddr(int vec, int pos, int n1) {
-  return COLS ? (size_t)pos * n1 + vec : (size_t)vec * n1 + pos;
-}
-
-
-// Bluestein convolution of the 16 chirped values in v: on return v holds
-// sum_j a_j conj(c_{k-j}) at the thread's positions (natural order).
-template <typename T>
-__device__ __forceinline__ void bluestein(cx<T>* v, cx<T>* buf, int t, const AxisTables<T>& ax) {
-  const int L = ax.L, Lq = L >> 4;
-  const cx<T>* tw = reinterpret_cast<const cx<T>*>(ax.tw);
-  fft16_forward<T>(v, buf, t, L, ax.log2L, tw);
-#pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = c_mul(v[k], ldc(ax.bspec, t + k * Lq));  // full spectrum
-  fft16_inverse<T>(v, buf, t, L, ax.log2L, tw);
-}
-
-// scale * x in the arithmetic type T: FP64 vectors are scaled in FP64 before
-// rounding; FP32 and double-FP32 vectors feeding an FP32 transform are scaled
-// in FP32, with no FP64 instruction.
-template <typename T>
-__device__ __forceinline__ T scaled_load(double sc, float, double x) {
-  return cvt<T>(sc * x);
-}
-template <typename T>
-__device__ __forceinline__ T scaled_load(double sc, float scf, df x);
-template <>
-__device__ __forceinline__ float scaled_load<float>(double, float scf, df x) {
-  return __fmul_rn(scf, cvt<float>(x));
-}
-template <>
-__device__ __forceinline__ double scaled_load<double>(double sc, float, df x) {
-  return sc * double(x);
-}
-template <>
-__device__ __forceinline__ df scaled_load<df>(double sc, float, df x) {
-  return df(sc) * x;
-}
-template <typename T>
-__device__ __forceinline__ T scaled_load(double sc, float scf, float x);
-template <>
-__device__ __forceinline__ float scaled_load<float>(double, float scf, float x) {
-  return __fmul_rn(scf, x);
-}
-template <>
-__device__ __forceinline__ double scaled_load<double>(double sc, float, float x) {
-  return sc * (double)x;
-}
-template <>
-__device__ __forceinline__ df scaled_load<df>(double sc, float, float x) {
-  return df(sc) * df(x, 0.0f);
-}
-
-// Im(c_out[pos] * y)
-template <typename T>
-__device__ __forceinline__ T dst_out(const AxisTables<T>& ax, int pos, cx<T> y) {
-  const cx<T> c = ldc(ax.chirp_out, pos);
-  return c.r * y.i + c.i * y.r;
-}
-
-// Two adjacent elements as one access (8 or 16 bytes; the address is aligned
-// to the pair's size).
-template <typename X>
-struct Pair {
-  X x, y;
-};
-template <typename X>
-__device__ __forceinline__ Pair<X> ld_pair(const X* p) {
-  if constexpr (std::is_same<X, float>::value) {
-    const float2 t = *reinterpret_cast<const float2*>(p);
-    return {t.x, t.y};
-  } else if constexpr (std::is_same<X, double>::value) {
-    const double2 t = *reinterpret_cast<const double2*>(p);
-    return {t.x, t.y};
-  } else if constexpr (std::is_same<X, df>::value) {
-    const float4 t = *reinterpret_cast<const float4*>(p);
-    return {df(t.x, t.y), df(t.z, t.w)};
-  } else {  // uint8_t
-    const uchar2 t = *reinterpret_cast<const uchar2*>(p);
-    return {t.x, t.y};
-  }
-}
-template <typename X>
-__device__ __forceinline__ void st_pair(X* p, X a, X b) {
-  if constexpr (std::is_same<X, float>::value) *reinterpret_cast<float2*>(p) = make_float2(a, b);
-  else if constexpr (std::is_same<X, double>::value) *reinterpret_cast<double2*>(p) = make_double2(a, b);
-  else *reinterpret_cast<float4*>(p) = make_float4(a.hi, a.lo, b.hi, b.lo);
-}
-
-// ---------------------------------------------------------------------------
-// Toeplitz product along rows (COLS = false: tmpx = A_x z, MODE_APPLY only) or
-// columns (COLS = true), two vectors per group; tmpx holds A_x z in the
-// arithmetic type T between the two passes.  Column epilogues:
-//   MODE_APPLY:    out = z - tmpx - A_y z + (dt/eta) phi z
-//   MODE_RESIDUAL: out = b - (z - tmpx - A_y z + (dt/eta) phi z), ||out||^2
-//                  reduced, and the last block restarts the solver.
-template <typename T, typename Tin, int MODE, bool COLS, typename Tout>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    toeplitz_kernel(const Tin* __restrict__ z, T* __restrict__ tmpx, const uint8_t* __restrict__ phi,
-                    double pen, const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2,
-                    AxisTables<T> ax, int F, int gstride, const int* gate, double* partials, SolverState* st) {
-  if (gate_closed<T>(gate)) return;
-  const T tpen = cvt<T>(pen);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
-  const int L = ax.L, Lq = L >> 4, G = Lq;
-  const GroupIdx gi = group_idx<COLS>(G, F);
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
-  const int nvec = COLS ? n1 : n2, len = COLS ? n2 : n1;
-  const int npairs = (nvec + 1) >> 1;
-  const int ngroups = (npairs + F - 1) / F;
-  // Column passes with even n1: the pair of columns a, a+1 a group transforms
-  // is adjacent in memory, so z, A_x z, the mask, b and the output move as
-  // pairs (the FP32 operator and the double-FP32 true residual).
-  constexpr bool kPairIO =
-      COLS && ((MODE == MODE_APPLY && std::is_same<T, float>::value && std::is_same<Tin, float>::value &&
-                std::is_same<Tout, float>::value) ||
-               (MODE == MODE_RESIDUAL && std::is_same<T, df>::value && std::is_same<Tin, double>::value));
-  const bool pair_io = kPairIO && (n1 & 1) == 0;
-  double acc = 0.0;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const int pr = grp * F + gi.g;
-    const int a = 2 * pr;
-    const bool live = pr < npairs;
-    const bool second = a + 1 < nvec;
-    cx<T> v[16];  // positions >= L/2 are zero (cleared by the forward transform)
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int pos = gi.t + k * Lq;
-      T re = T(0), im = T(0);
-      if (live && pos < len) {
-        if constexpr (kPairIO) {
-          if (pair_io) {
-            const Pair<Tin> t2 = ld_pair(z + vaddr<COLS>(a, pos, n1));
-            re = cvt<T>(t2.x);
-            im = cvt<T>(t2.y);
-          } else {
-            re = cvt<T>(z[vaddr<COLS>(a, pos, n1)]);
-            if (second) im = cvt<T>(z[vaddr<COLS>(a + 1, pos, n1)]);
-          }
-        } else {
-          re = cvt<T>(z[vaddr<COLS>(a, pos, n1)]);
-          if (second) im = cvt<T>(z[vaddr<COLS>(a + 1, pos, n1)]);
-        }
-      }
-      v[k] = {re, im};
-    }
-    const cx<T>* tw = reinterpret_cast<const cx<T>*>(ax.tw);
-    fft16_forward<T>(v, buf, gi.t, L, ax.log2L, tw);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const T sg = ldg_t(ax.sigma + gi.t + k * Lq);
-      v[k].r *= sg;
-      v[k].i *= sg;
-    }
-    fft16_inverse<T>(v, buf, gi.t, L, ax.log2L, tw);
-    if constexpr (kPairIO) {
-      if (pair_io) {
-        if (live) {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const int pos = gi.t + k * Lq;
-            if (pos >= len) continue;
-            const size_t p = vaddr<COLS>(a, pos, n1);
-            const Pair<Tin> z2 = ld_pair(z + p);
-            const Pair<T> t2 = ld_pair(tmpx + p);
-            const Pair<uint8_t> f2 = ld_pair(phi + p);
-            const T zz0 = cvt<T>(z2.x), zz1 = cvt<T>(z2.y);
-            T w0 = zz0 - t2.x - v[k].r, w1 = zz1 - t2.y - v[k].i;
-            if (f2.x) w0 = w0 + tpen * zz0;
-            if (f2.y) w1 = w1 + tpen * zz1;
-            if constexpr (MODE == MODE_APPLY) {
-              st_pair(out + p, cvt<Tout>(w0), cvt<Tout>(w1));
-            } else {
-              const Pair<double> b2 = ld_pair(b + p);
-              const double r0 = b2.x - cvt<double>(w0), r1 = b2.y - cvt<double>(w1);
-              st_pair(out + p, cvt<Tout>(r0), cvt<Tout>(r1));
-              acc += r0 * r0;
-              acc += r1 * r1;
-            }
-          }
-        }
-        continue;
-      }
-    }
-    if (live) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = gi.t + k * Lq;
-        if (pos >= len) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !second) break;
-          const size_t p = vaddr<COLS>(a + h, pos, n1);
-          const T az = h ? v[k].i : v[k].r;
-          if (!COLS) {
-            tmpx[p] = az;  // A_x z, kept in the arithmetic type T
-          } else {
-            // z - A_x z - A_y z + (dt/eta) phi z in T; only the result is rounded to Tout
-            const T zz = cvt<T>(z[p]);
-            T w = zz - tmpx[p] - az;
-            if (phi[p]) w = w + tpen * zz;
-            if (MODE == MODE_RAW) {
-              out[p] = cvt<Tout>(az);
-            } else if (MODE == MODE_APPLY) {
-              out[p] = cvt<Tout>(w);
-            } else if (MODE == MODE_RESID_ONLY) {
-              out[p] = cvt<Tout>(b[p] - cvt<double>(w));
-            } else {
-              const double r = b[p] - cvt<double>(w);
-              out[p] = cvt<Tout>(r);
-              acc += r * r;
-            }
-          }
-        }
-      }
-    }
-  }
-  if (MODE == MODE_RESIDUAL) {
-    const double bs = block_sum(acc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = bs;
-    if (arrive_last(&st->counter, gridDim.x)) {
-      const double tot = sum_partials(partials, gridDim.x, red);
-      if (threadIdx.x == 0) restart_prep(st, sqrt(tot));
-    }
-  }
-}
-
-// Sine transform of every row (COLS = false) or column: out = S (scale * in).
-template <typename T, typename Tin, typename Tout, bool COLS>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    dst_kernel(const Tin* __restrict__ in, const double* vscale, Tout* __restrict__ out, int n1, int n2,
-               AxisTables<T> ax, int F, int gstride, const int* gate) {
-  if (gate_closed<T>(gate)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = ax.L, Lq = L >> 4, G = Lq;
-  const GroupIdx gi = group_idx<COLS>(G, F);
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
-  const int nvec = COLS ? n1 : n2, len = COLS ? n2 : n1;
-  const double sc = vscale ? *vscale : 1.0;
-  const float scf = (float)sc;
-  const int ngroups = (nvec + F - 1) / F;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const int vec = grp * F + gi.g;
-    const bool live = vec < nvec;
-    cx<T> v[16];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int pos = gi.t + k * Lq;
-      cx<T> x = {T(0), T(0)};
-      if (live && pos < len) {
-        const T xv = scaled_load<T>(sc, scf, in[vaddr<COLS>(vec, pos, n1)]);
-        const cx<T> c = ldc(ax.chirp, pos);
-        x = {xv * c.r, xv * c.i};
-      }
-      v[k] = x;
-    }
-    bluestein<T>(v, buf, gi.t, ax);
-    if (live) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = gi.t + k * Lq;
-        if (pos < len) out[vaddr<COLS>(vec, pos, n1)] = Tout(dst_out(ax, pos, v[k]));
-      }
-    }
-  }
-}
-
-// Preconditioner, column pass.  For each x-frequency i (a column of T1, the
-// rows already sine-transformed): W = S_{n2} T1[:, i];
-// T2a[:, i] = S_{n2} (W / (1 - lam_x[i] - lam_y)),
-// T2b[:, i] = S_{n2} (W / (1 + dt/eta - lam_x[i] - lam_y)).
-template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    precond_cols_kernel(const T* __restrict__ T1, T* __restrict__ T2a, T* __restrict__ T2b, int n1, int n2,
-                        AxisTables<T> ay, const T* __restrict__ lamx, T pen, int F, int gstride, const int* gate) {
-  if (gate_closed<T>(gate)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = ay.L, Lq = L >> 4, G = Lq;
-  const GroupIdx gi = group_idx<true>(G, F);
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
-  const int ngroups = (n1 + F - 1) / F;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const int col = grp * F + gi.g;
-    const bool live = col < n1;
-    cx<T> v[16];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int pos = gi.t + k * Lq;
-      cx<T> x = {T(0), T(0)};
-      if (live && pos < n2) {
-        const T xv = T1[(size_t)pos * n1 + col];
-        const cx<T> c = ldc(ay.chirp, pos);
-        x = {xv * c.r, xv * c.i};
-      }
-      v[k] = x;
-    }
-    bluestein<T>(v, buf, gi.t, ay);
-    const T lx = live ? lamx[col] : T(0);
-    T W[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int pos = gi.t + k * Lq;
-      W[k] = (live && pos < n2) ? dst_out(ay, pos, v[k]) / (T(1) - lx - __ldg(ay.lam + pos)) : T(0);
-    }
-#pragma unroll
-    for (int ch = 0; ch < 2; ++ch) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = gi.t + k * Lq;
-        cx<T> x = {T(0), T(0)};
-        if (live && pos < n2) {
-          T w = W[k];
-          if (ch == 1) {  // W / (1 + pen - l) = W1 * (1 - l) / (1 + pen - l)
-            const T base = T(1) - lx - __ldg(ay.lam + pos);
-            w = w * base / (base + pen);
-          }
-          const cx<T> c = ldc(ay.chirp, pos);
-          x = {w * c.r, w * c.i};
-        }
-        v[k] = x;
-      }
-      bluestein<T>(v, buf, gi.t, ay);
-      if (live) {
-        T* dst = ch ? T2b : T2a;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int pos = gi.t + k * Lq;
-          if (pos < n2) dst[(size_t)pos * n1 + col] = dst_out(ay, pos, v[k]);
-        }
-      }
-    }
-  }
-}
-
-// Preconditioner, final row pass:  z[j, :] = (1 - phi) S_{n1} T2a[j, :] + phi S_{n1} T2b[j, :].
-template <typename T, typename Tz>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    precond_rows_kernel(const T* __restrict__ T2a, const T* __restrict__ T2b, const uint8_t* __restrict__ phi,
-                        Tz* __restrict__ z, int n1, int n2, AxisTables<T> ax, int F, int gstride, const int* gate) {
-  if (gate_closed<T>(gate)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = ax.L, Lq = L >> 4, G = Lq;
-  const GroupIdx gi = group_idx<false>(G, F);
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
-  const int ngroups = (n2 + F - 1) / F;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const int row = grp * F + gi.g;
-    const bool live = row < n2;
-    T res[8];
-#pragma unroll
-    for (int ch = 0; ch < 2; ++ch) {
-      const T* src = ch ? T2b : T2a;
-      cx<T> v[16];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = gi.t + k * Lq;
-        cx<T> x = {T(0), T(0)};
-        if (live && pos < n1) {
-          const T xv = src[(size_t)row * n1 + pos];
-          const cx<T> c = ldc(ax.chirp, pos);
-          x = {xv * c.r, xv * c.i};
-        }
-        v[k] = x;
-      }
-      bluestein<T>(v, buf, gi.t, ax);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = gi.t + k * Lq;
-        if (ch == 0) {
-          res[k] = (pos < n1) ? dst_out(ax, pos, v[k]) : T(0);
-        } else if (live && pos < n1) {
-          const size_t p = (size_t)row * n1 + pos;
-          if (phi[p]) res[k] = dst_out(ax, pos, v[k]);
-        }
-      }
-    }
-    if (live) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = gi.t + k * Lq;
-        if (pos < n1) z[(size_t)row * n1 + pos] = Tz(res[k]);
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Launch geometry: G = L/16 threads per group; F groups per block, the
-// largest power of two within the thread cap (512 FP64 / 1024 FP32), the
-// shared-memory budget and the work available (at least ~2 blocks per SM).
-// Complex values per 128-byte shared-memory phase: 16 (FP32), 8 (FP64).
-template <typename T>
-static int lanes_per_phase() {
-  return 128 / (int)(2 * sizeof(T));
-}
-
-// Distance between the groups' buffers (complex values).  Within one access
-// phase the lanes cover (t, g) pairs; the offset makes (g * stride + t) hit
-// distinct banks: groups interleaved across lanes (columns) need
-// stride = P/F mod P, consecutive groups smaller than a phase (rows) need
-// stride = G mod P.
-template <typename T>
-static int group_stride(int L, int F, bool cols) {
-  const int P = lanes_per_phase<T>();
-  const int base = L + L / 16, G = L / 16;
-  int target = 0;
-  if (cols) target = F >= P ? 1 : P / F;
-  else if (G < P) target = G;
-  return base + ((target - base) % P + P) % P;
-}
-
-// Tile shape (F, the vectors one block transforms) per kernel family,
-// transform length and 4/8-byte arithmetic: chosen by measurement
-// (rsfde_autotune) when recorded, else by the occupancy heuristic below.
 static int g_tuned[TK_COUNT][16][2];
 static thread_local int g_force_groups = 0;
+static std::atomic<int> g_unsupported{0};
 
 void tune_force_groups(int F) { g_force_groups = F; }
+int tune_forced() { return g_force_groups; }
 void tune_record(int kind, int log2L, int wide, int F) {
   if (kind >= 0 && kind < TK_COUNT && log2L >= 0 && log2L < 16) g_tuned[kind][log2L][wide ? 1 : 0] = F;
 }
 int tune_lookup(int kind, int log2L, int wide) {
   return (kind >= 0 && kind < TK_COUNT && log2L >= 0 && log2L < 16) ? g_tuned[kind][log2L][wide ? 1 : 0] : 0;
 }
-
-// Largest feasible F: the thread cap (512 for 8-byte arithmetic, else
-// RSFDE_FP32_THREADS), the shared-memory budget and the work available.
-template <typename T>
-int max_groups(int L, int items) {
-  const int G = L / 16;
-  const int cap = sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS;
-  const size_t per = (size_t)(L + L / 16 + lanes_per_phase<T>()) * 2 * sizeof(T);
-  int F = 1;
-  while (2 * F * G <= cap && per * 2 * F <= (size_t)kSmemBudget && 2 * F <= items) F *= 2;
-  return F;
-}
-
-template <typename T>
-static int pick_groups(int L, int items, int kind) {
-  const int Fmax = max_groups<T>(L, items);
-  int log2L = 0;
-  while ((1 << log2L) < L) ++log2L;
-  int F = g_force_groups ? g_force_groups : tune_lookup(kind, log2L, sizeof(T) == 8);
-  if (F > 0) return F < Fmax ? F : Fmax;
-  F = Fmax;  // heuristic: as wide as fits, but at least ~2 blocks per SM
-  while (F > 1 && (items + F - 1) / F < 2 * kNumSMs) F /= 2;
-  return F;
-}
-
-template <typename T>
-static size_t group_smem(int L, int F, bool cols) {
-  return (size_t)F * group_stride<T>(L, F, cols) * 2 * sizeof(T);
-}
-
-template <typename K>
-static void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <typename T, typename Tin>
-void launch_toeplitz_rows(const Tin* z, void* tmpx, int n1, int n2, const AxisTables<T>& ax, const int* gate,
-                          cudaStream_t s) {
-  const int npairs = (n2 + 1) / 2;
-  const int F = pick_groups<T>(ax.L, npairs, TK_TOEP_ROWS);
-  const size_t sm = group_smem<T>(ax.L, F, false);
-  auto k = toeplitz_kernel<T, Tin, MODE_APPLY, false, double>;
-  set_smem(k, sm);
-  k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), nullptr, 0.0, nullptr, nullptr,
-                                                      n1, n2, ax, F, group_stride<T>(ax.L, F, false), gate,
-                                                      nullptr, nullptr);
-}
-
-static std::atomic<int> g_unsupported{0};
 void note_unsupported_launch() { g_unsupported.store(1); }
 bool take_unsupported_launch() { return g_unsupported.exchange(0) != 0; }
 
-// Only the combinations the solver uses are instantiated: FP32 arithmetic
-// runs the operator (MODE_APPLY) alone, double-FP32 the operator and the true
-// residual; the raw Toeplitz products and the left variant's residual are FP64.
-template <typename T, typename Tin, typename Tout>
-void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi, double pen,
-                          const double* b, Tout* out, int n1, int n2, const AxisTables<T>& ay,
-                          const int* gate, double* partials, SolverState* st, cudaStream_t s) {
-  const int npairs = (n1 + 1) / 2;
-  const int F = pick_groups<T>(ay.L, npairs, TK_TOEP_COLS);
-  const size_t sm = group_smem<T>(ay.L, F, true);
-  const int gs = group_stride<T>(ay.L, F, true);
-  int grid = (npairs + F - 1) / F;
-  // the true residual: FP64 or double-FP32 arithmetic on an FP64 x
-  constexpr bool resid_mode = std::is_same<Tin, double>::value && !std::is_same<T, float>::value;
-  constexpr bool fp64_modes = std::is_same<T, double>::value && std::is_same<Tin, double>::value &&
-                              std::is_same<Tout, double>::value;
-  constexpr bool apply_mode = !std::is_same<T, double>::value || std::is_same<Tout, double>::value;
-  if constexpr (resid_mode) {
-    if (mode == MODE_RESIDUAL) {
-      if (grid > kMaxPartials) grid = kMaxPartials;
-      auto k = toeplitz_kernel<T, Tin, MODE_RESIDUAL, true, Tout>;
-      set_smem(k, sm);
-      k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
-                                          partials, st);
-      return;
-    }
-  }
-  if constexpr (fp64_modes) {
-    if (mode == MODE_RESID_ONLY || mode == MODE_RAW) {
-      auto k = mode == MODE_RAW ? toeplitz_kernel<T, Tin, MODE_RAW, true, Tout>
-                                : toeplitz_kernel<T, Tin, MODE_RESID_ONLY, true, Tout>;
-      set_smem(k, sm);
-      k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
-                                          partials, st);
-      return;
-    }
-  }
-  if constexpr (apply_mode) {
-    if (mode == MODE_APPLY) {
-      auto k = toeplitz_kernel<T, Tin, MODE_APPLY, true, Tout>;
-      set_smem(k, sm);
-      k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
-                                          partials, st);
-      return;
-    }
-  }
-  note_unsupported_launch();  // no kernel for this combination: reported as RSFDE_EINVAL
-}
-
-template <typename T, typename Tin, typename Tout>
-void launch_dst_rows(const Tin* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
-                     const int* gate, cudaStream_t s) {
-  const int F = pick_groups<T>(ax.L, n2, TK_DST_ROWS);
-  const size_t sm = group_smem<T>(ax.L, F, false);
-  auto k = dst_kernel<T, Tin, Tout, false>;
-  set_smem(k, sm);
-  k<<<(n2 + F - 1) / F, F * (ax.L / 16), sm, s>>>(v, vscale, out, n1, n2, ax, F, group_stride<T>(ax.L, F, false),
-                                                  gate);
-}
-
-template <typename T, typename Tin, typename Tout>
-void launch_dst_cols(const Tin* in, Tout* out, int n1, int n2, const AxisTables<T>& ay, cudaStream_t s) {
-  const int F = pick_groups<T>(ay.L, n1, TK_DST_COLS);
-  const size_t sm = group_smem<T>(ay.L, F, true);
-  auto k = dst_kernel<T, Tin, Tout, true>;
-  set_smem(k, sm);
-  k<<<(n1 + F - 1) / F, F * (ay.L / 16), sm, s>>>(in, nullptr, out, n1, n2, ay, F, group_stride<T>(ay.L, F, true),
-                                                  nullptr);
-}
-
-template <typename T>
-void launch_precond_cols(const T* T1, T* T2a, T* T2b, int n1, int n2, const AxisTables<T>& ay, const T* lamx,
-                         double pen, const int* gate, cudaStream_t s) {
-  const int F = pick_groups<T>(ay.L, n1, TK_PRE_COLS);
-  const size_t sm = group_smem<T>(ay.L, F, true);
-  auto k = precond_cols_kernel<T>;
-  set_smem(k, sm);
-  k<<<(n1 + F - 1) / F, F * (ay.L / 16), sm, s>>>(T1, T2a, T2b, n1, n2, ay, lamx, T(pen), F,
-                                                  group_stride<T>(ay.L, F, true), gate);
-}
-
-template <typename T, typename Tz>
-void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, int n1, int n2,
-                         const AxisTables<T>& ax, const int* gate, cudaStream_t s) {
-  const int F = pick_groups<T>(ax.L, n2, TK_PRE_ROWS);
-  const size_t sm = group_smem<T>(ax.L, F, false);
-  auto k = precond_rows_kernel<T, Tz>;
-  set_smem(k, sm);
-  k<<<(n2 + F - 1) / F, F * (ax.L / 16), sm, s>>>(T2a, T2b, phi, z, n1, n2, ax, F, group_stride<T>(ax.L, F, false),
-                                                  gate);
-}
-
-// explicit instantiations used by the solver
 template int max_groups<double>(int, int);
 template int max_groups<float>(int, int);
 template int max_groups<df>(int, int);
-template void launch_toeplitz_rows<double, double>(const double*, void*, int, int, const AxisTables<double>&,
-                                                   const int*, cudaStream_t);
-template void launch_toeplitz_rows<double, float>(const float*, void*, int, int, const AxisTables<double>&,
-                                                  const int*, cudaStream_t);
-#define RSFDE_TOEP_COLS(T, Tin, Tout)                                                                  \
-  template void launch_toeplitz_cols<T, Tin, Tout>(int, const Tin*, void*, const uint8_t*, double, const double*, \
-                                                   Tout*, int, int, const AxisTables<T>&, const int*, double*,    \
-                                                   SolverState*, cudaStream_t);
-RSFDE_TOEP_COLS(double, double, double)
-RSFDE_TOEP_COLS(double, float, double)
-RSFDE_TOEP_COLS(double, double, df)
-RSFDE_TOEP_COLS(df, double, double)
-RSFDE_TOEP_COLS(df, float, double)
-RSFDE_TOEP_COLS(df, double, df)
-RSFDE_TOEP_COLS(df, float, df)
-RSFDE_TOEP_COLS(df, double, float)
-RSFDE_TOEP_COLS(double, double, float)
-RSFDE_TOEP_COLS(float, float, float)
-RSFDE_TOEP_COLS(float, double, float)
-RSFDE_TOEP_COLS(float, float, double)
-RSFDE_TOEP_COLS(float, double, double)
-#undef RSFDE_TOEP_COLS
-template void launch_toeplitz_rows<float, double>(const double*, void*, int, int, const AxisTables<float>&,
-                                                  const int*, cudaStream_t);
-template void launch_toeplitz_rows<float, float>(const float*, void*, int, int, const AxisTables<float>&,
-                                                 const int*, cudaStream_t);
-template void launch_toeplitz_rows<df, double>(const double*, void*, int, int, const AxisTables<df>&,
-                                               const int*, cudaStream_t);
-template void launch_toeplitz_rows<df, float>(const float*, void*, int, int, const AxisTables<df>&,
-                                              const int*, cudaStream_t);
-#define RSFDE_DST_ROWS(T, Tin, Tout)                                                                        \
-  template void launch_dst_rows<T, Tin, Tout>(const Tin*, const double*, Tout*, int, int, const AxisTables<T>&, \
-                                              const int*, cudaStream_t);
-RSFDE_DST_ROWS(double, double, double)
-RSFDE_DST_ROWS(float, double, float)
-RSFDE_DST_ROWS(double, double, float)
-RSFDE_DST_ROWS(double, df, double)
-RSFDE_DST_ROWS(float, df, float)
-RSFDE_DST_ROWS(float, float, float)
-RSFDE_DST_ROWS(double, float, double)
-#undef RSFDE_DST_ROWS
-template void launch_dst_cols<double, double, double>(const double*, double*, int, int, const AxisTables<double>&,
-                                                      cudaStream_t);
-template void launch_precond_cols<double>(const double*, double*, double*, int, int, const AxisTables<double>&,
-                                          const double*, double, const int*, cudaStream_t);
-template void launch_precond_cols<float>(const float*, float*, float*, int, int, const AxisTables<float>&,
-                                         const float*, double, const int*, cudaStream_t);
-template void launch_precond_rows<double, double>(const double*, const double*, const uint8_t*, double*, int, int,
-                                                  const AxisTables<double>&, const int*, cudaStream_t);
-template void launch_precond_rows<double, float>(const double*, const double*, const uint8_t*, float*, int, int,
-                                                 const AxisTables<double>&, const int*, cudaStream_t);
-template void launch_precond_rows<float, float>(const float*, const float*, const uint8_t*, float*, int, int,
-                                                const AxisTables<float>&, const int*, cudaStream_t);
-template void launch_precond_rows<float, double>(const float*, const float*, const uint8_t*, double*, int, int,
-                                                 const AxisTables<float>&, const int*, cudaStream_t);
 
 }  // namespace rsfde

@@ -9,7 +9,11 @@
 
 namespace rsfde {
 
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s of SM clock before a wait gives up
+// Default bound of every wait: ~2 s of SM clock before it gives up.  The
+// pipeline waits of a launch take their bound from the launch (it can be set
+// lower to exercise the give-up path); the drain waits that must see every
+// issued copy and MMA complete before the block frees its memory keep this one.
+constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -33,13 +37,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Non-blocking probe of the same phase (returns at once).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Waits for the completion of the phase of parity `parity`; false (and *err
-// set) if it does not complete within kWaitCycles SM clock cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
-  if (mbar_try_wait(bar, parity)) return true;
+// set) if it does not complete within `budget` SM clock cycles.  try_wait may
+// suspend the thread inside one probe for a while, so bounds shorter than a
+// copy's latency (below 1e5 cycles) poll with the non-blocking test instead,
+// which lets them expire as set.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err,
+                                          long long budget = kWaitCycles) {
+  const bool short_bound = budget < 100000;
+  if (short_bound ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
+  while (!(short_bound ? mbar_test_wait(bar, parity) : mbar_try_wait(bar, parity))) {
+    if (clock64() - t0 > budget) {
       atomicExch(err, 1);
       return false;
     }

@@ -42,14 +42,15 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("prec,matvec", [("fp64", "fp64"), ("fp32", "df32"), ("bf16", "fp32")])
-def test_adjoint_matches_oracle(prec, matvec):
+@pytest.mark.parametrize("prec,matvec,basis", [("fp64", "fp64", "fp64"), ("fp32", "df32", "df32"), ("bf16", "fp32", "fp32"),
+                                               ("bf16x3", "fp32", "fp64")])
+def test_adjoint_matches_oracle(prec, matvec, basis):
     w = workloads.random_problem(31, 20, 16)
     rng = np.random.default_rng(1)
     u0 = rng.random((16, 20)) * w["in_omega"]
     src = rng.standard_normal((16, 20))
     target = rng.random((16, 20))
-    orc, gpu = setup(w, restart=12, tol=1e-13, precond=prec, matvec=matvec)
+    orc, gpu = setup(w, restart=12, tol=1e-13, precond=prec, matvec=matvec, basis=basis)
     steps = 6
     loss_o, _, gu_o, gs_o, (gkx_o, gky_o) = orc.adjoint_march(u0, steps, target, src=src, restart=12)
     loss, gu, gs, gkx, gky = grads(gpu, u0, w["kx"], w["ky"], src, target, steps, every=2)

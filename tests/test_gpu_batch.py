@@ -17,13 +17,14 @@ if not torch.cuda.is_available():
 from paper_2102_11576_gb300 import Batch, Solver  # noqa: E402
 
 
-@pytest.mark.parametrize("precond,matvec,resid", [("fp32", "df32", "fp64"), ("bf16", "fp32", "df32")])
-def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, resid):
+@pytest.mark.parametrize("precond,matvec,basis,resid", [("fp32", "df32", "df32", "fp64"), ("bf16", "fp32", "fp32", "df32"),
+                                                        ("fp32", "fp32", "fp64", "fp64")])
+def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, basis, resid):
     probs = workloads.make_batch(seed=5, count=7, n_range=(9, 96), steps=10)
     steps = 3
     rng = np.random.default_rng(0)
     srcs = [rng.standard_normal(p["u0"].shape) if i % 2 else None for i, p in enumerate(probs)]
-    b = Batch(probs, precond=precond, matvec=matvec, resid=resid)
+    b = Batch(probs, precond=precond, matvec=matvec, resid=resid, basis=basis)
     for i, p in enumerate(probs):
         b.set(i, p["u0"], srcs[i])
     st = b.run(steps)
@@ -32,7 +33,7 @@ def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, resi
     for i, p in enumerate(probs):
         args = (p["n1"], p["n2"], p["box"], p["in_omega"], p["alpha1"], p["alpha2"], p["kx"], p["ky"],
                 p["dt"], p["eta"])
-        single = Solver(*args, precond=precond, matvec=matvec, resid=resid)
+        single = Solver(*args, precond=precond, matvec=matvec, resid=resid, basis=basis)
         src = None if srcs[i] is None else torch.as_tensor(srcs[i]).cuda()
         prev, prevprev = torch.as_tensor(p["u0"]).cuda(), None
         orc = oracle.Problem(*args)

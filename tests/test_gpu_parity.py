@@ -100,14 +100,19 @@ def test_apply_precond(n1, n2, prec, tol):
     assert rel(got, ref) <= tol
 
 
+# (operator arithmetic, Krylov basis and Gram-Schmidt, true residual's M x)
+FORMS = [("fp64", "fp64", "fp64"), ("df32", "fp64", "fp64"), ("fp32", "fp64", "fp64"), ("df32", "df32", "fp64"),
+         ("fp32", "fp32", "fp64"), ("fp32", "fp32", "df32"), ("df32", "df32", "df32")]
+
+
 @pytest.mark.parametrize("n1,n2", [(1, 1), (5, 7), (33, 20), (64, 64), (65, 127)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16x3", "bf16"])
 @pytest.mark.parametrize("arnoldi", ["cgs", "cgs2"])
-@pytest.mark.parametrize("matvec,resid", [("fp64", "fp64"), ("df32", "fp64"), ("fp32", "fp64"), ("fp32", "df32"),
-                                          ("df32", "df32")])
-def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec, resid):
+@pytest.mark.parametrize("matvec,basis,resid", FORMS)
+def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec, basis, resid):
     w = workloads.random_problem(5, n1, n2)
-    orc, gpu = pair(w, precond=prec, arnoldi=arnoldi, tol=1e-11, restart=10, matvec=matvec, resid=resid)
+    orc, gpu = pair(w, precond=prec, arnoldi=arnoldi, tol=1e-11, restart=10, matvec=matvec, resid=resid,
+                    basis=basis)
     rng = np.random.default_rng(0)
     b = rng.standard_normal((n2, n1))
     x_ref, st_ref = orc.fgmres(b, restart=10, tol=1e-12)
@@ -121,17 +126,20 @@ def test_solve_matches_oracle(n1, n2, prec, arnoldi, matvec, resid):
     assert rel(x, x_ref) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,matvec,resid", [("fp64", "fp64", "fp64"), ("fp32", "df32", "fp64"),
-                                               ("fp32", "fp32", "fp64"), ("bf16", "fp32", "df32")])
-def test_graph_loop_equals_direct_launches(prec, matvec, resid):
+@pytest.mark.parametrize("prec,matvec,basis,resid", [("fp64", "fp64", "fp64", "fp64"), ("fp32", "df32", "df32", "fp64"),
+                                                     ("fp32", "fp32", "fp32", "fp64"), ("bf16", "fp32", "fp32", "df32"),
+                                                     ("bf16x3", "fp32", "fp64", "fp64"),
+                                                     ("bf16", "df32", "fp64", "fp64")])
+def test_graph_loop_equals_direct_launches(prec, matvec, basis, resid):
     """The device-side graph loop and the host-driven loop run the same
     kernels in the same order with deterministic reductions: identical bits."""
-    w = workloads.random_problem(8, 70, 45)
+    w = workloads.random_problem(8, 70, 46)
     rng = np.random.default_rng(3)
-    b = dev(rng.standard_normal((45, 70)))
+    b = dev(rng.standard_normal((46, 70)))
     res = []
     for use_graph in (True, False):
-        _, gpu = pair(w, precond=prec, matvec=matvec, restart=6, tol=1e-12, use_graph=use_graph, resid=resid)
+        _, gpu = pair(w, precond=prec, matvec=matvec, restart=6, tol=1e-12, use_graph=use_graph, resid=resid,
+                      basis=basis)
         for _ in range(2):  # the second solve replays the captured graph
             x, st = gpu.solve(b)
         res.append((host(x), st))
@@ -148,12 +156,16 @@ def test_unpreconditioned_and_dense_lu():
     assert st["converged"] and rel(host(x), x_lu) <= 1e-9
 
 
-@pytest.mark.parametrize("prec,matvec,resid", [("fp64", "fp64", "fp64"), ("fp32", "df32", "fp64"),
-                                               ("bf16x3", "df32", "fp64"), ("fp32", "fp32", "fp64"),
-                                               ("bf16x3", "fp32", "fp64"), ("bf16", "fp32", "df32")])
-def test_march_disk64_matches_oracle(prec, matvec, resid):
+@pytest.mark.parametrize("prec,matvec,basis,resid", [("fp64", "fp64", "fp64", "fp64"), ("fp32", "df32", "df32", "fp64"),
+                                                     ("bf16x3", "df32", "df32", "fp64"),
+                                                     ("fp32", "fp32", "fp32", "fp64"),
+                                                     ("bf16x3", "fp32", "fp32", "fp64"),
+                                                     ("bf16", "fp32", "fp32", "df32"),
+                                                     ("bf16x3", "fp32", "fp64", "fp64"),
+                                                     ("fp32", "fp32", "fp64", "fp64")])
+def test_march_disk64_matches_oracle(prec, matvec, basis, resid):
     w = workloads.make("disk64")
-    orc, gpu = pair(w, tol=1e-12, restart=w["restart"], precond=prec, matvec=matvec, resid=resid)
+    orc, gpu = pair(w, tol=1e-12, restart=w["restart"], precond=prec, matvec=matvec, resid=resid, basis=basis)
     steps = 16
     u_ref, st_ref = orc.march(w["u0"], steps, restart=w["restart"], tol=1e-12)
     u, st = gpu.march(dev(w["u0"]), steps)
@@ -226,34 +238,81 @@ def test_edge_cases():
         assert np.linalg.norm(b - orc2.apply_M(x)) <= 1.01e-12 * np.linalg.norm(b)
 
 
-def test_full_size_polygon2048_sampled():
-    """The benchmark's 2048^2 workload, one step each preconditioner precision:
-    M z on sampled points and the true residual of the step by the oracle."""
+@pytest.mark.parametrize("n1,n2", [(2048, 40), (40, 2048), (2049, 24), (24, 2049)])
+def test_full_length_transforms_elementwise(n1, n2):
+    """The transforms at the full workload's lengths, element by element
+    against the oracle: n = 2048 (GEMM K of 2048 through the TMA ring, the
+    symmetric form, the FFT length 4096) and n = 2049 (odd: the natural GEMM
+    layout, the FFT length 8192), along x and along y."""
+    w = workloads.random_problem(9, n1, n2)
+    orc = oracle.Problem(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
+                         w["dt"], w["eta"])
+    v = w["field"]
+    ref = orc.apply_precond(v)
+    for prec, tol in (("fp64", 1e-11), ("fp32", 2e-5), ("bf16x3", 2e-4), ("bf16", 2e-2)):
+        gpu = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
+                     w["dt"], w["eta"], precond=prec, matvec="fp32" if prec != "fp64" else "fp64")
+        assert rel(host(gpu.apply_precond(dev(v))), ref) <= tol, prec
+        if prec == "fp64":
+            assert rel(host(gpu.dst2(dev(v))), orc.dst2(v)) <= 1e-12
+        else:
+            z = rng_field(n2, n1)
+            scale = np.abs(z).max() * (1 + 2 * np.abs(orc.toeplitz()[0]).sum() + 2 * np.abs(orc.toeplitz()[1]).sum()
+                                       + orc.pen)
+            assert np.abs(host(gpu.apply_M(dev(z))) - orc.apply_M(z)).max() <= 2e-6 * scale
+        gpu.close()
+
+
+def rng_field(n2, n1, seed=12):
+    return np.random.default_rng(seed).standard_normal((n2, n1))
+
+
+@pytest.mark.slow
+def test_full_size_polygon2048_against_oracle():
+    """The benchmark's 2048^2 workload at its launch configuration.
+    (a) P-hat^-1 v in every precision against one full oracle P-hat^-1 v,
+    element by element; (b) one step of the headline form (split-BF16
+    preconditioner, FP32 operator arithmetic, FP64 basis, Gram-Schmidt,
+    Givens and true residual) and of the FP64 form: the oracle's full-grid
+    M x gives the true relative residual (<= 1e-10), and Lemma 3.1 with
+    Lemma 2.3 (||M^-1||_inf <= 1) bounds the two solutions' difference by
+    their residuals.  The oracle runs in two spawned processes while the GPU
+    works."""
+    import multiprocessing as mp
+    import _oracle_jobs
     w = workloads.make("polygon2048")
-    orc = oracle.Problem(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"],
-                         w["kx"], w["ky"], w["dt"], w["eta"])
-    rng = np.random.default_rng(0)
-    idx = rng.choice(w["n1"] * w["n2"], size=256, replace=False)
-    u0 = w["u0"]
-    for prec, matvec, resid in (("bf16", "fp32", "df32"), ("fp32", "fp32", "fp64"), ("fp32", "df32", "fp64"),
-                                ("bf16x3", "fp32", "df32"), ("fp32", "fp64", "fp64"), ("fp64", "fp64", "fp64")):
-        gpu = Solver(w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"],
-                     w["ky"], w["dt"], w["eta"], restart=w["restart"], precond=prec, matvec=matvec, resid=resid)
-        z = rng.standard_normal((w["n2"], w["n1"]))
-        mz = host(gpu.apply_M(dev(z))).reshape(-1)[idx]
-        ref = orc.apply_M_points(z, idx)
-        scale = np.abs(z).max() * (1 + 2 * np.abs(orc.toeplitz()[0]).sum()
-                                   + 2 * np.abs(orc.toeplitz()[1]).sum())
-        if matvec == "fp32":  # FP32 rounds the penalty term (dt/eta) phi z too
-            scale += np.abs(z).max() * orc.pen
-        assert np.abs(mz - ref).max() <= {"df32": 2e-12, "fp32": 2e-6, "fp64": 1e-13}[matvec] * scale
-        u1, st = gpu.step(dev(u0))
-        u1 = host(u1)
-        assert st["converged"] and st["rel_res"] <= 1e-10
-        b = orc.rhs(u0)
-        r_pts = b.reshape(-1)[idx] - orc.apply_M_points(u1, idx)
-        # pointwise residual at sampled points is consistent with the global bound
-        assert np.abs(r_pts).max() <= 1e-10 * np.linalg.norm(b)
+    args = (w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"], w["dt"],
+            w["eta"])
+    v = rng_field(w["n2"], w["n1"], seed=13)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(3) as pool:
+        job_p = pool.apply_async(_oracle_jobs.apply_precond, (args, v))
+        job_b = pool.apply_async(_oracle_jobs.rhs, (args, w["u0"]))
+        got = {}
+        for prec in ("fp64", "fp32", "bf16x3", "bf16"):
+            gpu = Solver(*args, restart=w["restart"], precond=prec)
+            got[prec] = host(gpu.apply_precond(dev(v)))
+            gpu.close()
+        steps = {}
+        for name, kw in (("headline", dict(precond="bf16x3", matvec="fp32", basis="fp64", resid="fp64")),
+                         ("fp64", dict(precond="fp64", matvec="fp64", basis="fp64", resid="fp64"))):
+            gpu = Solver(*args, restart=w["restart"], tol=w["tol"], **kw)
+            u1, st = gpu.step(dev(w["u0"]))
+            assert st["converged"] and st["rel_res"] <= 1e-10, (name, st)
+            steps[name] = host(u1)
+            gpu.close()
+        jobs_m = {k: pool.apply_async(_oracle_jobs.apply_M, (args, x)) for k, x in steps.items()}
+        ref = job_p.get()
+        b = job_b.get()
+        mx = {k: j.get() for k, j in jobs_m.items()}
+    for prec, tol in (("fp64", 1e-11), ("fp32", 2e-5), ("bf16x3", 2e-4), ("bf16", 2e-2)):
+        assert rel(got[prec], ref) <= tol, (prec, rel(got[prec], ref))
+    r = {k: b - mx[k] for k in steps}
+    for k in steps:
+        assert np.linalg.norm(r[k]) <= 1.01e-10 * np.linalg.norm(b), k
+    diff = np.abs(steps["headline"] - steps["fp64"]).max()
+    assert diff <= np.abs(r["headline"]).max() + np.abs(r["fp64"]).max() + 1e-15
+    assert diff / np.abs(steps["fp64"]).max() <= 1e-9
 
 
 def test_ellipse512_march_with_source():

@@ -49,6 +49,14 @@ def test_host_only_calls(libpath):
                            ctypes.c_double(1.5), ctypes.c_double(1.0), ctypes.c_double(1.0),
                            ctypes.c_double(0.1), ctypes.c_double(1e-3), None) == -1
     assert lib.rsfde_kernel_launches(None) == 0
+    # grid sides beyond 4096 (convolution length 16384) are rejected before any CUDA call
+    from paper_2102_11576_gb300 import _Grid
+    byte = ctypes.c_uint8(1)
+    for n1, n2 in ((4097, 8), (8, 4097), (0, 8)):
+        g = _Grid(n1, n2, -1.0, 1.0, -1.0, 1.0)
+        assert lib.rsfde_setup(ctypes.byref(out), ctypes.byref(g), ctypes.byref(byte), ctypes.c_double(1.5),
+                               ctypes.c_double(1.5), ctypes.c_double(1.0), ctypes.c_double(1.0),
+                               ctypes.c_double(0.1), ctypes.c_double(1e-3), None) == -1
 
 
 def test_workload_geometry():

@@ -291,6 +291,32 @@ def test_step_and_march_against_dense_lu():
         prevprev, prev = prev, out
 
 
+def test_rhs_nonlinear_source_converges_to_a_manufactured_solution():
+    """or_rhs's source f(u) = u - u^3 + s, zero outside Omega (Section 2),
+    against an exact solution of the continuous problem: with Example 1's
+    solution u_e = exp(-t) (x^2/a^2 + y^2/b^2 - 1)^2 and its Riesz terms
+    (oracle/example1.py), the PDE u_t = k R u + f(u) holds for
+    s = (u_e)_t - k R u_e - (u_e - u_e^3) = -exp(-t) bracket - 2 u_e + u_e^3.
+    The march built on or_rhs then converges to u_e at first order in h
+    (Lemma 3.3, dt proportional to h): a dropped or sign-flipped cubic term,
+    or a missing u term, leaves an O(1) error that does not halve."""
+    errs = []
+    for n in (16, 32, 64):
+        ex = Example1(n, 1.0)
+        prev, prevprev = ex.w.copy(), None
+        for kk in range(1, ex.m + 1):
+            t = (kk - 1) * ex.dt
+            ue = ex.exact(t)
+            s = -math.exp(-t) * ex.bracket - 2.0 * ue + ue ** 3
+            out, st = ex.prob.step(prev, prevprev, s, restart=20, tol=1e-12)
+            assert st["converged"]
+            prevprev, prev = prev, out
+        errs.append(ex.error(prev))
+    assert errs[2] < 1e-2
+    for coarse, fine in zip(errs, errs[1:]):
+        assert 1.6 < coarse / fine < 2.5, errs
+
+
 def test_left_and_right_gmres_agree():
     rng = np.random.default_rng(14)
     prob = tiny_problem(rng, 10, 7)
