@@ -312,14 +312,17 @@ const char* rsfde_kernel_class_name(int k);
  * this times every feasible F of each kernel family (reps calls each, CUDA
  * events on the context's stream, on its own buffers) and records the
  * fastest in a process-wide table that every later launch with the same
- * length and precision uses (captured graphs are rebuilt).  chosen: HOST
+ * length and precision uses (captured graphs are rebuilt).  With a
+ * tensor-core preconditioner it also times each of its four GEMMs with 64-
+ * and 128-wide tiles and records the faster width in the context.  chosen: HOST
  * array of RSFDE_TUNE_COUNT int32 (the chosen F per family, 0 = not tuned)
  * or NULL.  With a double-FP32 true residual and an operator in another
  * precision, the 8-byte shapes are timed on the residual's own two passes.
  * Overwrites the context's Krylov workspace, its internal right-hand side and
  * iterate, and its solver state (every solve and step re-initialises them). */
-#define RSFDE_TUNE_COUNT 6 /* Toeplitz rows, Toeplitz columns, sine rows, sine columns,
-                              preconditioner columns, preconditioner rows */
+#define RSFDE_TUNE_COUNT 10 /* F of: Toeplitz rows, Toeplitz columns, sine rows, sine columns,
+                               preconditioner columns, preconditioner rows; then the tile width
+                               (64 or 128) of each of the tensor-core preconditioner's four GEMMs */
 int rsfde_autotune(rsfde_ctx* ctx, int32_t reps, int32_t* chosen);
 int rsfde_batch_autotune(rsfde_batch* b, int32_t reps);
 

@@ -347,12 +347,14 @@ class Solver:
         """Bound of each tensor-core pipeline wait in SM clock cycles (0: the default, ~2 s)."""
         _check(self._lib.rsfde_set_wait_cycles(self._h, int(cycles)), "set_wait_cycles")
 
-    TUNE_NAMES = ("toeplitz_rows", "toeplitz_cols", "dst_rows", "dst_cols", "precond_cols", "precond_rows")
+    TUNE_NAMES = ("toeplitz_rows", "toeplitz_cols", "dst_rows", "dst_cols", "precond_cols", "precond_rows",
+                  "gemm1_bn", "gemm2_bn", "gemm3_bn", "gemm4_bn")
 
     def autotune(self, reps=5):
         """Measures every feasible tile shape of this context's transform
-        kernels and records the fastest (rsfde_autotune); returns them."""
-        out = np.zeros(6, dtype=np.int32)
+        kernels (and the tensor-core GEMMs' tile widths) and records the
+        fastest (rsfde_autotune); returns them."""
+        out = np.zeros(10, dtype=np.int32)
         _check(self._lib.rsfde_autotune(self._h, int(reps), ctypes.c_void_p(out.ctypes.data)), "autotune")
         return {n: int(f) for n, f in zip(self.TUNE_NAMES, out) if f}
 

@@ -901,10 +901,17 @@ int autotune_ctx(rsfde_ctx* c, int reps, int32_t* chosen_out) {
   }
   if (c->opts.precond_prec == RSFDE_FP32) tune_precond<float>(c, reps, c->x32.tab, c->y32.tab, chosen);
   else if (c->opts.precond_prec == RSFDE_FP64) tune_precond<double>(c, reps, c->x64.tab, c->y64.tab, chosen);
+  int bn[4] = {0, 0, 0, 0};
+  int rc = RSFDE_OK;
+  if (bf16_precond_on(c) && (rc = ensure_bf16(c)) == RSFDE_OK)
+    rc = bf16_plan_autotune(c->bf16, c->V, static_cast<float*>(c->Z), c->phi, c->pen, c->stream, reps, bn);
+  if (rc != RSFDE_OK) return rc;
   c->graph_key = -1;  // captured launches carry the old shapes
-  if (chosen_out)
+  if (chosen_out) {
     for (int k = 0; k < TK_COUNT; ++k) chosen_out[k] = chosen[k];
-  int rc = check_launch(c);
+    for (int k = 0; k < 4; ++k) chosen_out[TK_COUNT + k] = bn[k];
+  }
+  rc = check_launch(c);
   if (rc == RSFDE_OK) rc = cuda_fail(cudaStreamSynchronize(c->stream));
   return rc;
 }

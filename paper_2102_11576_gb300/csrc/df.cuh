@@ -62,6 +62,40 @@ __device__ __forceinline__ df df_fma(df acc, df a, df b) {
   return df_fast_two_sum(s, __fadd_rn(err, __fadd_rn(acc.lo, e)));
 }
 
+// Conversions between FP64 and FP32 on the integer pipe.  GB300's FP64 pipe
+// runs a double <-> float conversion at a small fraction of its FMA rate (a
+// conversion per element cost an FP64-bound Gram-Schmidt update as much as
+// ten FMAs), so the hot paths move the fields of the IEEE encodings instead.
+// f32_trunc: the float whose significand is the double's leading 24 bits
+// (rounded toward zero; |error| < 2^-23 |x|); values below the float range
+// become signed zero, above it infinity.
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7FF) - 896;  // float biased exponent
+  const unsigned int sign = hi & 0x80000000u;
+  const unsigned int man = (unsigned int)(b >> 29) & 0x7FFFFFu;
+  unsigned int f = sign;
+  if (e == 1151 && (b & 0xFFFFFFFFFFFFFull)) f |= 0x7FC00000u;  // NaN stays NaN
+  else if (e >= 255) f |= 0x7F800000u;
+  else if (e > 0) f |= ((unsigned int)e << 23) | man;
+  return __uint_as_float(f);
+}
+// f64_exact: the double equal to a float (every float is a double); normal
+// numbers, zeros, infinities and NaNs by their fields, subnormal floats (below
+// 2^-126) through the conversion instruction.
+__device__ __forceinline__ double f64_exact(float x) {
+  const unsigned int f = __float_as_uint(x);
+  const unsigned int e = (f >> 23) & 0xFF;
+  const unsigned int man = f & 0x7FFFFFu;
+  if (e == 0 && man != 0) return (double)x;
+  const unsigned long long sign = (unsigned long long)(f & 0x80000000u) << 32;
+  unsigned long long ed = 0;
+  if (e == 255) ed = 0x7FFull;
+  else if (e != 0) ed = e + 896;
+  return __longlong_as_double((long long)(sign | (ed << 52) | ((unsigned long long)man << 29)));
+}
+
 // Conversions between the storage and arithmetic types (float, double, df);
 // float -> df is exact and needs no FP64 instruction.
 template <typename To, typename From>
@@ -82,7 +116,11 @@ __device__ __forceinline__ df cvt<df, df>(df x) {
 }
 template <>
 __device__ __forceinline__ double cvt<double, df>(df x) {
-  return double(x);
+  return f64_exact(x.hi) + f64_exact(x.lo);
+}
+template <>
+__device__ __forceinline__ double cvt<double, float>(float x) {
+  return f64_exact(x);
 }
 template <>
 __device__ __forceinline__ float cvt<float, df>(df x) {

@@ -150,6 +150,7 @@ struct Bf16Plan {
   int* err = nullptr;
   void* mem = nullptr;
   long long wait_cycles = kWaitCycles;  // bound of each pipeline wait of the GEMM launches
+  int bn[4] = {0, 0, 0, 0};             // tile width of each GEMM of the chain (0: the default rule)
 };
 
 // S_n as a split BF16 pair: [S_n]_{ij} = sqrt(2/(n+1)) sin(pi i j/(n+1)), FP64 on the host.
@@ -289,30 +290,43 @@ static void launch_gemm_t(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int 
   const CUtensorMap& bl = BN == 64 ? B.map64_lo : B.map_lo;
   launch_pdl(k, grid, dim3(kGemmThreads), smem, s, A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
 }
-template <int EPI, int NT, bool SYM>
-static void launch_gemm_bn(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
-                           const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
-  // 64-wide tiles while 128-wide ones would leave SMs idle (measured: with
-  // at least one 128-wide tile per SM the wider tiles are faster)
+// Tile width of a GEMM: the plan's recorded choice (autotuner) or the default
+// rule.  Plain BF16 (two operand tiles per K slice) takes 64-wide tiles
+// while 128-wide ones would leave SMs idle (measured: with at least one
+// 128-wide tile per SM the wider tiles are faster).  Split BF16 feeds four
+// operand tiles per K slice for three products: a 64-wide tile brings 48 KB
+// per slice for 3.1 MFLOP and is bound by the SM's operand inflow, a 128-wide
+// one 64 KB for 6.3 MFLOP, so it takes 128 while that keeps 5/8 of the SMs busy.
+static int gemm_bn(int nt, int forced, int M, int N, int channels) {
+  if (forced == 64 || forced == 128) return forced;
   const long tiles128 = (long)((N + 127) / 128) * ((M + kGemmBM - 1) / kGemmBM) * channels;
-  if (tiles128 < kNumSMs) launch_gemm_t<EPI, NT, SYM, 64>(A, B, M, N, K, channels, ep, err, gate, s);
-  else launch_gemm_t<EPI, NT, SYM, 128>(A, B, M, N, K, channels, ep, err, gate, s);
+  if (nt == 3) return tiles128 * 8 >= 5L * kNumSMs ? 128 : 64;
+  return tiles128 < kNumSMs ? 64 : 128;
+}
+template <int EPI, int NT, bool SYM>
+static void launch_gemm_bn(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels, int forced,
+                           const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
+  if (gemm_bn(NT, forced, M, N, channels) == 64)
+    launch_gemm_t<EPI, NT, SYM, 64>(A, B, M, N, K, channels, ep, err, gate, s);
+  else
+    launch_gemm_t<EPI, NT, SYM, 128>(A, B, M, N, K, channels, ep, err, gate, s);
 }
 // D = A S for a transform of length n along K; the symmetric form (hk > 0)
 // computes the n/2 output pairs from the K operand's two halves.
 template <int EPI>
-static void launch_gemm(const Bf16Plan* p, int hk, const Bf16Mat& A, const Bf16Mat& B, int M, int n, int channels,
-                        GemmEpiParams ep, const int* gate, cudaStream_t s) {
+static void launch_gemm(const Bf16Plan* p, int stage, int hk, const Bf16Mat& A, const Bf16Mat& B, int M, int n,
+                        int channels, GemmEpiParams ep, const int* gate, cudaStream_t s) {
   ep.M = M;
   ep.N = hk ? n / 2 : n;
   ep.n_full = hk ? n : 0;
   const int K = hk ? 2 * hk : n;
+  const int f = p->bn[stage];
   if (p->nt == 3) {
-    if (hk) launch_gemm_bn<EPI, 3, true>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
-    else launch_gemm_bn<EPI, 3, false>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+    if (hk) launch_gemm_bn<EPI, 3, true>(A, B, M, ep.N, K, channels, f, ep, p->err, gate, s);
+    else launch_gemm_bn<EPI, 3, false>(A, B, M, ep.N, K, channels, f, ep, p->err, gate, s);
   } else {
-    if (hk) launch_gemm_bn<EPI, 1, true>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
-    else launch_gemm_bn<EPI, 1, false>(A, B, M, ep.N, K, channels, ep, p->err, gate, s);
+    if (hk) launch_gemm_bn<EPI, 1, true>(A, B, M, ep.N, K, channels, f, ep, p->err, gate, s);
+    else launch_gemm_bn<EPI, 1, false>(A, B, M, ep.N, K, channels, f, ep, p->err, gate, s);
   }
 }
 
@@ -324,7 +338,7 @@ bool bf16_plan_a0(const Bf16Plan* p, int vec, Bf16Out* out) {
 
 template <typename Tz, typename Tin>
 int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
-                 const int* gate, cudaStream_t s, bool skip_split, const double* zscale) {
+                 const int* gate, cudaStream_t s, bool skip_split, const double* zscale, cudaEvent_t* ev) {
   const int n1 = p->n1, n2 = p->n2;
   if (skip_split) {
     // A0 already holds the unscaled vector (update_kernel); scale at the end
@@ -334,6 +348,7 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   else
     launch_pdl(split_kernel<Tin, 1>, split_grid(n1, n2), dim3(kBlock), 0, s, v, vscale, p->A0.hi, p->A0.lo, n1, n2,
                p->ld1, p->h1, gate);
+  if (ev) cudaEventRecord(ev[0], s);
   GemmEpiParams ep{};
   // 1. T1t = (A0 S_x)^T, columns y in the layout of GEMM 2's K
   ep.wait_cycles = p->wait_cycles;
@@ -342,7 +357,8 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.ldo = p->ld2;
   ep.row_b = 1 << 30;
   ep.hk = p->h2;
-  launch_gemm<EPI_SPLIT_T>(p, p->h1, p->A0, p->Sx, n2, n1, 1, ep, gate, s);
+  launch_gemm<EPI_SPLIT_T>(p, 0, p->h1, p->A0, p->Sx, n2, n1, 1, ep, gate, s);
+  if (ev) cudaEventRecord(ev[1], s);
   // 2. W^T = T1t S_y; both tau divides (Eq. 4.6), stacked [W1; W2]
   ep = GemmEpiParams{};
   ep.wait_cycles = p->wait_cycles;
@@ -354,7 +370,8 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.pen = (float)pen;
   ep.chb_rows = n2;
   ep.hk = p->h1;
-  launch_gemm<EPI_DIVIDE_T>(p, p->h2, p->T1t, p->Sy, n1, n2, 1, ep, gate, s);
+  launch_gemm<EPI_DIVIDE_T>(p, 1, p->h2, p->T1t, p->Sy, n1, n2, 1, ep, gate, s);
+  if (ev) cudaEventRecord(ev[2], s);
   // 3. Yt = ([W1; W2] S_x)^T, the channels side by side (column offset ld2)
   ep = GemmEpiParams{};
   ep.wait_cycles = p->wait_cycles;
@@ -364,7 +381,8 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.row_b = n2;
   ep.col_b = p->ld2;
   ep.hk = p->h2;
-  launch_gemm<EPI_SPLIT_T>(p, p->h1, p->Wst, p->Sx, 2 * n2, n1, 1, ep, gate, s);
+  launch_gemm<EPI_SPLIT_T>(p, 2, p->h1, p->Wst, p->Sx, 2 * n2, n1, 1, ep, gate, s);
+  if (ev) cudaEventRecord(ev[3], s);
   // 4. z = (1-Phi) S_y W1 S_x + Phi S_y W2 S_x (channel = blockIdx.z)
   ep = GemmEpiParams{};
   ep.wait_cycles = p->wait_cycles;
@@ -375,21 +393,69 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
   ep.ldz = n1;
   ep.zscale = skip_split ? zscale : nullptr;
   ep.a_koff = p->ld2;
-  launch_gemm<EPI_COMBINE_T>(p, p->h2, p->Yt, p->Sy, n1, n2, 2, ep, gate, s);
+  launch_gemm<EPI_COMBINE_T>(p, 3, p->h2, p->Yt, p->Sy, n1, n2, 2, ep, gate, s);
+  if (ev) cudaEventRecord(ev[4], s);
   return cudaGetLastError() == cudaSuccess ? RSFDE_OK : RSFDE_ECUDA;
 }
 
+// Times the chain with every GEMM 64 wide, then 128 wide (reps applications
+// each, CUDA events between the GEMMs on stream s, the operand v and output z
+// the caller's scratch) and records the faster width per GEMM.  bn_out:
+// the four widths chosen.
+int bf16_plan_autotune(Bf16Plan* p, const double* v, float* z, const uint8_t* phi, double pen, cudaStream_t s,
+                       int reps, int* bn_out) {
+  if (!p || reps < 1) return RSFDE_EINVAL;
+  cudaEvent_t ev[5];
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return RSFDE_ECUDA;
+  float best[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+  int pick[4] = {0, 0, 0, 0};
+  for (int w : {64, 128}) {
+    for (int k = 0; k < 4; ++k) p->bn[k] = w;
+    bf16_precond<float, double>(p, v, nullptr, z, phi, pen, nullptr, s, false, nullptr, nullptr);  // warm-up
+    float ms[4] = {0, 0, 0, 0};
+    for (int r = 0; r < reps; ++r) {
+      bf16_precond<float, double>(p, v, nullptr, z, phi, pen, nullptr, s, false, nullptr, ev);
+      if (cudaEventSynchronize(ev[4]) != cudaSuccess) break;
+      for (int k = 0; k < 4; ++k) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+        ms[k] += t;
+      }
+    }
+    for (int k = 0; k < 4; ++k)
+      if (ms[k] < best[k]) {
+        best[k] = ms[k];
+        pick[k] = w;
+      }
+  }
+  for (int k = 0; k < 4; ++k) {
+    p->bn[k] = pick[k];
+    if (bn_out) bn_out[k] = pick[k];
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return RSFDE_ECUDA;
+  return bf16_plan_error(p, s);
+}
+
 template int bf16_precond<float, double>(Bf16Plan*, const double*, const double*, float*, const uint8_t*, double,
-                                         const int*, cudaStream_t, bool, const double*);
+                                         const int*, cudaStream_t, bool, const double*,
+                                         cudaEvent_t*);
 template int bf16_precond<double, double>(Bf16Plan*, const double*, const double*, double*, const uint8_t*,
-                                          double, const int*, cudaStream_t, bool, const double*);
+                                          double, const int*, cudaStream_t, bool, const double*,
+                                         cudaEvent_t*);
 template int bf16_precond<float, df>(Bf16Plan*, const df*, const double*, float*, const uint8_t*, double,
-                                     const int*, cudaStream_t, bool, const double*);
+                                     const int*, cudaStream_t, bool, const double*,
+                                         cudaEvent_t*);
 template int bf16_precond<double, df>(Bf16Plan*, const df*, const double*, double*, const uint8_t*, double,
-                                      const int*, cudaStream_t, bool, const double*);
+                                      const int*, cudaStream_t, bool, const double*,
+                                         cudaEvent_t*);
 template int bf16_precond<float, float>(Bf16Plan*, const float*, const double*, float*, const uint8_t*, double,
-                                        const int*, cudaStream_t, bool, const double*);
+                                        const int*, cudaStream_t, bool, const double*,
+                                         cudaEvent_t*);
 template int bf16_precond<double, float>(Bf16Plan*, const float*, const double*, double*, const uint8_t*, double,
-                                         const int*, cudaStream_t, bool, const double*);
+                                         const int*, cudaStream_t, bool, const double*,
+                                         cudaEvent_t*);
 
 }  // namespace rsfde

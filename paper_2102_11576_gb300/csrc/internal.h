@@ -158,9 +158,14 @@ int bf16_plan_error(Bf16Plan* p, cudaStream_t s);  // reads and clears the give-
 void bf16_plan_set_wait(Bf16Plan* p, long long cycles);  // <= 0: the default bound
 // skip_split: the first operand was already written (update_kernel's Bf16Out,
 // unscaled), and zscale multiplies the result instead.
+// ev: if set, five events recorded before the first GEMM and after each (timing).
 template <typename Tz, typename Tin>
 int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const uint8_t* phi, double pen,
-                 const int* gate, cudaStream_t s, bool skip_split = false, const double* zscale = nullptr);
+                 const int* gate, cudaStream_t s, bool skip_split = false, const double* zscale = nullptr,
+                 cudaEvent_t* ev = nullptr);
+// Measured tile width (64 or 128) per GEMM of the chain, recorded in the plan.
+int bf16_plan_autotune(Bf16Plan* p, const double* v, float* z, const uint8_t* phi, double pen, cudaStream_t s,
+                       int reps, int* bn_out);
 // The Bf16Out target of the plan's first operand, if the plan can take it
 // (symmetric layout, n1 a multiple of vec); returns false otherwise.
 bool bf16_plan_a0(const Bf16Plan* p, int vec, Bf16Out* out);

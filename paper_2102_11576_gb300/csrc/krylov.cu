@@ -222,13 +222,55 @@ __device__ __forceinline__ double warp_sum_partials(const double* p, int G) {
   return VecOps<double>::warp_sum((a[0] + a[1]) + (a[2] + a[3]));
 }
 
+// Partial sums acc[k] += <w, V_{i0+k}> over this thread's packs for exactly
+// C vectors (k < C).  C is a compile-time count, so no multiply-add is spent
+// on an empty slot (the FP64 forms are bound by the FP64 pipe).  A thread
+// takes UNR packs per round, so about eight loads are in flight; the packs are
+// visited in grid-stride order.
+template <typename Tv, int VEC, int C, int UNR>
+__device__ __forceinline__ void dot_rounds(const Tv* __restrict__ V, const Tv* __restrict__ w, size_t N, int i0,
+                                           Tv* acc) {
+  using Op = VecOps<Tv>;
+  const size_t NP = N / VEC;  // VEC divides N (launcher)
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q0 < NP; q0 += UNR * stride) {
+    Tv wv[UNR][VEC];
+    Tv a[UNR][C][VEC];  // all loads issued before the arithmetic
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const size_t q = q0 + u * stride;
+      const bool in = q < NP;
+      if (in) {
+        ld_vec<Tv, VEC>(w + q * VEC, wv[u]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) wv[u][e] = Op::zero();
+      }
+#pragma unroll
+      for (int k = 0; k < C; ++k) {
+        if (in) {
+          ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + q * VEC, a[u][k]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) a[u][k][e] = Op::zero();
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+#pragma unroll
+      for (int k = 0; k < C; ++k)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc[k] = Op::fma(acc[k], wv[u][e], a[u][k][e]);
+  }
+}
+
 // h_i = <w, v_i> = s_i <V_{j+1}, V_i> for i = 0..j  (w is stored in slot j+1).
 // blockIdx.y selects a chunk of at most CH basis vectors (the j+1 vectors
 // spread evenly over gridDim.y chunks); w is re-read per chunk (it stays in
-// L2).  A thread takes kDotChunk / CH packs per round, so about eight loads
-// are in flight whatever j is; the packs are still visited in grid-stride
-// order.  accumulate = 1 adds to H (second CGS pass).  The last block
-// finishes the j+1 sums, one warp per sum.
+// L2).  The chunk's exact count selects the unrolled body (dot_rounds).
+// accumulate = 1 adds to H (second CGS pass).  The last block finishes the
+// j+1 sums, one warp per sum.
 template <typename Tv, int VEC, int CH>
 __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__ V, size_t N, int j, int accumulate,
                                                           double* partials, SolverState* st) {
@@ -243,39 +285,22 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
   Tv acc[CH];
 #pragma unroll
   for (int k = 0; k < CH; ++k) acc[k] = Op::zero();
-  const size_t NP = N / VEC;  // VEC divides N (launcher)
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q0 < NP; q0 += UNR * stride) {
-    Tv wv[UNR][VEC];
-    Tv a[UNR][CH][VEC];  // all loads issued before the arithmetic
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-      const size_t q = q0 + u * stride;
-      const bool in = q < NP;
-      if (in) {
-        ld_vec<Tv, VEC>(w + q * VEC, wv[u]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) wv[u][e] = Op::zero();
-      }
-#pragma unroll
-      for (int k = 0; k < CH; ++k) {
-        if (in && k < cnt) {
-          ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + q * VEC, a[u][k]);
-        } else {
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) a[u][k][e] = Op::zero();
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u)
-#pragma unroll
-      for (int k = 0; k < CH; ++k)
-        if (k < cnt) {
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) acc[k] = Op::fma(acc[k], wv[u][e], a[u][k][e]);
-        }
+  switch (cnt) {  // uniform over the block
+#define RSFDE_DOT_CASE(C) \
+  case C:                \
+    if constexpr (C <= CH) dot_rounds<Tv, VEC, C, UNR>(V, w, N, i0, acc); \
+    break;
+    RSFDE_DOT_CASE(1)
+    RSFDE_DOT_CASE(2)
+    RSFDE_DOT_CASE(3)
+    RSFDE_DOT_CASE(4)
+    RSFDE_DOT_CASE(5)
+    RSFDE_DOT_CASE(6)
+    RSFDE_DOT_CASE(7)
+    RSFDE_DOT_CASE(8)
+#undef RSFDE_DOT_CASE
+    default:
+      break;
   }
   const int G = gridDim.x;
   const double bs = block_sums<Tv, CH>(acc, cnt, wsum);
@@ -373,7 +398,7 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size
         if (bo.a0 && final_pass) {  // x = p mod n1 is even (n1 is): x to column x/2, x+1 to hk + x/2
           const int y = (int)(p / (size_t)bo.n1), x = (int)(p - (size_t)y * bo.n1);
           const size_t o = (size_t)y * bo.ld + (x >> 1);
-          const float f0 = (float)val[u][0], f1 = (float)val[u][1];
+          const float f0 = f32_trunc(val[u][0]), f1 = f32_trunc(val[u][1]);
           const __nv_bfloat16 h0 = __float2bfloat16_rn(f0), h1 = __float2bfloat16_rn(f1);
           bo.a0[o] = h0;
           bo.a0[o + bo.hk] = h1;
@@ -427,7 +452,7 @@ struct XAcc<float> {
   static __device__ __forceinline__ df zero() { return df(0.0f, 0.0f); }
   static __device__ __forceinline__ df coef(double y) { return df(y); }
   static __device__ __forceinline__ df fma(df acc, df y, float z) { return df_fma(acc, y, df(z, 0.0f)); }
-  static __device__ __forceinline__ double value(df acc) { return double(acc); }
+  static __device__ __forceinline__ double value(df acc) { return cvt<double>(acc); }
 };
 
 template <typename Tz, int VEC>
