@@ -550,13 +550,14 @@ def run_batched_config(args, peaks, steps=None, count=None):
     from paper_2102_11576_gb300 import Batch, workloads
     probs = workloads.make_batch(seed=0, count=count or args.batch_count)
     t0 = time.perf_counter()
-    b = Batch(probs, precond=args.batch_precond, matvec="fp32", basis="fp64", resid="fp64")
+    b = Batch(probs, precond=args.batch_precond, matvec="fp32", basis="fp64", resid="fp64",
+              use_graph=not args.no_graph)
     for i, p in enumerate(probs):
         b.set(i, p["u0"])
     if not args.no_autotune:
         b.autotune(reps=2)
     setup_s = time.perf_counter() - t0
-    b.run(3)
+    b.run(max(args.warmup, 1))
     torch.cuda.synchronize()
     steps = steps or args.batch_steps
     l0 = b.kernel_launches

@@ -367,7 +367,7 @@ class Batch:
     ky, dt, eta; solver options as for Solver apply to all instances."""
 
     def __init__(self, problems, restart=20, max_iter=10000, tol=1e-10, precond="fp32", matvec="df32",
-                 arnoldi="cgs", stream=None, resid="fp64", basis=None):
+                 arnoldi="cgs", stream=None, resid="fp64", basis=None, use_graph=True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("rsfde needs a CUDA GPU; there is no CPU path")
@@ -394,6 +394,7 @@ class Batch:
         o.stream = ctypes.c_void_p(self.stream.cuda_stream)
         o.resid_prec = _RESIDS[resid]
         o.basis_prec = _BASES[basis if basis is not None else matvec]
+        o.use_graph = int(bool(use_graph))
         h = ctypes.c_void_p()
         pp = lambda a: ctypes.c_void_p(a.ctypes.data)
         _check(lib.rsfde_batch_create(ctypes.byref(h), self.count, grids, masks,

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
+#include <functional>
 #include <vector>
 
 #include "fft.cuh"  // host butterflies for the setup spectra
@@ -986,12 +987,27 @@ struct rsfde_batch {
   int64_t launches_pro[2] = {0, 0}, launches_epi = 0;
   int steps_done = 0;
   int64_t launches = 0;
+  // Multi-instance form: every phase of every instance in one launch.
+  bool multi = false;
+  BatchInst* inst = nullptr;  // device array of count descriptors
+  int* prefixes = nullptr;    // device: every MultiGrid's block offsets
+  int* runs = nullptr;        // device: loop-body runs of the current step's graph
+  MultiGrid g_trows, g_tcols, g_drows, g_pcols, g_prows, g_rhs, g_xupd, g_fin, g_rrows, g_rcols;
+  std::vector<MultiGrid> g_dot, g_upd;  // per Arnoldi column j (one active array shared by all j)
+  int* actives = nullptr;               // device: the active prefixes
+  int64_t launches_per_body = 0;
+  cudaStream_t cap = nullptr;
 };
 
 namespace {
 
 void free_batch(rsfde_batch* b) {
   if (!b) return;
+  if (b->inst) cudaFree(b->inst);
+  if (b->prefixes) cudaFree(b->prefixes);
+  if (b->actives) cudaFree(b->actives);
+  if (b->runs) cudaFree(b->runs);
+  if (b->cap) cudaStreamDestroy(b->cap);
   for (auto& x : b->exec)
     if (x) cudaGraphExecDestroy(x);
   for (double* r : b->ring)
@@ -1000,10 +1016,298 @@ void free_batch(rsfde_batch* b) {
   delete b;
 }
 
+// ---- multi-instance form ------------------------------------------------------
+// The batch advances in lock step: every kernel of the FGMRES cycle is one
+// launch over all instances (each on its own virtual grid, gated by its own
+// solver flags), and the cycles repeat while any instance still runs.  It
+// covers the FFT preconditioner in FP32 with the FP32 operator, an FP64 or
+// FP32 basis and the FP64 true residual; other options use the graph of
+// per-instance branches (build_batch_graph).
+enum { MV_FP32_B64, MV_FP32_B32, MV_NONE };
+int multi_form(const rsfde_opts& o) {
+  if (o.variant != RSFDE_FGMRES_RIGHT || !o.use_precond || o.precond_prec != RSFDE_FP32) return MV_NONE;
+  if (o.resid_prec != RSFDE_FP64 || o.matvec_prec != RSFDE_FP32) return MV_NONE;
+  return o.basis_prec == RSFDE_FP64 ? MV_FP32_B64 : MV_FP32_B32;
+}
+
+// One FGMRES cycle of every instance: operator arithmetic Tm, basis Tv,
+// true-residual arithmetic (FP64 or double-FP32).
+template <typename Tm, typename Tv>
+void enqueue_multi_residual(rsfde_batch* b, cudaStream_t s) {
+  launch_residual_multi<double, Tv>(b->inst, b->g_rrows, b->g_rcols, s);
+}
+// Active prefixes of the families a phase uses: the Arnoldi iteration at
+// column j (gate run_iter), or the cycle end (gate run_cycle).
+void enqueue_compact_iter(rsfde_batch* b, int j, cudaStream_t s) {
+  CompactArgs a{};
+  const MultiGrid* fam[] = {&b->g_drows, &b->g_pcols, &b->g_prows, &b->g_trows, &b->g_tcols, &b->g_dot[j],
+                            &b->g_upd[j]};
+  a.nfam = 7;
+  for (int f = 0; f < a.nfam; ++f) {
+    a.prefix[f] = fam[f]->prefix;
+    a.active[f] = fam[f]->active;
+  }
+  launch_compact_multi(b->inst, b->count, 0, a, s);
+}
+void enqueue_compact_cycle(rsfde_batch* b, cudaStream_t s) {
+  CompactArgs a{};
+  const MultiGrid* fam[] = {&b->g_xupd, &b->g_rrows, &b->g_rcols};
+  a.nfam = 3;
+  for (int f = 0; f < a.nfam; ++f) {
+    a.prefix[f] = fam[f]->prefix;
+    a.active[f] = fam[f]->active;
+  }
+  launch_compact_multi(b->inst, b->count, 1, a, s);
+}
+
+template <typename Tm, typename Tv>
+void enqueue_multi_cycle(rsfde_batch* b, cudaStream_t s) {
+  const rsfde_opts& o = b->ctx[0]->opts;
+  const bool cgs2 = o.arnoldi == RSFDE_CGS2;
+  for (int j = 0; j < o.restart; ++j) {
+    enqueue_compact_iter(b, j, s);
+    launch_precond_multi<float, float, Tv>(b->inst, b->g_drows, b->g_pcols, b->g_prows, j, s);
+    launch_operator_multi<Tm, float, Tv>(b->inst, b->g_trows, b->g_tcols, j, s);
+    for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
+      launch_multidot_multi<Tv>(b->inst, b->g_dot[j], j, pass, s);
+      launch_update_multi<Tv>(b->inst, b->g_upd[j], j, (!cgs2 || pass == 1) ? 1 : 0, s);
+    }
+  }
+  launch_solve_y_multi(b->inst, b->count, s);
+  enqueue_compact_cycle(b, s);
+  launch_xupdate_multi<float>(b->inst, b->g_xupd, s);
+  enqueue_multi_residual<Tm, Tv>(b, s);
+}
+void enqueue_multi_cycle_any(rsfde_batch* b, cudaStream_t s) {
+  if (multi_form(b->ctx[0]->opts) == MV_FP32_B64) enqueue_multi_cycle<float, double>(b, s);
+  else enqueue_multi_cycle<float, float>(b, s);
+}
+void enqueue_multi_residual_any(rsfde_batch* b, cudaStream_t s) {
+  if (multi_form(b->ctx[0]->opts) == MV_FP32_B64) enqueue_multi_residual<float, double>(b, s);
+  else enqueue_multi_residual<float, float>(b, s);
+}
+
+// Device descriptors and the prefixes of every multi-instance grid.
+int setup_multi(rsfde_batch* b) {
+  const rsfde_opts& o = b->ctx[0]->opts;
+  if (multi_form(o) == MV_NONE) return RSFDE_OK;
+  if (b->count > kMaxBatchMulti) return RSFDE_OK;  // the active prefix is held in shared memory
+  for (rsfde_ctx* c : b->ctx)
+    if (c->x64.tab.L > 4096 || c->y64.tab.L > 4096) return RSFDE_OK;  // one 256-thread group per transform at most
+  const int n = b->count, m = o.restart;
+  std::vector<BatchInst> hi(n);
+  for (int i = 0; i < n; ++i) {
+    rsfde_ctx* c = b->ctx[i];
+    BatchInst& I = hi[i];
+    I.n1 = c->n1;
+    I.n2 = c->n2;
+    I.N = c->N;
+    I.pen = c->pen;
+    I.dt = c->dt;
+    I.phi = c->phi;
+    I.V = c->V;
+    I.Z = c->Z;
+    I.tmpx = c->tmpx;
+    I.T1 = c->T1;
+    I.T2a = c->T2a;
+    I.T2b = c->T2b;
+    I.b = c->b;
+    I.x = c->x;
+    I.partials = c->partials;
+    I.st = c->st;
+    I.u_prev = b->ring[i];
+    I.u_pp = b->ring[i] + c->N;
+    I.src = b->has_src[i] ? b->ring[i] + 2 * c->N : nullptr;
+    I.x64 = c->x64.tab;
+    I.y64 = c->y64.tab;
+    I.x32 = c->x32.tab;
+    I.y32 = c->y32.tab;
+    I.xdf = c->xdf.tab;
+    I.ydf = c->ydf.tab;
+  }
+  // block counts of every family, instance by instance
+  const bool b64 = o.basis_prec == RSFDE_FP64;
+  auto ceil_div = [](long a, long q) { return (int)((a + q - 1) / q); };
+  std::vector<std::vector<int>> counts;
+  std::vector<MultiGrid*> grids;
+  auto family = [&](MultiGrid* g, std::function<int(rsfde_ctx*)> blocks, std::function<int(rsfde_ctx*)> log2L) {
+    std::vector<int> v(n);
+    g->l2mask = 0;
+    for (int i = 0; i < n; ++i) {
+      v[i] = blocks(b->ctx[i]);
+      if (log2L) g->l2mask |= 1u << log2L(b->ctx[i]);
+    }
+    counts.push_back(v);
+    grids.push_back(g);
+  };
+  auto lx = [](rsfde_ctx* c) { return c->x64.tab.log2L; };
+  auto ly = [](rsfde_ctx* c) { return c->y64.tab.log2L; };
+  family(&b->g_trows, [&](rsfde_ctx* c) { return ceil_div((c->n2 + 1) / 2, multi_groups(c->x64.tab.L)); }, lx);
+  family(&b->g_tcols, [&](rsfde_ctx* c) { return ceil_div((c->n1 + 1) / 2, multi_groups(c->y64.tab.L)); }, ly);
+  family(&b->g_drows, [&](rsfde_ctx* c) { return ceil_div(c->n2, multi_groups(c->x64.tab.L)); }, lx);
+  family(&b->g_pcols, [&](rsfde_ctx* c) { return ceil_div(c->n1, multi_groups(c->y64.tab.L)); }, ly);
+  family(&b->g_prows, [&](rsfde_ctx* c) { return ceil_div(c->n2, multi_groups(c->x64.tab.L)); }, lx);
+  family(&b->g_rrows, [&](rsfde_ctx* c) { return ceil_div((c->n2 + 1) / 2, multi_groups(c->x64.tab.L)); }, lx);
+  family(&b->g_rcols, [&](rsfde_ctx* c) { return ceil_div((c->n1 + 1) / 2, multi_groups(c->y64.tab.L)); }, ly);
+  family(&b->g_rhs, [&](rsfde_ctx* c) { return vec_grid(c->N); }, nullptr);
+  family(&b->g_xupd, [&](rsfde_ctx* c) { return xupdate_blocks(c->N, 4); }, nullptr);
+  family(&b->g_fin, [&](rsfde_ctx* c) { return vec_grid(c->N); }, nullptr);
+  b->g_dot.assign(m, MultiGrid{});
+  b->g_upd.assign(m, MultiGrid{});
+  for (int j = 0; j < m; ++j) {
+    family(&b->g_dot[j], [&](rsfde_ctx* c) {
+      return b64 ? multidot_blocks<double>(c->N, j) : multidot_blocks<float>(c->N, j);
+    }, nullptr);
+    family(&b->g_upd[j], [&](rsfde_ctx* c) {
+      return b64 ? update_blocks<double>(c->N, j) : update_blocks<float>(c->N, j);
+    }, nullptr);
+  }
+  std::vector<int> all;
+  std::vector<size_t> off;
+  for (auto& v : counts) {
+    off.push_back(all.size());
+    int acc = 0;
+    all.push_back(0);
+    for (int c : v) all.push_back(acc += c);
+  }
+  cudaError_t e = cudaMalloc((void**)&b->inst, sizeof(BatchInst) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->prefixes, sizeof(int) * all.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->runs, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->runs, 0, sizeof(int));  // loop runs over the batch's life
+  if (e == cudaSuccess) e = cudaMemcpy(b->inst, hi.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->prefixes, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice);
+  // active prefixes: the iteration families (drows, pcols, prows, trows, tcols,
+  // dot, upd) and the cycle-end ones (xupd, rrows, rcols); the right side and
+  // the epilogue run every instance (active = the full prefix)
+  const int nact = 10;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->actives, sizeof(int) * (size_t)nact * (n + 1));
+  if (e != cudaSuccess) return cuda_fail(e);
+  for (size_t k = 0; k < grids.size(); ++k) {
+    grids[k]->prefix = b->prefixes + off[k];
+    grids[k]->active = const_cast<int*>(grids[k]->prefix);
+    grids[k]->count = n;
+    grids[k]->total = all[off[k] + n];
+  }
+  MultiGrid* own[] = {&b->g_drows, &b->g_pcols, &b->g_prows, &b->g_trows, &b->g_tcols, &b->g_xupd, &b->g_rrows,
+                      &b->g_rcols};
+  for (int k = 0; k < 8; ++k) own[k]->active = b->actives + (size_t)k * (n + 1);
+  for (int j = 0; j < m; ++j) {
+    b->g_dot[j].active = b->actives + (size_t)8 * (n + 1);
+    b->g_upd[j].active = b->actives + (size_t)9 * (n + 1);
+  }
+  b->multi = true;
+  return RSFDE_OK;
+}
+
+// The source pointer of instance i's descriptor follows has_src.
+int update_multi_src(rsfde_batch* b, int i) {
+  if (!b->multi) return RSFDE_OK;
+  const double* src = b->has_src[i] ? b->ring[i] + 2 * b->ctx[i]->N : nullptr;
+  return cuda_fail(cudaMemcpyAsync(reinterpret_cast<char*>(b->inst + i) + offsetof(BatchInst, src), &src,
+                                   sizeof(src), cudaMemcpyHostToDevice, b->stream));
+}
+
+// Captures fn (work enqueued on stream cap) into a child-graph node of g.
+template <typename Fn>
+cudaError_t capture_child(cudaStream_t cap, cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, Fn fn,
+                          cudaGraphNode_t* out) {
+  cudaGraph_t child;
+  cudaError_t e = cudaGraphCreate(&child, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamBeginCaptureToGraph(cap, child, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    fn(cap);
+    e = cudaStreamEndCapture(cap, &child);
+  }
+  if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(out, g, deps, ndeps, child);
+  cudaGraphDestroy(child);
+  return e;
+}
+
+// One time step of every instance as one graph: [reset, right sides, initial
+// residuals] -> WHILE(any instance runs: one FGMRES cycle of all) -> [finish,
+// rotate the march rings].
+int build_batch_graph_multi(rsfde_batch* b, int later) {
+  cudaError_t e;
+  if (!b->cap && (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e);
+  const rsfde_opts& o = b->ctx[0]->opts;
+  cudaGraph_t g;
+  if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return cuda_fail(e);
+  cudaGraphNode_t pro, loop, epi;
+  e = capture_child(b->cap, g, nullptr, 0, [&](cudaStream_t s) {
+    launch_init_multi(b->inst, b->count, o.restart, o.max_iter, o.tol, s);
+    launch_rhs_multi(b->inst, b->g_rhs, later, s);
+    enqueue_compact_cycle(b, s);
+    enqueue_multi_residual_any(b, s);
+  }, &pro);
+  cudaGraphConditionalHandle h;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    e = cudaGraphAddNode(&loop, g, &pro, nullptr, 1, &np);
+    if (e == cudaSuccess) {
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        enqueue_multi_cycle_any(b, b->cap);
+        launch_loop_cond_multi(h, b->inst, b->count, b->runs, b->cap);
+        e = cudaStreamEndCapture(b->cap, &body);
+      }
+    }
+  }
+  if (e == cudaSuccess)
+    e = capture_child(b->cap, g, &loop, 1, [&](cudaStream_t s) { launch_finish_rotate_multi(b->inst, b->g_fin, s); },
+                      &epi);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[later], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e);
+  }
+  // launches: 5 in the prologue (reset, right sides, compaction, residual
+  // row and column pass), per loop run 8 per Arnoldi column (compaction,
+  // three preconditioner passes, two operator passes, multi-dot and update;
+  // two more with CGS2) plus the back substitution, compaction, solution
+  // update, residual (2) and loop condition, and 1 in the epilogue
+  b->launches_pro[later] = 5;
+  b->launches_epi = 1;
+  b->launches_per_body = (int64_t)o.restart * (o.arnoldi == RSFDE_CGS2 ? 10 : 8) + 6;
+  return RSFDE_OK;
+}
+
+// The same time step with direct launches and one host check per cycle
+// (use_graph = 0: the kernels are ordinary launches, which profilers see).
+int run_batch_step_direct(rsfde_batch* b, int later) {
+  const rsfde_opts& o = b->ctx[0]->opts;
+  cudaStream_t s = b->stream;
+  launch_init_multi(b->inst, b->count, o.restart, o.max_iter, o.tol, s);
+  launch_rhs_multi(b->inst, b->g_rhs, later, s);
+  enqueue_compact_cycle(b, s);
+  enqueue_multi_residual_any(b, s);
+  int* flag = b->runs;  // reused as the host-read flag in this mode
+  int any = 0;
+  for (long guard = 0;; ++guard) {
+    launch_any_running_multi(b->inst, b->count, flag, s);
+    cudaError_t e = cudaMemcpyAsync(&any, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (!any || guard > (long)o.max_iter + 1) break;
+    enqueue_multi_cycle_any(b, s);
+    b->launches += b->launches_per_body;  // the body, its loop check counted as the condition kernel
+  }
+  launch_finish_rotate_multi(b->inst, b->g_fin, s);
+  return cuda_fail(cudaGetLastError());
+}
+
 // Builds the graph of one time step of every instance: per instance the
 // chain [right side, initial residual] -> WHILE(FGMRES cycle) -> [finalise,
 // u^{k-2} <- u^{k-1}, u^{k-1} <- u^k]; the instances' chains are independent.
 int build_batch_graph(rsfde_batch* b, int later) {
+  if (b->multi) return build_batch_graph_multi(b, later);
   cudaGraph_t g;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -1424,8 +1728,14 @@ int rsfde_batch_create(rsfde_batch** out, int32_t count, const rsfde_grid* grids
     b->ring.push_back(r);
     b->has_src.push_back(0);
   }
+  int rc = cuda_fail(cudaStreamSynchronize(b->stream));
+  if (rc == RSFDE_OK) rc = setup_multi(b);
+  if (rc != RSFDE_OK) {
+    free_batch(b);
+    return rc;
+  }
   *out = b;
-  return cuda_fail(cudaStreamSynchronize(b->stream));
+  return RSFDE_OK;
 }
 
 int rsfde_batch_set(rsfde_batch* b, int32_t i, const double* u0, const double* src) {
@@ -1434,13 +1744,16 @@ int rsfde_batch_set(rsfde_batch* b, int32_t i, const double* u0, const double* s
   const size_t bytes = c->N * sizeof(double);
   cudaMemcpyAsync(b->ring[i], u0, bytes, cudaMemcpyDeviceToDevice, b->stream);
   if (src) cudaMemcpyAsync(b->ring[i] + 2 * c->N, src, bytes, cudaMemcpyDeviceToDevice, b->stream);
-  if ((src != nullptr) != (b->has_src[i] != 0)) {  // the graphs read the source or not
+  if ((src != nullptr) != (b->has_src[i] != 0)) {  // the graphs (or the descriptor) read the source or not
     b->has_src[i] = src != nullptr;
-    for (auto& x : b->exec)
-      if (x) {
-        cudaGraphExecDestroy(x);
-        x = nullptr;
-      }
+    int rc = update_multi_src(b, i);
+    if (rc != RSFDE_OK) return rc;
+    if (!b->multi)
+      for (auto& x : b->exec)
+        if (x) {
+          cudaGraphExecDestroy(x);
+          x = nullptr;
+        }
   }
   b->steps_done = 0;
   return cuda_fail(cudaStreamSynchronize(b->stream));
@@ -1448,8 +1761,22 @@ int rsfde_batch_set(rsfde_batch* b, int32_t i, const double* u0, const double* s
 
 int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats) {
   if (!b || steps < 0) return RSFDE_EINVAL;
+  const bool direct = b->multi && !b->ctx[0]->opts.use_graph;
   for (int k = 0; k < steps; ++k) {
     const int later = b->steps_done > 0;
+    if (direct) {
+      if (b->launches_per_body == 0) {
+        const rsfde_opts& o = b->ctx[0]->opts;
+        b->launches_pro[0] = b->launches_pro[1] = 5;
+        b->launches_epi = 1;
+        b->launches_per_body = (int64_t)o.restart * (o.arnoldi == RSFDE_CGS2 ? 10 : 8) + 6;
+      }
+      int rc = run_batch_step_direct(b, later);
+      if (rc) return rc;
+      b->steps_done += 1;
+      b->launches += b->launches_pro[later] + b->launches_epi;
+      continue;
+    }
     if (!b->exec[later]) {
       int rc = build_batch_graph(b, later);
       if (rc) return rc;
@@ -1457,7 +1784,7 @@ int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats) {
     cudaError_t e = cudaGraphLaunch(b->exec[later], b->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     b->steps_done += 1;
-    b->launches += (int64_t)b->count * (b->launches_pro[later] + b->launches_epi);
+    b->launches += (int64_t)(b->multi ? 1 : b->count) * (b->launches_pro[later] + b->launches_epi);
   }
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -1503,6 +1830,12 @@ int rsfde_batch_get(rsfde_batch* b, int32_t i, double* u_out) {
 
 int64_t rsfde_batch_kernel_launches(rsfde_batch* b) {
   if (!b) return 0;
+  if (b->multi && !b->ctx[0]->opts.use_graph) return b->launches;  // counted as launched
+  if (b->multi) {  // per step the prologue and epilogue, plus every run of the loop body
+    int runs = 0;
+    if (cudaMemcpy(&runs, b->runs, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return b->launches;
+    return b->launches + (int64_t)runs * b->launches_per_body;
+  }
   // prologue and epilogue launches per instance-step, plus every replayed cycle
   int64_t n = b->launches;
   for (rsfde_ctx* c : b->ctx) {

@@ -113,6 +113,58 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter, unsigned int 
   return is_last != 0;
 }
 
+// Sum of the `count` values p[0..count) by one warp in an order fixed by count
+// alone (lane 0 returns it): each lane takes every 32nd value, sixteen loads
+// in flight before they are added into four fixed accumulators, then a fixed
+// butterfly over the lanes.
+__device__ __forceinline__ double warp_sum_fixed(const double* p, int count) {
+  const int l = threadIdx.x & 31;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q0 = l; q0 < count; q0 += 16 * 32) {
+    double t[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const int q = q0 + 32 * k;
+      t[k] = q < count ? __ldcg(p + q) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k & 3] += t[k];
+  }
+  double v = (a[0] + a[1]) + (a[2] + a[3]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The same sum for a block of any size: a block narrower than a warp (tiny
+// grids) runs the warp's lanes and butterfly one after another in thread 0,
+// in the identical order, so the value never depends on the block size.
+// Valid in thread 0; every thread of the block must call it.
+__device__ __forceinline__ double block_sum_fixed(const double* p, int count) {
+  double v = 0.0;
+  if (blockDim.x >= 32) {
+    if (threadIdx.x < 32) v = warp_sum_fixed(p, count);
+    return v;
+  }
+  if (threadIdx.x != 0) return 0.0;
+  double s[32];
+  for (int l = 0; l < 32; ++l) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q0 = l; q0 < count; q0 += 16 * 32)
+      for (int k = 0; k < 16; ++k) {
+        const int q = q0 + 32 * k;
+        a[k & 3] += q < count ? __ldcg(p + q) : 0.0;
+      }
+    s[l] = (a[0] + a[1]) + (a[2] + a[3]);
+  }
+  for (int o = 16; o; o >>= 1) {
+    double t[32];
+    for (int l = 0; l < 32; ++l) t[l] = s[l] + s[l ^ o];
+    for (int l = 0; l < 32; ++l) s[l] = t[l];
+  }
+  return s[0];
+}
+
 // Deterministic sum of `count` partials (fixed order for a fixed count).
 __device__ __forceinline__ double sum_partials(const double* p, int count, double* sh) {
   double v = 0.0;

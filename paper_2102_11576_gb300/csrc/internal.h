@@ -170,6 +170,121 @@ int bf16_plan_autotune(Bf16Plan* p, const double* v, float* z, const uint8_t* ph
 // (symmetric layout, n1 a multiple of vec); returns false otherwise.
 bool bf16_plan_a0(const Bf16Plan* p, int vec, Bf16Out* out);
 
+// ---- batched instances: one launch per phase over every instance -------------
+// One instance of a batch as the multi-instance kernels see it (an array of
+// these lives in device memory).  Every buffer is the instance's own
+// context's; u_prev, u_pp and src are its time-march ring.
+struct BatchInst {
+  int n1, n2;
+  size_t N;
+  double pen, dt;
+  const uint8_t* phi;
+  double* V;   // Krylov basis, in the basis type
+  void* Z;     // preconditioned vectors
+  void* tmpx;  // operator scratch
+  void* T1;
+  void* T2a;
+  void* T2b;
+  double* b;
+  double* x;
+  double* partials;
+  SolverState* st;
+  double* u_prev;
+  double* u_pp;
+  const double* src;
+  AxisTables<double> x64, y64;
+  AxisTables<float> x32, y32;
+  AxisTables<df> xdf, ydf;
+};
+
+// The blocks of one multi-instance launch: instance i owns the blocks
+// [prefix[i], prefix[i+1]) -- exactly the grid a launch for that instance
+// alone would have, so every reduction is split the same way and the results
+// are bit-identical to single-instance solves.  l2mask (transform kernels):
+// bit k is set when an instance's transform length along the kernel's axis
+// is 2^k (it sizes the shared memory).
+//
+// A launch does not run every virtual block: a compaction kernel first writes
+// `active`, the same prefix with the counts of instances whose gate is
+// closed set to zero, and a fixed grid of `grid` blocks loops over the
+// active virtual blocks only (so finished instances cost nothing).
+struct MultiGrid {
+  const int* prefix = nullptr;  // device, count + 1 entries
+  int* active = nullptr;        // device, count + 1 entries (compaction output)
+  int count = 0, total = 0;
+  unsigned l2mask = 0;
+};
+// Threads of a multi-instance transform block: F = kMultiThreads / (L/16)
+// transforms per block, for every L up to 4096.
+constexpr int kMultiThreads = 256;
+__host__ __device__ constexpr int multi_groups(int L) { return kMultiThreads / (L / 16); }
+// Largest batch of the multi-instance form: a block holds the active prefix
+// (kMaxBatchMulti + 1 ints) in shared memory.
+constexpr int kMaxBatchMulti = 1024;
+
+// The last i in [0, count) with p[i] <= b (the instance owning virtual block b;
+// empty ranges are skipped because the next instance starts at the same value).
+__device__ __forceinline__ int multi_instance(const int* p, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Compaction: for up to kMaxCompact families, active[f][i] = sum over k < i of
+// the virtual-grid size of instance k if its gate (run_iter, or run_cycle with
+// use_cycle) is open, else 0; active[f][count] the total.
+constexpr int kMaxCompact = 8;
+struct CompactArgs {
+  const int* prefix[kMaxCompact];
+  int* active[kMaxCompact];
+  int nfam;
+};
+void launch_compact_multi(const BatchInst* bi, int count, int use_cycle, const CompactArgs& a, cudaStream_t s);
+void launch_any_running_multi(const BatchInst* bi, int count, int* out, cudaStream_t s);
+// Blocks of a multi-instance launch: every SM filled with resident blocks, at
+// most the total virtual blocks.
+template <typename K>
+int multi_launch_grid(K kernel, int threads, size_t smem, int total) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int g = kNumSMs * per_sm;
+  return total < g ? (total > 0 ? total : 1) : g;
+}
+
+// multi-instance launchers (transforms.cuh, instantiated per arithmetic type)
+template <typename T, typename Tz, typename Tv>
+void launch_operator_multi(const BatchInst* bi, const MultiGrid& rows, const MultiGrid& cols, int j, cudaStream_t s);
+template <typename T, typename Tv>
+void launch_residual_multi(const BatchInst* bi, const MultiGrid& rows, const MultiGrid& cols, cudaStream_t s);
+template <typename T, typename Tz, typename Tv>
+void launch_precond_multi(const BatchInst* bi, const MultiGrid& drows, const MultiGrid& pcols, const MultiGrid& prows,
+                          int j, cudaStream_t s);
+// multi-instance launchers (krylov.cu)
+void launch_init_multi(const BatchInst* bi, int count, int m, int max_iter, double tol, cudaStream_t s);
+void launch_rhs_multi(const BatchInst* bi, const MultiGrid& g, int later, cudaStream_t s);
+template <typename Tv>
+void launch_multidot_multi(const BatchInst* bi, const MultiGrid& g, int j, int accumulate, cudaStream_t s);
+template <typename Tv>
+void launch_update_multi(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, cudaStream_t s);
+void launch_solve_y_multi(const BatchInst* bi, int count, cudaStream_t s);
+template <typename Tz>
+void launch_xupdate_multi(const BatchInst* bi, const MultiGrid& g, cudaStream_t s);
+void launch_finish_rotate_multi(const BatchInst* bi, const MultiGrid& g, cudaStream_t s);
+void launch_loop_cond_multi(cudaGraphConditionalHandle h, const BatchInst* bi, int count, int* runs,
+                            cudaStream_t s);
+// The grid a single-instance launch uses (and a multi-instance launch gives
+// each instance): Gram-Schmidt at column j, the vector kernels.
+template <typename Tv>
+int multidot_blocks(size_t N, int j);  // grid.x * grid.y
+template <typename Tv>
+int update_blocks(size_t N, int j);
+int xupdate_blocks(size_t N, int zbytes);
+
 // ---- launchers (krylov.cu) -------------------------------------------------
 int vec_grid(size_t N);
 void launch_init_state(SolverState* st, int m, int max_iter, double tol, cudaStream_t s);

@@ -26,7 +26,7 @@ int vec_grid(size_t N) {
 
 static __device__ __forceinline__ bool closed(const int* gate) { return *(volatile const int*)gate == 0; }
 
-__global__ void init_state_kernel(SolverState* st, int m, int max_iter, double tol) {
+__device__ __forceinline__ void init_state_body(SolverState* st, int m, int max_iter, double tol) {
   st->run_iter = 0;
   st->run_cycle = 1;
   st->status = 0;
@@ -45,6 +45,9 @@ __global__ void init_state_kernel(SolverState* st, int m, int max_iter, double t
   st->beta = 0.0;
   st->rel_res = 0.0;
 }
+__global__ void init_state_kernel(SolverState* st, int m, int max_iter, double tol) {
+  init_state_body(st, m, max_iter, tol);
+}
 
 __global__ void mask_to_phi_kernel(const uint8_t* __restrict__ in_omega, uint8_t* __restrict__ phi, size_t N) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x)
@@ -53,13 +56,13 @@ __global__ void mask_to_phi_kernel(const uint8_t* __restrict__ in_omega, uint8_t
 
 // Eq. 2.17 right side with f(u) = u - u^3 + s, zero outside Omega (Section 2),
 // and the initial guess of Section 5; ||b||_2 goes to st->bnorm.
-__global__ void __launch_bounds__(kBlock) rhs_kernel(const double* __restrict__ u, const double* __restrict__ uu,
-                                                     const double* __restrict__ src, const uint8_t* __restrict__ phi,
-                                                     double dt, double* __restrict__ b, double* __restrict__ x0,
-                                                     size_t N, double* partials, SolverState* st) {
+__device__ __forceinline__ void rhs_body(const double* __restrict__ u, const double* __restrict__ uu,
+                                         const double* __restrict__ src, const uint8_t* __restrict__ phi, double dt,
+                                         double* __restrict__ b, double* __restrict__ x0, size_t N, double* partials,
+                                         SolverState* st, int bid, int nblk) {
   __shared__ double red[32];
   double acc = 0.0;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+  for (size_t p = bid * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)nblk * blockDim.x) {
     const double up = u[p];
     const double f = up - up * up * up + (src ? src[p] : 0.0);
     const double bp = up + (phi[p] ? 0.0 : dt * f);
@@ -68,11 +71,17 @@ __global__ void __launch_bounds__(kBlock) rhs_kernel(const double* __restrict__ 
     acc += bp * bp;
   }
   const double bs = block_sum(acc, red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
-  if (arrive_last(&st->counter, gridDim.x)) {
-    const double tot = sum_partials(partials, gridDim.x, red);
+  if (threadIdx.x == 0) partials[bid] = bs;
+  if (arrive_last(&st->counter, nblk)) {
+    const double tot = sum_partials(partials, nblk, red);
     if (threadIdx.x == 0) st->bnorm = sqrt(tot);
   }
+}
+__global__ void __launch_bounds__(kBlock) rhs_kernel(const double* __restrict__ u, const double* __restrict__ uu,
+                                                     const double* __restrict__ src, const uint8_t* __restrict__ phi,
+                                                     double dt, double* __restrict__ b, double* __restrict__ x0,
+                                                     size_t N, double* partials, SolverState* st) {
+  rhs_body(u, uu, src, phi, dt, b, x0, N, partials, st, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kBlock) norm_b_kernel(const double* __restrict__ b, size_t N, double* partials,
@@ -203,25 +212,6 @@ __device__ __forceinline__ double block_sums(const Tv* acc, int cnt, double (*sh
   return v;
 }
 
-// Sum of the G partials p[0..G) by one warp, fixed order (lane 0 returns it).
-// Sixteen loads per lane are issued before they are added, in four fixed
-// accumulators (the tail of every reduction waits on these L2 round trips).
-__device__ __forceinline__ double warp_sum_partials(const double* p, int G) {
-  const int l = threadIdx.x & 31;
-  double a[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int q0 = l; q0 < G; q0 += 16 * 32) {
-    double t[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int q = q0 + 32 * k;
-      t[k] = q < G ? __ldcg(p + q) : 0.0;
-    }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) a[k & 3] += t[k];
-  }
-  return VecOps<double>::warp_sum((a[0] + a[1]) + (a[2] + a[3]));
-}
-
 // Partial sums acc[k] += <w, V_{i0+k}> over this thread's packs for exactly
 // C vectors (k < C).  C is a compile-time count, so no multiply-add is spent
 // on an empty slot (the FP64 forms are bound by the FP64 pipe).  A thread
@@ -229,11 +219,11 @@ __device__ __forceinline__ double warp_sum_partials(const double* p, int G) {
 // visited in grid-stride order.
 template <typename Tv, int VEC, int C, int UNR>
 __device__ __forceinline__ void dot_rounds(const Tv* __restrict__ V, const Tv* __restrict__ w, size_t N, int i0,
-                                           Tv* acc) {
+                                           Tv* acc, int bx, int nbx) {
   using Op = VecOps<Tv>;
   const size_t NP = N / VEC;  // VEC divides N (launcher)
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q0 < NP; q0 += UNR * stride) {
+  const size_t stride = (size_t)nbx * blockDim.x;
+  for (size_t q0 = bx * (size_t)blockDim.x + threadIdx.x; q0 < NP; q0 += UNR * stride) {
     Tv wv[UNR][VEC];
     Tv a[UNR][C][VEC];  // all loads issued before the arithmetic
 #pragma unroll
@@ -272,14 +262,14 @@ __device__ __forceinline__ void dot_rounds(const Tv* __restrict__ V, const Tv* _
 // accumulate = 1 adds to H (second CGS pass).  The last block finishes the
 // j+1 sums, one warp per sum.
 template <typename Tv, int VEC, int CH>
-__global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__ V, size_t N, int j, int accumulate,
-                                                          double* partials, SolverState* st) {
+__device__ __forceinline__ void multidot_body(const Tv* __restrict__ V, size_t N, int j, int accumulate,
+                                              double* partials, SolverState* st, int bx, int nbx, int by, int nby) {
   if (closed(&st->run_iter)) return;
   using Op = VecOps<Tv>;
   constexpr int UNR = kDotChunk / CH;
   __shared__ double wsum[CH][kWarps];
-  const int per = (j + 1 + gridDim.y - 1) / gridDim.y;  // <= CH (launcher)
-  const int i0 = blockIdx.y * per;
+  const int per = (j + 1 + nby - 1) / nby;  // <= CH (launcher)
+  const int i0 = by * per;
   const int cnt = min(per, j + 1 - i0);
   const Tv* __restrict__ w = V + (size_t)(j + 1) * N;
   Tv acc[CH];
@@ -288,7 +278,7 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
   switch (cnt) {  // uniform over the block
 #define RSFDE_DOT_CASE(C) \
   case C:                \
-    if constexpr (C <= CH) dot_rounds<Tv, VEC, C, UNR>(V, w, N, i0, acc); \
+    if constexpr (C <= CH) dot_rounds<Tv, VEC, C, UNR>(V, w, N, i0, acc, bx, nbx); \
     break;
     RSFDE_DOT_CASE(1)
     RSFDE_DOT_CASE(2)
@@ -302,13 +292,13 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
     default:
       break;
   }
-  const int G = gridDim.x;
+  const int G = nbx;
   const double bs = block_sums<Tv, CH>(acc, cnt, wsum);
   const int wk = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0 && wk < cnt) partials[(size_t)(i0 + wk) * G + blockIdx.x] = bs;
-  if (arrive_last(&st->counter, gridDim.x * gridDim.y)) {
+  if ((threadIdx.x & 31) == 0 && wk < cnt) partials[(size_t)(i0 + wk) * G + bx] = bs;
+  if (arrive_last(&st->counter, nbx * nby)) {
     for (int i = wk; i <= j; i += kWarps) {
-      const double tot = warp_sum_partials(partials + (size_t)i * G, G);
+      const double tot = warp_sum_fixed(partials + (size_t)i * G, G);
       if ((threadIdx.x & 31) == 0) {
         const double h = st->s[i] * tot;
         st->hcol[i] = h;
@@ -318,6 +308,11 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
     }
   }
 }
+template <typename Tv, int VEC, int CH>
+__global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__ V, size_t N, int j, int accumulate,
+                                                          double* partials, SolverState* st) {
+  multidot_body<Tv, VEC, CH>(V, N, j, accumulate, partials, st, blockIdx.x, gridDim.x, blockIdx.y, gridDim.y);
+}
 
 // V_{j+1} <- V_{j+1} - sum_i (h_i s_i) V_i and ||V_{j+1}||; on the final pass
 // the last block runs the Givens step.  The basis vectors are read in groups
@@ -325,8 +320,8 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
 // dependent update chains (about eight loads in flight for every j); each
 // element still takes the terms in the order i = 0..j.
 template <typename Tv, int VEC, int CH>
-__global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size_t N, int j, int final_pass,
-                                                        double* partials, SolverState* st, Bf16Out bo) {
+__device__ __forceinline__ void update_body(Tv* __restrict__ V, size_t N, int j, int final_pass, double* partials,
+                                            SolverState* st, const Bf16Out& bo, int bid, int nblk) {
   if (closed(&st->run_iter)) return;
   using Op = VecOps<Tv>;
   constexpr int UNR = kDotChunk / CH;
@@ -337,8 +332,8 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size
   Tv* __restrict__ w = V + (size_t)(j + 1) * N;
   Tv acc = Op::zero();
   const size_t NP = N / VEC;  // VEC divides N (launcher)
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  for (size_t q0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q0 < NP; q0 += UNR * stride) {
+  const size_t stride = (size_t)nblk * blockDim.x;
+  for (size_t q0 = bid * (size_t)blockDim.x + threadIdx.x; q0 < NP; q0 += UNR * stride) {
     Tv val[UNR][VEC];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
@@ -413,15 +408,20 @@ __global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size
     }
   }
   const double bs = block_sums<Tv, 1>(&acc, 1, wsum);
-  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
-  if (arrive_last(&st->counter, gridDim.x) && threadIdx.x < 32) {
-    const double tot = warp_sum_partials(partials, gridDim.x);
+  if (threadIdx.x == 0) partials[bid] = bs;
+  if (arrive_last(&st->counter, nblk) && threadIdx.x < 32) {
+    const double tot = warp_sum_fixed(partials, nblk);
     if (threadIdx.x == 0 && final_pass) givens_step(st, j, sqrt(tot));
   }
 }
+template <typename Tv, int VEC, int CH>
+__global__ void __launch_bounds__(kBlock) update_kernel(Tv* __restrict__ V, size_t N, int j, int final_pass,
+                                                        double* partials, SolverState* st, Bf16Out bo) {
+  update_body<Tv, VEC, CH>(V, N, j, final_pass, partials, st, bo, blockIdx.x, gridDim.x);
+}
 
 // Back substitution R y = g for the jlast columns of the cycle.
-__global__ void solve_y_kernel(SolverState* st) {
+__device__ __forceinline__ void solve_y_body(SolverState* st) {
   if (closed(&st->run_cycle) || threadIdx.x != 0) return;
   const int J = st->jlast;
   for (int i = J - 1; i >= 0; --i) {
@@ -430,6 +430,7 @@ __global__ void solve_y_kernel(SolverState* st) {
     st->y[i] = s / st->H[i * kMaxRestart + i];
   }
 }
+__global__ void solve_y_kernel(SolverState* st) { solve_y_body(st); }
 
 // x <- x + sum_{i < jlast} y_i z_i  (flexible GMRES keeps the z_i).  With FP32
 // z_i the correction sum_i y_i z_i is accumulated in double-FP32 (FP32 pipe;
@@ -456,8 +457,8 @@ struct XAcc<float> {
 };
 
 template <typename Tz, int VEC>
-__global__ void __launch_bounds__(kBlock) xupdate_kernel(double* __restrict__ x, const Tz* __restrict__ Z, size_t N,
-                                                         SolverState* st) {
+__device__ __forceinline__ void xupdate_body(double* __restrict__ x, const Tz* __restrict__ Z, size_t N,
+                                             SolverState* st, int bid, int nblk) {
   if (closed(&st->run_cycle)) return;
   const int J = st->jlast;
   if (J == 0) return;
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(kBlock) xupdate_kernel(double* __restrict__ x,
   for (int i = threadIdx.x; i < J; i += blockDim.x) y[i] = A::coef(st->y[i]);
   __syncthreads();
   const size_t NP = N / VEC;  // VEC divides N (launcher)
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < NP; q += (size_t)gridDim.x * blockDim.x) {
+  for (size_t q = bid * (size_t)blockDim.x + threadIdx.x; q < NP; q += (size_t)nblk * blockDim.x) {
     const size_t p = q * VEC;
     typename A::C acc[VEC];
 #pragma unroll
@@ -492,6 +493,11 @@ __global__ void __launch_bounds__(kBlock) xupdate_kernel(double* __restrict__ x,
 #pragma unroll
     for (int e = 0; e < VEC; ++e) x[p + e] += A::value(acc[e]);
   }
+}
+template <typename Tz, int VEC>
+__global__ void __launch_bounds__(kBlock) xupdate_kernel(double* __restrict__ x, const Tz* __restrict__ Z, size_t N,
+                                                         SolverState* st) {
+  xupdate_body<Tz, VEC>(x, Z, N, st, blockIdx.x, gridDim.x);
 }
 
 __global__ void finalize_kernel(double* __restrict__ x, size_t N, SolverState* st) {
@@ -613,11 +619,13 @@ void launch_rhs(const double* u, const double* uu, const double* src, const uint
 void launch_norm_b(const double* b, size_t N, double* partials, SolverState* st, cudaStream_t s) {
   norm_b_kernel<<<vec_grid(N), kBlock, 0, s>>>(b, N, partials, st);
 }
-// Gram-Schmidt grid: the SMs times the resident blocks of the kernel (one
-// full wave), at most vec_grid(N) blocks (the partials buffer's width).
+// Gram-Schmidt grid: one full wave of resident blocks, but no more blocks
+// than give every thread eight 16-byte packs (small vectors: the block and
+// grid reductions would outweigh the loads).
 static int wave_grid(int per_sm, size_t N) {
   const int g = kNumSMs * per_sm;
-  const int cap = vec_grid(N);
+  size_t c = (N + kBlock * 8 - 1) / (kBlock * 8);
+  const int cap = c < 1 ? 1 : (int)c;
   return g < cap ? g : cap;
 }
 template <typename K>
@@ -632,14 +640,17 @@ static int resident_blocks(K kernel) {
 static int dot_chunk(int j) { return j + 1 <= 2 ? 2 : j + 1 <= 4 ? 4 : kDotChunk; }
 
 template <typename Tv, int VEC, int CH>
-static void launch_multidot_t(const Tv* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
-                              cudaStream_t s) {
+static dim3 multidot_grid(size_t N, int j) {
   static const int per_sm = resident_blocks(multidot_kernel<Tv, VEC, CH>);
   // the chunks share one wave: each takes 1/chunks of the resident blocks
   const int chunks = (j + 1 + CH - 1) / CH;
   const int gx = wave_grid(per_sm, N / VEC);
-  dim3 grid(gx / chunks > kNumSMs ? gx / chunks : (gx < kNumSMs ? gx : kNumSMs), chunks);
-  multidot_kernel<Tv, VEC, CH><<<grid, kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
+  return dim3(gx / chunks > kNumSMs ? gx / chunks : (gx < kNumSMs ? gx : kNumSMs), chunks);
+}
+template <typename Tv, int VEC, int CH>
+static void launch_multidot_t(const Tv* V, size_t N, int j, int accumulate, double* partials, SolverState* st,
+                              cudaStream_t s) {
+  multidot_kernel<Tv, VEC, CH><<<multidot_grid<Tv, VEC, CH>(N, j), kBlock, 0, s>>>(V, N, j, accumulate, partials, st);
 }
 // 16-byte accesses when every basis vector is 16-byte aligned, else one element.
 template <typename Tv>
@@ -658,10 +669,14 @@ void launch_multidot(const Tv* V, size_t N, int j, int accumulate, double* parti
   }
 }
 template <typename Tv, int VEC, int CH>
+static int update_grid(size_t N) {
+  static const int per_sm = resident_blocks(update_kernel<Tv, VEC, CH>);
+  return wave_grid(per_sm, N / VEC);
+}
+template <typename Tv, int VEC, int CH>
 static void launch_update_t(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st,
                             cudaStream_t s, const Bf16Out& bo) {
-  static const int per_sm = resident_blocks(update_kernel<Tv, VEC, CH>);
-  update_kernel<Tv, VEC, CH><<<wave_grid(per_sm, N / VEC), kBlock, 0, s>>>(V, N, j, final_pass, partials, st, bo);
+  update_kernel<Tv, VEC, CH><<<update_grid<Tv, VEC, CH>(N), kBlock, 0, s>>>(V, N, j, final_pass, partials, st, bo);
 }
 template <typename Tv>
 void launch_update(Tv* V, size_t N, int j, int final_pass, double* partials, SolverState* st, cudaStream_t s,
@@ -732,5 +747,245 @@ template void launch_scale_copy<float, double>(const float*, const double*, doub
                                                cudaStream_t);
 template void launch_scale_copy<float, float>(const float*, const double*, float*, size_t, const int*,
                                               cudaStream_t);
+
+// ---- multi-instance launches (batched form) ---------------------------------
+// A fixed grid loops over the active virtual blocks (active prefix staged in
+// shared memory); each virtual block runs the single-instance body on its
+// instance's own virtual grid, so the results are bit-identical to single
+// solves.
+template <typename Fn>
+__device__ __forceinline__ void multi_loop(const BatchInst* __restrict__ bi, const int* __restrict__ prefix,
+                                           const int* __restrict__ active, int count, Fn&& fn) {
+  __shared__ int sact[kMaxBatchMulti + 1];
+  for (int k = threadIdx.x; k <= count; k += blockDim.x) sact[k] = active[k];
+  __syncthreads();
+  const int total = sact[count];
+  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int mi = multi_instance(sact, count, vb);
+    const int b0 = __ldg(prefix + mi);
+    fn(bi[mi], vb - sact[mi], __ldg(prefix + mi + 1) - b0);
+    __syncthreads();  // the next virtual block reuses the block's shared memory
+  }
+}
+
+__global__ void init_multi_kernel(const BatchInst* __restrict__ bi, int count, int m, int max_iter, double tol) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) init_state_body(bi[i].st, m, max_iter, tol);
+}
+__global__ void __launch_bounds__(kBlock) rhs_multi_kernel(const BatchInst* __restrict__ bi,
+                                                           const int* __restrict__ prefix,
+                                                           const int* __restrict__ active, int count, int later) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    rhs_body(I.u_prev, later ? I.u_pp : nullptr, I.src, I.phi, I.dt, I.b, I.x, I.N, I.partials, I.st, lb, nb);
+  });
+}
+template <typename Tv, int CH>
+__global__ void __launch_bounds__(kBlock) multidot_multi_kernel(const BatchInst* __restrict__ bi,
+                                                                const int* __restrict__ prefix,
+                                                                const int* __restrict__ active, int count, int j,
+                                                                int accumulate, int chunks) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    constexpr int VEC = 16 / sizeof(Tv);
+    const int gx = nb / chunks;
+    const Tv* V = reinterpret_cast<const Tv*>(I.V);
+    if (I.N % VEC == 0)
+      multidot_body<Tv, VEC, CH>(V, I.N, j, accumulate, I.partials, I.st, lb % gx, gx, lb / gx, chunks);
+    else
+      multidot_body<Tv, 1, CH>(V, I.N, j, accumulate, I.partials, I.st, lb % gx, gx, lb / gx, chunks);
+  });
+}
+template <typename Tv, int CH>
+__global__ void __launch_bounds__(kBlock) update_multi_kernel(const BatchInst* __restrict__ bi,
+                                                              const int* __restrict__ prefix,
+                                                              const int* __restrict__ active, int count, int j,
+                                                              int final_pass) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    constexpr int VEC = 16 / sizeof(Tv);
+    const Bf16Out none{nullptr, nullptr, 1, 0, 0};
+    Tv* V = reinterpret_cast<Tv*>(I.V);
+    if (I.N % VEC == 0) update_body<Tv, VEC, CH>(V, I.N, j, final_pass, I.partials, I.st, none, lb, nb);
+    else update_body<Tv, 1, CH>(V, I.N, j, final_pass, I.partials, I.st, none, lb, nb);
+  });
+}
+__global__ void solve_y_multi_kernel(const BatchInst* __restrict__ bi) { solve_y_body(bi[blockIdx.x].st); }
+template <typename Tz>
+__global__ void __launch_bounds__(kBlock) xupdate_multi_kernel(const BatchInst* __restrict__ bi,
+                                                               const int* __restrict__ prefix,
+                                                               const int* __restrict__ active, int count) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    constexpr int VEC = 16 / sizeof(Tz);
+    const Tz* Z = static_cast<const Tz*>(I.Z);
+    if (I.N % VEC == 0) xupdate_body<Tz, VEC>(I.x, Z, I.N, I.st, lb, nb);
+    else xupdate_body<Tz, 1>(I.x, Z, I.N, I.st, lb, nb);
+  });
+}
+// End of a batch step: x = 0 where the right side was zero, then the march
+// ring moves on (u^{k-2} <- u^{k-1}, u^{k-1} <- u^k).
+__global__ void __launch_bounds__(kBlock) finish_rotate_multi_kernel(const BatchInst* __restrict__ bi,
+                                                                     const int* __restrict__ prefix,
+                                                                     const int* __restrict__ active, int count) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    const bool zero = I.st->zero_solution != 0;
+    for (size_t p = lb * (size_t)blockDim.x + threadIdx.x; p < I.N; p += (size_t)nb * blockDim.x) {
+      const double xv = zero ? 0.0 : I.x[p];
+      I.x[p] = xv;
+      I.u_pp[p] = I.u_prev[p];
+      I.u_prev[p] = xv;
+    }
+  });
+}
+// Condition of the batch's device-side loop over FGMRES cycles: go on while
+// any instance runs; each running instance counts the cycle and is stopped
+// (RSFDE_ENOTCONV) past max_iter + 2 cycles, as in the single-instance loop.
+__global__ void loop_cond_multi_kernel(cudaGraphConditionalHandle h, const BatchInst* __restrict__ bi, int count,
+                                       int* runs) {
+  int go = 0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    SolverState* st = bi[i].st;
+    int g = st->run_cycle;
+    if (g) {
+      st->body_runs += 1;
+      st->total_body_runs += 1;
+      if (st->body_runs > st->max_iter + 2) {
+        st->status = RSFDE_ENOTCONV;
+        st->run_cycle = 0;
+        st->run_iter = 0;
+        g = 0;
+      }
+    }
+    go |= g;
+  }
+  go = __syncthreads_or(go);
+  if (threadIdx.x == 0) {
+    *runs += 1;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+  }
+}
+// Active prefixes (one block; count <= kMaxBatchMulti): an inclusive scan per
+// family of the instances' virtual-grid sizes, zero where the gate is closed.
+__global__ void __launch_bounds__(kMaxBatchMulti) compact_multi_kernel(const BatchInst* __restrict__ bi, int count,
+                                                                       int use_cycle, CompactArgs a) {
+  __shared__ int sc[kMaxBatchMulti];
+  const int i = threadIdx.x;
+  int open = 0;
+  if (i < count) {
+    const SolverState* st = bi[i].st;
+    open = use_cycle ? *(volatile const int*)&st->run_cycle : *(volatile const int*)&st->run_iter;
+  }
+  for (int f = 0; f < a.nfam; ++f) {
+    const int v = (i < count && open) ? __ldg(a.prefix[f] + i + 1) - __ldg(a.prefix[f] + i) : 0;
+    sc[i] = v;
+    __syncthreads();
+    for (int d = 1; d < kMaxBatchMulti; d <<= 1) {  // Hillis-Steele inclusive scan
+      const int t = i >= d ? sc[i - d] : 0;
+      __syncthreads();
+      sc[i] += t;
+      __syncthreads();
+    }
+    if (i < count) a.active[f][i] = sc[i] - v;
+    if (i == count - 1) a.active[f][count] = sc[i];
+    __syncthreads();
+  }
+}
+
+// 1 in *out while any instance of the batch still runs a cycle (direct launches).
+__global__ void any_running_multi_kernel(const BatchInst* __restrict__ bi, int count, int* out) {
+  int go = 0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) go |= bi[i].st->run_cycle;
+  go = __syncthreads_or(go);
+  if (threadIdx.x == 0) *out = go;
+}
+void launch_any_running_multi(const BatchInst* bi, int count, int* out, cudaStream_t s) {
+  any_running_multi_kernel<<<1, 256, 0, s>>>(bi, count, out);
+}
+
+void launch_compact_multi(const BatchInst* bi, int count, int use_cycle, const CompactArgs& a, cudaStream_t s) {
+  compact_multi_kernel<<<1, kMaxBatchMulti, 0, s>>>(bi, count, use_cycle, a);
+}
+void launch_init_multi(const BatchInst* bi, int count, int m, int max_iter, double tol, cudaStream_t s) {
+  init_multi_kernel<<<(count + 127) / 128, 128, 0, s>>>(bi, count, m, max_iter, tol);
+}
+void launch_rhs_multi(const BatchInst* bi, const MultiGrid& g, int later, cudaStream_t s) {
+  static const int grid = multi_launch_grid(rhs_multi_kernel, kBlock, 0, 1 << 30);
+  rhs_multi_kernel<<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(bi, g.prefix, g.active, g.count, later);
+}
+template <typename Tv, int CH>
+static void launch_multidot_multi_t(const BatchInst* bi, const MultiGrid& g, int j, int accumulate, cudaStream_t s) {
+  static const int grid = multi_launch_grid(multidot_multi_kernel<Tv, CH>, kBlock, 0, 1 << 30);
+  multidot_multi_kernel<Tv, CH><<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(
+      bi, g.prefix, g.active, g.count, j, accumulate, (j + CH) / CH);
+}
+template <typename Tv>
+void launch_multidot_multi(const BatchInst* bi, const MultiGrid& g, int j, int accumulate, cudaStream_t s) {
+  const int ch = dot_chunk(j);
+  if (ch == 2) launch_multidot_multi_t<Tv, 2>(bi, g, j, accumulate, s);
+  else if (ch == 4) launch_multidot_multi_t<Tv, 4>(bi, g, j, accumulate, s);
+  else launch_multidot_multi_t<Tv, kDotChunk>(bi, g, j, accumulate, s);
+}
+template <typename Tv, int CH>
+static void launch_update_multi_t(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, cudaStream_t s) {
+  static const int grid = multi_launch_grid(update_multi_kernel<Tv, CH>, kBlock, 0, 1 << 30);
+  update_multi_kernel<Tv, CH><<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(bi, g.prefix, g.active, g.count, j,
+                                                                               final_pass);
+}
+template <typename Tv>
+void launch_update_multi(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, cudaStream_t s) {
+  const int ch = dot_chunk(j);
+  if (ch == 2) launch_update_multi_t<Tv, 2>(bi, g, j, final_pass, s);
+  else if (ch == 4) launch_update_multi_t<Tv, 4>(bi, g, j, final_pass, s);
+  else launch_update_multi_t<Tv, kDotChunk>(bi, g, j, final_pass, s);
+}
+void launch_solve_y_multi(const BatchInst* bi, int count, cudaStream_t s) {
+  solve_y_multi_kernel<<<count, 32, 0, s>>>(bi);
+}
+template <typename Tz>
+void launch_xupdate_multi(const BatchInst* bi, const MultiGrid& g, cudaStream_t s) {
+  static const int grid = multi_launch_grid(xupdate_multi_kernel<Tz>, kBlock, 0, 1 << 30);
+  xupdate_multi_kernel<Tz><<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(bi, g.prefix, g.active, g.count);
+}
+void launch_finish_rotate_multi(const BatchInst* bi, const MultiGrid& g, cudaStream_t s) {
+  static const int grid = multi_launch_grid(finish_rotate_multi_kernel, kBlock, 0, 1 << 30);
+  finish_rotate_multi_kernel<<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(bi, g.prefix, g.active, g.count);
+}
+void launch_loop_cond_multi(cudaGraphConditionalHandle h, const BatchInst* bi, int count, int* runs,
+                            cudaStream_t s) {
+  loop_cond_multi_kernel<<<1, 256, 0, s>>>(h, bi, count, runs);
+}
+
+// The grids of the single-instance launches, for the multi-instance prefixes.
+template <typename Tv>
+int multidot_blocks(size_t N, int j) {
+  constexpr int VEC = 16 / sizeof(Tv);
+  const int ch = dot_chunk(j);
+  dim3 g;
+  if (N % VEC == 0)
+    g = ch == 2 ? multidot_grid<Tv, VEC, 2>(N, j) : ch == 4 ? multidot_grid<Tv, VEC, 4>(N, j)
+                                                             : multidot_grid<Tv, VEC, kDotChunk>(N, j);
+  else
+    g = ch == 2 ? multidot_grid<Tv, 1, 2>(N, j) : ch == 4 ? multidot_grid<Tv, 1, 4>(N, j)
+                                                           : multidot_grid<Tv, 1, kDotChunk>(N, j);
+  return (int)(g.x * g.y);
+}
+template <typename Tv>
+int update_blocks(size_t N, int j) {
+  constexpr int VEC = 16 / sizeof(Tv);
+  const int ch = dot_chunk(j);
+  if (N % VEC == 0)
+    return ch == 2 ? update_grid<Tv, VEC, 2>(N) : ch == 4 ? update_grid<Tv, VEC, 4>(N) : update_grid<Tv, VEC, kDotChunk>(N);
+  return ch == 2 ? update_grid<Tv, 1, 2>(N) : ch == 4 ? update_grid<Tv, 1, 4>(N) : update_grid<Tv, 1, kDotChunk>(N);
+}
+int xupdate_blocks(size_t N, int zbytes) {
+  const size_t VEC = 16 / (size_t)zbytes;
+  return N % VEC == 0 ? vec_grid(N / VEC) : vec_grid(N);
+}
+#define RSFDE_GS_MULTI(Tv)                                                                              \
+  template void launch_multidot_multi<Tv>(const BatchInst*, const MultiGrid&, int, int, cudaStream_t); \
+  template void launch_update_multi<Tv>(const BatchInst*, const MultiGrid&, int, int, cudaStream_t);   \
+  template int multidot_blocks<Tv>(size_t, int);                                                       \
+  template int update_blocks<Tv>(size_t, int);
+RSFDE_GS_MULTI(double)
+RSFDE_GS_MULTI(float)
+#undef RSFDE_GS_MULTI
+template void launch_xupdate_multi<float>(const BatchInst*, const MultiGrid&, cudaStream_t);
 
 }  // namespace rsfde

@@ -2,7 +2,7 @@
 // tile-shape table the autotuner records, the shape it forces while timing,
 // and the flag of a launch with no kernel for its (type, mode) pair.  The
 // kernels and launchers are in transforms.cuh, instantiated per arithmetic
-// type in transforms_f64.cu, transforms_f32.cu and transforms_df_*.cu.
+// type in transforms_f64.cu, transforms_f32.cu and transforms_df_a.cu, _b.cu and _c.cu.
 #include <atomic>
 
 #include "transforms.cuh"

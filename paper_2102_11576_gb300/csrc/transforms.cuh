@@ -166,15 +166,25 @@ __device__ __forceinline__ void st_pair(X* p, X a, X b) {
 //   MODE_APPLY:    out = z - tmpx - A_y z + (dt/eta) phi z
 //   MODE_RESIDUAL: out = b - (z - tmpx - A_y z + (dt/eta) phi z), ||out||^2
 //                  reduced, and the last block restarts the solver.
+//
+// The residual's ||r||^2 is summed per column pair -- each thread's terms in
+// a fixed order, then the group's threads by a fixed tree over t, then the
+// pairs in order by one warp -- so the value depends only on the grid, not on
+// how many pairs a block holds or how many blocks there are (single and
+// batched launches give identical bits).
+//
+// The body takes its block index and block count explicitly: a kernel
+// launch passes blockIdx.x and gridDim.x, a batched launch the instance's
+// own block of its virtual grid.
 template <typename T, typename Tin, int MODE, bool COLS, typename Tout>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    toeplitz_kernel(const Tin* __restrict__ z, T* __restrict__ tmpx, const uint8_t* __restrict__ phi,
-                    double pen, const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2,
-                    AxisTables<T> ax, int F, int gstride, const int* gate, double* partials, SolverState* st) {
+__device__ __forceinline__ void toeplitz_body(const Tin* __restrict__ z, T* __restrict__ tmpx,
+                                              const uint8_t* __restrict__ phi, double pen,
+                                              const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2,
+                                              const AxisTables<T>& ax, int F, int gstride, const int* gate,
+                                              double* partials, SolverState* st, int bid, int nblk) {
   if (gate_closed<T>(gate)) return;
   const T tpen = cvt<T>(pen);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
   const int L = ax.L, Lq = L >> 4, G = Lq;
   const GroupIdx gi = group_idx<COLS>(G, F);
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
@@ -189,12 +199,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
       COLS && ((MODE == MODE_APPLY && !std::is_same<T, double>::value && std::is_same<Tin, float>::value) ||
                (MODE == MODE_RESIDUAL && std::is_same<T, df>::value && std::is_same<Tin, double>::value));
   const bool pair_io = kPairIO && (n1 & 1) == 0;
-  double acc = 0.0;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+  for (int grp = bid; grp < ngroups; grp += nblk) {
     const int pr = grp * F + gi.g;
     const int a = 2 * pr;
     const bool live = pr < npairs;
     const bool second = a + 1 < nvec;
+    double acc = 0.0;  // this thread's part of the pair's ||r||^2
     cx<T> v[16];  // positions >= L/2 are zero (cleared by the forward transform)
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -252,10 +262,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
             }
           }
         }
-        continue;
       }
     }
-    if (live) {
+    if (!pair_io && live) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int pos = gi.t + k * Lq;
@@ -287,22 +296,42 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
         }
       }
     }
+    if constexpr (MODE == MODE_RESIDUAL) {
+      // the group's sum by a fixed tree over t in its own buffer (free now)
+      double* gsum = reinterpret_cast<double*>(buf);
+      __syncthreads();
+      gsum[gi.t] = acc;
+      __syncthreads();
+      for (int h = G >> 1; h > 0; h >>= 1) {
+        if (gi.t < h) gsum[gi.t] += gsum[gi.t + h];
+        __syncthreads();
+      }
+      if (gi.t == 0 && live) partials[pr] = gsum[0];
+      __syncthreads();  // the next group's transform reuses the buffer
+    }
   }
-  if (MODE == MODE_RESIDUAL) {
-    const double bs = block_sum(acc, red);
-    if (threadIdx.x == 0) partials[blockIdx.x] = bs;
-    if (arrive_last(&st->counter, gridDim.x)) {
-      const double tot = sum_partials(partials, gridDim.x, red);
+  if constexpr (MODE == MODE_RESIDUAL) {
+    if (arrive_last(&st->counter, nblk)) {
+      const double tot = block_sum_fixed(partials, npairs);
       if (threadIdx.x == 0) restart_prep(st, sqrt(tot));
     }
   }
 }
 
+template <typename T, typename Tin, int MODE, bool COLS, typename Tout>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
+    toeplitz_kernel(const Tin* __restrict__ z, T* __restrict__ tmpx, const uint8_t* __restrict__ phi,
+                    double pen, const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2,
+                    AxisTables<T> ax, int F, int gstride, const int* gate, double* partials, SolverState* st) {
+  toeplitz_body<T, Tin, MODE, COLS, Tout>(z, tmpx, phi, pen, b, out, n1, n2, ax, F, gstride, gate, partials, st,
+                                          blockIdx.x, gridDim.x);
+}
+
 // Sine transform of every row (COLS = false) or column: out = S (scale * in).
 template <typename T, typename Tin, typename Tout, bool COLS>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    dst_kernel(const Tin* __restrict__ in, const double* vscale, Tout* __restrict__ out, int n1, int n2,
-               AxisTables<T> ax, int F, int gstride, const int* gate) {
+__device__ __forceinline__ void dst_body(const Tin* __restrict__ in, const double* vscale, Tout* __restrict__ out,
+                                         int n1, int n2, const AxisTables<T>& ax, int F, int gstride, const int* gate,
+                                         int bid, int nblk) {
   if (gate_closed<T>(gate)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = ax.L, Lq = L >> 4, G = Lq;
@@ -312,7 +341,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
   const double sc = vscale ? *vscale : 1.0;
   const float scf = (float)sc;
   const int ngroups = (nvec + F - 1) / F;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+  for (int grp = bid; grp < ngroups; grp += nblk) {
     const int vec = grp * F + gi.g;
     const bool live = vec < nvec;
     cx<T> v[16];
@@ -338,21 +367,28 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
   }
 }
 
+template <typename T, typename Tin, typename Tout, bool COLS>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
+    dst_kernel(const Tin* __restrict__ in, const double* vscale, Tout* __restrict__ out, int n1, int n2,
+               AxisTables<T> ax, int F, int gstride, const int* gate) {
+  dst_body<T, Tin, Tout, COLS>(in, vscale, out, n1, n2, ax, F, gstride, gate, blockIdx.x, gridDim.x);
+}
+
 // Preconditioner, column pass.  For each x-frequency i (a column of T1, the
 // rows already sine-transformed): W = S_{n2} T1[:, i];
 // T2a[:, i] = S_{n2} (W / (1 - lam_x[i] - lam_y)),
 // T2b[:, i] = S_{n2} (W / (1 + dt/eta - lam_x[i] - lam_y)).
 template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    precond_cols_kernel(const T* __restrict__ T1, T* __restrict__ T2a, T* __restrict__ T2b, int n1, int n2,
-                        AxisTables<T> ay, const T* __restrict__ lamx, T pen, int F, int gstride, const int* gate) {
+__device__ __forceinline__ void precond_cols_body(const T* __restrict__ T1, T* __restrict__ T2a, T* __restrict__ T2b,
+                                                  int n1, int n2, const AxisTables<T>& ay, const T* __restrict__ lamx,
+                                                  T pen, int F, int gstride, const int* gate, int bid, int nblk) {
   if (gate_closed<T>(gate)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = ay.L, Lq = L >> 4, G = Lq;
   const GroupIdx gi = group_idx<true>(G, F);
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
   const int ngroups = (n1 + F - 1) / F;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+  for (int grp = bid; grp < ngroups; grp += nblk) {
     const int col = grp * F + gi.g;
     const bool live = col < n1;
     cx<T> v[16];
@@ -405,18 +441,26 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
+    precond_cols_kernel(const T* __restrict__ T1, T* __restrict__ T2a, T* __restrict__ T2b, int n1, int n2,
+                        AxisTables<T> ay, const T* __restrict__ lamx, T pen, int F, int gstride, const int* gate) {
+  precond_cols_body<T>(T1, T2a, T2b, n1, n2, ay, lamx, pen, F, gstride, gate, blockIdx.x, gridDim.x);
+}
+
 // Preconditioner, final row pass:  z[j, :] = (1 - phi) S_{n1} T2a[j, :] + phi S_{n1} T2b[j, :].
 template <typename T, typename Tz>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
-    precond_rows_kernel(const T* __restrict__ T2a, const T* __restrict__ T2b, const uint8_t* __restrict__ phi,
-                        Tz* __restrict__ z, int n1, int n2, AxisTables<T> ax, int F, int gstride, const int* gate) {
+__device__ __forceinline__ void precond_rows_body(const T* __restrict__ T2a, const T* __restrict__ T2b,
+                                                  const uint8_t* __restrict__ phi, Tz* __restrict__ z, int n1, int n2,
+                                                  const AxisTables<T>& ax, int F, int gstride, const int* gate,
+                                                  int bid, int nblk) {
   if (gate_closed<T>(gate)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = ax.L, Lq = L >> 4, G = Lq;
   const GroupIdx gi = group_idx<false>(G, F);
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
   const int ngroups = (n2 + F - 1) / F;
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+  for (int grp = bid; grp < ngroups; grp += nblk) {
     const int row = grp * F + gi.g;
     const bool live = row < n2;
     T res[8];
@@ -457,13 +501,20 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
   }
 }
 
+template <typename T, typename Tz>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
+    precond_rows_kernel(const T* __restrict__ T2a, const T* __restrict__ T2b, const uint8_t* __restrict__ phi,
+                        Tz* __restrict__ z, int n1, int n2, AxisTables<T> ax, int F, int gstride, const int* gate) {
+  precond_rows_body<T, Tz>(T2a, T2b, phi, z, n1, n2, ax, F, gstride, gate, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // Launch geometry: G = L/16 threads per group; F groups per block, the
 // largest power of two within the thread cap (512 FP64 / 1024 FP32), the
 // shared-memory budget and the work available (at least ~2 blocks per SM).
 // Complex values per 128-byte shared-memory phase: 16 (FP32), 8 (FP64).
 template <typename T>
-static int lanes_per_phase() {
+__host__ __device__ static int lanes_per_phase() {
   return 128 / (int)(2 * sizeof(T));
 }
 
@@ -473,7 +524,7 @@ static int lanes_per_phase() {
 // stride = P/F mod P, consecutive groups smaller than a phase (rows) need
 // stride = G mod P.
 template <typename T>
-static int group_stride(int L, int F, bool cols) {
+__host__ __device__ static int group_stride(int L, int F, bool cols) {
   const int P = lanes_per_phase<T>();
   const int base = L + L / 16, G = L / 16;
   int target = 0;
@@ -554,8 +605,7 @@ void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi
                               std::is_same<Tout, double>::value;
   constexpr bool apply_mode = !std::is_same<T, double>::value || std::is_same<Tout, double>::value;
   if constexpr (resid_mode) {
-    if (mode == MODE_RESIDUAL) {
-      if (grid > kMaxPartials) grid = kMaxPartials;
+    if (mode == MODE_RESIDUAL) {  // partials: one per column pair (npairs <= 2048)
       auto k = toeplitz_kernel<T, Tin, MODE_RESIDUAL, true, Tout>;
       set_smem(k, sm);
       k<<<grid, F * (ay.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, b, out, n1, n2, ay, F, gs, gate,
@@ -626,6 +676,181 @@ void launch_precond_rows(const T* T2a, const T* T2b, const uint8_t* phi, Tz* z, 
   set_smem(k, sm);
   k<<<(n2 + F - 1) / F, F * (ax.L / 16), sm, s>>>(T2a, T2b, phi, z, n1, n2, ax, F, group_stride<T>(ax.L, F, false),
                                                   gate);
+}
+
+// ---------------------------------------------------------------------------
+// Multi-instance transform launches (batched form): every block finds its
+// instance by the prefix of block counts and runs the same body as a
+// single-instance launch, with F = kMultiThreads / (L/16) transforms per block
+// and the instance's own virtual grid, so one launch covers every instance.
+template <typename T>
+__device__ __forceinline__ const AxisTables<T>& inst_tab(const BatchInst& I, bool y);
+template <>
+__device__ __forceinline__ const AxisTables<double>& inst_tab<double>(const BatchInst& I, bool y) {
+  return y ? I.y64 : I.x64;
+}
+template <>
+__device__ __forceinline__ const AxisTables<float>& inst_tab<float>(const BatchInst& I, bool y) {
+  return y ? I.y32 : I.x32;
+}
+template <>
+__device__ __forceinline__ const AxisTables<df>& inst_tab<df>(const BatchInst& I, bool y) {
+  return y ? I.ydf : I.xdf;
+}
+
+// The loop over the active virtual blocks (as in krylov.cu).  The kernels ask
+// for the register budget of the single-instance kernels (4 blocks of 256
+// FP32 threads, 2 of FP64 or double-FP32, per SM), which their occupancy and
+// latency hiding depend on.
+template <typename Fn>
+__device__ __forceinline__ void multi_loop_fft(const BatchInst* __restrict__ bi, const int* __restrict__ prefix,
+                                               const int* __restrict__ active, int count, Fn&& fn) {
+  __shared__ int sact[kMaxBatchMulti + 1];
+  for (int k = threadIdx.x; k <= count; k += blockDim.x) sact[k] = active[k];
+  __syncthreads();
+  const int total = sact[count];
+  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int mi = multi_instance(sact, count, vb);
+    const int b0 = __ldg(prefix + mi);
+    fn(bi[mi], vb - sact[mi], __ldg(prefix + mi + 1) - b0);
+    __syncthreads();
+  }
+}
+
+// w_j = M z_j for every instance (MODE_APPLY; rows write the scratch).
+template <typename T, typename Tz, typename Tv, bool COLS>
+__global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) operator_multi_kernel(const BatchInst* __restrict__ bi,
+                                                                       const int* __restrict__ prefix,
+                                                                       const int* __restrict__ active, int count,
+                                                                       int j) {
+  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    const AxisTables<T>& ax = inst_tab<T>(I, COLS);
+    const int F = multi_groups(ax.L);
+    const Tz* z = static_cast<const Tz*>(I.Z) + (size_t)j * I.N;
+    Tv* w = reinterpret_cast<Tv*>(I.V) + (size_t)(j + 1) * I.N;
+    toeplitz_body<T, Tz, MODE_APPLY, COLS, Tv>(z, static_cast<T*>(I.tmpx), I.phi, I.pen, nullptr, w, I.n1, I.n2, ax,
+                                               F, group_stride<T>(ax.L, F, COLS), &I.st->run_iter, nullptr, nullptr,
+                                               lb, nb);
+  });
+}
+
+// V_0 = b - M x and the restart decision (rows: A_x x into the scratch).
+template <typename T, typename Tv, bool COLS>
+__global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) residual_multi_kernel(const BatchInst* __restrict__ bi,
+                                                                       const int* __restrict__ prefix,
+                                                                       const int* __restrict__ active, int count) {
+  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    const AxisTables<T>& ax = inst_tab<T>(I, COLS);
+    const int F = multi_groups(ax.L);
+    const int gs = group_stride<T>(ax.L, F, COLS);
+    if constexpr (COLS)
+      toeplitz_body<T, double, MODE_RESIDUAL, true, Tv>(I.x, static_cast<T*>(I.tmpx), I.phi, I.pen, I.b,
+                                                        reinterpret_cast<Tv*>(I.V), I.n1, I.n2, ax, F, gs,
+                                                        &I.st->run_cycle, I.partials, I.st, lb, nb);
+    else
+      toeplitz_body<T, double, MODE_APPLY, false, double>(I.x, static_cast<T*>(I.tmpx), nullptr, 0.0, nullptr,
+                                                          nullptr, I.n1, I.n2, ax, F, gs, &I.st->run_cycle, nullptr,
+                                                          nullptr, lb, nb);
+  });
+}
+
+// The three passes of the FFT preconditioner, z_j = P-hat^-1 (s_j V_j).
+template <typename T, typename Tv>
+__global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) dst_rows_multi_kernel(const BatchInst* __restrict__ bi,
+                                                                       const int* __restrict__ prefix,
+                                                                       const int* __restrict__ active, int count,
+                                                                       int j) {
+  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    const AxisTables<T>& ax = inst_tab<T>(I, false);
+    const int F = multi_groups(ax.L);
+    dst_body<T, Tv, T, false>(reinterpret_cast<const Tv*>(I.V) + (size_t)j * I.N, &I.st->s[j],
+                              static_cast<T*>(I.T1), I.n1, I.n2, ax, F, group_stride<T>(ax.L, F, false),
+                              &I.st->run_iter, lb, nb);
+  });
+}
+template <typename T>
+__global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) precond_cols_multi_kernel(const BatchInst* __restrict__ bi,
+                                                                           const int* __restrict__ prefix,
+                                                                           const int* __restrict__ active,
+                                                                           int count) {
+  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    const AxisTables<T>& ay = inst_tab<T>(I, true);
+    const int F = multi_groups(ay.L);
+    precond_cols_body<T>(static_cast<const T*>(I.T1), static_cast<T*>(I.T2a), static_cast<T*>(I.T2b), I.n1, I.n2,
+                         ay, inst_tab<T>(I, false).lam, T(I.pen), F, group_stride<T>(ay.L, F, true),
+                         &I.st->run_iter, lb, nb);
+  });
+}
+template <typename T, typename Tz>
+__global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) precond_rows_multi_kernel(const BatchInst* __restrict__ bi,
+                                                                           const int* __restrict__ prefix,
+                                                                           const int* __restrict__ active, int count,
+                                                                           int j) {
+  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    const AxisTables<T>& ax = inst_tab<T>(I, false);
+    const int F = multi_groups(ax.L);
+    precond_rows_body<T, Tz>(static_cast<const T*>(I.T2a), static_cast<const T*>(I.T2b), I.phi,
+                             static_cast<Tz*>(I.Z) + (size_t)j * I.N, I.n1, I.n2, ax, F,
+                             group_stride<T>(ax.L, F, false), &I.st->run_iter, lb, nb);
+  });
+}
+
+// Dynamic shared memory of a multi-instance transform launch: the largest any
+// of its transform lengths needs.
+template <typename T>
+static size_t multi_smem(const MultiGrid& g, bool cols) {
+  size_t m = 0;
+  for (int k = 4; k <= 12; ++k)
+    if (g.l2mask & (1u << k)) {
+      const int L = 1 << k, F = multi_groups(L);
+      const size_t b = group_smem<T>(L, F, cols);
+      if (b > m) m = b;
+    }
+  return m;
+}
+
+template <typename T, typename Tz, typename Tv>
+void launch_operator_multi(const BatchInst* bi, const MultiGrid& rows, const MultiGrid& cols, int j, cudaStream_t s) {
+  auto kr = operator_multi_kernel<T, Tz, Tv, false>;
+  auto kc = operator_multi_kernel<T, Tz, Tv, true>;
+  const size_t sr = multi_smem<T>(rows, false), sc = multi_smem<T>(cols, true);
+  set_smem(kr, sr);
+  set_smem(kc, sc);
+  kr<<<multi_launch_grid(kr, kMultiThreads, sr, rows.total), kMultiThreads, sr, s>>>(bi, rows.prefix, rows.active,
+                                                                                   rows.count, j);
+  kc<<<multi_launch_grid(kc, kMultiThreads, sc, cols.total), kMultiThreads, sc, s>>>(bi, cols.prefix, cols.active,
+                                                                                   cols.count, j);
+}
+
+template <typename T, typename Tv>
+void launch_residual_multi(const BatchInst* bi, const MultiGrid& rows, const MultiGrid& cols, cudaStream_t s) {
+  auto kr = residual_multi_kernel<T, Tv, false>;
+  auto kc = residual_multi_kernel<T, Tv, true>;
+  const size_t sr = multi_smem<T>(rows, false), sc = multi_smem<T>(cols, true);
+  set_smem(kr, sr);
+  set_smem(kc, sc);
+  kr<<<multi_launch_grid(kr, kMultiThreads, sr, rows.total), kMultiThreads, sr, s>>>(bi, rows.prefix, rows.active,
+                                                                                   rows.count);
+  kc<<<multi_launch_grid(kc, kMultiThreads, sc, cols.total), kMultiThreads, sc, s>>>(bi, cols.prefix, cols.active,
+                                                                                   cols.count);
+}
+
+template <typename T, typename Tz, typename Tv>
+void launch_precond_multi(const BatchInst* bi, const MultiGrid& drows, const MultiGrid& pcols, const MultiGrid& prows,
+                          int j, cudaStream_t s) {
+  auto k1 = dst_rows_multi_kernel<T, Tv>;
+  auto k2 = precond_cols_multi_kernel<T>;
+  auto k3 = precond_rows_multi_kernel<T, Tz>;
+  const size_t s1 = multi_smem<T>(drows, false), s2 = multi_smem<T>(pcols, true), s3 = multi_smem<T>(prows, false);
+  set_smem(k1, s1);
+  set_smem(k2, s2);
+  set_smem(k3, s3);
+  k1<<<multi_launch_grid(k1, kMultiThreads, s1, drows.total), kMultiThreads, s1, s>>>(bi, drows.prefix, drows.active,
+                                                                                    drows.count, j);
+  k2<<<multi_launch_grid(k2, kMultiThreads, s2, pcols.total), kMultiThreads, s2, s>>>(bi, pcols.prefix, pcols.active,
+                                                                                    pcols.count);
+  k3<<<multi_launch_grid(k3, kMultiThreads, s3, prows.total), kMultiThreads, s3, s>>>(bi, prows.prefix, prows.active,
+                                                                                    prows.count, j);
 }
 
 }  // namespace rsfde

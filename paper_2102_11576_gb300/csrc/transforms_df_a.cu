@@ -16,4 +16,5 @@ RSFDE_TOEP_COLS(df, float, df)
 RSFDE_TOEP_ROWS(df, double)
 RSFDE_TOEP_ROWS(df, float)
 
+
 }  // namespace rsfde

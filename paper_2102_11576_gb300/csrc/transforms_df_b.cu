@@ -11,6 +11,6 @@ namespace rsfde {
                                                    SolverState*, cudaStream_t);
 RSFDE_TOEP_COLS(df, double, double)
 RSFDE_TOEP_COLS(df, double, df)
-RSFDE_TOEP_COLS(df, double, float)
+
 
 }  // namespace rsfde

@@ -1,0 +1,15 @@
+// transforms_df_c.cu -- explicit instantiations of the transform kernels
+// (transforms.cuh) in double-FP32 (true-residual passes) arithmetic; one translation unit per
+// arithmetic type so that the library's objects compile in parallel.
+#include "transforms.cuh"
+
+namespace rsfde {
+
+#define RSFDE_TOEP_COLS(T, Tin, Tout)                                                                           \
+  template void launch_toeplitz_cols<T, Tin, Tout>(int, const Tin*, void*, const uint8_t*, double, const double*, \
+                                                   Tout*, int, int, const AxisTables<T>&, const int*, double*,    \
+                                                   SolverState*, cudaStream_t);
+RSFDE_TOEP_COLS(df, double, float)
+
+
+}  // namespace rsfde

@@ -30,4 +30,13 @@ template void launch_precond_rows<float, float>(const float*, const float*, cons
 template void launch_precond_rows<float, double>(const float*, const float*, const uint8_t*, double*, int, int,
                                                  const AxisTables<float>&, const int*, cudaStream_t);
 
+#define RSFDE_OP_MULTI(T, Tz, Tv) \
+  template void launch_operator_multi<T, Tz, Tv>(const BatchInst*, const MultiGrid&, const MultiGrid&, int, cudaStream_t);
+RSFDE_OP_MULTI(float, float, double)
+RSFDE_OP_MULTI(float, float, float)
+template void launch_precond_multi<float, float, double>(const BatchInst*, const MultiGrid&, const MultiGrid&,
+                                                         const MultiGrid&, int, cudaStream_t);
+template void launch_precond_multi<float, float, float>(const BatchInst*, const MultiGrid&, const MultiGrid&,
+                                                        const MultiGrid&, int, cudaStream_t);
+
 }  // namespace rsfde

@@ -33,4 +33,8 @@ template void launch_precond_rows<double, double>(const double*, const double*, 
 template void launch_precond_rows<double, float>(const double*, const double*, const uint8_t*, float*, int, int,
                                                  const AxisTables<double>&, const int*, cudaStream_t);
 
+template void launch_residual_multi<double, double>(const BatchInst*, const MultiGrid&, const MultiGrid&,
+                                                   cudaStream_t);
+template void launch_residual_multi<double, float>(const BatchInst*, const MultiGrid&, const MultiGrid&, cudaStream_t);
+
 }  // namespace rsfde
