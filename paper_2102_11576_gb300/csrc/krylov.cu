@@ -314,21 +314,45 @@ __global__ void __launch_bounds__(kBlock) multidot_kernel(const Tv* __restrict__
   multidot_body<Tv, VEC, CH>(V, N, j, accumulate, partials, st, blockIdx.x, gridDim.x, blockIdx.y, gridDim.y);
 }
 
-// V_{j+1} <- V_{j+1} - sum_i (h_i s_i) V_i and ||V_{j+1}||; on the final pass
-// the last block runs the Givens step.  The basis vectors are read in groups
-// of CH independent loads for each of kDotChunk / CH packs ahead of the
-// dependent update chains (about eight loads in flight for every j); each
-// element still takes the terms in the order i = 0..j.
-template <typename Tv, int VEC, int CH>
-__device__ __forceinline__ void update_body(Tv* __restrict__ V, size_t N, int j, int final_pass, double* partials,
-                                            SolverState* st, const Bf16Out& bo, int bid, int nblk) {
-  if (closed(&st->run_iter)) return;
+// Loads chunk k < C of the basis (vectors i0 .. i0+C-1) for UNR packs, then
+// subtracts them from val in the order i0, i0+1, ...; every load is issued
+// before the dependent chains.
+template <typename Tv, int VEC, int C, int UNR>
+__device__ __forceinline__ void update_chunk(const Tv* __restrict__ V, size_t N, size_t NP, size_t q0,
+                                             size_t stride, int i0, const Tv* ncoef, Tv (&val)[UNR][VEC]) {
+  using Op = VecOps<Tv>;
+  Tv a[UNR][C][VEC];
+#pragma unroll
+  for (int u = 0; u < UNR; ++u) {
+    const bool in = q0 + u * stride < NP;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+      if (in) {
+        ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + (q0 + u * stride) * VEC, a[u][k]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) a[u][k][e] = Op::zero();
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < UNR; ++u)
+#pragma unroll
+    for (int k = 0; k < C; ++k)
+#pragma unroll
+      for (int e = 0; e < VEC; ++e) val[u][e] = Op::fma(val[u][e], ncoef[i0 + k], a[u][k][e]);
+}
+
+// The update's sweep over this block's packs for j + 1 = nfull * CH + R basis
+// vectors: nfull chunks of CH, then a tail of R (a compile-time count, so no
+// multiply-add is issued for an empty slot -- the FP64 form is bound by the
+// FP64 pipe).  Each element takes the terms in the order i = 0..j.  Returns
+// this thread's part of ||w||^2.
+template <typename Tv, int VEC, int CH, int R>
+__device__ __forceinline__ Tv update_rounds(Tv* __restrict__ V, size_t N, int j, int nfull, int final_pass,
+                                            const Tv* ncoef, const Bf16Out& bo, int bid, int nblk) {
   using Op = VecOps<Tv>;
   constexpr int UNR = kDotChunk / CH;
-  __shared__ double wsum[1][kWarps];
-  __shared__ Tv ncoef[kMaxRestart + 1];
-  for (int i = threadIdx.x; i <= j; i += blockDim.x) ncoef[i] = Op::from(-(st->hcol[i] * st->s[i]));
-  __syncthreads();
   Tv* __restrict__ w = V + (size_t)(j + 1) * N;
   Tv acc = Op::zero();
   const size_t NP = N / VEC;  // VEC divides N (launcher)
@@ -344,29 +368,8 @@ __device__ __forceinline__ void update_body(Tv* __restrict__ V, size_t N, int j,
         for (int e = 0; e < VEC; ++e) val[u][e] = Op::zero();
       }
     }
-    for (int i0 = 0; i0 <= j; i0 += CH) {
-      Tv a[UNR][CH][VEC];  // all loads issued before the dependent chains
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-#pragma unroll
-        for (int k = 0; k < CH; ++k) {
-          if (i0 + k <= j && q0 + u * stride < NP) {
-            ld_vec<Tv, VEC>(V + (size_t)(i0 + k) * N + (q0 + u * stride) * VEC, a[u][k]);
-          } else {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) a[u][k][e] = Op::zero();
-          }
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u)
-#pragma unroll
-        for (int k = 0; k < CH; ++k)
-          if (i0 + k <= j) {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) val[u][e] = Op::fma(val[u][e], ncoef[i0 + k], a[u][k][e]);
-          }
-    }
+    for (int c = 0; c < nfull; ++c) update_chunk<Tv, VEC, CH, UNR>(V, N, NP, q0, stride, c * CH, ncoef, val);
+    if constexpr (R > 0) update_chunk<Tv, VEC, R, UNR>(V, N, NP, q0, stride, nfull * CH, ncoef, val);
 #pragma unroll
     for (int u = 0; u < UNR; ++u) {
       const size_t q = q0 + u * stride;
@@ -406,6 +409,41 @@ __device__ __forceinline__ void update_body(Tv* __restrict__ V, size_t N, int j,
 #pragma unroll
       for (int e = 0; e < VEC; ++e) acc = Op::fma(acc, val[u][e], val[u][e]);
     }
+  }
+  return acc;
+}
+
+// V_{j+1} <- V_{j+1} - sum_i (h_i s_i) V_i and ||V_{j+1}||; on the final pass
+// the last block runs the Givens step.  The basis vectors are read in chunks
+// of CH independent loads for each of kDotChunk / CH packs ahead of the
+// dependent update chains (about eight loads in flight for every j).
+template <typename Tv, int VEC, int CH>
+__device__ __forceinline__ void update_body(Tv* __restrict__ V, size_t N, int j, int final_pass, double* partials,
+                                            SolverState* st, const Bf16Out& bo, int bid, int nblk) {
+  if (closed(&st->run_iter)) return;
+  using Op = VecOps<Tv>;
+  __shared__ double wsum[1][kWarps];
+  __shared__ Tv ncoef[kMaxRestart + 1];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) ncoef[i] = Op::from(-(st->hcol[i] * st->s[i]));
+  __syncthreads();
+  const int nfull = (j + 1) / CH;
+  Tv acc = Op::zero();
+  switch (j + 1 - nfull * CH) {  // uniform over the grid
+#define RSFDE_UPD_CASE(R)                                                                            \
+  case R:                                                                                            \
+    if constexpr (R < CH) acc = update_rounds<Tv, VEC, CH, R>(V, N, j, nfull, final_pass, ncoef, bo, bid, nblk); \
+    break;
+    RSFDE_UPD_CASE(0)
+    RSFDE_UPD_CASE(1)
+    RSFDE_UPD_CASE(2)
+    RSFDE_UPD_CASE(3)
+    RSFDE_UPD_CASE(4)
+    RSFDE_UPD_CASE(5)
+    RSFDE_UPD_CASE(6)
+    RSFDE_UPD_CASE(7)
+#undef RSFDE_UPD_CASE
+    default:
+      break;
   }
   const double bs = block_sums<Tv, 1>(&acc, 1, wsum);
   if (threadIdx.x == 0) partials[bid] = bs;
