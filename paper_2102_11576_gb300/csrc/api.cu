@@ -369,7 +369,7 @@ void enqueue_apply_M_t(rsfde_ctx* c, const Tz* z, Tw* w, const int* gate, const 
                        const AxisTables<T>& ty) {
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
-    launch_toeplitz_rows<T, Tz>(z, c->tmpx, c->n1, c->n2, tx, gate, c->stream);
+    launch_toeplitz_rows<T, Tz>(z, c->tmpx, c->phi, c->pen, c->n1, c->n2, tx, gate, c->stream);
   }
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);
@@ -422,7 +422,7 @@ void enqueue_residual_left(rsfde_ctx* c, const int* gate) {
   double* r = c->opts.use_precond ? static_cast<double*>(c->Z) : c->V;
   {
     ProfScope ps(c, RSFDE_K_RESID_ROWS);
-    launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->n1, c->n2, c->x64.tab, gate, c->stream);
+    launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->x64.tab, gate, c->stream);
   }
   {
     ProfScope ps(c, RSFDE_K_RESID_COLS);
@@ -451,7 +451,7 @@ template <typename T>
 void enqueue_residual_t(rsfde_ctx* c, const int* gate, const AxisTables<T>& tx, const AxisTables<T>& ty) {
   {
     ProfScope ps(c, RSFDE_K_RESID_ROWS);
-    launch_toeplitz_rows<T, double>(c->x, c->tmpx, c->n1, c->n2, tx, gate, c->stream);
+    launch_toeplitz_rows<T, double>(c->x, c->tmpx, c->phi, c->pen, c->n1, c->n2, tx, gate, c->stream);
   }
   ProfScope ps(c, RSFDE_K_RESID_COLS);
   if (basis_kind(c) == BASIS_DF32)
@@ -826,7 +826,7 @@ void tune_operator(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTa
   const Tz* z = reinterpret_cast<const Tz*>(c->V);
   Tw* w = reinterpret_cast<Tw*>(c->V + c->N);
   chosen[TK_TOEP_ROWS] = tune_one<T>(c, TK_TOEP_ROWS, tx.L, (c->n2 + 1) / 2, reps, [&] {
-    launch_toeplitz_rows<T, Tz>(z, c->tmpx, c->n1, c->n2, tx, nullptr, c->stream);
+    launch_toeplitz_rows<T, Tz>(z, c->tmpx, c->phi, c->pen, c->n1, c->n2, tx, nullptr, c->stream);
   });
   chosen[TK_TOEP_COLS] = tune_one<T>(c, TK_TOEP_COLS, ty.L, (c->n1 + 1) / 2, reps, [&] {
     launch_toeplitz_cols<T, Tz, Tw>(MODE_APPLY, z, c->tmpx, c->phi, c->pen, nullptr, w, c->n1, c->n2, ty, nullptr,
@@ -842,7 +842,7 @@ void tune_residual(rsfde_ctx* c, int reps, const AxisTables<T>& tx, const AxisTa
   cudaMemsetAsync(c->x, 0, c->N * sizeof(double), c->stream);
   cudaMemsetAsync(c->b, 0, c->N * sizeof(double), c->stream);
   chosen[TK_TOEP_ROWS] = tune_one<T>(c, TK_TOEP_ROWS, tx.L, (c->n2 + 1) / 2, reps, [&] {
-    launch_toeplitz_rows<T, double>(c->x, c->tmpx, c->n1, c->n2, tx, nullptr, c->stream);
+    launch_toeplitz_rows<T, double>(c->x, c->tmpx, c->phi, c->pen, c->n1, c->n2, tx, nullptr, c->stream);
   });
   chosen[TK_TOEP_COLS] = tune_one<T>(c, TK_TOEP_COLS, ty.L, (c->n1 + 1) / 2, reps, [&] {
     if (basis_kind(c) == BASIS_FP32)
@@ -1583,7 +1583,7 @@ int rsfde_adjoint_step(rsfde_ctx* c, const double* u_prev, const double* u_k, co
   double* ay_u = static_cast<double*>(c->T2a);  // scratch, free after the solve
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_ROWS);
-    launch_toeplitz_rows<double, double>(u_k, c->tmpx, c->n1, c->n2, c->x64.tab, nullptr, c->stream);
+    launch_toeplitz_rows<double, double>(u_k, c->tmpx, nullptr, 0.0, c->n1, c->n2, c->x64.tab, nullptr, c->stream);
   }
   {
     ProfScope ps(c, RSFDE_K_TOEPLITZ_COLS);

@@ -1,0 +1,122 @@
+// exact.cu -- host tables and launchers of the exact Toeplitz products of the
+// true residual (the transforms and kernels are in exact.cuh).
+#include <cmath>
+#include <vector>
+
+#include "exact.cuh"
+
+namespace rsfde {
+
+namespace {
+
+uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p) { return (uint32_t)((uint64_t)a * b % p); }
+
+// Natural-order transform sum_j a_j w^(jk) mod p (iterative radix-2 after a
+// bit-reversal permutation).
+void host_ntt(std::vector<uint32_t>& a, uint32_t w, uint32_t p) {
+  const int L = (int)a.size();
+  for (int i = 1, j = 0; i < L; ++i) {
+    int bit = L >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) std::swap(a[i], a[j]);
+  }
+  for (int len = 2; len <= L; len <<= 1) {
+    const uint32_t wl = ntt_pow(w, (uint64_t)(L / len), p);
+    for (int i = 0; i < L; i += len) {
+      uint32_t wk = 1;
+      for (int k = 0; k < len / 2; ++k) {
+        const uint32_t u = a[i + k], v = mulmod(a[i + k + len / 2], wk, p);
+        a[i + k] = (uint32_t)(((uint64_t)u + v) % p);
+        a[i + k + len / 2] = (uint32_t)(((uint64_t)u + p - v) % p);
+        wk = mulmod(wk, wl, p);
+      }
+    }
+  }
+}
+
+uint2 with_shoup(uint32_t w, uint32_t p) { return make_uint2(w, ntt_shoup(w, p)); }
+
+}  // namespace
+
+std::vector<uint2> build_exact_tables(const std::vector<double>& t, int L, int* St) {
+  const int n = (int)t.size();
+  double mx = 0.0;
+  for (double v : t) mx = std::fmax(mx, std::fabs(v));
+  *St = mx > 0.0 ? 51 - std::ilogb(mx) : 0;  // mx 2^St < 2^52
+  std::vector<long long> tq(n);
+  for (int k = 0; k < n; ++k) tq[k] = std::llround(std::ldexp(t[k], *St));
+  std::vector<uint2> out((size_t)kNttPrimes * 3 * L);
+  for (int pi = 0; pi < kNttPrimes; ++pi) {
+    const uint32_t p = kNttP[pi];
+    const uint32_t w = ntt_pow(kNttG[pi], (uint64_t)(p - 1) / (uint64_t)L, p);
+    const uint32_t wi = ntt_pow(w, (uint64_t)(p - 2), p);
+    uint2* tw = out.data() + (size_t)pi * 3 * L;
+    uint2* twi = tw + L;
+    uint2* spec = twi + L;
+    uint32_t a = 1, ai = 1;
+    for (int m = 0; m < L; ++m) {
+      tw[m] = with_shoup(a, p);
+      twi[m] = with_shoup(ai, p);
+      a = mulmod(a, w, p);
+      ai = mulmod(ai, wi, p);
+    }
+    // circulant embedding of the symmetric Toeplitz column, residues mod p
+    std::vector<uint32_t> c(L, 0u);
+    auto res = [&](long long v) { return (uint32_t)(((v % (long long)p) + (long long)p) % (long long)p); };
+    c[0] = res(tq[0]);
+    for (int k = 1; k < n; ++k) c[k] = c[L - k] = res(tq[k]);
+    host_ntt(c, w, p);
+    const uint32_t linv = ntt_pow((uint32_t)L % p, (uint64_t)(p - 2), p);
+    for (int k = 0; k < L; ++k) spec[k] = with_shoup(mulmod(c[k], linv, p), p);
+  }
+  return out;
+}
+
+template <typename K>
+static void exact_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void launch_exact_rows(const double* x, double* tmpx, const uint8_t* phi, double pen, int n1, int n2,
+                       const ExactAxis& ax, const int* gate, cudaStream_t s) {
+  const int npairs = (n2 + 1) / 2;
+  const int F = exact_groups(ax.L, false), gs = exact_stride(ax.L);
+  const size_t sm = (size_t)F * gs * sizeof(uint32_t);
+  auto k = exact_kernel<MODE_APPLY, false, double>;
+  exact_smem(k, sm);
+  k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(x, tmpx, phi, pen, nullptr, nullptr, n1, n2, ax, F, gs, gate,
+                                                      nullptr, nullptr);
+}
+
+template <typename Tout>
+void launch_exact_cols(int mode, const double* x, double* tmpx, const uint8_t* phi, double pen, const double* b,
+                       Tout* out, int n1, int n2, const ExactAxis& ay, const int* gate, double* partials,
+                       SolverState* st, cudaStream_t s) {
+  const int npairs = (n1 + 1) / 2;
+  const int F = exact_groups(ay.L, true), gs = exact_stride(ay.L);
+  const size_t sm = (size_t)F * gs * sizeof(uint32_t);
+  const int grid = (npairs + F - 1) / F;
+  if (mode == MODE_RESIDUAL) {
+    auto k = exact_kernel<MODE_RESIDUAL, true, Tout>;
+    exact_smem(k, sm);
+    k<<<grid, F * (ay.L / 16), sm, s>>>(x, tmpx, phi, pen, b, out, n1, n2, ay, F, gs, gate, partials, st);
+    return;
+  }
+  if constexpr (std::is_same<Tout, double>::value) {
+    if (mode == MODE_RESID_ONLY) {
+      auto k = exact_kernel<MODE_RESID_ONLY, true, double>;
+      exact_smem(k, sm);
+      k<<<grid, F * (ay.L / 16), sm, s>>>(x, tmpx, phi, pen, b, out, n1, n2, ay, F, gs, gate, partials, st);
+      return;
+    }
+  }
+  note_unsupported_launch();
+}
+template void launch_exact_cols<double>(int, const double*, double*, const uint8_t*, double, const double*,
+                                        double*, int, int, const ExactAxis&, const int*, double*, SolverState*,
+                                        cudaStream_t);
+template void launch_exact_cols<float>(int, const double*, double*, const uint8_t*, double, const double*, float*,
+                                       int, int, const ExactAxis&, const int*, double*, SolverState*, cudaStream_t);
+
+}  // namespace rsfde

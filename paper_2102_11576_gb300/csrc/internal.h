@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/rsfde.h"
 #include "common.cuh"
 #include "df.cuh"
@@ -114,15 +116,29 @@ int max_groups(int L, int items);
 // nothing and raises a flag that the next launch check reports.
 void note_unsupported_launch();
 bool take_unsupported_launch();
-// tmpx: scratch of N values of the arithmetic type T (A_x z between the passes)
+// tmpx: scratch of N values of the arithmetic type T between the passes:
+// z - A_x z + pen phi z when phi is given, else A_x z
 template <typename T, typename Tin>
-void launch_toeplitz_rows(const Tin* z, void* tmpx, int n1, int n2, const AxisTables<T>& ax, const int* gate,
-                          cudaStream_t s);
+void launch_toeplitz_rows(const Tin* z, void* tmpx, const uint8_t* phi, double pen, int n1, int n2,
+                          const AxisTables<T>& ax, const int* gate, cudaStream_t s);
 // out: Tout = double, or df for a double-FP32 Krylov basis
 template <typename T, typename Tin, typename Tout>
 void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi, double pen,
                           const double* b, Tout* out, int n1, int n2, const AxisTables<T>& ay,
                           const int* gate, double* partials, SolverState* st, cudaStream_t s);
+// Exact Toeplitz products of the true residual (exact.cuh): the row pass
+// writes tmpx = x - A_x x + pen phi x; the column pass MODE_RESIDUAL (Tout
+// double or float, with the norm and restart) or MODE_RESID_ONLY (double).
+// build_exact_tables: the host tables of one axis (Toeplitz column t, length
+// L), 3 L entries per prime in the order tw, twi, spec; *St the quantisation
+// exponent of t.
+std::vector<uint2> build_exact_tables(const std::vector<double>& t, int L, int* St);
+void launch_exact_rows(const double* x, double* tmpx, const uint8_t* phi, double pen, int n1, int n2,
+                       const ExactAxis& ax, const int* gate, cudaStream_t s);
+template <typename Tout>
+void launch_exact_cols(int mode, const double* x, double* tmpx, const uint8_t* phi, double pen, const double* b,
+                       Tout* out, int n1, int n2, const ExactAxis& ay, const int* gate, double* partials,
+                       SolverState* st, cudaStream_t s);
 template <typename T, typename Tin, typename Tout>
 void launch_dst_rows(const Tin* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
                      const int* gate, cudaStream_t s);

@@ -160,12 +160,19 @@ __device__ __forceinline__ void st_pair(X* p, X a, X b) {
 }
 
 // ---------------------------------------------------------------------------
-// Toeplitz product along rows (COLS = false: tmpx = A_x z, MODE_APPLY only) or
-// columns (COLS = true), two vectors per group; tmpx holds A_x z in the
-// arithmetic type T between the two passes.  Column epilogues:
-//   MODE_APPLY:    out = z - tmpx - A_y z + (dt/eta) phi z
-//   MODE_RESIDUAL: out = b - (z - tmpx - A_y z + (dt/eta) phi z), ||out||^2
-//                  reduced, and the last block restarts the solver.
+// Toeplitz product along rows (COLS = false) or columns (COLS = true), two
+// vectors per group.  The row pass writes the scratch tmpx in the arithmetic
+// type T:
+//   MODE_RAW:      tmpx = A_x z
+//   other modes:   tmpx = z - A_x z + (dt/eta) phi z   (every term of M z but
+//                  A_y z, so the column pass reads one array besides z's
+//                  column pairs)
+// Column epilogues:
+//   MODE_RAW:        out = A_y z
+//   MODE_APPLY:      out = tmpx - A_y z  (= M z)
+//   MODE_RESID_ONLY: out = b - (tmpx - A_y z)
+//   MODE_RESIDUAL:   out = b - (tmpx - A_y z), ||out||^2 reduced, and the
+//                    last block restarts the solver.
 //
 // The residual's ||r||^2 is summed per column pair -- each thread's terms in
 // a fixed order, then the group's threads by a fixed tree over t, then the
@@ -244,13 +251,8 @@ __device__ __forceinline__ void toeplitz_body(const Tin* __restrict__ z, T* __re
             const int pos = gi.t + k * Lq;
             if (pos >= len) continue;
             const size_t p = vaddr<COLS>(a, pos, n1);
-            const Pair<Tin> z2 = ld_pair(z + p);
             const Pair<T> t2 = ld_pair(tmpx + p);
-            const Pair<uint8_t> f2 = ld_pair(phi + p);
-            const T zz0 = cvt<T>(z2.x), zz1 = cvt<T>(z2.y);
-            T w0 = zz0 - t2.x - v[k].r, w1 = zz1 - t2.y - v[k].i;
-            if (f2.x) w0 = w0 + tpen * zz0;
-            if (f2.y) w1 = w1 + tpen * zz1;
+            const T w0 = t2.x - v[k].r, w1 = t2.y - v[k].i;
             if constexpr (MODE == MODE_APPLY) {
               st_pair(out + p, cvt<Tout>(w0), cvt<Tout>(w1));
             } else {
@@ -275,12 +277,17 @@ __device__ __forceinline__ void toeplitz_body(const Tin* __restrict__ z, T* __re
           const size_t p = vaddr<COLS>(a + h, pos, n1);
           const T az = h ? v[k].i : v[k].r;
           if (!COLS) {
-            tmpx[p] = az;  // A_x z, kept in the arithmetic type T
+            if (MODE == MODE_RAW) {
+              tmpx[p] = az;  // A_x z, kept in the arithmetic type T
+            } else {
+              const T zz = cvt<T>(z[p]);  // (the pass read this row at the start: an L1 or L2 hit)
+              T sx = zz - az;
+              if (phi[p]) sx = sx + tpen * zz;
+              tmpx[p] = sx;
+            }
           } else {
-            // z - A_x z - A_y z + (dt/eta) phi z in T; only the result is rounded to Tout
-            const T zz = cvt<T>(z[p]);
-            T w = zz - tmpx[p] - az;
-            if (phi[p]) w = w + tpen * zz;
+            // M z = (z - A_x z + (dt/eta) phi z) - A_y z in T; only the result is rounded to Tout
+            const T w = MODE == MODE_RAW ? az : tmpx[p] - az;
             if (MODE == MODE_RAW) {
               out[p] = cvt<Tout>(az);
             } else if (MODE == MODE_APPLY) {
@@ -573,15 +580,17 @@ static void set_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// phi != nullptr: tmpx = z - A_x z + pen phi z (ahead of a MODE_APPLY,
+// MODE_RESIDUAL or MODE_RESID_ONLY column pass); phi == nullptr: tmpx = A_x z.
 template <typename T, typename Tin>
-void launch_toeplitz_rows(const Tin* z, void* tmpx, int n1, int n2, const AxisTables<T>& ax, const int* gate,
-                          cudaStream_t s) {
+void launch_toeplitz_rows(const Tin* z, void* tmpx, const uint8_t* phi, double pen, int n1, int n2,
+                          const AxisTables<T>& ax, const int* gate, cudaStream_t s) {
   const int npairs = (n2 + 1) / 2;
   const int F = pick_groups<T>(ax.L, npairs, TK_TOEP_ROWS);
   const size_t sm = group_smem<T>(ax.L, F, false);
-  auto k = toeplitz_kernel<T, Tin, MODE_APPLY, false, double>;
+  auto k = phi ? toeplitz_kernel<T, Tin, MODE_APPLY, false, double> : toeplitz_kernel<T, Tin, MODE_RAW, false, double>;
   set_smem(k, sm);
-  k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), nullptr, 0.0, nullptr, nullptr,
+  k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(z, static_cast<T*>(tmpx), phi, pen, nullptr, nullptr,
                                                       n1, n2, ax, F, group_stride<T>(ax.L, F, false), gate,
                                                       nullptr, nullptr);
 }
@@ -717,7 +726,8 @@ __device__ __forceinline__ void multi_loop_fft(const BatchInst* __restrict__ bi,
   }
 }
 
-// w_j = M z_j for every instance (MODE_APPLY; rows write the scratch).
+// w_j = M z_j for every instance (MODE_APPLY; rows write z - A_x z + pen phi z
+// into the scratch).
 template <typename T, typename Tz, typename Tv, bool COLS>
 __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) operator_multi_kernel(const BatchInst* __restrict__ bi,
                                                                        const int* __restrict__ prefix,
@@ -734,7 +744,8 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) operato
   });
 }
 
-// V_0 = b - M x and the restart decision (rows: A_x x into the scratch).
+// V_0 = b - M x and the restart decision (rows: x - A_x x + pen phi x into the
+// scratch).
 template <typename T, typename Tv, bool COLS>
 __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) residual_multi_kernel(const BatchInst* __restrict__ bi,
                                                                        const int* __restrict__ prefix,
@@ -748,7 +759,7 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) residua
                                                         reinterpret_cast<Tv*>(I.V), I.n1, I.n2, ax, F, gs,
                                                         &I.st->run_cycle, I.partials, I.st, lb, nb);
     else
-      toeplitz_body<T, double, MODE_APPLY, false, double>(I.x, static_cast<T*>(I.tmpx), nullptr, 0.0, nullptr,
+      toeplitz_body<T, double, MODE_APPLY, false, double>(I.x, static_cast<T*>(I.tmpx), I.phi, I.pen, nullptr,
                                                           nullptr, I.n1, I.n2, ax, F, gs, &I.st->run_cycle, nullptr,
                                                           nullptr, lb, nb);
   });

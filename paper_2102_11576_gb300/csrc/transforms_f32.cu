@@ -10,7 +10,8 @@ namespace rsfde {
                                                    Tout*, int, int, const AxisTables<T>&, const int*, double*,    \
                                                    SolverState*, cudaStream_t);
 #define RSFDE_TOEP_ROWS(T, Tin) \
-  template void launch_toeplitz_rows<T, Tin>(const Tin*, void*, int, int, const AxisTables<T>&, const int*, cudaStream_t);
+  template void launch_toeplitz_rows<T, Tin>(const Tin*, void*, const uint8_t*, double, int, int,   \
+                                              const AxisTables<T>&, const int*, cudaStream_t);
 #define RSFDE_DST_ROWS(T, Tin, Tout)                                                                        \
   template void launch_dst_rows<T, Tin, Tout>(const Tin*, const double*, Tout*, int, int, const AxisTables<T>&, \
                                               const int*, cudaStream_t);
