@@ -54,7 +54,7 @@ extern "C" {
  *    Gram-Schmidt orthogonalisation, RSFDE_FP64 (any operator), RSFDE_DF32
  *    (with the double-FP32 operator) or RSFDE_FP32 (with the FP32 operator);
  *  - resid_prec: the arithmetic of M x in the true residual b - M x that
- *    decides convergence, RSFDE_FP64 or RSFDE_DF32.
+ *    decides convergence, RSFDE_FP64, RSFDE_EXACT or RSFDE_DF32.
  * The Hessenberg matrix, the Givens least squares, the solution x and the
  * subtraction b - M x and its norm are FP64 in every mode.  Flexible GMRES
  * tolerates the inexact preconditioner.  With every choice FP64 except the
@@ -73,6 +73,18 @@ extern "C" {
  * error-free transforms of Dekker and Knuth) for the operator, the Krylov
  * basis or the M x of the true residual. */
 #define RSFDE_DF32 2
+/* True residual only: the Toeplitz products of M x (Eq. 2.14-2.16) computed
+ * exactly in integer arithmetic -- each row or column of x scaled by a power
+ * of two to integers below 2^55, the Toeplitz column to integers whose row
+ * sums stay below 2^63, the convolution (an integer below 2^118) by
+ * number-theoretic transforms modulo four 30-bit primes and the Chinese
+ * remainder theorem -- then rounded to FP64 (53 bits, truncated).  Its only
+ * errors are the two scalings (2^-54 of each vector's largest entry; 2^-63
+ * of the Toeplitz row sum per coefficient) and that final rounding: below
+ * the rounding error bounds of FP64 evaluation.  The rest of b - M x and its
+ * norm are FP64 arithmetic.  It runs on the integer pipes, which GB300 has
+ * in far greater number than FP64 units. */
+#define RSFDE_EXACT 5
 
 /* Krylov variant.  RSFDE_FGMRES_RIGHT (default): right-preconditioned flexible
  * GMRES, stop when the true ||b - M x||_2 <= tol ||b||_2.  RSFDE_GMRES_LEFT:
@@ -110,12 +122,13 @@ typedef struct {
                            loop (one host synchronisation per solve); 0: direct launches with
                            one host check per cycle.  Profiling always uses direct launches. */
   void* stream;         /* cudaStream_t; NULL = the legacy default stream */
-  int32_t resid_prec;   /* RSFDE_FP64 (default) | RSFDE_DF32: arithmetic of M x in the true
-                           residual b - M x that decides convergence (right-preconditioned
-                           FGMRES; paper mode always FP64).  b - M x and its norm are FP64 either
-                           way.  Double-FP32 carries ~48 significant bits: its rounding error is
-                           a few units of 1e-14 times |M||x|, far below a 1e-10 tolerance, but it
-                           is not FP64 arithmetic. */
+  int32_t resid_prec;   /* RSFDE_FP64 (default) | RSFDE_EXACT | RSFDE_DF32: arithmetic of M x in
+                           the true residual b - M x that decides convergence (paper mode: FP64
+                           or exact; double-FP32 is taken as FP64 there).  b - M x and its norm
+                           are FP64 in every case.  RSFDE_EXACT needs an FP64 or FP32 basis.
+                           Double-FP32 carries ~48 significant bits: its rounding error is a few
+                           units of 1e-14 times |M||x|, far below a 1e-10 tolerance, but it is
+                           not FP64 arithmetic. */
   int32_t basis_prec;   /* RSFDE_FP64 (default) | RSFDE_DF32 | RSFDE_FP32: Krylov basis storage and
                            Gram-Schmidt arithmetic (right-preconditioned FGMRES; paper mode always
                            FP64).  RSFDE_DF32 needs matvec_prec RSFDE_DF32, RSFDE_FP32 needs
@@ -235,6 +248,10 @@ void rsfde_batch_destroy(rsfde_batch* b);
 /* Eq. 2.14-2.17: w = M z in the context's operator precision (matvec_prec).
  * z, w device N doubles (distinct). */
 int rsfde_apply_M(rsfde_ctx* ctx, const double* z, double* w);
+/* The true residual r = b - M x (Eq. 2.17's system) with M x in the context's
+ * resid_prec, RSFDE_FP64 or RSFDE_EXACT (RSFDE_DF32: RSFDE_EINVAL).  x, b, r
+ * device N doubles (r distinct from x and b). */
+int rsfde_residual(rsfde_ctx* ctx, const double* x, const double* b, double* r);
 /* Eq. 4.6: z = P-hat^-1 v in the context's preconditioner precision (result in FP64). */
 int rsfde_apply_precond(rsfde_ctx* ctx, const double* v, double* z);
 /* Section 4.1: out = (S_{n2} (x) S_{n1}) v, the orthonormal 2D sine transform, FP64. */

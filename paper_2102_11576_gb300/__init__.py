@@ -16,16 +16,17 @@ import os
 
 import numpy as np
 
-__all__ = ["Solver", "Batch", "RsfdeError", "load_library", "LIB_PATH", "FP64", "FP32", "DF32"]
+__all__ = ["Solver", "Batch", "RsfdeError", "load_library", "LIB_PATH", "FP64", "FP32", "DF32", "EXACT"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librsfde.so")
 
 FP64, FP32, DF32 = 0, 1, 2
+EXACT = 5  # true residual only: exact integer Toeplitz products, rounded to FP64
 _VARIANTS = {"fgmres_right": 0, "gmres_left": 1}
 _PRECONDS = {"fp64": 0, "fp32": 1, "bf16x3": 3, "bf16": 4}
 _MATVECS = {"fp64": FP64, "df32": DF32, "fp32": FP32}
-_RESIDS = {"fp64": FP64, "df32": DF32}
+_RESIDS = {"fp64": FP64, "df32": DF32, "exact": EXACT}
 _BASES = {"fp64": FP64, "df32": DF32, "fp32": FP32}
 CGS, CGS2 = 0, 1
 _ERR = {0: "ok", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV", -5: "ENONFINITE",
@@ -92,6 +93,7 @@ def load_library(path=LIB_PATH):
     lib.rsfde_step_host.argtypes = [vp, dp, dp, dp, dp, ctypes.POINTER(_Stats)]
     lib.rsfde_adjoint.argtypes = [vp, dp, dp, ctypes.POINTER(_Stats)]
     lib.rsfde_apply_M.argtypes = [vp, dp, dp]
+    lib.rsfde_residual.argtypes = [vp, dp, dp, dp]
     lib.rsfde_apply_precond.argtypes = [vp, dp, dp]
     lib.rsfde_dst2.argtypes = [vp, dp, dp]
     lib.rsfde_rhs.argtypes = [vp, dp, dp, dp, dp, dp]
@@ -242,6 +244,13 @@ class Solver:
     def apply_M(self, z, out=None):
         out = self.empty() if out is None else out
         _check(self._lib.rsfde_apply_M(self._h, _ptr(self._grid(z, "z")), _ptr(out)), "apply_M")
+        return out
+
+    def residual(self, x, b, out=None):
+        """r = b - M x with M x in the solver's resid precision ("fp64" or "exact")."""
+        out = self.empty() if out is None else out
+        _check(self._lib.rsfde_residual(self._h, _ptr(self._grid(x, "x")), _ptr(self._grid(b, "b")),
+                                        _ptr(out)), "residual")
         return out
 
     def apply_precond(self, v, out=None):

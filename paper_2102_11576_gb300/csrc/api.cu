@@ -176,6 +176,38 @@ struct DevAxis {
   }
 };
 
+// Device copy of one axis' exact-product tables (one allocation).
+struct DevExact {
+  void* mem = nullptr;
+  size_t bytes = 0;
+  ExactAxis tab{};
+  void release() {
+    if (mem) cudaFree(mem);
+    mem = nullptr;
+    bytes = 0;
+  }
+  cudaError_t upload(const HostAxis& h, cudaStream_t s) {
+    int St = 0;
+    const std::vector<uint2> t = build_exact_tables(h.t, h.L, &St);
+    const size_t need = t.size() * sizeof(uint2);
+    if (mem && bytes != need) release();
+    if (!mem) {
+      cudaError_t e = cudaMalloc(&mem, need);
+      if (e != cudaSuccess) return e;
+      bytes = need;
+    }
+    cudaError_t e = cudaMemcpyAsync(mem, t.data(), need, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    tab.n = h.n;
+    tab.L = h.L;
+    tab.log2L = h.log2L;
+    tab.St = St;
+    tab.tab = static_cast<const uint2*>(mem);
+    return e;
+  }
+};
+
 }  // namespace
 
 struct rsfde_ctx {
@@ -190,6 +222,7 @@ struct rsfde_ctx {
   int m_alloc = 0;
   HostAxis hx_axis, hy_axis;
   DevAxis<double> x64, y64;
+  DevExact xex, yex;  // exact Toeplitz products of the true residual
   DevAxis<float> x32, y32;
   DevAxis<df> xdf, ydf;
   uint8_t* phi = nullptr;
@@ -300,6 +333,8 @@ int build_tables(rsfde_ctx* c) {
   if ((e = c->y32.upload(c->hy_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
   if ((e = c->xdf.upload(c->hx_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
   if ((e = c->ydf.upload(c->hy_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
+  if ((e = c->xex.upload(c->hx_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
+  if ((e = c->yex.upload(c->hy_axis, c->stream)) != cudaSuccess) return cuda_fail(e);
   return RSFDE_OK;
 }
 
@@ -316,6 +351,8 @@ void free_ctx(rsfde_ctx* c) {
   c->y32.release();
   c->xdf.release();
   c->ydf.release();
+  c->xex.release();
+  c->yex.release();
   void* ptrs[] = {c->phi, c->V, c->Z, c->tmpx, c->T1, c->T2a, c->T2b, c->b, c->x, c->hbuf, c->partials, c->st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -418,17 +455,27 @@ void enqueue_precond64(rsfde_ctx* c, const double* v, const double* vscale, doub
 
 // Left-preconditioned GMRES: V_0 = P^-1 (b - M x) (or b - M x without a
 // preconditioner), beta = ||V_0||, then restart_prep.
-void enqueue_residual_left(rsfde_ctx* c, const int* gate) {
-  double* r = c->opts.use_precond ? static_cast<double*>(c->Z) : c->V;
+// r = b - M x (no norm) with M x in FP64 or, for resid_prec RSFDE_EXACT, exact
+// Toeplitz products.
+void enqueue_resid_only(rsfde_ctx* c, const double* x, const double* b, double* r, const int* gate) {
+  const bool exact = c->opts.resid_prec == RSFDE_EXACT;
   {
     ProfScope ps(c, RSFDE_K_RESID_ROWS);
-    launch_toeplitz_rows<double, double>(c->x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->x64.tab, gate, c->stream);
+    if (exact) launch_exact_rows(x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->xex.tab, gate, c->stream);
+    else launch_toeplitz_rows<double, double>(x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->x64.tab, gate, c->stream);
   }
-  {
-    ProfScope ps(c, RSFDE_K_RESID_COLS);
-    launch_toeplitz_cols<double, double>(MODE_RESID_ONLY, c->x, c->tmpx, c->phi, c->pen, c->b, r, c->n1, c->n2,
+  ProfScope ps(c, RSFDE_K_RESID_COLS);
+  if (exact)
+    launch_exact_cols<double>(MODE_RESID_ONLY, x, c->tmpx, c->phi, c->pen, b, r, c->n1, c->n2, c->yex.tab, gate,
+                              nullptr, nullptr, c->stream);
+  else
+    launch_toeplitz_cols<double, double>(MODE_RESID_ONLY, x, c->tmpx, c->phi, c->pen, b, r, c->n1, c->n2,
                                          c->y64.tab, gate, nullptr, nullptr, c->stream);
-  }
+}
+
+void enqueue_residual_left(rsfde_ctx* c, const int* gate) {
+  double* r = c->opts.use_precond ? static_cast<double*>(c->Z) : c->V;
+  enqueue_resid_only(c, c->x, c->b, r, gate);
   if (c->opts.use_precond) enqueue_precond64(c, r, nullptr, c->V, gate);
   ProfScope ps(c, RSFDE_K_OTHER);
   launch_restart_norm(c->V, c->N, c->partials, c->st, gate, c->stream);
@@ -467,12 +514,28 @@ void enqueue_residual_t(rsfde_ctx* c, const int* gate, const AxisTables<T>& tx, 
                                             ty, gate, c->partials, c->st, c->stream);
 }
 
+// V_0 = b - M x with exact Toeplitz products, beta = ||V_0||, restart_prep.
+void enqueue_residual_exact(rsfde_ctx* c, const int* gate) {
+  {
+    ProfScope ps(c, RSFDE_K_RESID_ROWS);
+    launch_exact_rows(c->x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->xex.tab, gate, c->stream);
+  }
+  ProfScope ps(c, RSFDE_K_RESID_COLS);
+  if (basis_kind(c) == BASIS_FP32)
+    launch_exact_cols<float>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, reinterpret_cast<float*>(c->V),
+                             c->n1, c->n2, c->yex.tab, gate, c->partials, c->st, c->stream);
+  else
+    launch_exact_cols<double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1, c->n2, c->yex.tab,
+                              gate, c->partials, c->st, c->stream);
+}
+
 void enqueue_residual(rsfde_ctx* c, const int* gate) {
   if (left_variant(c)) {
     enqueue_residual_left(c, gate);
     return;
   }
   if (c->opts.resid_prec == RSFDE_DF32) enqueue_residual_t<df>(c, gate, c->xdf.tab, c->ydf.tab);
+  else if (c->opts.resid_prec == RSFDE_EXACT) enqueue_residual_exact(c, gate);
   else enqueue_residual_t<double>(c, gate, c->x64.tab, c->y64.tab);
 }
 
@@ -631,7 +694,7 @@ void enqueue_cycle(rsfde_ctx* c) {
 int graph_key(const rsfde_ctx* c) {
   const rsfde_opts& o = c->opts;
   int k = o.basis_prec;
-  k = k * 2 + (o.resid_prec == RSFDE_DF32 ? 1 : 0);
+  k = k * 3 + (o.resid_prec == RSFDE_DF32 ? 1 : o.resid_prec == RSFDE_EXACT ? 2 : 0);
   k = k * 65 + o.restart;
   k = k * 5 + o.precond_prec;
   k = k * 4 + o.matvec_prec;
@@ -1394,7 +1457,9 @@ static int valid_opts(const rsfde_opts* o) {
   if (o->arnoldi != RSFDE_CGS && o->arnoldi != RSFDE_CGS2) return 0;
   if (o->matvec_prec != RSFDE_FP64 && o->matvec_prec != RSFDE_DF32 && o->matvec_prec != RSFDE_FP32) return 0;
   if (o->variant != RSFDE_FGMRES_RIGHT && o->variant != RSFDE_GMRES_LEFT) return 0;
-  if (o->resid_prec != RSFDE_FP64 && o->resid_prec != RSFDE_DF32) return 0;
+  if (o->resid_prec != RSFDE_FP64 && o->resid_prec != RSFDE_DF32 && o->resid_prec != RSFDE_EXACT) return 0;
+  // the exact residual writes an FP64 or FP32 first basis vector
+  if (o->resid_prec == RSFDE_EXACT && o->basis_prec == RSFDE_DF32) return 0;
   // the basis stores the operator's output: FP64 takes any operator, the
   // double-FP32 and FP32 bases only their own
   if (o->basis_prec != RSFDE_FP64 && o->basis_prec != o->matvec_prec) return 0;
@@ -1602,6 +1667,13 @@ int rsfde_adjoint_step(rsfde_ctx* c, const double* u_prev, const double* u_k, co
 int rsfde_apply_M(rsfde_ctx* c, const double* z, double* w) {
   if (!c || !z || !w) return RSFDE_EINVAL;
   enqueue_apply_M<double>(c, z, w, nullptr);
+  return check_launch(c);
+}
+
+int rsfde_residual(rsfde_ctx* c, const double* x, const double* b, double* r) {
+  if (!c || !x || !b || !r || r == x || r == b) return RSFDE_EINVAL;
+  if (c->opts.resid_prec == RSFDE_DF32) return RSFDE_EINVAL;
+  enqueue_resid_only(c, x, b, r, nullptr);
   return check_launch(c);
 }
 

@@ -72,15 +72,14 @@ struct AxisTables {
 };
 
 // Tables of the exact Toeplitz product along one axis (exact.cuh): for each of
-// the four primes, the Stockham twiddles of w = g^((p-1)/L) and of w^-1, and
-// the transform of the quantised circulant column times L^-1 (natural order),
-// each entry {value, Shoup companion floor(value 2^32 / p)}.
+// the four primes i, at tab + 3 i L: the L Stockham twiddles of w =
+// g^((p-1)/L), then those of w^-1, then the transform of the quantised
+// circulant column times L^-1 (natural order); each entry {value, Shoup
+// companion floor(value 2^32 / p)}.
 struct ExactAxis {
   int n, L, log2L;
   int St;  // the Toeplitz column was quantised as round(t 2^St), |t_q| < 2^52
-  const uint2* tw[4];
-  const uint2* twi[4];
-  const uint2* spec[4];
+  const uint2* tab;
 };
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {

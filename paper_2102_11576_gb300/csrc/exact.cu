@@ -41,11 +41,27 @@ uint2 with_shoup(uint32_t w, uint32_t p) { return make_uint2(w, ntt_shoup(w, p))
 
 std::vector<uint2> build_exact_tables(const std::vector<double>& t, int L, int* St) {
   const int n = (int)t.size();
-  double mx = 0.0;
-  for (double v : t) mx = std::fmax(mx, std::fabs(v));
-  *St = mx > 0.0 ? 51 - std::ilogb(mx) : 0;  // mx 2^St < 2^52
-  std::vector<long long> tq(n);
-  for (int k = 0; k < n; ++k) tq[k] = std::llround(std::ldexp(t[k], *St));
+  // largest St with T1_q = |t_q[0]| + 2 sum_{k>=1} |t_q[k]| < 2^63 (a bound on
+  // every row's absolute sum), so that |sum_l t_q x_q| < 2^63 2^55 = 2^118,
+  // below half the primes' product
+  double t1 = std::fabs(t[0]);
+  for (int k = 1; k < n; ++k) t1 += 2.0 * std::fabs(t[k]);
+  std::vector<long long> tq(n, 0);
+  *St = 0;
+  if (t1 > 0.0) {
+    for (int s = 62 - std::ilogb(t1);; --s) {
+      unsigned __int128 sum = 0;
+      for (int k = 0; k < n; ++k) {
+        tq[k] = std::llround(std::ldexp(t[k], s));
+        const unsigned long long a = (unsigned long long)(tq[k] < 0 ? -tq[k] : tq[k]);
+        sum += (unsigned __int128)a * (k ? 2u : 1u);
+      }
+      if (sum < ((unsigned __int128)1 << 63)) {
+        *St = s;
+        break;
+      }
+    }
+  }
   std::vector<uint2> out((size_t)kNttPrimes * 3 * L);
   for (int pi = 0; pi < kNttPrimes; ++pi) {
     const uint32_t p = kNttP[pi];
@@ -82,7 +98,7 @@ void launch_exact_rows(const double* x, double* tmpx, const uint8_t* phi, double
                        const ExactAxis& ax, const int* gate, cudaStream_t s) {
   const int npairs = (n2 + 1) / 2;
   const int F = exact_groups(ax.L, false), gs = exact_stride(ax.L);
-  const size_t sm = (size_t)F * gs * sizeof(uint32_t);
+  const size_t sm = exact_smem_bytes(ax.L, F);
   auto k = exact_kernel<MODE_APPLY, false, double>;
   exact_smem(k, sm);
   k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(x, tmpx, phi, pen, nullptr, nullptr, n1, n2, ax, F, gs, gate,
@@ -95,7 +111,7 @@ void launch_exact_cols(int mode, const double* x, double* tmpx, const uint8_t* p
                        SolverState* st, cudaStream_t s) {
   const int npairs = (n1 + 1) / 2;
   const int F = exact_groups(ay.L, true), gs = exact_stride(ay.L);
-  const size_t sm = (size_t)F * gs * sizeof(uint32_t);
+  const size_t sm = exact_smem_bytes(ay.L, F);
   const int grid = (npairs + F - 1) / F;
   if (mode == MODE_RESIDUAL) {
     auto k = exact_kernel<MODE_RESIDUAL, true, Tout>;

@@ -3,24 +3,24 @@
 //
 // GB300 executes FP64 at 1/64 of its FP32/INT32 rate, so an FP64 FFT of the
 // residual is bound by the FP64 pipe.  Here each vector x (a row or a column
-// of the grid) is scaled by a power of two to integers below 2^52 in
-// magnitude (x_q = trunc(x 2^(1074-E)), E the largest biased exponent in the
-// vector), the Toeplitz column t likewise on the host (t_q = round(t 2^St),
-// |t_q| < 2^52), and the convolution sum_l t_q[|i-l|] x_q[l] -- an integer
-// below n 2^104 <= 2^116 in magnitude for n <= 4096 -- is computed exactly
-// modulo four primes p < 2^30 (product ~2^120) by number-theoretic transforms
-// of length L >= 2n-1, then reconstructed by Garner's mixed-radix form of the
-// Chinese remainder theorem and scaled back to FP64 (truncated to 53 bits).
-// The product's only errors are the two quantisations (|x - x_q 2^(E-1074)|
-// < 2^-51 max|x|, t likewise) and the final truncation: smaller than the
-// rounding of an FP64 FFT, whose error grows with log2 L.  What follows the
-// product (z - A_x z + (dt/eta) phi z, b - ..., ||r||^2) is FP64 arithmetic.
+// of the grid) is scaled by a power of two to integers x_q below 2^55 in
+// magnitude (E the largest biased exponent in the vector: x_q = trunc(x
+// 2^(1077-E))), the Toeplitz column t on the host to integers t_q =
+// round(t 2^St) whose row sum T1_q = |t_q[0]| + 2 sum_k |t_q[k]| is below
+// 2^63, so the convolution sum_l t_q[|i-l|] x_q[l] is an integer below 2^118
+// in magnitude.  It is computed exactly modulo four primes p < 2^30 (product
+// > 2^119.99) by number-theoretic transforms of length L >= 2n-1, then
+// reconstructed by Garner's mixed-radix form of the Chinese remainder theorem
+// and scaled back to FP64 (truncated to 53 bits).  The product's only errors
+// are the two scalings (|x - x_q 2^(E-1077)| < 2^-54 max|x|; each t_k within
+// 2^-63 T1) and the final truncation -- below the rounding error bounds of
+// FP64 evaluation, direct or by FFT.  What follows the product (x - A_x x +
+// (dt/eta) phi x, b - ..., ||r||^2) is FP64 arithmetic.
 //
 // Transforms: the register-resident Stockham layout of fft16.cuh (a group of
 // L/16 threads, thread t holding positions t + k L/16), with values in
 // [0, p), Shoup's multiplication by precomputed constants (w, floor(w 2^32 /
-// p)) and radix-16/8/4/2 butterflies whose internal roots of unity are
-// compile-time constants of each prime.  NTT_p(x)[k] = sum_j x_j w^(jk) with
+// p)) and radix-16/8/4/2 butterflies.  NTT_p(x)[k] = sum_j x_j w^(jk) with
 // w = g^((p-1)/L), g a generator of Z_p^*.
 #pragma once
 #include <stdint.h>
@@ -67,43 +67,113 @@ __device__ __forceinline__ uint32_t redq(uint32_t a, uint32_t p) {  // a < 2p
   return min(a, a - p);
 }
 
-// times W16^K (forward) or W16^-K (inverse), W16 = g^((p-1)/16) = w^(L/16)
-template <int PI, bool INV, int K>
-__device__ __forceinline__ uint32_t nrot(uint32_t a) {
-  constexpr uint32_t p = kNttP[PI];
-  constexpr uint32_t w16 = ntt_pow(kNttG[PI], (p - 1) / 16, p);
-  constexpr uint32_t w = ntt_pow(w16, INV ? (16 - K) % 16 : K, p);
-  constexpr uint32_t wq = ntt_shoup(w, p);
-  return mulq(a, w, wq, p);
+// Table entry through the read-only path, issued where it is written: the
+// twiddle and spectrum reads are the same for every vector a block
+// transforms, and hoisting them out of the vector loops would hold ~100
+// registers.
+__device__ __forceinline__ uint2 ld_tab(const uint2* p) {
+  uint2 r;
+  asm volatile("ld.global.nc.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+  return r;
+}
+
+// Constants of each prime: p, 2^32 mod p and floor(2^32/p) (for residues),
+// and the powers W16^K (K = 1, 2, 3, 4, 6, 9: the radix-16/8/4 butterflies'
+// internal roots) of W16 = g^((p-1)/16) = w^(L/16), forward and inverse, with
+// Shoup companions.  The prime is a runtime index: one copy of the transform
+// code serves the four primes, and a transform keeps only its own prime's
+// constants in registers.
+struct NttPrimeConsts {
+  uint32_t p, r32, r32q, oneq;
+  uint32_t w[2][6], wq[2][6];
+};
+struct NttConstTable {
+  NttPrimeConsts c[kNttPrimes];
+};
+constexpr NttConstTable make_ntt_consts() {
+  NttConstTable t{};
+  const int ks[6] = {1, 2, 3, 4, 6, 9};
+  for (int i = 0; i < kNttPrimes; ++i) {
+    const uint32_t p = kNttP[i];
+    const uint32_t w16 = ntt_pow(kNttG[i], (p - 1) / 16, p);
+    t.c[i].p = p;
+    t.c[i].r32 = (uint32_t)((1ull << 32) % p);
+    t.c[i].r32q = ntt_shoup(t.c[i].r32, p);
+    t.c[i].oneq = ntt_shoup(1u, p);
+    for (int j = 0; j < 6; ++j)
+      for (int inv = 0; inv < 2; ++inv) {
+        const uint32_t w = ntt_pow(w16, (uint64_t)(inv ? (16 - ks[j]) % 16 : ks[j]), p);
+        t.c[i].w[inv][j] = w;
+        t.c[i].wq[inv][j] = ntt_shoup(w, p);
+      }
+  }
+  return t;
+}
+__constant__ NttConstTable c_ntt = make_ntt_consts();
+
+// One direction's butterfly constants of one prime, in registers.
+struct NttK {
+  uint32_t p;
+  uint32_t w[6], wq[6];
+};
+template <bool INV>
+__device__ __forceinline__ NttK ntt_consts(int q) {
+  NttK k;
+  k.p = c_ntt.c[q].p;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    k.w[j] = c_ntt.c[q].w[INV][j];
+    k.wq[j] = c_ntt.c[q].wq[INV][j];
+  }
+  return k;
+}
+// x and the mask read again in the row epilogue, issued there: otherwise the
+// compiler keeps the first reads of x alive across the four transforms.
+__device__ __forceinline__ double ld_again(const double* p) {
+  double r;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(r) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ uint32_t ld_again(const uint8_t* p) {
+  uint32_t r;
+  asm volatile("ld.global.nc.u8 %0, [%1];" : "=r"(r) : "l"(p));
+  return r;
+}
+
+// times W16^K (K in 1, 2, 3, 4, 6, 9) in the direction K holds
+template <int K>
+__device__ __forceinline__ uint32_t nrot(uint32_t a, const NttK& c) {
+  constexpr int j = K == 1 ? 0 : K == 2 ? 1 : K == 3 ? 2 : K == 4 ? 3 : K == 6 ? 4 : 5;
+  static_assert(K == 1 || K == 2 || K == 3 || K == 4 || K == 6 || K == 9, "stored powers");
+  return mulq(a, c.w[j], c.wq[j], c.p);
 }
 
 // Natural-order DFTs over Z_p on v[0], v[S], ..., v[(R-1)S] (the factorings of
 // fft16.cuh with W4 = W16^4 in place of -i).
-template <int PI, bool INV, int S>
-__device__ __forceinline__ void ndft2(uint32_t* v) {
-  constexpr uint32_t p = kNttP[PI];
+template <int S>
+__device__ __forceinline__ void ndft2(uint32_t* v, const NttK& c) {
   const uint32_t a = v[0], b = v[S];
-  v[0] = addq(a, b, p);
-  v[S] = subq(a, b, p);
+  v[0] = addq(a, b, c.p);
+  v[S] = subq(a, b, c.p);
 }
-template <int PI, bool INV, int S>
-__device__ __forceinline__ void ndft4(uint32_t* v) {
-  constexpr uint32_t p = kNttP[PI];
+template <int S>
+__device__ __forceinline__ void ndft4(uint32_t* v, const NttK& c) {
+  const uint32_t p = c.p;
   const uint32_t t0 = addq(v[0], v[2 * S], p), t1 = subq(v[0], v[2 * S], p);
-  const uint32_t t2 = addq(v[S], v[3 * S], p), t3 = nrot<PI, INV, 4>(subq(v[S], v[3 * S], p));
+  const uint32_t t2 = addq(v[S], v[3 * S], p), t3 = nrot<4>(subq(v[S], v[3 * S], p), c);
   v[0] = addq(t0, t2, p);
   v[2 * S] = subq(t0, t2, p);
   v[S] = addq(t1, t3, p);
   v[3 * S] = subq(t1, t3, p);
 }
-template <int PI, bool INV, int S>
-__device__ __forceinline__ void ndft8(uint32_t* v) {
-  constexpr uint32_t p = kNttP[PI];
-  ndft4<PI, INV, 2 * S>(v);
-  ndft4<PI, INV, 2 * S>(v + S);
-  v[3 * S] = nrot<PI, INV, 2>(v[3 * S]);
-  v[5 * S] = nrot<PI, INV, 4>(v[5 * S]);
-  v[7 * S] = nrot<PI, INV, 6>(v[7 * S]);
+template <int S>
+__device__ __forceinline__ void ndft8(uint32_t* v, const NttK& c) {
+  const uint32_t p = c.p;
+  ndft4<2 * S>(v, c);
+  ndft4<2 * S>(v + S, c);
+  v[3 * S] = nrot<2>(v[3 * S], c);
+  v[5 * S] = nrot<4>(v[5 * S], c);
+  v[7 * S] = nrot<6>(v[7 * S], c);
   uint32_t o[8];
 #pragma unroll
   for (int r1 = 0; r1 < 4; ++r1) {
@@ -113,25 +183,24 @@ __device__ __forceinline__ void ndft8(uint32_t* v) {
 #pragma unroll
   for (int r = 0; r < 8; ++r) v[r * S] = o[r];
 }
-template <int PI, bool INV>
-__device__ __forceinline__ void ndft16(uint32_t* v) {
-  ndft4<PI, INV, 4>(v);
-  ndft4<PI, INV, 4>(v + 1);
-  ndft4<PI, INV, 4>(v + 2);
-  ndft4<PI, INV, 4>(v + 3);
-  v[5] = nrot<PI, INV, 1>(v[5]);
-  v[9] = nrot<PI, INV, 2>(v[9]);
-  v[13] = nrot<PI, INV, 3>(v[13]);
-  v[6] = nrot<PI, INV, 2>(v[6]);
-  v[10] = nrot<PI, INV, 4>(v[10]);
-  v[14] = nrot<PI, INV, 6>(v[14]);
-  v[7] = nrot<PI, INV, 3>(v[7]);
-  v[11] = nrot<PI, INV, 6>(v[11]);
-  v[15] = nrot<PI, INV, 9>(v[15]);
-  ndft4<PI, INV, 1>(v);
-  ndft4<PI, INV, 1>(v + 4);
-  ndft4<PI, INV, 1>(v + 8);
-  ndft4<PI, INV, 1>(v + 12);
+__device__ __forceinline__ void ndft16(uint32_t* v, const NttK& c) {
+  ndft4<4>(v, c);
+  ndft4<4>(v + 1, c);
+  ndft4<4>(v + 2, c);
+  ndft4<4>(v + 3, c);
+  v[5] = nrot<1>(v[5], c);
+  v[9] = nrot<2>(v[9], c);
+  v[13] = nrot<3>(v[13], c);
+  v[6] = nrot<2>(v[6], c);
+  v[10] = nrot<4>(v[10], c);
+  v[14] = nrot<6>(v[14], c);
+  v[7] = nrot<3>(v[7], c);
+  v[11] = nrot<6>(v[11], c);
+  v[15] = nrot<9>(v[15], c);
+  ndft4<1>(v, c);
+  ndft4<1>(v + 4, c);
+  ndft4<1>(v + 8, c);
+  ndft4<1>(v + 12, c);
   uint32_t o[16];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -140,19 +209,19 @@ __device__ __forceinline__ void ndft16(uint32_t* v) {
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = o[r];
 }
-template <int PI, bool INV, int R, int S>
-__device__ __forceinline__ void ndft_r(uint32_t* v) {
-  if (R == 16) ndft16<PI, INV>(v);
-  else if (R == 8) ndft8<PI, INV, S>(v);
-  else if (R == 4) ndft4<PI, INV, S>(v);
-  else ndft2<PI, INV, S>(v);
+template <int R, int S>
+__device__ __forceinline__ void ndft_r(uint32_t* v, const NttK& c) {
+  if (R == 16) ndft16(v, c);
+  else if (R == 8) ndft8<S>(v, c);
+  else if (R == 4) ndft4<S>(v, c);
+  else ndft2<S>(v, c);
 }
 
 // One Stockham pass (the index arithmetic of fft_pass); tw: {w^m, Shoup} of
-// the forward (w) or inverse (w^-1) root.
-template <int PI, bool INV, int R>
-__device__ __forceinline__ void ntt_pass(uint32_t* v, int t, int L, int Ns, const uint2* __restrict__ tw) {
-  constexpr uint32_t p = kNttP[PI];
+// the forward (w) or inverse (w^-1) root, matching the direction of c.
+template <int R>
+__device__ __forceinline__ void ntt_pass(uint32_t* v, int t, int L, int Ns, const uint2* __restrict__ tw,
+                                         const NttK& c) {
   constexpr int S = 16 / R;
   const int Lq = L >> 4;
 #pragma unroll
@@ -162,11 +231,11 @@ __device__ __forceinline__ void ntt_pass(uint32_t* v, int t, int L, int Ns, cons
       const int step = (j & (Ns - 1)) * (L / (Ns * R));
 #pragma unroll
       for (int q = 1; q < R; ++q) {
-        const uint2 w = __ldg(tw + q * step);
-        v[i + q * S] = mulq(v[i + q * S], w.x, w.y, p);
+        const uint2 w = ld_tab(tw + q * step);
+        v[i + q * S] = mulq(v[i + q * S], w.x, w.y, c.p);
       }
     }
-    ndft_r<PI, INV, R, S>(v + i);
+    ndft_r<R, S>(v + i, c);
   }
 }
 
@@ -190,70 +259,67 @@ __device__ __forceinline__ void ntt_exchange(uint32_t* v, uint32_t* buf, int t, 
 
 // Forward transform of a sequence that is zero on positions >= L/2 (k >= 8);
 // spectrum in natural order at the thread's positions.  Block-uniform L.
-template <int PI>
 __device__ __forceinline__ void ntt16_forward(uint32_t* v, uint32_t* buf, int t, int L, int log2L,
-                                              const uint2* __restrict__ tw) {
+                                              const uint2* __restrict__ tw, const NttK& c) {
 #pragma unroll
   for (int k = 8; k < 16; ++k) v[k] = 0u;
   const int small = log2L & 3, n16 = log2L >> 2;
   int Ns = 1;
   if (small == 1) {
-    ntt_pass<PI, false, 2>(v, t, L, Ns, tw);
+    ntt_pass<2>(v, t, L, Ns, tw, c);
     ntt_exchange<2>(v, buf, t, L, Ns);
     Ns = 2;
   } else if (small == 2) {
-    ntt_pass<PI, false, 4>(v, t, L, Ns, tw);
+    ntt_pass<4>(v, t, L, Ns, tw, c);
     ntt_exchange<4>(v, buf, t, L, Ns);
     Ns = 4;
   } else if (small == 3) {
-    ntt_pass<PI, false, 8>(v, t, L, Ns, tw);
+    ntt_pass<8>(v, t, L, Ns, tw, c);
     ntt_exchange<8>(v, buf, t, L, Ns);
     Ns = 8;
   }
   for (int q = 0; q < n16; ++q) {
-    ntt_pass<PI, false, 16>(v, t, L, Ns, tw);
+    ntt_pass<16>(v, t, L, Ns, tw, c);
     if (q + 1 < n16) ntt_exchange<16>(v, buf, t, L, Ns);
     Ns <<= 4;
   }
 }
 // Inverse (unnormalised) from the forward's layout; positions < L/2 are read.
-template <int PI>
 __device__ __forceinline__ void ntt16_inverse(uint32_t* v, uint32_t* buf, int t, int L, int log2L,
-                                              const uint2* __restrict__ twi) {
+                                              const uint2* __restrict__ twi, const NttK& c) {
   const int small = log2L & 3, n16 = log2L >> 2;
   int Ns = 1;
   for (int q = 0; q < n16; ++q) {
-    ntt_pass<PI, true, 16>(v, t, L, Ns, twi);
+    ntt_pass<16>(v, t, L, Ns, twi, c);
     if (q + 1 < n16 || small) ntt_exchange<16>(v, buf, t, L, Ns);
     Ns <<= 4;
   }
-  if (small == 1) ntt_pass<PI, true, 2>(v, t, L, Ns, twi);
-  else if (small == 2) ntt_pass<PI, true, 4>(v, t, L, Ns, twi);
-  else if (small == 3) ntt_pass<PI, true, 8>(v, t, L, Ns, twi);
+  if (small == 1) ntt_pass<2>(v, t, L, Ns, twi, c);
+  else if (small == 2) ntt_pass<4>(v, t, L, Ns, twi, c);
+  else if (small == 3) ntt_pass<8>(v, t, L, Ns, twi, c);
 }
 
-// x_q = trunc(|x| 2^(1074 - E)) with E >= the biased exponent of x (E >= 1):
-// the significand shifted right by E - e + 1 (e the biased exponent, taken
-// as 1 for subnormals), below 2^52.
+// x_q = trunc(|x| 2^(1077 - E)) for E >= the biased exponent of x (E >= 1):
+// the 53-bit significand (e the biased exponent, taken as 1 for subnormals)
+// times 2^(e - E + 2), below 2^55.
 __device__ __forceinline__ uint64_t quantize(double x, int E) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int e = (int)((b >> 52) & 0x7FF);
   const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
   const unsigned long long mag = e ? (m | (1ull << 52)) : m;
-  const int sh = E - (e ? e : 1) + 1;
+  const int sh = E - (e ? e : 1) - 2;
+  if (sh < 0) return mag << (-sh);
   return sh < 64 ? mag >> sh : 0ull;
 }
 __device__ __forceinline__ int biased_exponent(double x) {
   return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// q mod p for q < 2^52 (negated when neg): q = h 2^32 + l, h < 2^20.
-template <int PI>
-__device__ __forceinline__ uint32_t residue(uint64_t q, bool neg) {
-  constexpr uint32_t p = kNttP[PI];
-  constexpr uint32_t r32 = (uint32_t)((1ull << 32) % p);
-  constexpr uint32_t r32q = ntt_shoup(r32, p), oneq = ntt_shoup(1u, p);
-  const uint32_t r = addq(mulq((uint32_t)(q >> 32), r32, r32q, p), mulq((uint32_t)q, 1u, oneq, p), p);
+// q mod p_i for q < 2^55 (negated when neg): q = h 2^32 + l, h < 2^23 < p_i.
+__device__ __forceinline__ uint32_t residue(int i, uint64_t q, bool neg) {
+  const uint32_t p = c_ntt.c[i].p;
+  const uint32_t r = addq(mulq((uint32_t)(q >> 32), c_ntt.c[i].r32, c_ntt.c[i].r32q, p),
+                          mulq((uint32_t)q, 1u, c_ntt.c[i].oneq, p), p);
   return (neg && r) ? p - r : r;
 }
 
@@ -318,26 +384,30 @@ __device__ __forceinline__ double crt_to_double(uint32_t r0, uint32_t r1, uint32
   return __longlong_as_double((long long)bits);
 }
 
-// The residues mod prime PI of the Toeplitz product of one vector at the
-// thread's output positions t + k L/16 (k < 8): transform, times the scaled
-// spectrum of the quantised Toeplitz column, inverse transform.
-template <int PI>
-__device__ __forceinline__ void ntt_conv(const uint64_t* xq, unsigned negmask, uint32_t* buf, int t,
-                                         const ExactAxis& ax, uint32_t* out) {
-  constexpr uint32_t p = kNttP[PI];
+// The residues mod prime i of the Toeplitz product of one vector at the
+// thread's output positions t + k L/16 (k < 8): transform of the input
+// residues, times the scaled spectrum of the quantised Toeplitz column,
+// inverse transform.  rs[k] holds the input residue at position t + k L/16
+// on entry and the product's on return (this thread's slots only).
+__device__ __forceinline__ void ntt_conv(int i, uint32_t* rs, uint32_t* buf, int t, const ExactAxis& ax) {
+  const uint2* tw = ax.tab + (size_t)3 * i * ax.L;
   uint32_t v[16];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = residue<PI>(xq[k], (negmask >> k) & 1u);
-  ntt16_forward<PI>(v, buf, t, ax.L, ax.log2L, ax.tw[PI]);
-  const int Lq = ax.L >> 4;
+  for (int k = 0; k < 8; ++k) v[k] = rs[k];
+  {
+    const NttK c = ntt_consts<false>(i);
+    ntt16_forward(v, buf, t, ax.L, ax.log2L, tw, c);
+    const int Lq = ax.L >> 4;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const uint2 s = __ldg(ax.spec[PI] + t + k * Lq);
-    v[k] = mulq(v[k], s.x, s.y, p);
+    for (int k = 0; k < 16; ++k) {
+      const uint2 s = ld_tab(tw + 2 * ax.L + t + k * Lq);
+      v[k] = mulq(v[k], s.x, s.y, c.p);
+    }
   }
-  ntt16_inverse<PI>(v, buf, t, ax.L, ax.log2L, ax.twi[PI]);
+  const NttK c = ntt_consts<true>(i);
+  ntt16_inverse(v, buf, t, ax.L, ax.log2L, tw + ax.L, c);
 #pragma unroll
-  for (int k = 0; k < 8; ++k) out[k] = v[k];
+  for (int k = 0; k < 8; ++k) rs[k] = v[k];
 }
 
 // Largest biased exponent over one group's values: shuffles over the lanes of
@@ -380,6 +450,9 @@ __device__ __forceinline__ void exact_body(const double* __restrict__ x, double*
   const GroupIdx gi = group_idx<COLS>(G, F);
   uint32_t* buf = reinterpret_cast<uint32_t*>(smem_raw) + (size_t)gi.g * gstride;
   int* slot = reinterpret_cast<int*>(buf);
+  // this thread's 32 residue slots (prime q, position k at rs[8 q + k]), 33
+  // words apart so that a warp's accesses fall in 32 different banks
+  uint32_t* rs = reinterpret_cast<uint32_t*>(smem_raw) + (size_t)F * gstride + (size_t)threadIdx.x * 33;
   const int nvec = COLS ? n1 : n2, len = COLS ? n2 : n1;
   const int npairs = (nvec + 1) >> 1;
   const int ngroups = (npairs + F - 1) / F;
@@ -403,35 +476,32 @@ __device__ __forceinline__ void exact_body(const double* __restrict__ x, double*
       __syncthreads();
       const int E = group_max<COLS>(e, slot, G, F);
       const int Ee = E ? E : 1;
-      uint64_t xq[8];
-      unsigned negm = 0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        xq[k] = quantize(xv[k], Ee);
-        negm |= (unsigned)(__double_as_longlong(xv[k]) < 0) << k;
-      }  // (x is read again in the epilogue: an L1 or L2 hit)
-      uint32_t res[4][8];
-      ntt_conv<0>(xq, negm, buf, gi.t, ax, res[0]);
-      ntt_conv<1>(xq, negm, buf, gi.t, ax, res[1]);
-      ntt_conv<2>(xq, negm, buf, gi.t, ax, res[2]);
-      ntt_conv<3>(xq, negm, buf, gi.t, ax, res[3]);
+      for (int k = 0; k < 8; ++k) {  // (x is read again in the epilogue: an L1 or L2 hit)
+        const uint64_t q = quantize(xv[k], Ee);
+        const bool neg = __double_as_longlong(xv[k]) < 0;
+#pragma unroll
+        for (int i = 0; i < kNttPrimes; ++i) rs[8 * i + k] = residue(i, q, neg);
+      }
+#pragma unroll 1
+      for (int i = 0; i < kNttPrimes; ++i) ntt_conv(i, rs + 8 * i, buf, gi.t, ax);
       __syncthreads();  // the next vector's exponent slot reuses the buffer
       if (!has) continue;
-      const int scale = Ee - 1074 - ax.St;
+      const int scale = Ee - 1077 - ax.St;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int pos = gi.t + k * Lq;
         if (pos >= len) continue;
         const double az = E == 2047 ? __longlong_as_double(0x7FF8000000000000ll)
-                                    : crt_to_double(res[0][k], res[1][k], res[2][k], res[3][k], scale);
+                                    : crt_to_double(rs[k], rs[8 + k], rs[16 + k], rs[24 + k], scale);
         const size_t p = vaddr<COLS>(a + h, pos, n1);
         if (!COLS) {
           if (MODE == MODE_RAW) {
             tmpx[p] = az;
           } else {
-            const double xx = x[p];
+            const double xx = ld_again(x + p);
             double sx = xx - az;
-            if (phi[p]) sx = sx + pen * xx;
+            if (ld_again(phi + p)) sx = sx + pen * xx;
             tmpx[p] = sx;
           }
         } else {
@@ -488,11 +558,18 @@ __host__ __device__ inline int exact_groups(int L, bool cols) {
   while (F > 1 && F * G > 512) F >>= 1;
   return F;
 }
-// words per group buffer: the padded exchange buffer, odd so that the groups'
-// buffers start in different banks; at least G doubles for the norm tree
+// words per group exchange buffer: the padded exchange buffer (the largest
+// padded index is L - 1 + (L - 1)/16), even so that every group's buffer can
+// hold the norm tree's G doubles 8-byte aligned, and 2 mod 4 so that
+// neighbouring groups' buffers start in different banks
 __host__ __device__ inline int exact_stride(int L) {
   const int w = L + (L >> 4) + 1;
-  return w | 1;
+  return (w + 3) / 4 * 4 + 2;
+}
+// shared memory of a block of F groups: the exchange buffers, then 33 words
+// (32 residues) per thread
+__host__ __device__ inline size_t exact_smem_bytes(int L, int F) {
+  return (size_t)F * ((size_t)exact_stride(L) + 33 * (size_t)(L >> 4)) * sizeof(uint32_t);
 }
 
 }  // namespace rsfde
