@@ -455,19 +455,33 @@ void enqueue_precond64(rsfde_ctx* c, const double* v, const double* vscale, doub
 
 // Left-preconditioned GMRES: V_0 = P^-1 (b - M x) (or b - M x without a
 // preconditioner), beta = ||V_0||, then restart_prep.
+// Scratch of the exact residual: the FFT preconditioner's work arrays T1 and
+// T2a (8 N bytes each: two residue arrays each) and T2b (the exponents),
+// free whenever a residual runs.
+ExactScratch exact_scratch(rsfde_ctx* c) {
+  ExactScratch sc;
+  sc.res[0] = static_cast<uint32_t*>(c->T1);
+  sc.res[1] = sc.res[0] + c->N;
+  sc.res[2] = static_cast<uint32_t*>(c->T2a);
+  sc.res[3] = sc.res[2] + c->N;
+  sc.ebuf = static_cast<int*>(c->T2b);
+  return sc;
+}
+
 // r = b - M x (no norm) with M x in FP64 or, for resid_prec RSFDE_EXACT, exact
 // Toeplitz products.
 void enqueue_resid_only(rsfde_ctx* c, const double* x, const double* b, double* r, const int* gate) {
   const bool exact = c->opts.resid_prec == RSFDE_EXACT;
   {
     ProfScope ps(c, RSFDE_K_RESID_ROWS);
-    if (exact) launch_exact_rows(x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->xex.tab, gate, c->stream);
+    if (exact)
+      launch_exact_rows(x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->xex.tab, exact_scratch(c), gate, c->stream);
     else launch_toeplitz_rows<double, double>(x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->x64.tab, gate, c->stream);
   }
   ProfScope ps(c, RSFDE_K_RESID_COLS);
   if (exact)
-    launch_exact_cols<double>(MODE_RESID_ONLY, x, c->tmpx, c->phi, c->pen, b, r, c->n1, c->n2, c->yex.tab, gate,
-                              nullptr, nullptr, c->stream);
+    launch_exact_cols<double>(MODE_RESID_ONLY, x, c->tmpx, c->phi, c->pen, b, r, c->n1, c->n2, c->yex.tab,
+                              exact_scratch(c), gate, nullptr, nullptr, c->stream);
   else
     launch_toeplitz_cols<double, double>(MODE_RESID_ONLY, x, c->tmpx, c->phi, c->pen, b, r, c->n1, c->n2,
                                          c->y64.tab, gate, nullptr, nullptr, c->stream);
@@ -518,15 +532,15 @@ void enqueue_residual_t(rsfde_ctx* c, const int* gate, const AxisTables<T>& tx, 
 void enqueue_residual_exact(rsfde_ctx* c, const int* gate) {
   {
     ProfScope ps(c, RSFDE_K_RESID_ROWS);
-    launch_exact_rows(c->x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->xex.tab, gate, c->stream);
+    launch_exact_rows(c->x, c->tmpx, c->phi, c->pen, c->n1, c->n2, c->xex.tab, exact_scratch(c), gate, c->stream);
   }
   ProfScope ps(c, RSFDE_K_RESID_COLS);
   if (basis_kind(c) == BASIS_FP32)
     launch_exact_cols<float>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, reinterpret_cast<float*>(c->V),
-                             c->n1, c->n2, c->yex.tab, gate, c->partials, c->st, c->stream);
+                             c->n1, c->n2, c->yex.tab, exact_scratch(c), gate, c->partials, c->st, c->stream);
   else
     launch_exact_cols<double>(MODE_RESIDUAL, c->x, c->tmpx, c->phi, c->pen, c->b, c->V, c->n1, c->n2, c->yex.tab,
-                              gate, c->partials, c->st, c->stream);
+                              exact_scratch(c), gate, c->partials, c->st, c->stream);
 }
 
 void enqueue_residual(rsfde_ctx* c, const int* gate) {

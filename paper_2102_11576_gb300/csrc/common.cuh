@@ -81,6 +81,12 @@ struct ExactAxis {
   int St;  // the Toeplitz column was quantised as round(t 2^St), |t_q| < 2^52
   const uint2* tab;
 };
+// Scratch of an exact Toeplitz pass: the product's residues modulo each prime
+// (N words each, the grid's layout) and each vector's exponent.
+struct ExactScratch {
+  uint32_t* res[4];
+  int* ebuf;
+};
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   if (blockDim.x < 32) {  // blocks smaller than a warp (tiny grids): serial sum in a fixed order

@@ -94,45 +94,53 @@ static void exact_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-void launch_exact_rows(const double* x, double* tmpx, const uint8_t* phi, double pen, int n1, int n2,
-                       const ExactAxis& ax, const int* gate, cudaStream_t s) {
-  const int npairs = (n2 + 1) / 2;
-  const int F = exact_groups(ax.L, false), gs = exact_stride(ax.L);
-  const size_t sm = exact_smem_bytes(ax.L, F);
-  auto k = exact_kernel<MODE_APPLY, false, double>;
+// The transform kernel for rows or columns: blockIdx.y is the prime.
+template <bool COLS>
+static void launch_ntt(const double* x, const ExactScratch& sc, int n1, int n2, const ExactAxis& ax,
+                       const int* gate, cudaStream_t s) {
+  const int nvec = COLS ? n1 : n2;
+  const int F = exact_groups(ax.L, COLS), gs = exact_stride(ax.L);
+  const size_t sm = (size_t)F * gs * sizeof(uint32_t);
+  auto k = ntt_kernel<COLS>;
   exact_smem(k, sm);
-  k<<<(npairs + F - 1) / F, F * (ax.L / 16), sm, s>>>(x, tmpx, phi, pen, nullptr, nullptr, n1, n2, ax, F, gs, gate,
-                                                      nullptr, nullptr);
+  k<<<dim3((nvec + F - 1) / F, kNttPrimes), F * (ax.L / 16), sm, s>>>(x, sc, n1, n2, ax, F, gs, gate);
+}
+
+void launch_exact_rows(const double* x, double* tmpx, const uint8_t* phi, double pen, int n1, int n2,
+                       const ExactAxis& ax, const ExactScratch& sc, const int* gate, cudaStream_t s) {
+  launch_ntt<false>(x, sc, n1, n2, ax, gate, s);
+  crt_kernel<MODE_APPLY, false, double><<<vec_grid((size_t)n1 * n2), kBlock, 0, s>>>(
+      x, sc, tmpx, phi, pen, nullptr, nullptr, n1, n2, ax.St, gate, nullptr, nullptr);
 }
 
 template <typename Tout>
 void launch_exact_cols(int mode, const double* x, double* tmpx, const uint8_t* phi, double pen, const double* b,
-                       Tout* out, int n1, int n2, const ExactAxis& ay, const int* gate, double* partials,
-                       SolverState* st, cudaStream_t s) {
-  const int npairs = (n1 + 1) / 2;
-  const int F = exact_groups(ay.L, true), gs = exact_stride(ay.L);
-  const size_t sm = exact_smem_bytes(ay.L, F);
-  const int grid = (npairs + F - 1) / F;
+                       Tout* out, int n1, int n2, const ExactAxis& ay, const ExactScratch& sc, const int* gate,
+                       double* partials, SolverState* st, cudaStream_t s) {
+  ExactScratch sy = sc;
+  sy.ebuf = sc.ebuf + n2;  // the rows' exponents stay apart
+  const int grid = vec_grid((size_t)n1 * n2);
   if (mode == MODE_RESIDUAL) {
-    auto k = exact_kernel<MODE_RESIDUAL, true, Tout>;
-    exact_smem(k, sm);
-    k<<<grid, F * (ay.L / 16), sm, s>>>(x, tmpx, phi, pen, b, out, n1, n2, ay, F, gs, gate, partials, st);
+    launch_ntt<true>(x, sy, n1, n2, ay, gate, s);
+    crt_kernel<MODE_RESIDUAL, true, Tout><<<grid, kBlock, 0, s>>>(x, sy, tmpx, phi, pen, b, out, n1, n2, ay.St,
+                                                                  gate, partials, st);
     return;
   }
   if constexpr (std::is_same<Tout, double>::value) {
     if (mode == MODE_RESID_ONLY) {
-      auto k = exact_kernel<MODE_RESID_ONLY, true, double>;
-      exact_smem(k, sm);
-      k<<<grid, F * (ay.L / 16), sm, s>>>(x, tmpx, phi, pen, b, out, n1, n2, ay, F, gs, gate, partials, st);
+      launch_ntt<true>(x, sy, n1, n2, ay, gate, s);
+      crt_kernel<MODE_RESID_ONLY, true, double><<<grid, kBlock, 0, s>>>(x, sy, tmpx, phi, pen, b, out, n1, n2,
+                                                                        ay.St, gate, partials, st);
       return;
     }
   }
   note_unsupported_launch();
 }
 template void launch_exact_cols<double>(int, const double*, double*, const uint8_t*, double, const double*,
-                                        double*, int, int, const ExactAxis&, const int*, double*, SolverState*,
-                                        cudaStream_t);
+                                        double*, int, int, const ExactAxis&, const ExactScratch&, const int*,
+                                        double*, SolverState*, cudaStream_t);
 template void launch_exact_cols<float>(int, const double*, double*, const uint8_t*, double, const double*, float*,
-                                       int, int, const ExactAxis&, const int*, double*, SolverState*, cudaStream_t);
+                                       int, int, const ExactAxis&, const ExactScratch&, const int*, double*,
+                                       SolverState*, cudaStream_t);
 
 }  // namespace rsfde

@@ -80,9 +80,7 @@ __device__ __forceinline__ uint2 ld_tab(const uint2* p) {
 // Constants of each prime: p, 2^32 mod p and floor(2^32/p) (for residues),
 // and the powers W16^K (K = 1, 2, 3, 4, 6, 9: the radix-16/8/4 butterflies'
 // internal roots) of W16 = g^((p-1)/16) = w^(L/16), forward and inverse, with
-// Shoup companions.  The prime is a runtime index: one copy of the transform
-// code serves the four primes, and a transform keeps only its own prime's
-// constants in registers.
+// Shoup companions, all evaluated at compile time.
 struct NttPrimeConsts {
   uint32_t p, r32, r32q, oneq;
   uint32_t w[2][6], wq[2][6];
@@ -109,37 +107,25 @@ constexpr NttConstTable make_ntt_consts() {
   }
   return t;
 }
-__constant__ NttConstTable c_ntt = make_ntt_consts();
 
-// One direction's butterfly constants of one prime, in registers.
+// One direction's butterfly constants of one prime (compile-time values: the
+// multiplications take them as immediates).
 struct NttK {
   uint32_t p;
   uint32_t w[6], wq[6];
 };
-template <bool INV>
-__device__ __forceinline__ NttK ntt_consts(int q) {
+template <int PI, bool INV>
+__device__ __forceinline__ NttK ntt_consts() {
+  constexpr NttConstTable T = make_ntt_consts();
   NttK k;
-  k.p = c_ntt.c[q].p;
+  k.p = T.c[PI].p;
 #pragma unroll
   for (int j = 0; j < 6; ++j) {
-    k.w[j] = c_ntt.c[q].w[INV][j];
-    k.wq[j] = c_ntt.c[q].wq[INV][j];
+    k.w[j] = T.c[PI].w[INV][j];
+    k.wq[j] = T.c[PI].wq[INV][j];
   }
   return k;
 }
-// x and the mask read again in the row epilogue, issued there: otherwise the
-// compiler keeps the first reads of x alive across the four transforms.
-__device__ __forceinline__ double ld_again(const double* p) {
-  double r;
-  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(r) : "l"(p));
-  return r;
-}
-__device__ __forceinline__ uint32_t ld_again(const uint8_t* p) {
-  uint32_t r;
-  asm volatile("ld.global.nc.u8 %0, [%1];" : "=r"(r) : "l"(p));
-  return r;
-}
-
 // times W16^K (K in 1, 2, 3, 4, 6, 9) in the direction K holds
 template <int K>
 __device__ __forceinline__ uint32_t nrot(uint32_t a, const NttK& c) {
@@ -209,17 +195,78 @@ __device__ __forceinline__ void ndft16(uint32_t* v, const NttK& c) {
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = o[r];
 }
-template <int R, int S>
+// The same DFTs when the upper half of the inputs is zero (the forward
+// transform's first pass: positions >= L/2 of every input are zero).
+template <int S>
+__device__ __forceinline__ void ndft4h(uint32_t* v, const NttK& c) {  // v[2S] = v[3S] = 0
+  const uint32_t p = c.p, a = v[0], b = v[S], t3 = nrot<4>(b, c);
+  v[0] = addq(a, b, p);
+  v[2 * S] = subq(a, b, p);
+  v[S] = addq(a, t3, p);
+  v[3 * S] = subq(a, t3, p);
+}
+template <int S>
+__device__ __forceinline__ void ndft8h(uint32_t* v, const NttK& c) {
+  const uint32_t p = c.p;
+  ndft4h<2 * S>(v, c);
+  ndft4h<2 * S>(v + S, c);
+  v[3 * S] = nrot<2>(v[3 * S], c);
+  v[5 * S] = nrot<4>(v[5 * S], c);
+  v[7 * S] = nrot<6>(v[7 * S], c);
+  uint32_t o[8];
+#pragma unroll
+  for (int r1 = 0; r1 < 4; ++r1) {
+    o[r1] = addq(v[2 * r1 * S], v[(2 * r1 + 1) * S], p);
+    o[r1 + 4] = subq(v[2 * r1 * S], v[(2 * r1 + 1) * S], p);
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r * S] = o[r];
+}
+__device__ __forceinline__ void ndft16h(uint32_t* v, const NttK& c) {
+  ndft4h<4>(v, c);
+  ndft4h<4>(v + 1, c);
+  ndft4h<4>(v + 2, c);
+  ndft4h<4>(v + 3, c);
+  v[5] = nrot<1>(v[5], c);
+  v[9] = nrot<2>(v[9], c);
+  v[13] = nrot<3>(v[13], c);
+  v[6] = nrot<2>(v[6], c);
+  v[10] = nrot<4>(v[10], c);
+  v[14] = nrot<6>(v[14], c);
+  v[7] = nrot<3>(v[7], c);
+  v[11] = nrot<6>(v[11], c);
+  v[15] = nrot<9>(v[15], c);
+  ndft4<1>(v, c);
+  ndft4<1>(v + 4, c);
+  ndft4<1>(v + 8, c);
+  ndft4<1>(v + 12, c);
+  uint32_t o[16];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) o[a + 4 * b] = v[4 * a + b];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = o[r];
+}
+
+template <int R, int S, bool HALF>
 __device__ __forceinline__ void ndft_r(uint32_t* v, const NttK& c) {
-  if (R == 16) ndft16(v, c);
-  else if (R == 8) ndft8<S>(v, c);
-  else if (R == 4) ndft4<S>(v, c);
-  else ndft2<S>(v, c);
+  if (HALF) {
+    if (R == 16) ndft16h(v, c);
+    else if (R == 8) ndft8h<S>(v, c);
+    else if (R == 4) ndft4h<S>(v, c);
+    else v[S] = v[0];  // radix 2 with a zero second input
+  } else {
+    if (R == 16) ndft16(v, c);
+    else if (R == 8) ndft8<S>(v, c);
+    else if (R == 4) ndft4<S>(v, c);
+    else ndft2<S>(v, c);
+  }
 }
 
 // One Stockham pass (the index arithmetic of fft_pass); tw: {w^m, Shoup} of
 // the forward (w) or inverse (w^-1) root, matching the direction of c.
-template <int R>
+template <int R, bool HALF = false>
 __device__ __forceinline__ void ntt_pass(uint32_t* v, int t, int L, int Ns, const uint2* __restrict__ tw,
                                          const NttK& c) {
   constexpr int S = 16 / R;
@@ -235,7 +282,7 @@ __device__ __forceinline__ void ntt_pass(uint32_t* v, int t, int L, int Ns, cons
         v[i + q * S] = mulq(v[i + q * S], w.x, w.y, c.p);
       }
     }
-    ndft_r<R, S>(v + i, c);
+    ndft_r<R, S, HALF>(v + i, c);
   }
 }
 
@@ -264,21 +311,27 @@ __device__ __forceinline__ void ntt16_forward(uint32_t* v, uint32_t* buf, int t,
 #pragma unroll
   for (int k = 8; k < 16; ++k) v[k] = 0u;
   const int small = log2L & 3, n16 = log2L >> 2;
-  int Ns = 1;
+  int Ns = 1, q = 0;
+  // the first pass (Ns = 1, no twiddles) sees the zero upper half
   if (small == 1) {
-    ntt_pass<2>(v, t, L, Ns, tw, c);
+    ntt_pass<2, true>(v, t, L, Ns, tw, c);
     ntt_exchange<2>(v, buf, t, L, Ns);
     Ns = 2;
   } else if (small == 2) {
-    ntt_pass<4>(v, t, L, Ns, tw, c);
+    ntt_pass<4, true>(v, t, L, Ns, tw, c);
     ntt_exchange<4>(v, buf, t, L, Ns);
     Ns = 4;
   } else if (small == 3) {
-    ntt_pass<8>(v, t, L, Ns, tw, c);
+    ntt_pass<8, true>(v, t, L, Ns, tw, c);
     ntt_exchange<8>(v, buf, t, L, Ns);
     Ns = 8;
+  } else {
+    ntt_pass<16, true>(v, t, L, Ns, tw, c);
+    if (n16 > 1) ntt_exchange<16>(v, buf, t, L, Ns);
+    Ns = 16;
+    q = 1;
   }
-  for (int q = 0; q < n16; ++q) {
+  for (; q < n16; ++q) {
     ntt_pass<16>(v, t, L, Ns, tw, c);
     if (q + 1 < n16) ntt_exchange<16>(v, buf, t, L, Ns);
     Ns <<= 4;
@@ -315,11 +368,13 @@ __device__ __forceinline__ int biased_exponent(double x) {
   return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
 }
 
-// q mod p_i for q < 2^55 (negated when neg): q = h 2^32 + l, h < 2^23 < p_i.
-__device__ __forceinline__ uint32_t residue(int i, uint64_t q, bool neg) {
-  const uint32_t p = c_ntt.c[i].p;
-  const uint32_t r = addq(mulq((uint32_t)(q >> 32), c_ntt.c[i].r32, c_ntt.c[i].r32q, p),
-                          mulq((uint32_t)q, 1u, c_ntt.c[i].oneq, p), p);
+// q mod p for q < 2^55 (negated when neg): q = h 2^32 + l, h < 2^23 < p.
+template <int PI>
+__device__ __forceinline__ uint32_t residue(uint64_t q, bool neg) {
+  constexpr NttConstTable T = make_ntt_consts();
+  constexpr uint32_t p = T.c[PI].p;
+  const uint32_t r = addq(mulq((uint32_t)(q >> 32), T.c[PI].r32, T.c[PI].r32q, p),
+                          mulq((uint32_t)q, 1u, T.c[PI].oneq, p), p);
   return (neg && r) ? p - r : r;
 }
 
@@ -384,32 +439,6 @@ __device__ __forceinline__ double crt_to_double(uint32_t r0, uint32_t r1, uint32
   return __longlong_as_double((long long)bits);
 }
 
-// The residues mod prime i of the Toeplitz product of one vector at the
-// thread's output positions t + k L/16 (k < 8): transform of the input
-// residues, times the scaled spectrum of the quantised Toeplitz column,
-// inverse transform.  rs[k] holds the input residue at position t + k L/16
-// on entry and the product's on return (this thread's slots only).
-__device__ __forceinline__ void ntt_conv(int i, uint32_t* rs, uint32_t* buf, int t, const ExactAxis& ax) {
-  const uint2* tw = ax.tab + (size_t)3 * i * ax.L;
-  uint32_t v[16];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = rs[k];
-  {
-    const NttK c = ntt_consts<false>(i);
-    ntt16_forward(v, buf, t, ax.L, ax.log2L, tw, c);
-    const int Lq = ax.L >> 4;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const uint2 s = ld_tab(tw + 2 * ax.L + t + k * Lq);
-      v[k] = mulq(v[k], s.x, s.y, c.p);
-    }
-  }
-  const NttK c = ntt_consts<true>(i);
-  ntt16_inverse(v, buf, t, ax.L, ax.log2L, tw + ax.L, c);
-#pragma unroll
-  for (int k = 0; k < 8; ++k) rs[k] = v[k];
-}
-
 // Largest biased exponent over one group's values: shuffles over the lanes of
 // this warp in the group (rows: G consecutive lanes; columns: lanes F apart),
 // then the warps' maxima by a shared-memory atomic.  slot: this group's word,
@@ -429,147 +458,138 @@ __device__ __forceinline__ int group_max(int e, int* slot, int G, int F) {
   return r;
 }
 
-// Exact Toeplitz pass over an FP64 vector field (rows: COLS = false; columns:
-// COLS = true); two vectors (a, a+1) per group, one after the other, as in
-// toeplitz_body, whose modes and epilogues this follows with T = double:
-//   rows  MODE_RAW: tmpx = A_x x;  other modes: tmpx = x - A_x x + pen phi x
-//   cols  MODE_RAW: out = A_y x;  MODE_APPLY: out = tmpx - A_y x;
-//         MODE_RESID_ONLY: out = b - (tmpx - A_y x);  MODE_RESIDUAL: that and
-//         ||out||^2 per column pair by a fixed tree, the last block summing
-//         the pairs in order and restarting the solver.
-// A vector holding an infinity or NaN yields NaN products.
-template <int MODE, bool COLS, typename Tout>
-__device__ __forceinline__ void exact_body(const double* __restrict__ x, double* __restrict__ tmpx,
-                                           const uint8_t* __restrict__ phi, double pen,
-                                           const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2,
-                                           const ExactAxis& ax, int F, int gstride, const int* gate,
-                                           double* partials, SolverState* st, int bid, int nblk) {
-  if (gate_closed<double>(gate)) return;
+// Pass 1 of an exact Toeplitz product along rows (COLS = false) or columns:
+// for prime PI, every vector's product modulo p at every position, into
+// sc.res[PI] (the grid's layout), and (PI = 0) each vector's largest biased
+// exponent E into sc.ebuf[vector] (2047: the vector holds an infinity or
+// NaN).  One vector per group of L/16 threads.
+template <int PI, bool COLS>
+__device__ __forceinline__ void ntt_body(const double* __restrict__ x, const ExactScratch& sc, int n1, int n2,
+                                         const ExactAxis& ax, int F, int gstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = ax.L, Lq = L >> 4, G = Lq;
   const GroupIdx gi = group_idx<COLS>(G, F);
   uint32_t* buf = reinterpret_cast<uint32_t*>(smem_raw) + (size_t)gi.g * gstride;
   int* slot = reinterpret_cast<int*>(buf);
-  // this thread's 32 residue slots (prime q, position k at rs[8 q + k]), 33
-  // words apart so that a warp's accesses fall in 32 different banks
-  uint32_t* rs = reinterpret_cast<uint32_t*>(smem_raw) + (size_t)F * gstride + (size_t)threadIdx.x * 33;
   const int nvec = COLS ? n1 : n2, len = COLS ? n2 : n1;
-  const int npairs = (nvec + 1) >> 1;
-  const int ngroups = (npairs + F - 1) / F;
-  for (int grp = bid; grp < ngroups; grp += nblk) {
-    const int pr = grp * F + gi.g;
-    const int a = 2 * pr;
-    const bool live = pr < npairs;
-    const bool second = a + 1 < nvec;
-    double acc = 0.0;
-    for (int h = 0; h < 2; ++h) {  // uniform over the block (every group runs both)
-      const bool has = live && (h == 0 || second);
-      double xv[8];
-      int e = 0;
+  const int ngroups = (nvec + F - 1) / F;
+  const uint2* tw = ax.tab + (size_t)3 * PI * L;
+  uint32_t* __restrict__ res = sc.res[PI];
+  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int vec = grp * F + gi.g;
+    const bool has = vec < nvec;
+    double xv[8];
+    int e = 0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = gi.t + k * Lq;
-        xv[k] = (has && pos < len) ? x[vaddr<COLS>(a + h, pos, n1)] : 0.0;
-        e = max(e, biased_exponent(xv[k]));
-      }
-      if (gi.t == 0) slot[0] = 0;
-      __syncthreads();
-      const int E = group_max<COLS>(e, slot, G, F);
-      const int Ee = E ? E : 1;
+    for (int k = 0; k < 8; ++k) {
+      const int pos = gi.t + k * Lq;
+      xv[k] = (has && pos < len) ? x[vaddr<COLS>(vec, pos, n1)] : 0.0;
+      e = max(e, biased_exponent(xv[k]));
+    }
+    if (gi.t == 0) slot[0] = 0;
+    __syncthreads();
+    const int E = group_max<COLS>(e, slot, G, F);
+    if (PI == 0 && gi.t == 0 && has) sc.ebuf[vec] = E;
+    const int Ee = E ? E : 1;
+    uint32_t v[16];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {  // (x is read again in the epilogue: an L1 or L2 hit)
-        const uint64_t q = quantize(xv[k], Ee);
-        const bool neg = __double_as_longlong(xv[k]) < 0;
+    for (int k = 0; k < 8; ++k) v[k] = residue<PI>(quantize(xv[k], Ee), __double_as_longlong(xv[k]) < 0);
+    {
+      const NttK c = ntt_consts<PI, false>();
+      ntt16_forward(v, buf, gi.t, L, ax.log2L, tw, c);
 #pragma unroll
-        for (int i = 0; i < kNttPrimes; ++i) rs[8 * i + k] = residue(i, q, neg);
-      }
-#pragma unroll 1
-      for (int i = 0; i < kNttPrimes; ++i) ntt_conv(i, rs + 8 * i, buf, gi.t, ax);
-      __syncthreads();  // the next vector's exponent slot reuses the buffer
-      if (!has) continue;
-      const int scale = Ee - 1077 - ax.St;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = gi.t + k * Lq;
-        if (pos >= len) continue;
-        const double az = E == 2047 ? __longlong_as_double(0x7FF8000000000000ll)
-                                    : crt_to_double(rs[k], rs[8 + k], rs[16 + k], rs[24 + k], scale);
-        const size_t p = vaddr<COLS>(a + h, pos, n1);
-        if (!COLS) {
-          if (MODE == MODE_RAW) {
-            tmpx[p] = az;
-          } else {
-            const double xx = ld_again(x + p);
-            double sx = xx - az;
-            if (ld_again(phi + p)) sx = sx + pen * xx;
-            tmpx[p] = sx;
-          }
-        } else {
-          const double w = MODE == MODE_RAW ? az : tmpx[p] - az;
-          if (MODE == MODE_RAW || MODE == MODE_APPLY) {
-            out[p] = (Tout)w;
-          } else if (MODE == MODE_RESID_ONLY) {
-            out[p] = (Tout)(b[p] - w);
-          } else {
-            const double r = b[p] - w;
-            out[p] = (Tout)r;
-            acc += r * r;
-          }
-        }
+      for (int k = 0; k < 16; ++k) {
+        const uint2 s = ld_tab(tw + 2 * L + gi.t + k * Lq);
+        v[k] = mulq(v[k], s.x, s.y, c.p);
       }
     }
-    if constexpr (MODE == MODE_RESIDUAL) {
-      double* gsum = reinterpret_cast<double*>(buf);
-      __syncthreads();
-      gsum[gi.t] = acc;
-      __syncthreads();
-      for (int hh = G >> 1; hh > 0; hh >>= 1) {
-        if (gi.t < hh) gsum[gi.t] += gsum[gi.t + hh];
-        __syncthreads();
+    ntt16_inverse(v, buf, gi.t, L, ax.log2L, tw + L, ntt_consts<PI, true>());
+    if (has) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int pos = gi.t + k * Lq;
+        if (pos < len) res[vaddr<COLS>(vec, pos, n1)] = v[k];
       }
-      if (gi.t == 0 && live) partials[pr] = gsum[0];
-      __syncthreads();
+    }
+    __syncthreads();  // the next vector's exponent slot reuses the buffer
+  }
+}
+
+// 64 registers: at least 32 warps per SM (the transforms wait on shared
+// memory and the twiddle reads; at 16 warps they ran 1.3x longer)
+template <bool COLS>
+__global__ void __launch_bounds__(COLS ? 1024 : 512, COLS ? 1 : 2)
+    ntt_kernel(const double* __restrict__ x, ExactScratch sc, int n1, int n2, ExactAxis ax, int F, int gstride,
+               const int* gate) {
+  if (gate_closed<double>(gate)) return;
+  switch (blockIdx.y) {  // the prime: uniform over the block
+    case 0: ntt_body<0, COLS>(x, sc, n1, n2, ax, F, gstride); break;
+    case 1: ntt_body<1, COLS>(x, sc, n1, n2, ax, F, gstride); break;
+    case 2: ntt_body<2, COLS>(x, sc, n1, n2, ax, F, gstride); break;
+    default: ntt_body<3, COLS>(x, sc, n1, n2, ax, F, gstride); break;
+  }
+}
+
+// Pass 2, elementwise over the grid: the product at p from its four residues
+// (Garner), scaled by its vector's exponent, then the FP64 epilogue of
+// toeplitz_body with T = double:
+//   rows:  tmpx = x - A_x x + pen phi x
+//   cols   MODE_RESID_ONLY: out = b - (tmpx - A_y x);  MODE_RESIDUAL: that,
+//          and ||out||^2 by a fixed-order block sum per block and
+//          block_sum_fixed over the blocks (the grid is a function of N), the
+//          last block restarting the solver.
+template <int MODE, bool COLS, typename Tout>
+__global__ void __launch_bounds__(kBlock)
+    crt_kernel(const double* __restrict__ x, ExactScratch sc, double* __restrict__ tmpx,
+               const uint8_t* __restrict__ phi, double pen, const double* __restrict__ b, Tout* __restrict__ out,
+               int n1, int n2, int St, const int* gate, double* partials, SolverState* st) {
+  if (gate_closed<double>(gate)) return;
+  const size_t N = (size_t)n1 * n2;
+  double acc = 0.0;
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+    const int vec = COLS ? (int)(p % (size_t)n1) : (int)(p / (size_t)n1);
+    const int E = __ldg(sc.ebuf + vec);
+    const double az = E == 2047 ? __longlong_as_double(0x7FF8000000000000ll)
+                                : crt_to_double(__ldg(sc.res[0] + p), __ldg(sc.res[1] + p), __ldg(sc.res[2] + p),
+                                                __ldg(sc.res[3] + p), (E ? E : 1) - 1077 - St);
+    if (!COLS) {
+      const double xx = x[p];
+      double sx = xx - az;
+      if (phi[p]) sx = sx + pen * xx;
+      tmpx[p] = sx;
+    } else {
+      const double r = b[p] - (tmpx[p] - az);
+      out[p] = (Tout)r;
+      if (MODE == MODE_RESIDUAL) acc += r * r;
     }
   }
   if constexpr (MODE == MODE_RESIDUAL) {
-    if (arrive_last(&st->counter, nblk)) {
-      const double tot = block_sum_fixed(partials, npairs);
+    __shared__ double sh[kBlock / 32];
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+    if (arrive_last(&st->counter, gridDim.x)) {
+      const double tot = block_sum_fixed(partials, gridDim.x);
       if (threadIdx.x == 0) restart_prep(st, sqrt(tot));
     }
   }
 }
 
-template <int MODE, bool COLS, typename Tout>
-__global__ void __launch_bounds__(512)
-    exact_kernel(const double* __restrict__ x, double* __restrict__ tmpx, const uint8_t* __restrict__ phi,
-                 double pen, const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2, ExactAxis ax,
-                 int F, int gstride, const int* gate, double* partials, SolverState* st) {
-  exact_body<MODE, COLS, Tout>(x, tmpx, phi, pen, b, out, n1, n2, ax, F, gstride, gate, partials, st, blockIdx.x,
-                               gridDim.x);
-}
-
-// Groups per block (a power of two): at least 128 threads per block, columns
-// at least two groups (two adjacent column pairs fill a 32-byte sector), at
-// most 512 threads.
+// Groups per block (a power of two) of the transform kernel: at least 128
+// threads per block; columns at least four groups (four adjacent columns
+// fill a 32-byte sector of x); at most 1024 threads.
 __host__ __device__ inline int exact_groups(int L, bool cols) {
   const int G = L >> 4;
   int F = G >= 128 ? 1 : 128 / G;
-  if (cols && F < 2) F = 2;
-  while (F > 1 && F * G > 512) F >>= 1;
+  if (cols && F < 4) F = 4;
+  while (F > 1 && F * G > 1024) F >>= 1;
   return F;
 }
 // words per group exchange buffer: the padded exchange buffer (the largest
-// padded index is L - 1 + (L - 1)/16), even so that every group's buffer can
-// hold the norm tree's G doubles 8-byte aligned, and 2 mod 4 so that
-// neighbouring groups' buffers start in different banks
+// padded index is L - 1 + (L - 1)/16), 16 mod 32 so that the buffers of
+// neighbouring groups start half a bank row apart
 __host__ __device__ inline int exact_stride(int L) {
   const int w = L + (L >> 4) + 1;
-  return (w + 3) / 4 * 4 + 2;
-}
-// shared memory of a block of F groups: the exchange buffers, then 33 words
-// (32 residues) per thread
-__host__ __device__ inline size_t exact_smem_bytes(int L, int F) {
-  return (size_t)F * ((size_t)exact_stride(L) + 33 * (size_t)(L >> 4)) * sizeof(uint32_t);
+  return (w + 31) / 32 * 32 + 16;
 }
 
 }  // namespace rsfde

@@ -126,19 +126,21 @@ template <typename T, typename Tin, typename Tout>
 void launch_toeplitz_cols(int mode, const Tin* z, void* tmpx, const uint8_t* phi, double pen,
                           const double* b, Tout* out, int n1, int n2, const AxisTables<T>& ay,
                           const int* gate, double* partials, SolverState* st, cudaStream_t s);
-// Exact Toeplitz products of the true residual (exact.cuh): the row pass
-// writes tmpx = x - A_x x + pen phi x; the column pass MODE_RESIDUAL (Tout
-// double or float, with the norm and restart) or MODE_RESID_ONLY (double).
+// Exact Toeplitz products of the true residual (exact.cuh), two launches per
+// pass (the transforms for the four primes, then the Chinese remaindering
+// with the epilogue): the row pass writes tmpx = x - A_x x + pen phi x; the
+// column pass MODE_RESIDUAL (Tout double or float, with the norm and restart)
+// or MODE_RESID_ONLY (double).  sc: four arrays of N words and n1 + n2 ints.
 // build_exact_tables: the host tables of one axis (Toeplitz column t, length
 // L), 3 L entries per prime in the order tw, twi, spec; *St the quantisation
 // exponent of t.
 std::vector<uint2> build_exact_tables(const std::vector<double>& t, int L, int* St);
 void launch_exact_rows(const double* x, double* tmpx, const uint8_t* phi, double pen, int n1, int n2,
-                       const ExactAxis& ax, const int* gate, cudaStream_t s);
+                       const ExactAxis& ax, const ExactScratch& sc, const int* gate, cudaStream_t s);
 template <typename Tout>
 void launch_exact_cols(int mode, const double* x, double* tmpx, const uint8_t* phi, double pen, const double* b,
-                       Tout* out, int n1, int n2, const ExactAxis& ay, const int* gate, double* partials,
-                       SolverState* st, cudaStream_t s);
+                       Tout* out, int n1, int n2, const ExactAxis& ay, const ExactScratch& sc, const int* gate,
+                       double* partials, SolverState* st, cudaStream_t s);
 template <typename T, typename Tin, typename Tout>
 void launch_dst_rows(const Tin* v, const double* vscale, Tout* out, int n1, int n2, const AxisTables<T>& ax,
                      const int* gate, cudaStream_t s);
