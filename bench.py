@@ -387,6 +387,28 @@ def run_ours(args, rank, world, local_rank):
                                  "gram_schmidt": "one Arnoldi iteration (multi-dot + update)",
                                  "residual": "one true residual", "xupdate": "one solution update"}[dom],
                 "us_per_unit": d["us_per_unit"], "algorithmic_bytes_per_unit": d["algorithmic_bytes_per_unit"]}
+        if dom == "gram_schmidt" and head_form[2] == "fp64":
+            # an FP64 basis makes Gram-Schmidt FP64-pipe bound (ncu: the multi-dot
+            # and the update keep the FP64 pipe 86-93 % busy at under 50 % of
+            # HBM): (2j + 3) FP64 multiply-adds per grid element at column j
+            # (the j + 1 dots, the j + 1 subtractions, the norm), 2 flops each,
+            # against 152 SMs x 2 FP64 FMA per clock x 2 flops x the SM clock
+            sj = sum(sum_j(s["iters"], s["restarts"], m) for s in pstats)
+            it = sum(s["iters"] for s in pstats)
+            fl_unit = 2.0 * N * (2 * sj + 3 * it) / it
+            gfs = fl_unit / (d["us_per_unit"] / 1e6) / 1e9
+            pk = fp64_peak_gflops(peaks.get("sm_max_mhz", 2070.0))
+            roof = {"kernel": dom, "bound": "alu", "achieved": round(gfs, 1), "peak": round(pk, 1),
+                    "unit": "GFLOP/s (FP64)", "frac": round(gfs / pk, 4), "traffic": traffic,
+                    "peak_source": "152 SMs x 2 FP64 FMA/clock x 2 flops x sm_max_mhz (GB300 unit counts)",
+                    "unit_of_work": "one Arnoldi iteration (multi-dot + update)",
+                    "us_per_unit": d["us_per_unit"], "fp64_flops_per_unit": round(fl_unit),
+                    "algorithmic_bytes_per_unit": d["algorithmic_bytes_per_unit"],
+                    "hbm": {"achieved": d["achieved_GBs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": d["frac_of_hbm"],
+                            "traffic_over_algorithmic": (round(traffic / d["algorithmic_bytes_per_unit"], 3)
+                                                         if traffic else None),
+                            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src}; of measured)"}}
         if dom == "precond" and head_form[0] in ("bf16", "bf16x3"):
             nt = 3 if head_form[0] == "bf16x3" else 1
             fl = gemm_issued_flops(n1, n2, nt)

@@ -266,10 +266,13 @@ __device__ __forceinline__ void ndft_r(uint32_t* v, const NttK& c) {
 
 // One Stockham pass (the index arithmetic of fft_pass); tw: {w^m, Shoup} of
 // the forward (w) or inverse (w^-1) root, matching the direction of c.
-template <int R, bool HALF = false>
-__device__ __forceinline__ void ntt_pass(uint32_t* v, int t, int L, int Ns, const uint2* __restrict__ tw,
+// LG > 0: the transform length 2^LG is a compile-time constant (the index
+// arithmetic folds); LG = 0: L is the runtime argument.
+template <int R, bool HALF = false, int LG = 0>
+__device__ __forceinline__ void ntt_pass(uint32_t* v, int t, int Lrt, int Ns, const uint2* __restrict__ tw,
                                          const NttK& c) {
   constexpr int S = 16 / R;
+  const int L = LG ? (1 << LG) : Lrt;
   const int Lq = L >> 4;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
@@ -286,9 +289,10 @@ __device__ __forceinline__ void ntt_pass(uint32_t* v, int t, int L, int Ns, cons
   }
 }
 
-template <int R>
-__device__ __forceinline__ void ntt_exchange(uint32_t* v, uint32_t* buf, int t, int L, int Ns) {
+template <int R, int LG = 0>
+__device__ __forceinline__ void ntt_exchange(uint32_t* v, uint32_t* buf, int t, int Lrt, int Ns) {
   constexpr int S = 16 / R;
+  const int L = LG ? (1 << LG) : Lrt;
   const int Lq = L >> 4;
   __syncthreads();
 #pragma unroll
@@ -306,50 +310,56 @@ __device__ __forceinline__ void ntt_exchange(uint32_t* v, uint32_t* buf, int t, 
 
 // Forward transform of a sequence that is zero on positions >= L/2 (k >= 8);
 // spectrum in natural order at the thread's positions.  Block-uniform L.
-__device__ __forceinline__ void ntt16_forward(uint32_t* v, uint32_t* buf, int t, int L, int log2L,
+template <int LG = 0>
+__device__ __forceinline__ void ntt16_forward(uint32_t* v, uint32_t* buf, int t, int Lrt, int lgrt,
                                               const uint2* __restrict__ tw, const NttK& c) {
 #pragma unroll
   for (int k = 8; k < 16; ++k) v[k] = 0u;
+  const int L = LG ? (1 << LG) : Lrt, log2L = LG ? LG : lgrt;
   const int small = log2L & 3, n16 = log2L >> 2;
   int Ns = 1, q = 0;
   // the first pass (Ns = 1, no twiddles) sees the zero upper half
   if (small == 1) {
-    ntt_pass<2, true>(v, t, L, Ns, tw, c);
-    ntt_exchange<2>(v, buf, t, L, Ns);
+    ntt_pass<2, true, LG>(v, t, L, Ns, tw, c);
+    ntt_exchange<2, LG>(v, buf, t, L, Ns);
     Ns = 2;
   } else if (small == 2) {
-    ntt_pass<4, true>(v, t, L, Ns, tw, c);
-    ntt_exchange<4>(v, buf, t, L, Ns);
+    ntt_pass<4, true, LG>(v, t, L, Ns, tw, c);
+    ntt_exchange<4, LG>(v, buf, t, L, Ns);
     Ns = 4;
   } else if (small == 3) {
-    ntt_pass<8, true>(v, t, L, Ns, tw, c);
-    ntt_exchange<8>(v, buf, t, L, Ns);
+    ntt_pass<8, true, LG>(v, t, L, Ns, tw, c);
+    ntt_exchange<8, LG>(v, buf, t, L, Ns);
     Ns = 8;
   } else {
-    ntt_pass<16, true>(v, t, L, Ns, tw, c);
-    if (n16 > 1) ntt_exchange<16>(v, buf, t, L, Ns);
+    ntt_pass<16, true, LG>(v, t, L, Ns, tw, c);
+    if (n16 > 1) ntt_exchange<16, LG>(v, buf, t, L, Ns);
     Ns = 16;
     q = 1;
   }
+#pragma unroll 1
   for (; q < n16; ++q) {
-    ntt_pass<16>(v, t, L, Ns, tw, c);
-    if (q + 1 < n16) ntt_exchange<16>(v, buf, t, L, Ns);
+    ntt_pass<16, false, LG>(v, t, L, Ns, tw, c);
+    if (q + 1 < n16) ntt_exchange<16, LG>(v, buf, t, L, Ns);
     Ns <<= 4;
   }
 }
 // Inverse (unnormalised) from the forward's layout; positions < L/2 are read.
-__device__ __forceinline__ void ntt16_inverse(uint32_t* v, uint32_t* buf, int t, int L, int log2L,
+template <int LG = 0>
+__device__ __forceinline__ void ntt16_inverse(uint32_t* v, uint32_t* buf, int t, int Lrt, int lgrt,
                                               const uint2* __restrict__ twi, const NttK& c) {
+  const int L = LG ? (1 << LG) : Lrt, log2L = LG ? LG : lgrt;
   const int small = log2L & 3, n16 = log2L >> 2;
   int Ns = 1;
+#pragma unroll 1
   for (int q = 0; q < n16; ++q) {
-    ntt_pass<16>(v, t, L, Ns, twi, c);
-    if (q + 1 < n16 || small) ntt_exchange<16>(v, buf, t, L, Ns);
+    ntt_pass<16, false, LG>(v, t, L, Ns, twi, c);
+    if (q + 1 < n16 || small) ntt_exchange<16, LG>(v, buf, t, L, Ns);
     Ns <<= 4;
   }
-  if (small == 1) ntt_pass<2>(v, t, L, Ns, twi, c);
-  else if (small == 2) ntt_pass<4>(v, t, L, Ns, twi, c);
-  else if (small == 3) ntt_pass<8>(v, t, L, Ns, twi, c);
+  if (small == 1) ntt_pass<2, false, LG>(v, t, L, Ns, twi, c);
+  else if (small == 2) ntt_pass<4, false, LG>(v, t, L, Ns, twi, c);
+  else if (small == 3) ntt_pass<8, false, LG>(v, t, L, Ns, twi, c);
 }
 
 // x_q = trunc(|x| 2^(1077 - E)) for E >= the biased exponent of x (E >= 1):
@@ -463,11 +473,11 @@ __device__ __forceinline__ int group_max(int e, int* slot, int G, int F) {
 // sc.res[PI] (the grid's layout), and (PI = 0) each vector's largest biased
 // exponent E into sc.ebuf[vector] (2047: the vector holds an infinity or
 // NaN).  One vector per group of L/16 threads.
-template <int PI, bool COLS>
+template <int PI, bool COLS, int LG>
 __device__ __forceinline__ void ntt_body(const double* __restrict__ x, const ExactScratch& sc, int n1, int n2,
                                          const ExactAxis& ax, int F, int gstride) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = ax.L, Lq = L >> 4, G = Lq;
+  const int L = LG ? (1 << LG) : ax.L, Lq = L >> 4, G = Lq;
   const GroupIdx gi = group_idx<COLS>(G, F);
   uint32_t* buf = reinterpret_cast<uint32_t*>(smem_raw) + (size_t)gi.g * gstride;
   int* slot = reinterpret_cast<int*>(buf);
@@ -496,14 +506,14 @@ __device__ __forceinline__ void ntt_body(const double* __restrict__ x, const Exa
     for (int k = 0; k < 8; ++k) v[k] = residue<PI>(quantize(xv[k], Ee), __double_as_longlong(xv[k]) < 0);
     {
       const NttK c = ntt_consts<PI, false>();
-      ntt16_forward(v, buf, gi.t, L, ax.log2L, tw, c);
+      ntt16_forward<LG>(v, buf, gi.t, L, ax.log2L, tw, c);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const uint2 s = ld_tab(tw + 2 * L + gi.t + k * Lq);
         v[k] = mulq(v[k], s.x, s.y, c.p);
       }
     }
-    ntt16_inverse(v, buf, gi.t, L, ax.log2L, tw + L, ntt_consts<PI, true>());
+    ntt16_inverse<LG>(v, buf, gi.t, L, ax.log2L, tw + L, ntt_consts<PI, true>());
     if (has) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
@@ -522,11 +532,21 @@ __global__ void __launch_bounds__(COLS ? 1024 : 512, COLS ? 1 : 2)
     ntt_kernel(const double* __restrict__ x, ExactScratch sc, int n1, int n2, ExactAxis ax, int F, int gstride,
                const int* gate) {
   if (gate_closed<double>(gate)) return;
-  switch (blockIdx.y) {  // the prime: uniform over the block
-    case 0: ntt_body<0, COLS>(x, sc, n1, n2, ax, F, gstride); break;
-    case 1: ntt_body<1, COLS>(x, sc, n1, n2, ax, F, gstride); break;
-    case 2: ntt_body<2, COLS>(x, sc, n1, n2, ax, F, gstride); break;
-    default: ntt_body<3, COLS>(x, sc, n1, n2, ax, F, gstride); break;
+  // the prime (uniform over the block), and the length 4096 (n 1025..2048) compiled apart
+  if (ax.log2L == 12) {
+    switch (blockIdx.y) {
+      case 0: ntt_body<0, COLS, 12>(x, sc, n1, n2, ax, F, gstride); break;
+      case 1: ntt_body<1, COLS, 12>(x, sc, n1, n2, ax, F, gstride); break;
+      case 2: ntt_body<2, COLS, 12>(x, sc, n1, n2, ax, F, gstride); break;
+      default: ntt_body<3, COLS, 12>(x, sc, n1, n2, ax, F, gstride); break;
+    }
+    return;
+  }
+  switch (blockIdx.y) {
+    case 0: ntt_body<0, COLS, 0>(x, sc, n1, n2, ax, F, gstride); break;
+    case 1: ntt_body<1, COLS, 0>(x, sc, n1, n2, ax, F, gstride); break;
+    case 2: ntt_body<2, COLS, 0>(x, sc, n1, n2, ax, F, gstride); break;
+    default: ntt_body<3, COLS, 0>(x, sc, n1, n2, ax, F, gstride); break;
   }
 }
 
