@@ -183,9 +183,13 @@ __device__ __forceinline__ void twiddle_apply(cx<T>* v, int i, int step, const c
 
 // One Stockham pass: twiddles for sub-transforms of length Ns * R, radix-R
 // DFTs of the 16/R items this thread owns (item i = position t + i L/16).
-template <typename T, bool INV, int R>
-__device__ __forceinline__ void fft_pass(cx<T>* v, int t, int L, int Ns, const cx<T>* __restrict__ tw) {
+// LG > 0: the transform length 2^LG is a compile-time constant (the index
+// arithmetic folds); LG = 0: L is the runtime argument.  Both give the same
+// arithmetic in the same order.
+template <typename T, bool INV, int R, int LG = 0>
+__device__ __forceinline__ void fft_pass(cx<T>* v, int t, int Lrt, int Ns, const cx<T>* __restrict__ tw) {
   constexpr int S = 16 / R;
+  const int L = LG ? (1 << LG) : Lrt;
   const int Lq = L >> 4;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
@@ -200,9 +204,10 @@ __device__ __forceinline__ void fft_pass(cx<T>* v, int t, int L, int Ns, const c
 
 // Moves the pass outputs through shared memory so that every thread again
 // holds the positions t + k L/16 that the next pass reads.
-template <typename T, int R>
-__device__ __forceinline__ void fft_exchange(cx<T>* v, cx<T>* buf, int t, int L, int Ns) {
+template <typename T, int R, int LG = 0>
+__device__ __forceinline__ void fft_exchange(cx<T>* v, cx<T>* buf, int t, int Lrt, int Ns) {
   constexpr int S = 16 / R;
+  const int L = LG ? (1 << LG) : Lrt;
   const int Lq = L >> 4;
   __syncthreads();
 #pragma unroll
@@ -223,30 +228,32 @@ __device__ __forceinline__ void fft_exchange(cx<T>* v, cx<T>* buf, int t, int L,
 // is zero on the upper half (positions >= L/2, i.e. k >= 8): those registers
 // are cleared here so the first pass's arithmetic on them folds away.  All
 // threads of the block must call it with the same L (it synchronises).
-template <typename T>
-__device__ __forceinline__ void fft16_forward(cx<T>* v, cx<T>* buf, int t, int L, int log2L,
+template <typename T, int LG = 0>
+__device__ __forceinline__ void fft16_forward(cx<T>* v, cx<T>* buf, int t, int Lrt, int lgrt,
                                               const cx<T>* __restrict__ tw) {
 #pragma unroll
   for (int k = 8; k < 16; ++k) v[k] = {T(0), T(0)};
+  const int L = LG ? (1 << LG) : Lrt, log2L = LG ? LG : lgrt;
   const int small = log2L & 3;
   const int n16 = log2L >> 2;
   int Ns = 1;
   if (small == 1) {
-    fft_pass<T, false, 2>(v, t, L, Ns, tw);
-    fft_exchange<T, 2>(v, buf, t, L, Ns);
+    fft_pass<T, false, 2, LG>(v, t, L, Ns, tw);
+    fft_exchange<T, 2, LG>(v, buf, t, L, Ns);
     Ns = 2;
   } else if (small == 2) {
-    fft_pass<T, false, 4>(v, t, L, Ns, tw);
-    fft_exchange<T, 4>(v, buf, t, L, Ns);
+    fft_pass<T, false, 4, LG>(v, t, L, Ns, tw);
+    fft_exchange<T, 4, LG>(v, buf, t, L, Ns);
     Ns = 4;
   } else if (small == 3) {
-    fft_pass<T, false, 8>(v, t, L, Ns, tw);
-    fft_exchange<T, 8>(v, buf, t, L, Ns);
+    fft_pass<T, false, 8, LG>(v, t, L, Ns, tw);
+    fft_exchange<T, 8, LG>(v, buf, t, L, Ns);
     Ns = 8;
   }
+#pragma unroll 1
   for (int p = 0; p < n16; ++p) {
-    fft_pass<T, false, 16>(v, t, L, Ns, tw);
-    if (p + 1 < n16) fft_exchange<T, 16>(v, buf, t, L, Ns);
+    fft_pass<T, false, 16, LG>(v, t, L, Ns, tw);
+    if (p + 1 < n16) fft_exchange<T, 16, LG>(v, buf, t, L, Ns);
     Ns <<= 4;
   }
 }
@@ -254,20 +261,22 @@ __device__ __forceinline__ void fft16_forward(cx<T>* v, cx<T>* buf, int t, int L
 // Inverse transform (unnormalised, times L) from the forward's register layout;
 // output in natural order at positions t + k L/16.  Callers read only k < 8
 // (positions < L/2), so the last pass's other outputs are never formed.
-template <typename T>
-__device__ __forceinline__ void fft16_inverse(cx<T>* v, cx<T>* buf, int t, int L, int log2L,
+template <typename T, int LG = 0>
+__device__ __forceinline__ void fft16_inverse(cx<T>* v, cx<T>* buf, int t, int Lrt, int lgrt,
                                               const cx<T>* __restrict__ tw) {
+  const int L = LG ? (1 << LG) : Lrt, log2L = LG ? LG : lgrt;
   const int small = log2L & 3;
   const int n16 = log2L >> 2;
   int Ns = 1;
+#pragma unroll 1
   for (int p = 0; p < n16; ++p) {
-    fft_pass<T, true, 16>(v, t, L, Ns, tw);
-    if (p + 1 < n16 || small) fft_exchange<T, 16>(v, buf, t, L, Ns);
+    fft_pass<T, true, 16, LG>(v, t, L, Ns, tw);
+    if (p + 1 < n16 || small) fft_exchange<T, 16, LG>(v, buf, t, L, Ns);
     Ns <<= 4;
   }
-  if (small == 1) fft_pass<T, true, 2>(v, t, L, Ns, tw);
-  else if (small == 2) fft_pass<T, true, 4>(v, t, L, Ns, tw);
-  else if (small == 3) fft_pass<T, true, 8>(v, t, L, Ns, tw);
+  if (small == 1) fft_pass<T, true, 2, LG>(v, t, L, Ns, tw);
+  else if (small == 2) fft_pass<T, true, 4, LG>(v, t, L, Ns, tw);
+  else if (small == 3) fft_pass<T, true, 8, LG>(v, t, L, Ns, tw);
 }
 
 }  // namespace rsfde

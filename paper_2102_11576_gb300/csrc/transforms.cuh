@@ -183,7 +183,7 @@ __device__ __forceinline__ void st_pair(X* p, X a, X b) {
 // The body takes its block index and block count explicitly: a kernel
 // launch passes blockIdx.x and gridDim.x, a batched launch the instance's
 // own block of its virtual grid.
-template <typename T, typename Tin, int MODE, bool COLS, typename Tout>
+template <typename T, typename Tin, int MODE, bool COLS, typename Tout, int LG = 0>
 __device__ __forceinline__ void toeplitz_body(const Tin* __restrict__ z, T* __restrict__ tmpx,
                                               const uint8_t* __restrict__ phi, double pen,
                                               const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2,
@@ -192,7 +192,7 @@ __device__ __forceinline__ void toeplitz_body(const Tin* __restrict__ z, T* __re
   if (gate_closed<T>(gate)) return;
   const T tpen = cvt<T>(pen);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int L = ax.L, Lq = L >> 4, G = Lq;
+  const int L = LG ? (1 << LG) : ax.L, Lq = L >> 4, G = Lq;
   const GroupIdx gi = group_idx<COLS>(G, F);
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw) + (size_t)gi.g * gstride;
   const int nvec = COLS ? n1 : n2, len = COLS ? n2 : n1;
@@ -235,14 +235,14 @@ __device__ __forceinline__ void toeplitz_body(const Tin* __restrict__ z, T* __re
       v[k] = {re, im};
     }
     const cx<T>* tw = reinterpret_cast<const cx<T>*>(ax.tw);
-    fft16_forward<T>(v, buf, gi.t, L, ax.log2L, tw);
+    fft16_forward<T, LG>(v, buf, gi.t, L, ax.log2L, tw);
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const T sg = ldg_t(ax.sigma + gi.t + k * Lq);
       v[k].r *= sg;
       v[k].i *= sg;
     }
-    fft16_inverse<T>(v, buf, gi.t, L, ax.log2L, tw);
+    fft16_inverse<T, LG>(v, buf, gi.t, L, ax.log2L, tw);
     if constexpr (kPairIO) {
       if (pair_io) {
         if (live) {
@@ -330,6 +330,14 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : RSFDE_FP32_THREADS)
     toeplitz_kernel(const Tin* __restrict__ z, T* __restrict__ tmpx, const uint8_t* __restrict__ phi,
                     double pen, const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2,
                     AxisTables<T> ax, int F, int gstride, const int* gate, double* partials, SolverState* st) {
+  // the FP32 operator at length 4096 (n 1025..2048) compiled apart (the same arithmetic)
+  if constexpr (std::is_same<T, float>::value && MODE == MODE_APPLY) {
+    if (ax.log2L == 12) {
+      toeplitz_body<T, Tin, MODE, COLS, Tout, 12>(z, tmpx, phi, pen, b, out, n1, n2, ax, F, gstride, gate, partials,
+                                                  st, blockIdx.x, gridDim.x);
+      return;
+    }
+  }
   toeplitz_body<T, Tin, MODE, COLS, Tout>(z, tmpx, phi, pen, b, out, n1, n2, ax, F, gstride, gate, partials, st,
                                           blockIdx.x, gridDim.x);
 }
