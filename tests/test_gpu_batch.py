@@ -22,7 +22,8 @@ from paper_2102_11576_gb300 import Batch, Solver  # noqa: E402
 # all instances); the other forms the graph of per-instance branches
 @pytest.mark.parametrize("precond,matvec,basis,resid", [("fp32", "df32", "df32", "fp64"), ("bf16", "fp32", "fp32", "df32"),
                                                         ("fp32", "fp32", "fp64", "fp64"),
-                                                        ("fp32", "fp32", "fp32", "fp64")])
+                                                        ("fp32", "fp32", "fp32", "fp64"),
+                                                        ("bf16x3", "fp32", "fp64", "exact")])
 def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, basis, resid):
     probs = workloads.make_batch(seed=5, count=7, n_range=(9, 96), steps=10)
     steps = 3
