@@ -288,7 +288,7 @@ static void launch_gemm_t(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int 
   dim3 grid((N + BN - 1) / BN, (M + kGemmBM - 1) / kGemmBM, channels);
   const CUtensorMap& bh = BN == 64 ? B.map64_hi : B.map_hi;
   const CUtensorMap& bl = BN == 64 ? B.map64_lo : B.map_lo;
-  launch_pdl(k, grid, dim3(kGemmThreads), smem, s, A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
+  launch_pdl(k, grid, dim3(gemm_threads(NT)), smem, s, A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
 }
 // Tile width of a GEMM: the plan's recorded choice (autotuner) or the default
 // rule.  Plain BF16 (two operand tiles per K slice) takes 64-wide tiles

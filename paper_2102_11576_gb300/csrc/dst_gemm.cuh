@@ -88,11 +88,13 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
 }
 
 // Threads of a CTA: warp 0 lane 0 issues the TMA loads, warp 1 lane 0 the MMAs,
-// and all eight warps run the epilogue (two per TMEM lane quarter, alternate
-// 32-column chunks), which is latency-bound with fewer warps.
-constexpr int kGemmThreads = 256;
+// and every warp runs the epilogue (the warps of a TMEM lane quarter take
+// alternate 32-column chunks), which is latency-bound: split BF16 (one CTA
+// per SM) runs sixteen warps, four per quarter; plain BF16 (two CTAs per SM)
+// eight.
+__host__ __device__ constexpr int gemm_threads(int NT) { return NT == 3 ? 512 : 256; }
 template <int EPI, int NT, bool SYM, int BN>
-__global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
+__global__ void __launch_bounds__(gemm_threads(NT), gemm_ctas_per_sm(NT, BN))
     dst_gemm_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                     const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, int K,
                     GemmEpiParams ep, int* err, const int* gate) {
@@ -102,6 +104,8 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
   constexpr int kB = gemm_btile_bytes(BN);
   constexpr int kGemmStages = gemm_stages(NT, BN);
   constexpr uint32_t kCols = SYM ? 2 * BN : BN;  // TMEM columns: one or two accumulators
+  constexpr int kGemmThreads = gemm_threads(NT);
+  constexpr int kPerQuarter = kGemmThreads / 128;  // warps per TMEM lane quarter
   pdl_wait();
   pdl_trigger();
   if (gate && *(volatile const int*)gate == 0) return;
@@ -210,6 +214,7 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
   }
   if (staged) {
     const int q4 = warp & 3, half = warp >> 2;
+    static_assert(!kCanStage || kPerQuarter == 2, "the staged path runs two warps per quarter");
     const int lc = (lane & 1) * kStRun + q4 * 16 + (lane >> 1);  // this lane's m within a staged row
     __nv_bfloat16* st = reinterpret_cast<__nv_bfloat16*>(smem);
     const float lm = EPI == EPI_DIVIDE_T ? __ldg(ep.lam_m + m0 + q4 * 32 + lane) : 0.0f;
@@ -258,8 +263,8 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
       *reinterpret_cast<uint4*>(ep.out_hi + (size_t)grow * ep.ldo + colbase + run * ep.hk + off) = val;
     }
   } else if (ok && !*(volatile int*)err) {
-    const int q4 = warp & 3, half = warp >> 2;  // TMEM lane quarter, chunk parity
-    const int mloc = q4 * 32 + lane;            // TMEM lane = row of the tile
+    const int q4 = warp & 3, cq = warp >> 2;  // TMEM lane quarter, first chunk
+    const int mloc = q4 * 32 + lane;          // TMEM lane = row of the tile
     const int m = m0 + mloc;
     const bool mvalid = m < ep.M;
     const float lm = (EPI == EPI_DIVIDE_T && mvalid) ? __ldg(ep.lam_m + m) : 0.0f;
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(kGemmThreads, gemm_ctas_per_sm(NT, BN))
     const int col = (EPI == EPI_SPLIT_T && m >= ep.row_b) ? ep.col_b + sym_perm(m - ep.row_b, ep.hk)
                                                            : sym_perm(m, ep.hk);
     const uint32_t lane_off = (uint32_t)(q4 * 32) << 16;
-    for (int c = half; c < BN / 32; c += 2) {
+    for (int c = cq; c < BN / 32; c += kPerQuarter) {
       float u[32], e[32];
       if constexpr (SYM) tmem_ld32x2(taddr + lane_off + (uint32_t)(c * 32), taddr + lane_off + (uint32_t)(BN + c * 32), u, e);
       else tmem_ld32(taddr + lane_off + (uint32_t)(c * 32), u);  // whole warp
