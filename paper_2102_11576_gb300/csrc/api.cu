@@ -10,6 +10,8 @@
 #include <functional>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>  // header-only: ranges reach a profiler when one is attached
+
 #include "fft.cuh"  // host butterflies for the setup spectra
 
 #include "internal.h"
@@ -289,11 +291,21 @@ cudaEvent_t prof_event(rsfde_ctx* c) {
 }
 
 // Brackets one launch of kernel class k with events when profiling is on.
+// A named NVTX range over a host-side scope (an entry point, or the enqueue
+// of one kernel of a class), for timeline profilers.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 struct ProfScope {
   rsfde_ctx* c;
   int k;
   cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(rsfde_ctx* c_, int k_) : c(c_), k(k_) {
+  NvtxRange range;
+  ProfScope(rsfde_ctx* c_, int k_) : c(c_), k(k_), range(rsfde_kernel_class_name(k_)) {
     c->launches += 1;
     if (!c->prof_on) return;
     a = prof_event(c);
@@ -1575,6 +1587,7 @@ int rsfde_set_stream(rsfde_ctx* c, void* stream) {
 }
 
 int rsfde_solve(rsfde_ctx* c, const double* b, double* x, rsfde_stats* stats) {
+  NvtxRange range("rsfde_solve");
   if (!c || !b || !x) return RSFDE_EINVAL;
   const size_t bytes = c->N * sizeof(double);
   begin_call(c);
@@ -1603,6 +1616,7 @@ int rsfde_rhs(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, cons
 
 int rsfde_step(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, const double* src, double* u_next,
                rsfde_stats* stats) {
+  NvtxRange range("rsfde_step");
   if (!c || !u_prev || !u_next) return RSFDE_EINVAL;
   begin_call(c);
   c->call_bytes = rhs_bytes(c, u_prevprev != nullptr, src != nullptr);
@@ -1621,6 +1635,7 @@ int rsfde_step(rsfde_ctx* c, const double* u_prev, const double* u_prevprev, con
 
 int rsfde_step_host(rsfde_ctx* c, const double* u_prev_h, const double* u_prevprev_h, const double* src_h,
                     double* u_next_h, rsfde_stats* stats) {
+  NvtxRange range("rsfde_step_host");
   if (!c || !u_prev_h || !u_next_h) return RSFDE_EINVAL;
   const size_t bytes = c->N * sizeof(double);
   if (!c->hbuf) {
@@ -1649,12 +1664,14 @@ int rsfde_step_host(rsfde_ctx* c, const double* u_prev_h, const double* u_prevpr
 }
 
 int rsfde_adjoint(rsfde_ctx* c, const double* lam, double* mu, rsfde_stats* stats) {
+  NvtxRange range("rsfde_adjoint");
   // M is symmetric (Lemma 2.3): M^T mu = lam is the forward system.
   return rsfde_solve(c, lam, mu, stats);
 }
 
 int rsfde_adjoint_step(rsfde_ctx* c, const double* u_prev, const double* u_k, const double* lam, double* mu,
                        double* lam_prev, double* grad_src, double* grad_k, rsfde_stats* stats) {
+  NvtxRange range("rsfde_adjoint_step");
   if (!c || !u_prev || !u_k || !lam || !mu || !lam_prev || !grad_k) return RSFDE_EINVAL;
   int rc = rsfde_solve(c, lam, mu, stats);  // M^T = M (Lemma 2.3)
   if (rc == RSFDE_ECUDA || rc == RSFDE_ENOMEM || rc == RSFDE_EINVAL) return rc;
@@ -1679,12 +1696,14 @@ int rsfde_adjoint_step(rsfde_ctx* c, const double* u_prev, const double* u_k, co
 }
 
 int rsfde_apply_M(rsfde_ctx* c, const double* z, double* w) {
+  NvtxRange range("rsfde_apply_M");
   if (!c || !z || !w) return RSFDE_EINVAL;
   enqueue_apply_M<double>(c, z, w, nullptr);
   return check_launch(c);
 }
 
 int rsfde_residual(rsfde_ctx* c, const double* x, const double* b, double* r) {
+  NvtxRange range("rsfde_residual");
   if (!c || !x || !b || !r || r == x || r == b) return RSFDE_EINVAL;
   if (c->opts.resid_prec == RSFDE_DF32) return RSFDE_EINVAL;
   enqueue_resid_only(c, x, b, r, nullptr);
@@ -1692,6 +1711,7 @@ int rsfde_residual(rsfde_ctx* c, const double* x, const double* b, double* r) {
 }
 
 int rsfde_apply_precond(rsfde_ctx* c, const double* v, double* z) {
+  NvtxRange range("rsfde_apply_precond");
   if (!c || !v || !z) return RSFDE_EINVAL;
   if (bf16_precond_on(c)) {
     int rc = ensure_bf16(c);
@@ -1706,6 +1726,7 @@ int rsfde_apply_precond(rsfde_ctx* c, const double* v, double* z) {
 }
 
 int rsfde_dst2(rsfde_ctx* c, const double* v, double* out) {
+  NvtxRange range("rsfde_dst2");
   if (!c || !v || !out) return RSFDE_EINVAL;
   {
     ProfScope ps(c, RSFDE_K_DST_ROWS);
@@ -1747,6 +1768,7 @@ int rsfde_set_wait_cycles(rsfde_ctx* c, int64_t cycles) {
 }
 
 int rsfde_autotune(rsfde_ctx* c, int32_t reps, int32_t* chosen) {
+  NvtxRange range("rsfde_autotune");
   if (!c || reps < 1) return RSFDE_EINVAL;
   return autotune_ctx(c, reps, chosen);
 }
@@ -1846,6 +1868,7 @@ int rsfde_batch_set(rsfde_batch* b, int32_t i, const double* u0, const double* s
 }
 
 int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats) {
+  NvtxRange range("rsfde_batch_run");
   if (!b || steps < 0) return RSFDE_EINVAL;
   const bool direct = b->multi && !b->ctx[0]->opts.use_graph;
   for (int k = 0; k < steps; ++k) {

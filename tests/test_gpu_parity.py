@@ -338,3 +338,30 @@ def test_ellipse512_march_with_source():
         assert diff <= np.abs(r).max() + np.abs(b - orc.apply_M(host(ref))).max() + 1e-15
         assert diff / np.abs(host(ref)).max() <= 1e-9
         prevprev, prev = prev, nxt
+
+
+def test_resume_from_saved_state_reproduces_the_march():
+    """Checkpoint and resume: the march's state is the pair (u^{k-1}, u^{k-2})
+    (the extrapolated guess needs both, Section 5).  A fresh context started
+    from a pair saved after step 3 reproduces steps 4-6 of the uninterrupted
+    march bit for bit (the kernels and reductions are deterministic)."""
+    w = workloads.random_problem(31, 60, 44)
+    args = (w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"],
+            w["dt"], w["eta"])
+    kw = dict(precond="bf16x3", matvec="fp32", basis="fp64", resid="exact", restart=10, tol=1e-11)
+    a = Solver(*args, **kw)
+    prev, pp = dev(np.abs(w["field"])), None
+    saved = []
+    for _ in range(6):
+        nxt, st = a.step(prev, pp)
+        assert st["converged"]
+        pp, prev = prev, nxt.clone()
+        saved.append((prev.clone(), pp.clone()))
+    a.close()
+    b = Solver(*args, **kw)
+    prev, pp = saved[2]
+    for k in range(3, 6):
+        nxt, st = b.step(prev, pp)
+        pp, prev = prev, nxt.clone()
+        assert torch.equal(prev, saved[k][0]), k
+    b.close()
