@@ -282,8 +282,7 @@ int rsfde_get_params(rsfde_ctx* ctx, double* out5);
  * else RSFDE_EINVAL.  Calls no cudaMalloc, cudaFree or other allocating routine.
  *
  * The first call on each device looks up the static arrays' device
- * addresses (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  A call whose (n1, n2) or stream
+ * addresses (cudaGetSymbolAddress) with that device current.  A call whose (n1, n2) or stream
  * differs from the previous call's on that device copies the tables from
  * host memory, which makes the host wait for the stream's earlier work; a
  * repeat with the same sizes and stream reuses them.  Every call uses the
