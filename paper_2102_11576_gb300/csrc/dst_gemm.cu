@@ -279,16 +279,32 @@ void bf16_plan_set_wait(Bf16Plan* p, long long cycles) {
   if (p) p->wait_cycles = cycles > 0 ? cycles : kWaitCycles;
 }
 
+// One tile per CTA while the tiles fit one wave; split BF16 with between one
+// and two waves of tiles runs one CTA per SM with two tiles each (the second
+// tile's main loop overlaps the first one's epilogue; the makespan is two
+// main loops and one epilogue instead of two of each).
 template <int EPI, int NT, bool SYM, int BN>
 static void launch_gemm_t(const Bf16Mat& A, const Bf16Mat& B, int M, int N, int K, int channels,
-                          const GemmEpiParams& ep, int* err, const int* gate, cudaStream_t s) {
-  auto k = dst_gemm_kernel<EPI, NT, SYM, BN>;
+                          GemmEpiParams ep, int* err, const int* gate, cudaStream_t s) {
   constexpr int smem = gemm_smem(NT, BN);
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  dim3 grid((N + BN - 1) / BN, (M + kGemmBM - 1) / kGemmBM, channels);
   const CUtensorMap& bh = BN == 64 ? B.map64_hi : B.map_hi;
   const CUtensorMap& bl = BN == 64 ? B.map64_lo : B.map_lo;
-  launch_pdl(k, grid, dim3(gemm_threads(NT)), smem, s, A.map_hi, A.map_lo, bh, bl, K, ep, err, gate);
+  const int gx = (N + BN - 1) / BN, gy = (M + kGemmBM - 1) / kGemmBM;
+  const long tiles = (long)gx * gy * channels;
+  ep.nch = channels;
+  if constexpr (NT == 3) {
+    if (tiles > kNumSMs && tiles <= 2L * kNumSMs) {
+      auto k = dst_gemm_kernel<EPI, NT, SYM, BN, 2>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      launch_pdl(k, dim3(kNumSMs), dim3(gemm_threads(NT)), smem, s, A.map_hi, A.map_lo, bh, bl, K, ep, err,
+                 gate);
+      return;
+    }
+  }
+  auto k = dst_gemm_kernel<EPI, NT, SYM, BN, 1>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  launch_pdl(k, dim3(gx, gy, channels), dim3(gemm_threads(NT)), smem, s, A.map_hi, A.map_lo, bh, bl, K, ep, err,
+             gate);
 }
 // Tile width of a GEMM: the plan's recorded choice (autotuner) or the default
 // rule.  Plain BF16 (two operand tiles per K slice) takes 64-wide tiles

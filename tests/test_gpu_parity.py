@@ -276,22 +276,34 @@ def test_full_size_polygon2048_against_oracle():
     Givens and true residual, the residual's Toeplitz products exact) and of the FP64 form: the oracle's full-grid
     M x gives the true relative residual (<= 1e-10), and Lemma 3.1 with
     Lemma 2.3 (||M^-1||_inf <= 1) bounds the two solutions' difference by
-    their residuals.  The oracle runs in two spawned processes while the GPU
-    works."""
+    their residuals.  (c) P-hat^-1 v at 2048 x 1232 in the split-BF16 and FP32
+    forms: between one and two waves of GEMM tiles (two tiles per CTA), with
+    ragged last tiles in both GEMM dimensions.  The oracle runs in spawned
+    processes while the GPU works."""
     import multiprocessing as mp
     import _oracle_jobs
     w = workloads.make("polygon2048")
     args = (w["n1"], w["n2"], w["box"], w["in_omega"], w["alpha1"], w["alpha2"], w["kx"], w["ky"], w["dt"],
             w["eta"])
     v = rng_field(w["n2"], w["n1"], seed=13)
+    w2 = workloads.random_problem(9, 2048, 1232)
+    args2 = (w2["n1"], w2["n2"], w2["box"], w2["in_omega"], w2["alpha1"], w2["alpha2"], w2["kx"], w2["ky"],
+             w2["dt"], w2["eta"])
+    v2 = w2["field"]
     ctx = mp.get_context("spawn")
-    with ctx.Pool(3) as pool:
+    with ctx.Pool(4) as pool:
         job_p = pool.apply_async(_oracle_jobs.apply_precond, (args, v))
+        job_p2 = pool.apply_async(_oracle_jobs.apply_precond, (args2, v2))
         job_b = pool.apply_async(_oracle_jobs.rhs, (args, w["u0"]))
         got = {}
         for prec in ("fp64", "fp32", "bf16x3", "bf16"):
             gpu = Solver(*args, restart=w["restart"], precond=prec)
             got[prec] = host(gpu.apply_precond(dev(v)))
+            gpu.close()
+        got2 = {}
+        for prec in ("fp32", "bf16x3"):
+            gpu = Solver(*args2, precond=prec)
+            got2[prec] = host(gpu.apply_precond(dev(v2)))
             gpu.close()
         steps = {}
         for name, kw in (("headline", dict(precond="bf16x3", matvec="fp32", basis="fp64", resid="exact")),
@@ -303,10 +315,13 @@ def test_full_size_polygon2048_against_oracle():
             gpu.close()
         jobs_m = {k: pool.apply_async(_oracle_jobs.apply_M, (args, x)) for k, x in steps.items()}
         ref = job_p.get()
+        ref2 = job_p2.get()
         b = job_b.get()
         mx = {k: j.get() for k, j in jobs_m.items()}
     for prec, tol in (("fp64", 1e-11), ("fp32", 2e-5), ("bf16x3", 2e-4), ("bf16", 2e-2)):
         assert rel(got[prec], ref) <= tol, (prec, rel(got[prec], ref))
+    for prec, tol in (("fp32", 2e-5), ("bf16x3", 2e-4)):
+        assert rel(got2[prec], ref2) <= tol, (prec, rel(got2[prec], ref2))
     r = {k: b - mx[k] for k in steps}
     for k in steps:
         assert np.linalg.norm(r[k]) <= 1.01e-10 * np.linalg.norm(b), k
