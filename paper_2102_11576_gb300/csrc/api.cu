@@ -1084,6 +1084,12 @@ struct rsfde_batch {
   MultiGrid g_trows, g_tcols, g_drows, g_pcols, g_prows, g_rhs, g_xupd, g_fin, g_rrows, g_rcols;
   std::vector<MultiGrid> g_dot, g_upd;  // per Arnoldi column j (one active array shared by all j)
   int* actives = nullptr;               // device: the active prefixes
+  // split-BF16 preconditioner of the lock-step form: the split and the four
+  // grouped GEMMs, their descriptors, and the GEMM launches' give-up flag
+  bool bf16 = false;
+  MultiGrid g_split, g_gemm[4];
+  void* gdesc = nullptr;
+  int* gemm_err = nullptr;
   int64_t launches_per_body = 0;
   cudaStream_t cap = nullptr;
 };
@@ -1096,6 +1102,8 @@ void free_batch(rsfde_batch* b) {
   if (b->prefixes) cudaFree(b->prefixes);
   if (b->actives) cudaFree(b->actives);
   if (b->runs) cudaFree(b->runs);
+  bf16_group_destroy(b->gdesc);
+  if (b->gemm_err) cudaFree(b->gemm_err);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (auto& x : b->exec)
     if (x) cudaGraphExecDestroy(x);
@@ -1110,12 +1118,16 @@ void free_batch(rsfde_batch* b) {
 // launch over all instances (each on its own virtual grid, gated by its own
 // solver flags), and the cycles repeat while any instance still runs.  It
 // covers the FFT preconditioner in FP32 with the FP32 operator, an FP64 or
-// FP32 basis and the FP64 true residual; other options use the graph of
-// per-instance branches (build_batch_graph).
-enum { MV_FP32_B64, MV_FP32_B32, MV_NONE };
+// FP32 basis and the FP64 true residual, and the split-BF16 tensor-core
+// preconditioner with the FP32 operator, the FP64 basis and the FP64 true
+// residual; other options use the graph of per-instance branches
+// (build_batch_graph).
+enum { MV_FP32_B64, MV_FP32_B32, MV_BF16X3_B64, MV_NONE };
 int multi_form(const rsfde_opts& o) {
-  if (o.variant != RSFDE_FGMRES_RIGHT || !o.use_precond || o.precond_prec != RSFDE_FP32) return MV_NONE;
+  if (o.variant != RSFDE_FGMRES_RIGHT || !o.use_precond) return MV_NONE;
   if (o.resid_prec != RSFDE_FP64 || o.matvec_prec != RSFDE_FP32) return MV_NONE;
+  if (o.precond_prec == RSFDE_BF16X3) return o.basis_prec == RSFDE_FP64 ? MV_BF16X3_B64 : MV_NONE;
+  if (o.precond_prec != RSFDE_FP32) return MV_NONE;
   return o.basis_prec == RSFDE_FP64 ? MV_FP32_B64 : MV_FP32_B32;
 }
 
@@ -1129,9 +1141,12 @@ void enqueue_multi_residual(rsfde_batch* b, cudaStream_t s) {
 // column j (gate run_iter), or the cycle end (gate run_cycle).
 void enqueue_compact_iter(rsfde_batch* b, int j, cudaStream_t s) {
   CompactArgs a{};
-  const MultiGrid* fam[] = {&b->g_drows, &b->g_pcols, &b->g_prows, &b->g_trows, &b->g_tcols, &b->g_dot[j],
+  const MultiGrid* fft[] = {&b->g_drows, &b->g_pcols, &b->g_prows, &b->g_trows, &b->g_tcols, &b->g_dot[j],
                             &b->g_upd[j]};
-  a.nfam = 7;
+  const MultiGrid* gem[] = {&b->g_split,    &b->g_gemm[0], &b->g_gemm[1], &b->g_gemm[2], &b->g_gemm[3],
+                            &b->g_trows,    &b->g_tcols,   &b->g_dot[j],  &b->g_upd[j]};
+  const MultiGrid* const* fam = b->bf16 ? gem : fft;
+  a.nfam = b->bf16 ? 9 : 7;
   for (int f = 0; f < a.nfam; ++f) {
     a.prefix[f] = fam[f]->prefix;
     a.active[f] = fam[f]->active;
@@ -1155,11 +1170,18 @@ void enqueue_multi_cycle(rsfde_batch* b, cudaStream_t s) {
   const bool cgs2 = o.arnoldi == RSFDE_CGS2;
   for (int j = 0; j < o.restart; ++j) {
     enqueue_compact_iter(b, j, s);
-    launch_precond_multi<float, float, Tv>(b->inst, b->g_drows, b->g_pcols, b->g_prows, j, s);
+    if (b->bf16) {
+      launch_split_multi(b->inst, b->g_split, j, s);
+      for (int k = 0; k < 4; ++k)
+        launch_bf16_group(k, b->gdesc, b->count, b->g_gemm[k].active, b->g_gemm[k].total, j, b->gemm_err, s);
+    } else {
+      launch_precond_multi<float, float, Tv>(b->inst, b->g_drows, b->g_pcols, b->g_prows, j, s);
+    }
     launch_operator_multi<Tm, float, Tv>(b->inst, b->g_trows, b->g_tcols, j, s);
     for (int pass = 0; pass < (cgs2 ? 2 : 1); ++pass) {
       launch_multidot_multi<Tv>(b->inst, b->g_dot[j], j, pass, s);
-      launch_update_multi<Tv>(b->inst, b->g_upd[j], j, (!cgs2 || pass == 1) ? 1 : 0, s);
+      launch_update_multi<Tv>(b->inst, b->g_upd[j], j, (!cgs2 || pass == 1) ? 1 : 0,
+                              b->bf16 && j + 1 < o.restart ? 1 : 0, s);
     }
   }
   launch_solve_y_multi(b->inst, b->count, s);
@@ -1168,12 +1190,21 @@ void enqueue_multi_cycle(rsfde_batch* b, cudaStream_t s) {
   enqueue_multi_residual<Tm, Tv>(b, s);
 }
 void enqueue_multi_cycle_any(rsfde_batch* b, cudaStream_t s) {
-  if (multi_form(b->ctx[0]->opts) == MV_FP32_B64) enqueue_multi_cycle<float, double>(b, s);
+  if (multi_form(b->ctx[0]->opts) != MV_FP32_B32) enqueue_multi_cycle<float, double>(b, s);
   else enqueue_multi_cycle<float, float>(b, s);
 }
 void enqueue_multi_residual_any(rsfde_batch* b, cudaStream_t s) {
-  if (multi_form(b->ctx[0]->opts) == MV_FP32_B64) enqueue_multi_residual<float, double>(b, s);
+  if (multi_form(b->ctx[0]->opts) != MV_FP32_B32) enqueue_multi_residual<float, double>(b, s);
   else enqueue_multi_residual<float, float>(b, s);
+}
+// Launches of one loop-body run: per Arnoldi column the compaction, the
+// preconditioner (three FFT passes, or the split and four GEMMs), two
+// operator passes, multi-dot and update (two more with CGS2); then the back
+// substitution, compaction, solution update, residual (2) and loop condition.
+int64_t multi_body_launches(const rsfde_batch* b) {
+  const rsfde_opts& o = b->ctx[0]->opts;
+  const int per_col = 1 + (b->bf16 ? 5 : 3) + 2 + (o.arnoldi == RSFDE_CGS2 ? 4 : 2);
+  return (int64_t)o.restart * per_col + 6;
 }
 
 // Device descriptors and the prefixes of every multi-instance grid.
@@ -1184,7 +1215,14 @@ int setup_multi(rsfde_batch* b) {
   for (rsfde_ctx* c : b->ctx)
     if (c->x64.tab.L > 4096 || c->y64.tab.L > 4096) return RSFDE_OK;  // one 256-thread group per transform at most
   const int n = b->count, m = o.restart;
+  const bool bf16 = multi_form(o) == MV_BF16X3_B64;
+  if (bf16)
+    for (rsfde_ctx* c : b->ctx) {
+      const int rc = ensure_bf16(c);
+      if (rc != RSFDE_OK) return rc;
+    }
   std::vector<BatchInst> hi(n);
+  std::vector<Bf16GroupInst> gin;
   for (int i = 0; i < n; ++i) {
     rsfde_ctx* c = b->ctx[i];
     BatchInst& I = hi[i];
@@ -1213,6 +1251,20 @@ int setup_multi(rsfde_batch* b) {
     I.y32 = c->y32.tab;
     I.xdf = c->xdf.tab;
     I.ydf = c->ydf.tab;
+    I.a0 = I.a0_lo = nullptr;
+    I.a0_ld = I.a0_hk = I.a0_fused = 0;
+    if (bf16) {
+      // as the single-instance cycle: the basis update writes the next
+      // operand when the plan takes it (enqueue_cycle_t's `fused`)
+      Bf16Out bo{};
+      I.a0_fused = (c->N % 2 == 0 && bf16_plan_a0(c->bf16, 2, &bo)) ? 1 : 0;
+      bf16_plan_a0_any(c->bf16, &bo);
+      I.a0 = bo.a0;
+      I.a0_lo = bo.lo;
+      I.a0_ld = bo.ld;
+      I.a0_hk = bo.hk;
+      gin.push_back(Bf16GroupInst{c->bf16, c->pen, c->Z, c->N * sizeof(float), 0, c->st->s, I.a0_fused});
+    }
   }
   // block counts of every family, instance by instance
   const bool b64 = o.basis_prec == RSFDE_FP64;
@@ -1251,6 +1303,16 @@ int setup_multi(rsfde_batch* b) {
       return b64 ? update_blocks<double>(c->N, j) : update_blocks<float>(c->N, j);
     }, nullptr);
   }
+  if (bf16) {  // the split (four elements a thread) and each GEMM's tiles
+    std::vector<int> tiles[4];
+    const int rc = bf16_group_create(gin, &b->gdesc, tiles);
+    if (rc != RSFDE_OK) return rc;
+    family(&b->g_split, [&](rsfde_ctx* c) { return ceil_div((long)c->N, 4L * kBlock); }, nullptr);
+    for (int k = 0; k < 4; ++k) {
+      int next = 0;  // family() visits the instances in order
+      family(&b->g_gemm[k], [&](rsfde_ctx*) { return tiles[k][next++]; }, nullptr);
+    }
+  }
   std::vector<int> all;
   std::vector<size_t> off;
   for (auto& v : counts) {
@@ -1268,8 +1330,10 @@ int setup_multi(rsfde_batch* b) {
   // active prefixes: the iteration families (drows, pcols, prows, trows, tcols,
   // dot, upd) and the cycle-end ones (xupd, rrows, rcols); the right side and
   // the epilogue run every instance (active = the full prefix)
-  const int nact = 10;
+  const int nact = bf16 ? 15 : 10;
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->actives, sizeof(int) * (size_t)nact * (n + 1));
+  if (e == cudaSuccess && bf16) e = cudaMalloc((void**)&b->gemm_err, sizeof(int));
+  if (e == cudaSuccess && bf16) e = cudaMemset(b->gemm_err, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e);
   for (size_t k = 0; k < grids.size(); ++k) {
     grids[k]->prefix = b->prefixes + off[k];
@@ -1284,6 +1348,11 @@ int setup_multi(rsfde_batch* b) {
     b->g_dot[j].active = b->actives + (size_t)8 * (n + 1);
     b->g_upd[j].active = b->actives + (size_t)9 * (n + 1);
   }
+  if (bf16) {
+    b->g_split.active = b->actives + (size_t)10 * (n + 1);
+    for (int k = 0; k < 4; ++k) b->g_gemm[k].active = b->actives + (size_t)(11 + k) * (n + 1);
+  }
+  b->bf16 = bf16;
   b->multi = true;
   return RSFDE_OK;
 }
@@ -1364,7 +1433,7 @@ int build_batch_graph_multi(rsfde_batch* b, int later) {
   // update, residual (2) and loop condition, and 1 in the epilogue
   b->launches_pro[later] = 5;
   b->launches_epi = 1;
-  b->launches_per_body = (int64_t)o.restart * (o.arnoldi == RSFDE_CGS2 ? 10 : 8) + 6;
+  b->launches_per_body = multi_body_launches(b);
   return RSFDE_OK;
 }
 
@@ -1875,10 +1944,9 @@ int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats) {
     const int later = b->steps_done > 0;
     if (direct) {
       if (b->launches_per_body == 0) {
-        const rsfde_opts& o = b->ctx[0]->opts;
         b->launches_pro[0] = b->launches_pro[1] = 5;
         b->launches_epi = 1;
-        b->launches_per_body = (int64_t)o.restart * (o.arnoldi == RSFDE_CGS2 ? 10 : 8) + 6;
+        b->launches_per_body = multi_body_launches(b);
       }
       int rc = run_batch_step_direct(b, later);
       if (rc) return rc;
@@ -1899,6 +1967,13 @@ int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats) {
   if (e != cudaSuccess) return cuda_fail(e);
   const size_t head = offsetof(SolverState, counter);
   int worst = RSFDE_OK;
+  if (b->bf16) {  // a GEMM pipeline wait gave up: that launch's output is incomplete
+    int flag = 0;
+    e = cudaMemcpy(&flag, b->gemm_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && flag) e = cudaMemset(b->gemm_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (flag) worst = RSFDE_ETIMEOUT;
+  }
   for (int i = 0; i < b->count; ++i) {
     rsfde_ctx* c = b->ctx[i];
     e = cudaMemcpy(c->st_host, c->st, head, cudaMemcpyDeviceToHost);

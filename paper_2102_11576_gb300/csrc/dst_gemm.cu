@@ -346,6 +346,53 @@ static void launch_gemm(const Bf16Plan* p, int stage, int hk, const Bf16Mat& A, 
   }
 }
 
+// GEMM k of the chain (bf16_precond's steps 1-4): operands, the product
+// shape (M rows of A, transform length n, hk: the symmetric form's half K
+// extent or 0) and the epilogue parameters (for k = 3 without z).
+struct ChainGemm {
+  const Bf16Mat* A;
+  const Bf16Mat* B;
+  int M, n, channels, hk;
+  GemmEpiParams ep;
+};
+static void chain_gemm(const Bf16Plan* p, int k, double pen, ChainGemm* g) {
+  const int n1 = p->n1, n2 = p->n2;
+  GemmEpiParams ep{};
+  ep.wait_cycles = p->wait_cycles;
+  if (k == 0) {  // 1. T1t = (A0 S_x)^T, columns y in the layout of GEMM 2's K
+    *g = ChainGemm{&p->A0, &p->Sx, n2, n1, 1, p->h1, ep};
+    g->ep.out_hi = p->T1t.hi;
+    g->ep.out_lo = p->T1t.lo;
+    g->ep.ldo = p->ld2;
+    g->ep.row_b = 1 << 30;
+    g->ep.hk = p->h2;
+  } else if (k == 1) {  // 2. W^T = T1t S_y; both tau divides (Eq. 4.6), stacked [W1; W2]
+    *g = ChainGemm{&p->T1t, &p->Sy, n1, n2, 1, p->h2, ep};
+    g->ep.out_hi = p->Wst.hi;
+    g->ep.out_lo = p->Wst.lo;
+    g->ep.ldo = p->ld1;
+    g->ep.lam_m = p->lamx;
+    g->ep.lam_n = p->lamy;
+    g->ep.pen = (float)pen;
+    g->ep.chb_rows = n2;
+    g->ep.hk = p->h1;
+  } else if (k == 2) {  // 3. Yt = ([W1; W2] S_x)^T, the channels side by side (column offset ld2)
+    *g = ChainGemm{&p->Wst, &p->Sx, 2 * n2, n1, 1, p->h1, ep};
+    g->ep.out_hi = p->Yt.hi;
+    g->ep.out_lo = p->Yt.lo;
+    g->ep.ldo = 2 * p->ld2;
+    g->ep.row_b = n2;
+    g->ep.col_b = p->ld2;
+    g->ep.hk = p->h2;
+  } else {  // 4. z = (1-Phi) S_y W1 S_x + Phi S_y W2 S_x (channel = blockIdx.z)
+    *g = ChainGemm{&p->Yt, &p->Sy, n1, n2, 2, p->h2, ep};
+    g->ep.phibits = p->phibits;
+    g->ep.wpc = p->wpc;
+    g->ep.ldz = n1;
+    g->ep.a_koff = p->ld2;
+  }
+}
+
 bool bf16_plan_a0(const Bf16Plan* p, int vec, Bf16Out* out) {
   if (!p || p->h1 == 0 || vec < 1 || p->n1 % vec != 0) return false;
   *out = Bf16Out{p->A0.hi, p->nt == 3 ? p->A0.lo : nullptr, p->n1, p->ld1, p->h1};
@@ -365,52 +412,19 @@ int bf16_precond(Bf16Plan* p, const Tin* v, const double* vscale, Tz* z, const u
     launch_pdl(split_kernel<Tin, 1>, split_grid(n1, n2), dim3(kBlock), 0, s, v, vscale, p->A0.hi, p->A0.lo, n1, n2,
                p->ld1, p->h1, gate);
   if (ev) cudaEventRecord(ev[0], s);
-  GemmEpiParams ep{};
-  // 1. T1t = (A0 S_x)^T, columns y in the layout of GEMM 2's K
-  ep.wait_cycles = p->wait_cycles;
-  ep.out_hi = p->T1t.hi;
-  ep.out_lo = p->T1t.lo;
-  ep.ldo = p->ld2;
-  ep.row_b = 1 << 30;
-  ep.hk = p->h2;
-  launch_gemm<EPI_SPLIT_T>(p, 0, p->h1, p->A0, p->Sx, n2, n1, 1, ep, gate, s);
-  if (ev) cudaEventRecord(ev[1], s);
-  // 2. W^T = T1t S_y; both tau divides (Eq. 4.6), stacked [W1; W2]
-  ep = GemmEpiParams{};
-  ep.wait_cycles = p->wait_cycles;
-  ep.out_hi = p->Wst.hi;
-  ep.out_lo = p->Wst.lo;
-  ep.ldo = p->ld1;
-  ep.lam_m = p->lamx;
-  ep.lam_n = p->lamy;
-  ep.pen = (float)pen;
-  ep.chb_rows = n2;
-  ep.hk = p->h1;
-  launch_gemm<EPI_DIVIDE_T>(p, 1, p->h2, p->T1t, p->Sy, n1, n2, 1, ep, gate, s);
-  if (ev) cudaEventRecord(ev[2], s);
-  // 3. Yt = ([W1; W2] S_x)^T, the channels side by side (column offset ld2)
-  ep = GemmEpiParams{};
-  ep.wait_cycles = p->wait_cycles;
-  ep.out_hi = p->Yt.hi;
-  ep.out_lo = p->Yt.lo;
-  ep.ldo = 2 * p->ld2;
-  ep.row_b = n2;
-  ep.col_b = p->ld2;
-  ep.hk = p->h2;
-  launch_gemm<EPI_SPLIT_T>(p, 2, p->h1, p->Wst, p->Sx, 2 * n2, n1, 1, ep, gate, s);
-  if (ev) cudaEventRecord(ev[3], s);
-  // 4. z = (1-Phi) S_y W1 S_x + Phi S_y W2 S_x (channel = blockIdx.z)
-  ep = GemmEpiParams{};
-  ep.wait_cycles = p->wait_cycles;
-  ep.z = z;
-  ep.z_double = sizeof(Tz) == 8;
-  ep.phibits = p->phibits;
-  ep.wpc = p->wpc;
-  ep.ldz = n1;
-  ep.zscale = skip_split ? zscale : nullptr;
-  ep.a_koff = p->ld2;
-  launch_gemm<EPI_COMBINE_T>(p, 3, p->h2, p->Yt, p->Sy, n1, n2, 2, ep, gate, s);
-  if (ev) cudaEventRecord(ev[4], s);
+  for (int k = 0; k < 4; ++k) {
+    ChainGemm g;
+    chain_gemm(p, k, pen, &g);
+    if (k == 3) {
+      g.ep.z = z;
+      g.ep.z_double = sizeof(Tz) == 8;
+      g.ep.zscale = skip_split ? zscale : nullptr;
+    }
+    if (k == 1) launch_gemm<EPI_DIVIDE_T>(p, k, g.hk, *g.A, *g.B, g.M, g.n, g.channels, g.ep, gate, s);
+    else if (k == 3) launch_gemm<EPI_COMBINE_T>(p, k, g.hk, *g.A, *g.B, g.M, g.n, g.channels, g.ep, gate, s);
+    else launch_gemm<EPI_SPLIT_T>(p, k, g.hk, *g.A, *g.B, g.M, g.n, g.channels, g.ep, gate, s);
+    if (ev) cudaEventRecord(ev[k + 1], s);
+  }
   return cudaGetLastError() == cudaSuccess ? RSFDE_OK : RSFDE_ECUDA;
 }
 
@@ -453,6 +467,114 @@ int bf16_plan_autotune(Bf16Plan* p, const double* v, float* z, const uint8_t* ph
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return RSFDE_ECUDA;
   return bf16_plan_error(p, s);
+}
+
+// ---- the batch's lock-step form: every instance's GEMM in one launch ---------
+void bf16_plan_a0_any(const Bf16Plan* p, Bf16Out* out) {
+  *out = Bf16Out{p->A0.hi, p->nt == 3 ? p->A0.lo : nullptr, p->n1, p->ld1, p->h1};
+}
+
+// The descriptors of the four GEMMs of every instance (stage-major: stage k,
+// instance i at k * count + i), 64-wide tiles, and their tile counts.
+int bf16_group_create(const std::vector<Bf16GroupInst>& in, void** descs, std::vector<int>* tiles) {
+  *descs = nullptr;
+  const int n = (int)in.size();
+  std::vector<GemmGroupDesc> h(4 * (size_t)n);
+  for (int k = 0; k < 4; ++k) tiles[k].assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    const Bf16Plan* p = in[i].plan;
+    if (!p || p->nt != 3) return RSFDE_EINVAL;
+    for (int k = 0; k < 4; ++k) {
+      ChainGemm g;
+      chain_gemm(p, k, in[i].pen, &g);
+      GemmGroupDesc& D = h[(size_t)k * n + i];
+      std::memset(static_cast<void*>(&D), 0, sizeof(D));
+      D.a_hi = g.A->map_hi;
+      D.a_lo = g.A->map_lo;
+      D.b_hi = g.B->map64_hi;
+      D.b_lo = g.B->map64_lo;
+      g.ep.M = g.M;
+      g.ep.N = g.hk ? g.n / 2 : g.n;
+      g.ep.n_full = g.hk ? g.n : 0;
+      g.ep.nch = g.channels;
+      if (k == 3) {
+        g.ep.z = in[i].z;
+        g.ep.z_double = in[i].z_double;
+        D.z_col_bytes = (long long)in[i].z_col_bytes;
+        D.s = in[i].s;
+        D.fused = in[i].fused;
+      }
+      D.ep = g.ep;
+      D.K = g.hk ? 2 * g.hk : g.n;
+      D.sym = g.hk > 0;
+      tiles[k][i] = ((g.ep.N + 63) / 64) * ((g.M + kGemmBM - 1) / kGemmBM) * g.channels;
+    }
+  }
+  cudaError_t e = cudaMalloc(descs, h.size() * sizeof(GemmGroupDesc));
+  if (e == cudaSuccess) e = cudaMemcpy(*descs, h.data(), h.size() * sizeof(GemmGroupDesc), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (*descs) cudaFree(*descs);
+    *descs = nullptr;
+    return e == cudaErrorMemoryAllocation ? RSFDE_ENOMEM : RSFDE_ECUDA;
+  }
+  return RSFDE_OK;
+}
+void bf16_group_destroy(void* descs) {
+  if (descs) cudaFree(descs);
+}
+
+// GEMM k of every running instance's chain at Krylov column j: grid = the
+// tiles of all instances (max_tiles); the compacted prefix `active` skips
+// the finished ones.
+template <int EPI>
+static void launch_group_t(const GemmGroupDesc* d, int count, const int* active, int max_tiles, int j, int* err,
+                           cudaStream_t s) {
+  auto k = dst_gemm_group_kernel<EPI, 3, 64>;
+  constexpr int smem = gemm_group_smem(3, 64);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k<<<max_tiles, kGroupThreads, smem, s>>>(d, active, count, j, err);
+}
+void launch_bf16_group(int k, const void* descs, int count, const int* active, int max_tiles, int j, int* err,
+                       cudaStream_t s) {
+  if (max_tiles <= 0) return;
+  const GemmGroupDesc* d = static_cast<const GemmGroupDesc*>(descs) + (size_t)k * count;
+  if (k == 1) launch_group_t<EPI_DIVIDE_T>(d, count, active, max_tiles, j, err, s);
+  else if (k == 3) launch_group_t<EPI_COMBINE_T>(d, count, active, max_tiles, j, err, s);
+  else launch_group_t<EPI_SPLIT_T>(d, count, active, max_tiles, j, err, s);
+}
+
+// A0 = split(s_j V_j) of every running instance (split_kernel's arithmetic,
+// element by element); instances whose basis update already wrote A0
+// unscaled (fused, j > 0) are skipped.
+__global__ void __launch_bounds__(kBlock) split_multi_kernel(const BatchInst* __restrict__ bi,
+                                                             const int* __restrict__ prefix,
+                                                             const int* __restrict__ active, int count, int j) {
+  __shared__ int sact[kMaxBatchMulti + 1];
+  for (int k = threadIdx.x; k <= count; k += blockDim.x) sact[k] = active[k];
+  __syncthreads();
+  const int total = sact[count];
+  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int mi = multi_instance(sact, count, vb);
+    const BatchInst& I = bi[mi];
+    if (j > 0 && I.a0_fused) continue;  // uniform over the block
+    const int lb = vb - sact[mi], nb = __ldg(prefix + mi + 1) - __ldg(prefix + mi);
+    const double* v = I.V + (size_t)j * I.N;
+    const double sc = I.st->s[j];
+    __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(I.a0);
+    __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(I.a0_lo);
+    for (size_t e = (size_t)lb * blockDim.x + threadIdx.x; e < I.N; e += (size_t)nb * blockDim.x) {
+      const int y = (int)(e / (size_t)I.n1), x = (int)(e - (size_t)y * I.n1);
+      const float xv = scaled_f32(sc, (float)sc, v[e]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(xv);
+      const size_t o = (size_t)y * I.a0_ld + sym_perm(x, I.a0_hk);
+      hi[o] = h;
+      lo[o] = __float2bfloat16_rn(xv - __bfloat162float(h));
+    }
+  }
+}
+void launch_split_multi(const BatchInst* bi, const MultiGrid& g, int j, cudaStream_t s) {
+  static const int grid = multi_launch_grid(split_multi_kernel, kBlock, 0, 1 << 30);
+  split_multi_kernel<<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(bi, g.prefix, g.active, g.count, j);
 }
 
 template int bf16_precond<float, double>(Bf16Plan*, const double*, const double*, float*, const uint8_t*, double,

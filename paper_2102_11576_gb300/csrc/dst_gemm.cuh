@@ -97,23 +97,29 @@ __device__ __forceinline__ void split_store(__nv_bfloat16* hi, __nv_bfloat16* lo
 // warps 2..15 run the first tile's epilogue, so the tensor pipe does not wait
 // for it; all sixteen run the last one.
 __host__ __device__ constexpr int gemm_threads(int NT) { return NT == 3 ? 512 : 256; }
-template <int EPI, int NT, bool SYM, int BN, int TPC = 1>
-__global__ void __launch_bounds__(gemm_threads(NT), gemm_ctas_per_sm(NT, BN))
-    dst_gemm_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
-                    const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, int K,
-                    GemmEpiParams ep, int* err, const int* gate) {
+//
+// The CTA's work: ntile tiles (at most TPC) of the linear tile order (x
+// fastest, then y, then channel), tiles t0 and t0 + tstride; GRID: the one
+// tile (blockIdx.x, blockIdx.y, blockIdx.z).  The tensor maps
+// may sit in the kernel's parameters or in global memory; the epilogue
+// parameters come by value (a kernel parameter, read from the constant bank)
+// or by reference (EPT = const GemmEpiParams&, a copy in shared memory).
+// THR threads and STG ring stages (defaults: gemm_threads, gemm_stages).
+template <int EPI, int NT, bool SYM, int BN, int TPC, bool GRID, typename EPT, int THR = gemm_threads(NT),
+          int STG = gemm_stages(NT, BN)>
+__device__ __forceinline__ void dst_gemm_body(const CUtensorMap* tA_hi, const CUtensorMap* tA_lo,
+                                              const CUtensorMap* tB_hi, const CUtensorMap* tB_lo, int K, EPT ep,
+                                              int* err, int t0, int tstride, int ntile_arg) {
   static_assert(NT == 1 || NT == 3, "one or three BF16 products");
   static_assert(BN == 64 || BN == 128, "64- or 128-wide tiles");
   static_assert(TPC == 1 || (TPC == 2 && NT == 3), "two tiles per CTA: split BF16 (one CTA per SM)");
   constexpr int kStageBytes = gemm_stage_bytes(NT, BN);
   constexpr int kB = gemm_btile_bytes(BN);
-  constexpr int kGemmStages = gemm_stages(NT, BN);
+  constexpr int kGemmStages = STG;
   constexpr uint32_t kCols = SYM ? 2 * BN : BN;  // TMEM columns of a tile: one or two accumulators
-  constexpr int kGemmThreads = gemm_threads(NT);
+  constexpr int kGemmThreads = THR;
+  static_assert(THR == 256 || THR == 512, "two or four warps per TMEM lane quarter");
   constexpr int kPerQuarter = kGemmThreads / 128;  // warps per TMEM lane quarter
-  pdl_wait();
-  pdl_trigger();
-  if (gate && *(volatile const int*)gate == 0) return;
   extern __shared__ __align__(1024) uint8_t gemm_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gemm_smem_raw) + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t full[kGemmStages], empty[kGemmStages], done[TPC];
@@ -139,18 +145,18 @@ __global__ void __launch_bounds__(gemm_threads(NT), gemm_ctas_per_sm(NT, BN))
   // blockIdx.x and blockIdx.x + gridDim.x of the linear order (x fastest,
   // then y, then channel; the launcher keeps every tile below 2 gridDim.x).
   const int gx = (ep.N + BN - 1) / BN, gy = (ep.M + kGemmBM - 1) / kGemmBM;
-  const int ntile = TPC == 1 ? 1 : (blockIdx.x + gridDim.x < gx * gy * ep.nch ? 2 : 1);
+  const int ntile = TPC == 1 ? 1 : ntile_arg;
   auto tile_of = [&](int i, int& m0, int& n0, int& ch) {
-    if constexpr (TPC == 1) {
+    if constexpr (GRID) {  // the grid is the tile grid (x, y, channel)
       m0 = blockIdx.y * kGemmBM;
       n0 = blockIdx.x * BN;
       ch = blockIdx.z;
-    } else {
-      const int t = blockIdx.x + i * gridDim.x;
-      n0 = (t % gx) * BN;
-      m0 = ((t / gx) % gy) * kGemmBM;
-      ch = t / (gx * gy);
+      return;
     }
+    const int t = t0 + i * tstride;
+    n0 = (t % gx) * BN;
+    m0 = ((t / gx) % gy) * kGemmBM;
+    ch = t / (gx * gy);
   };
   const int KB = (K + kGemmBK - 1) / kGemmBK;  // SYM: K = 2 hk, KB even
   const int KBh = SYM ? KB / 2 : KB;
@@ -174,11 +180,11 @@ __global__ void __launch_bounds__(gemm_threads(NT), gemm_ctas_per_sm(NT, BN))
           break;
         }
         mbar_expect_tx(&full[s], kStageBytes);
-        tma_load_2d(a_tile(s, 0), &tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
-        tma_load_2d(b_tile(s, 0), &tB_hi, kb * kGemmBK, n0, &full[s]);
+        tma_load_2d(a_tile(s, 0), tA_hi, a_koff + kb * kGemmBK, m0, &full[s]);
+        tma_load_2d(b_tile(s, 0), tB_hi, kb * kGemmBK, n0, &full[s]);
         if (NT == 3) {
-          tma_load_2d(a_tile(s, 1), &tA_lo, a_koff + kb * kGemmBK, m0, &full[s]);
-          tma_load_2d(b_tile(s, 1), &tB_lo, kb * kGemmBK, n0, &full[s]);
+          tma_load_2d(a_tile(s, 1), tA_lo, a_koff + kb * kGemmBK, m0, &full[s]);
+          tma_load_2d(b_tile(s, 1), tB_lo, kb * kGemmBK, n0, &full[s]);
         }
         issued = g + 1;
       }
@@ -257,7 +263,7 @@ __global__ void __launch_bounds__(gemm_threads(NT), gemm_ctas_per_sm(NT, BN))
     constexpr int kStPitch = 144, kStRun = 80;  // BF16 elements
     constexpr int kStRows = (EPI == EPI_DIVIDE_T ? 4 : 2) * BN;
     constexpr bool kCanStage = SYM && NT == 1 && TPC == 1 && EPI != EPI_COMBINE_T &&
-                               kStRows * kStPitch * 2 <= gemm_stages(NT, BN) * kStageBytes;
+                               kStRows * kStPitch * 2 <= kGemmStages * kStageBytes;
     bool staged = false;
     if constexpr (kCanStage) {
       const bool regular =
@@ -413,6 +419,87 @@ __global__ void __launch_bounds__(gemm_threads(NT), gemm_ctas_per_sm(NT, BN))
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(taddr, TPC * kCols);
+}
+
+template <int EPI, int NT, bool SYM, int BN, int TPC = 1>
+__global__ void __launch_bounds__(gemm_threads(NT), gemm_ctas_per_sm(NT, BN))
+    dst_gemm_kernel(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+                    const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo, int K,
+                    GemmEpiParams ep, int* err, const int* gate) {
+  pdl_wait();
+  pdl_trigger();
+  if (gate && *(volatile const int*)gate == 0) return;
+  __shared__ GemmEpiParams sep;
+  if (threadIdx.x == 0) sep = ep;
+  __syncthreads();
+  if constexpr (TPC == 1) {  // the grid is the tile grid (x, y, channel)
+    dst_gemm_body<EPI, NT, SYM, BN, 1, true, const GemmEpiParams&>(&tA_hi, &tA_lo, &tB_hi, &tB_lo, K, sep, err, 0,
+                                                                   0, 1);
+  } else {  // one CTA per SM: tiles blockIdx.x and blockIdx.x + gridDim.x
+    const int gx = (ep.N + BN - 1) / BN, gy = (ep.M + kGemmBM - 1) / kGemmBM;
+    const int ntile = blockIdx.x + gridDim.x < gx * gy * ep.nch ? 2 : 1;
+    dst_gemm_body<EPI, NT, SYM, BN, TPC, false, const GemmEpiParams&>(&tA_hi, &tA_lo, &tB_hi, &tB_lo, K, sep, err,
+                                                                      blockIdx.x, gridDim.x, ntile);
+  }
+}
+
+
+// ---- grouped launches: one GEMM of the chain for many instances -------------
+// One instance's GEMM: its operand maps (in global memory, 128-byte aligned
+// as the CUtensorMap type is), its epilogue parameters, and for the combine
+// epilogue the per-column output: z of Krylov column j at ep.z + j
+// z_col_bytes, scaled by s[j] when the instance's first operand is taken
+// unscaled from the basis update (fused, columns j > 0).
+struct GemmGroupDesc {
+  CUtensorMap a_hi, a_lo, b_hi, b_lo;
+  GemmEpiParams ep;
+  long long z_col_bytes;
+  const double* s;
+  int fused;
+  int K;
+  int sym;  // symmetric form (even transform length)
+};
+
+// One CTA per tile over every instance's tile grid: instance i owns the CTAs
+// [active[i], active[i+1]) (a compacted prefix: finished instances own none),
+// local tile t = blockIdx.x - active[i] in the linear tile order.  CTAs past
+// active[count] return at once (the grid covers every instance running).
+// The instances' K extents are short (a few 64-wide slices), so a tile is
+// mostly pipeline fill and epilogue: two CTAs share an SM (eight warps each,
+// a two-stage ring) and one's epilogue overlaps the other's MMAs.
+constexpr int kGroupThreads = 256, kGroupStages = 2;
+__host__ __device__ constexpr int gemm_group_smem(int NT, int BN) {
+  return kGroupStages * gemm_stage_bytes(NT, BN) + 1024;
+}
+template <int EPI, int NT, int BN>
+__global__ void __launch_bounds__(kGroupThreads, 2)
+    dst_gemm_group_kernel(const GemmGroupDesc* __restrict__ d, const int* __restrict__ active, int count, int j,
+                          int* err) {
+  const int b = blockIdx.x;
+  if (b >= active[count]) return;  // uniform over the block
+  int i = 0;  // the last i with active[i] <= b (empty ranges skipped)
+  for (int hi = count - 1; i < hi;) {
+    const int mid = (i + hi + 1) >> 1;
+    if (active[mid] <= b) i = mid;
+    else hi = mid - 1;
+  }
+  const GemmGroupDesc& D = d[i];
+  __shared__ GemmEpiParams sep;
+  if (threadIdx.x == 0) {
+    sep = D.ep;
+    if (EPI == EPI_COMBINE_T) {
+      sep.z = static_cast<char*>(D.ep.z) + (size_t)j * (size_t)D.z_col_bytes;
+      sep.zscale = (D.fused && j > 0) ? D.s + j : nullptr;
+    }
+  }
+  __syncthreads();
+  const int t = b - active[i];
+  if (D.sym)
+    dst_gemm_body<EPI, NT, true, BN, 1, false, const GemmEpiParams&, kGroupThreads, kGroupStages>(
+        &D.a_hi, &D.a_lo, &D.b_hi, &D.b_lo, D.K, sep, err, t, 0, 1);
+  else
+    dst_gemm_body<EPI, NT, false, BN, 1, false, const GemmEpiParams&, kGroupThreads, kGroupStages>(
+        &D.a_hi, &D.a_lo, &D.b_hi, &D.b_lo, D.K, sep, err, t, 0, 1);
 }
 
 }  // namespace rsfde

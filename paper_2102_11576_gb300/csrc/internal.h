@@ -213,6 +213,12 @@ struct BatchInst {
   AxisTables<double> x64, y64;
   AxisTables<float> x32, y32;
   AxisTables<df> xdf, ydf;
+  // split-BF16 preconditioner (lock-step form): the instance's first GEMM
+  // operand (BF16 pair, leading dimension a0_ld, symmetric half a0_hk), and
+  // whether the basis update writes it for columns j > 0 (a0_fused)
+  void* a0;
+  void* a0_lo;
+  int a0_ld, a0_hk, a0_fused;
 };
 
 // The blocks of one multi-instance launch: instance i owns the blocks
@@ -255,7 +261,7 @@ __device__ __forceinline__ int multi_instance(const int* p, int count, int b) {
 // Compaction: for up to kMaxCompact families, active[f][i] = sum over k < i of
 // the virtual-grid size of instance k if its gate (run_iter, or run_cycle with
 // use_cycle) is open, else 0; active[f][count] the total.
-constexpr int kMaxCompact = 8;
+constexpr int kMaxCompact = 16;
 struct CompactArgs {
   const int* prefix[kMaxCompact];
   int* active[kMaxCompact];
@@ -287,8 +293,28 @@ void launch_init_multi(const BatchInst* bi, int count, int m, int max_iter, doub
 void launch_rhs_multi(const BatchInst* bi, const MultiGrid& g, int later, cudaStream_t s);
 template <typename Tv>
 void launch_multidot_multi(const BatchInst* bi, const MultiGrid& g, int j, int accumulate, cudaStream_t s);
+// write_a0: instances with a0_fused also write V_{j+1} as their BF16 operand
 template <typename Tv>
-void launch_update_multi(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, cudaStream_t s);
+void launch_update_multi(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, int write_a0, cudaStream_t s);
+// Split-BF16 preconditioner of the lock-step form (dst_gemm.cu): one launch
+// per pass over every running instance.
+struct Bf16GroupInst {
+  const Bf16Plan* plan;
+  double pen;
+  void* z;             // Z, the instance's preconditioned vectors (column j at z + j z_col_bytes)
+  size_t z_col_bytes;
+  int z_double;
+  const double* s;     // the basis scales s_j
+  int fused;           // A0 of columns j > 0 written unscaled by the basis update
+};
+// descs: device array of the four GEMMs of every instance; tiles[4]: the tile
+// counts per instance of each GEMM (the grids of the grouped launches).
+int bf16_group_create(const std::vector<Bf16GroupInst>& in, void** descs, std::vector<int>* tiles);
+void bf16_group_destroy(void* descs);
+void launch_bf16_group(int k, const void* descs, int count, const int* active, int max_tiles, int j, int* err,
+                       cudaStream_t s);
+void launch_split_multi(const BatchInst* bi, const MultiGrid& g, int j, cudaStream_t s);
+void bf16_plan_a0_any(const Bf16Plan* p, Bf16Out* out);
 void launch_solve_y_multi(const BatchInst* bi, int count, cudaStream_t s);
 template <typename Tz>
 void launch_xupdate_multi(const BatchInst* bi, const MultiGrid& g, cudaStream_t s);

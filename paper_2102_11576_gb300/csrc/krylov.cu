@@ -836,12 +836,16 @@ template <typename Tv, int CH>
 __global__ void __launch_bounds__(kBlock) update_multi_kernel(const BatchInst* __restrict__ bi,
                                                               const int* __restrict__ prefix,
                                                               const int* __restrict__ active, int count, int j,
-                                                              int final_pass) {
+                                                              int final_pass, int write_a0) {
   multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
     constexpr int VEC = 16 / sizeof(Tv);
     const Bf16Out none{nullptr, nullptr, 1, 0, 0};
     Tv* V = reinterpret_cast<Tv*>(I.V);
-    if (I.N % VEC == 0) update_body<Tv, VEC, CH>(V, I.N, j, final_pass, I.partials, I.st, none, lb, nb);
+    if (write_a0 && I.a0_fused) {  // (a0_fused implies N % VEC == 0)
+      const Bf16Out bo{static_cast<__nv_bfloat16*>(I.a0), static_cast<__nv_bfloat16*>(I.a0_lo), I.n1, I.a0_ld,
+                       I.a0_hk};
+      update_body<Tv, VEC, CH>(V, I.N, j, final_pass, I.partials, I.st, bo, lb, nb);
+    } else if (I.N % VEC == 0) update_body<Tv, VEC, CH>(V, I.N, j, final_pass, I.partials, I.st, none, lb, nb);
     else update_body<Tv, 1, CH>(V, I.N, j, final_pass, I.partials, I.st, none, lb, nb);
   });
 }
@@ -961,17 +965,18 @@ void launch_multidot_multi(const BatchInst* bi, const MultiGrid& g, int j, int a
   else launch_multidot_multi_t<Tv, kDotChunk>(bi, g, j, accumulate, s);
 }
 template <typename Tv, int CH>
-static void launch_update_multi_t(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, cudaStream_t s) {
+static void launch_update_multi_t(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, int write_a0,
+                                  cudaStream_t s) {
   static const int grid = multi_launch_grid(update_multi_kernel<Tv, CH>, kBlock, 0, 1 << 30);
   update_multi_kernel<Tv, CH><<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(bi, g.prefix, g.active, g.count, j,
-                                                                               final_pass);
+                                                                               final_pass, write_a0);
 }
 template <typename Tv>
-void launch_update_multi(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, cudaStream_t s) {
+void launch_update_multi(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, int write_a0, cudaStream_t s) {
   const int ch = dot_chunk(j);
-  if (ch == 2) launch_update_multi_t<Tv, 2>(bi, g, j, final_pass, s);
-  else if (ch == 4) launch_update_multi_t<Tv, 4>(bi, g, j, final_pass, s);
-  else launch_update_multi_t<Tv, kDotChunk>(bi, g, j, final_pass, s);
+  if (ch == 2) launch_update_multi_t<Tv, 2>(bi, g, j, final_pass, write_a0, s);
+  else if (ch == 4) launch_update_multi_t<Tv, 4>(bi, g, j, final_pass, write_a0, s);
+  else launch_update_multi_t<Tv, kDotChunk>(bi, g, j, final_pass, write_a0, s);
 }
 void launch_solve_y_multi(const BatchInst* bi, int count, cudaStream_t s) {
   solve_y_multi_kernel<<<count, 32, 0, s>>>(bi);
@@ -1018,7 +1023,7 @@ int xupdate_blocks(size_t N, int zbytes) {
 }
 #define RSFDE_GS_MULTI(Tv)                                                                              \
   template void launch_multidot_multi<Tv>(const BatchInst*, const MultiGrid&, int, int, cudaStream_t); \
-  template void launch_update_multi<Tv>(const BatchInst*, const MultiGrid&, int, int, cudaStream_t);   \
+  template void launch_update_multi<Tv>(const BatchInst*, const MultiGrid&, int, int, int, cudaStream_t);   \
   template int multidot_blocks<Tv>(size_t, int);                                                       \
   template int update_blocks<Tv>(size_t, int);
 RSFDE_GS_MULTI(double)

@@ -18,14 +18,18 @@ from paper_2102_11576_gb300 import Batch, Solver  # noqa: E402
 
 
 # the FP32 FFT preconditioner with the FP32 operator and the FP64 residual
-# (FP64 or FP32 basis) runs the multi-instance form (one launch per phase over
-# all instances); the other forms the graph of per-instance branches
-@pytest.mark.parametrize("precond,matvec,basis,resid", [("fp32", "df32", "df32", "fp64"), ("bf16", "fp32", "fp32", "df32"),
-                                                        ("fp32", "fp32", "fp64", "fp64"),
-                                                        ("fp32", "fp32", "fp32", "fp64"),
-                                                        ("bf16x3", "fp32", "fp64", "exact")])
-def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, basis, resid):
-    probs = workloads.make_batch(seed=5, count=7, n_range=(9, 96), steps=10)
+# (FP64 or FP32 basis), and the split-BF16 preconditioner with the FP32
+# operator, FP64 basis and FP64 residual, run the multi-instance form (one
+# launch per phase over all instances: the BF16 GEMMs of every instance in
+# one grouped launch per pass); the other forms the graph of per-instance
+# branches
+@pytest.mark.parametrize("precond,matvec,basis,resid,n_range", [
+    ("fp32", "df32", "df32", "fp64", (9, 96)), ("bf16", "fp32", "fp32", "df32", (9, 96)),
+    ("fp32", "fp32", "fp64", "fp64", (9, 96)), ("fp32", "fp32", "fp32", "fp64", (9, 96)),
+    ("bf16x3", "fp32", "fp64", "exact", (9, 96)), ("bf16x3", "fp32", "fp64", "fp64", (9, 96)),
+    ("bf16x3", "fp32", "fp64", "fp64", (100, 400))])
+def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, basis, resid, n_range):
+    probs = workloads.make_batch(seed=5, count=7, n_range=n_range, steps=10)
     steps = 3
     rng = np.random.default_rng(0)
     srcs = [rng.standard_normal(p["u0"].shape) if i % 2 else None for i, p in enumerate(probs)]
@@ -36,11 +40,13 @@ def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, basi
     assert all(s["converged"] and s["rel_res"] <= 1e-10 for s in st)
     launches = b.kernel_launches
     assert launches > 0
-    if precond == "fp32" and matvec == "fp32" and resid == "fp64":
+    if precond in ("fp32", "bf16x3") and matvec == "fp32" and resid == "fp64":
         # lock step: per step 6 launches plus, per run of the loop body, 8 per
-        # Arnoldi column and 6 more, however many instances there are (these
-        # small problems need at most a few cycles a step)
-        assert launches <= steps * (6 + 12 * (8 * 20 + 6))
+        # Arnoldi column (10 with the split and four grouped GEMMs) and 6
+        # more, however many instances there are (these problems need at most
+        # a few cycles a step)
+        per_col = 10 if precond == "bf16x3" else 8
+        assert launches <= steps * (6 + 12 * (per_col * 20 + 6))
     for i, p in enumerate(probs):
         args = (p["n1"], p["n2"], p["box"], p["in_omega"], p["alpha1"], p["alpha2"], p["kx"], p["ky"],
                 p["dt"], p["eta"])
