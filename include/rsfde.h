@@ -223,13 +223,18 @@ int rsfde_adjoint_step(rsfde_ctx* ctx, const double* u_prev, const double* u_k, 
 
 /* ---- batched instances ------------------------------------------------------ */
 /* Many independent problems (each its own grid, mask, alphas, k, dt, eta)
- * advanced together: every time step of every instance -- right side,
- * initial residual, the device-side loop over FGMRES cycles, the state
- * rotation -- is one branch of a single CUDA graph, so one graph launch
- * advances the whole batch by one step and the GPU overlaps the instances'
- * kernels.  The paper solves one instance; this is the batched deployment of
- * the same step.  Arguments are arrays of `count` entries (grids, masks:
- * device pointers as in rsfde_setup); opts (may be NULL) apply to all. */
+ * advanced together; one CUDA graph launch advances the whole batch by one
+ * step.  With right-preconditioned FGMRES, the FP32 operator, the FP64 true
+ * residual and either the FP32 preconditioner (FP64 or FP32 basis) or the
+ * split-BF16 one (FP64 basis), the instances run in lock step: every kernel
+ * of the FGMRES cycle is one launch over all instances still iterating (the
+ * split-BF16 GEMMs of all instances in one grouped launch per pass), with
+ * each instance's results bit-identical to its single-instance solve (up to
+ * 1024 instances, grid sides up to 2048).  Other options run every
+ * instance's step as one branch of the graph.  The paper solves one
+ * instance; this is the batched deployment of the same step.  Arguments
+ * are arrays of `count` entries (grids, masks: device pointers as in
+ * rsfde_setup); opts (may be NULL) apply to all. */
 int rsfde_batch_create(rsfde_batch** out, int32_t count, const rsfde_grid* grids, const uint8_t* const* masks,
                        const double* alpha1, const double* alpha2, const double* kx, const double* ky,
                        const double* dt, const double* eta, const rsfde_opts* opts);
@@ -237,7 +242,9 @@ int rsfde_batch_create(rsfde_batch** out, int32_t count, const rsfde_grid* grids
 int rsfde_batch_set(rsfde_batch* b, int32_t i, const double* u0, const double* src);
 /* Advances every instance by `steps` implicit steps (f = u - u^3 + src, Eq. 2.17).
  * stats: HOST array of `count` (statistics of each instance's last step) or
- * NULL.  Returns the first non-OK instance status, else RSFDE_OK.  Synchronises. */
+ * NULL.  Returns RSFDE_ETIMEOUT if a grouped split-BF16 GEMM's pipeline wait
+ * gave up (its output was incomplete; the batch stays usable), else the first
+ * non-OK instance status, else RSFDE_OK.  Synchronises. */
 int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats);
 /* Copies instance i's current u^k to the device array u_out (N_i doubles). */
 int rsfde_batch_get(rsfde_batch* b, int32_t i, double* u_out);
