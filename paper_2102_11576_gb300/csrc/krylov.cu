@@ -817,8 +817,11 @@ __global__ void __launch_bounds__(kBlock) rhs_multi_kernel(const BatchInst* __re
     rhs_body(I.u_prev, later ? I.u_pp : nullptr, I.src, I.phi, I.dt, I.b, I.x, I.N, I.partials, I.st, lb, nb);
   });
 }
+// 64 registers (four blocks per SM), as the single-instance kernels take by
+// themselves: the virtual-block loop and the two pack widths would otherwise
+// raise them and halve the resident warps of these FP64-pipe-bound loops.
 template <typename Tv, int CH>
-__global__ void __launch_bounds__(kBlock) multidot_multi_kernel(const BatchInst* __restrict__ bi,
+__global__ void __launch_bounds__(kBlock, 4) multidot_multi_kernel(const BatchInst* __restrict__ bi,
                                                                 const int* __restrict__ prefix,
                                                                 const int* __restrict__ active, int count, int j,
                                                                 int accumulate, int chunks) {
@@ -833,7 +836,7 @@ __global__ void __launch_bounds__(kBlock) multidot_multi_kernel(const BatchInst*
   });
 }
 template <typename Tv, int CH>
-__global__ void __launch_bounds__(kBlock) update_multi_kernel(const BatchInst* __restrict__ bi,
+__global__ void __launch_bounds__(kBlock, 4) update_multi_kernel(const BatchInst* __restrict__ bi,
                                                               const int* __restrict__ prefix,
                                                               const int* __restrict__ active, int count, int j,
                                                               int final_pass, int write_a0) {
@@ -841,11 +844,12 @@ __global__ void __launch_bounds__(kBlock) update_multi_kernel(const BatchInst* _
     constexpr int VEC = 16 / sizeof(Tv);
     const Bf16Out none{nullptr, nullptr, 1, 0, 0};
     Tv* V = reinterpret_cast<Tv*>(I.V);
-    if (write_a0 && I.a0_fused) {  // (a0_fused implies N % VEC == 0)
-      const Bf16Out bo{static_cast<__nv_bfloat16*>(I.a0), static_cast<__nv_bfloat16*>(I.a0_lo), I.n1, I.a0_ld,
-                       I.a0_hk};
+    if (I.N % VEC == 0) {  // (a0_fused implies N % VEC == 0)
+      const bool wr = write_a0 && I.a0_fused;
+      const Bf16Out bo{wr ? static_cast<__nv_bfloat16*>(I.a0) : nullptr,
+                       wr ? static_cast<__nv_bfloat16*>(I.a0_lo) : nullptr, wr ? I.n1 : 1, I.a0_ld, I.a0_hk};
       update_body<Tv, VEC, CH>(V, I.N, j, final_pass, I.partials, I.st, bo, lb, nb);
-    } else if (I.N % VEC == 0) update_body<Tv, VEC, CH>(V, I.N, j, final_pass, I.partials, I.st, none, lb, nb);
+    }
     else update_body<Tv, 1, CH>(V, I.N, j, final_pass, I.partials, I.st, none, lb, nb);
   });
 }
