@@ -1090,6 +1090,7 @@ struct rsfde_batch {
   MultiGrid g_split, g_gemm[4];
   void* gdesc = nullptr;
   int* gemm_err = nullptr;
+  int* sched = nullptr;  // device: the dynamic hand-out counters of the Gram-Schmidt launches
   int64_t launches_per_body = 0;
   cudaStream_t cap = nullptr;
 };
@@ -1104,6 +1105,7 @@ void free_batch(rsfde_batch* b) {
   if (b->runs) cudaFree(b->runs);
   bf16_group_destroy(b->gdesc);
   if (b->gemm_err) cudaFree(b->gemm_err);
+  if (b->sched) cudaFree(b->sched);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (auto& x : b->exec)
     if (x) cudaGraphExecDestroy(x);
@@ -1334,6 +1336,8 @@ int setup_multi(rsfde_batch* b) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->actives, sizeof(int) * (size_t)nact * (n + 1));
   if (e == cudaSuccess && bf16) e = cudaMalloc((void**)&b->gemm_err, sizeof(int));
   if (e == cudaSuccess && bf16) e = cudaMemset(b->gemm_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->sched, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(b->sched, 0, 4 * sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e);
   for (size_t k = 0; k < grids.size(); ++k) {
     grids[k]->prefix = b->prefixes + off[k];
@@ -1344,9 +1348,11 @@ int setup_multi(rsfde_batch* b) {
   MultiGrid* own[] = {&b->g_drows, &b->g_pcols, &b->g_prows, &b->g_trows, &b->g_tcols, &b->g_xupd, &b->g_rrows,
                       &b->g_rcols};
   for (int k = 0; k < 8; ++k) own[k]->active = b->actives + (size_t)k * (n + 1);
-  for (int j = 0; j < m; ++j) {
+  for (int j = 0; j < m; ++j) {  // the Gram-Schmidt launches hand their virtual blocks out dynamically
     b->g_dot[j].active = b->actives + (size_t)8 * (n + 1);
     b->g_upd[j].active = b->actives + (size_t)9 * (n + 1);
+    b->g_dot[j].sched = b->sched;
+    b->g_upd[j].sched = b->sched + 2;
   }
   if (bf16) {
     b->g_split.active = b->actives + (size_t)10 * (n + 1);

@@ -237,6 +237,10 @@ struct MultiGrid {
   int* active = nullptr;        // device, count + 1 entries (compaction output)
   int count = 0, total = 0;
   unsigned l2mask = 0;
+  // device, 2 ints, zero between launches: if set, the launch hands its
+  // virtual blocks out one at a time (next block, finished blocks) instead
+  // of round robin; the last block to finish zeroes both again
+  int* sched = nullptr;
 };
 // Threads of a multi-instance transform block: F = kMultiThreads / (L/16)
 // transforms per block, for every L up to 4096.

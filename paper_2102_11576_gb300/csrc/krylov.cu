@@ -793,11 +793,36 @@ template void launch_scale_copy<float, float>(const float*, const double*, float
 // solves.
 template <typename Fn>
 __device__ __forceinline__ void multi_loop(const BatchInst* __restrict__ bi, const int* __restrict__ prefix,
-                                           const int* __restrict__ active, int count, Fn&& fn) {
+                                           const int* __restrict__ active, int count, Fn&& fn,
+                                           int* sched = nullptr) {
   __shared__ int sact[kMaxBatchMulti + 1];
+  __shared__ int snext;
   for (int k = threadIdx.x; k <= count; k += blockDim.x) sact[k] = active[k];
   __syncthreads();
   const int total = sact[count];
+  if (sched) {  // dynamic hand-out: blocks that finish early take the remaining virtual blocks
+    for (;;) {
+      if (threadIdx.x == 0) snext = atomicAdd(sched, 1);
+      __syncthreads();
+      const int vb = snext;
+      if (vb >= total) break;  // uniform over the block
+      const int mi = multi_instance(sact, count, vb);
+      const int b0 = __ldg(prefix + mi);
+      fn(bi[mi], vb - sact[mi], __ldg(prefix + mi + 1) - b0);
+      __syncthreads();  // shared memory (and snext) reused by the next virtual block
+    }
+    // every block counts itself out after its last hand-out; the last one
+    // zeroes the counters for the next launch on the stream
+    if (threadIdx.x == 0) {
+      __threadfence();
+      if (atomicAdd(sched + 1, 1) == (int)gridDim.x - 1) {
+        sched[0] = 0;
+        sched[1] = 0;
+        __threadfence();
+      }
+    }
+    return;
+  }
   for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
     const int mi = multi_instance(sact, count, vb);
     const int b0 = __ldg(prefix + mi);
@@ -824,7 +849,7 @@ template <typename Tv, int CH>
 __global__ void __launch_bounds__(kBlock, 4) multidot_multi_kernel(const BatchInst* __restrict__ bi,
                                                                 const int* __restrict__ prefix,
                                                                 const int* __restrict__ active, int count, int j,
-                                                                int accumulate, int chunks) {
+                                                                int accumulate, int chunks, int* sched) {
   multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
     constexpr int VEC = 16 / sizeof(Tv);
     const int gx = nb / chunks;
@@ -833,13 +858,13 @@ __global__ void __launch_bounds__(kBlock, 4) multidot_multi_kernel(const BatchIn
       multidot_body<Tv, VEC, CH>(V, I.N, j, accumulate, I.partials, I.st, lb % gx, gx, lb / gx, chunks);
     else
       multidot_body<Tv, 1, CH>(V, I.N, j, accumulate, I.partials, I.st, lb % gx, gx, lb / gx, chunks);
-  });
+  }, sched);
 }
 template <typename Tv, int CH>
 __global__ void __launch_bounds__(kBlock, 4) update_multi_kernel(const BatchInst* __restrict__ bi,
                                                               const int* __restrict__ prefix,
                                                               const int* __restrict__ active, int count, int j,
-                                                              int final_pass, int write_a0) {
+                                                              int final_pass, int write_a0, int* sched) {
   multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
     constexpr int VEC = 16 / sizeof(Tv);
     const Bf16Out none{nullptr, nullptr, 1, 0, 0};
@@ -851,7 +876,7 @@ __global__ void __launch_bounds__(kBlock, 4) update_multi_kernel(const BatchInst
       update_body<Tv, VEC, CH>(V, I.N, j, final_pass, I.partials, I.st, bo, lb, nb);
     }
     else update_body<Tv, 1, CH>(V, I.N, j, final_pass, I.partials, I.st, none, lb, nb);
-  });
+  }, sched);
 }
 __global__ void solve_y_multi_kernel(const BatchInst* __restrict__ bi) { solve_y_body(bi[blockIdx.x].st); }
 template <typename Tz>
@@ -959,7 +984,7 @@ template <typename Tv, int CH>
 static void launch_multidot_multi_t(const BatchInst* bi, const MultiGrid& g, int j, int accumulate, cudaStream_t s) {
   static const int grid = multi_launch_grid(multidot_multi_kernel<Tv, CH>, kBlock, 0, 1 << 30);
   multidot_multi_kernel<Tv, CH><<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(
-      bi, g.prefix, g.active, g.count, j, accumulate, (j + CH) / CH);
+      bi, g.prefix, g.active, g.count, j, accumulate, (j + CH) / CH, g.sched);
 }
 template <typename Tv>
 void launch_multidot_multi(const BatchInst* bi, const MultiGrid& g, int j, int accumulate, cudaStream_t s) {
@@ -973,7 +998,7 @@ static void launch_update_multi_t(const BatchInst* bi, const MultiGrid& g, int j
                                   cudaStream_t s) {
   static const int grid = multi_launch_grid(update_multi_kernel<Tv, CH>, kBlock, 0, 1 << 30);
   update_multi_kernel<Tv, CH><<<g.total < grid ? g.total : grid, kBlock, 0, s>>>(bi, g.prefix, g.active, g.count, j,
-                                                                               final_pass, write_a0);
+                                                                               final_pass, write_a0, g.sched);
 }
 template <typename Tv>
 void launch_update_multi(const BatchInst* bi, const MultiGrid& g, int j, int final_pass, int write_a0, cudaStream_t s) {
