@@ -1348,6 +1348,10 @@ int setup_multi(rsfde_batch* b) {
   MultiGrid* own[] = {&b->g_drows, &b->g_pcols, &b->g_prows, &b->g_trows, &b->g_tcols, &b->g_xupd, &b->g_rrows,
                       &b->g_rcols};
   for (int k = 0; k < 8; ++k) own[k]->active = b->actives + (size_t)k * (n + 1);
+  // the transform launches hand out their virtual blocks dynamically too (one
+  // launch at a time on the batch's stream, so they share one counter pair)
+  for (MultiGrid* g : {&b->g_drows, &b->g_pcols, &b->g_prows, &b->g_trows, &b->g_tcols, &b->g_rrows, &b->g_rcols})
+    g->sched = b->sched + 2;
   for (int j = 0; j < m; ++j) {  // the Gram-Schmidt launches hand their virtual blocks out dynamically
     b->g_dot[j].active = b->actives + (size_t)8 * (n + 1);
     b->g_upd[j].active = b->actives + (size_t)9 * (n + 1);

@@ -791,45 +791,6 @@ template void launch_scale_copy<float, float>(const float*, const double*, float
 // shared memory); each virtual block runs the single-instance body on its
 // instance's own virtual grid, so the results are bit-identical to single
 // solves.
-template <typename Fn>
-__device__ __forceinline__ void multi_loop(const BatchInst* __restrict__ bi, const int* __restrict__ prefix,
-                                           const int* __restrict__ active, int count, Fn&& fn,
-                                           int* sched = nullptr) {
-  __shared__ int sact[kMaxBatchMulti + 1];
-  __shared__ int snext;
-  for (int k = threadIdx.x; k <= count; k += blockDim.x) sact[k] = active[k];
-  __syncthreads();
-  const int total = sact[count];
-  if (sched) {  // dynamic hand-out: blocks that finish early take the remaining virtual blocks
-    for (;;) {
-      if (threadIdx.x == 0) snext = atomicAdd(sched, 1);
-      __syncthreads();
-      const int vb = snext;
-      if (vb >= total) break;  // uniform over the block
-      const int mi = multi_instance(sact, count, vb);
-      const int b0 = __ldg(prefix + mi);
-      fn(bi[mi], vb - sact[mi], __ldg(prefix + mi + 1) - b0);
-      __syncthreads();  // shared memory (and snext) reused by the next virtual block
-    }
-    // every block counts itself out after its last hand-out; the last one
-    // zeroes the counters for the next launch on the stream
-    if (threadIdx.x == 0) {
-      __threadfence();
-      if (atomicAdd(sched + 1, 1) == (int)gridDim.x - 1) {
-        sched[0] = 0;
-        sched[1] = 0;
-        __threadfence();
-      }
-    }
-    return;
-  }
-  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
-    const int mi = multi_instance(sact, count, vb);
-    const int b0 = __ldg(prefix + mi);
-    fn(bi[mi], vb - sact[mi], __ldg(prefix + mi + 1) - b0);
-    __syncthreads();  // the next virtual block reuses the block's shared memory
-  }
-}
 
 __global__ void init_multi_kernel(const BatchInst* __restrict__ bi, int count, int m, int max_iter, double tol) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -715,24 +715,9 @@ __device__ __forceinline__ const AxisTables<df>& inst_tab<df>(const BatchInst& I
   return y ? I.ydf : I.xdf;
 }
 
-// The loop over the active virtual blocks (as in krylov.cu).  The kernels ask
-// for the register budget of the single-instance kernels (4 blocks of 256
-// FP32 threads, 2 of FP64 or double-FP32, per SM), which their occupancy and
-// latency hiding depend on.
-template <typename Fn>
-__device__ __forceinline__ void multi_loop_fft(const BatchInst* __restrict__ bi, const int* __restrict__ prefix,
-                                               const int* __restrict__ active, int count, Fn&& fn) {
-  __shared__ int sact[kMaxBatchMulti + 1];
-  for (int k = threadIdx.x; k <= count; k += blockDim.x) sact[k] = active[k];
-  __syncthreads();
-  const int total = sact[count];
-  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
-    const int mi = multi_instance(sact, count, vb);
-    const int b0 = __ldg(prefix + mi);
-    fn(bi[mi], vb - sact[mi], __ldg(prefix + mi + 1) - b0);
-    __syncthreads();
-  }
-}
+// The multi-instance kernels below ask for the register budget of the
+// single-instance kernels (4 blocks of 256 FP32 threads, 2 of FP64 or
+// double-FP32, per SM), which their occupancy and latency hiding depend on.
 
 // w_j = M z_j for every instance (MODE_APPLY; rows write z - A_x z + pen phi z
 // into the scratch).
@@ -740,8 +725,8 @@ template <typename T, typename Tz, typename Tv, bool COLS>
 __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) operator_multi_kernel(const BatchInst* __restrict__ bi,
                                                                        const int* __restrict__ prefix,
                                                                        const int* __restrict__ active, int count,
-                                                                       int j) {
-  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+                                                                       int j, int* sched) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
     const AxisTables<T>& ax = inst_tab<T>(I, COLS);
     const int F = multi_groups(ax.L);
     const Tz* z = static_cast<const Tz*>(I.Z) + (size_t)j * I.N;
@@ -749,7 +734,7 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) operato
     toeplitz_body<T, Tz, MODE_APPLY, COLS, Tv>(z, static_cast<T*>(I.tmpx), I.phi, I.pen, nullptr, w, I.n1, I.n2, ax,
                                                F, group_stride<T>(ax.L, F, COLS), &I.st->run_iter, nullptr, nullptr,
                                                lb, nb);
-  });
+  }, sched);
 }
 
 // V_0 = b - M x and the restart decision (rows: x - A_x x + pen phi x into the
@@ -757,8 +742,8 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) operato
 template <typename T, typename Tv, bool COLS>
 __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) residual_multi_kernel(const BatchInst* __restrict__ bi,
                                                                        const int* __restrict__ prefix,
-                                                                       const int* __restrict__ active, int count) {
-  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+                                                                       const int* __restrict__ active, int count, int* sched) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
     const AxisTables<T>& ax = inst_tab<T>(I, COLS);
     const int F = multi_groups(ax.L);
     const int gs = group_stride<T>(ax.L, F, COLS);
@@ -770,7 +755,7 @@ __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) residua
       toeplitz_body<T, double, MODE_APPLY, false, double>(I.x, static_cast<T*>(I.tmpx), I.phi, I.pen, nullptr,
                                                           nullptr, I.n1, I.n2, ax, F, gs, &I.st->run_cycle, nullptr,
                                                           nullptr, lb, nb);
-  });
+  }, sched);
 }
 
 // The three passes of the FFT preconditioner, z_j = P-hat^-1 (s_j V_j).
@@ -778,40 +763,40 @@ template <typename T, typename Tv>
 __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) dst_rows_multi_kernel(const BatchInst* __restrict__ bi,
                                                                        const int* __restrict__ prefix,
                                                                        const int* __restrict__ active, int count,
-                                                                       int j) {
-  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+                                                                       int j, int* sched) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
     const AxisTables<T>& ax = inst_tab<T>(I, false);
     const int F = multi_groups(ax.L);
     dst_body<T, Tv, T, false>(reinterpret_cast<const Tv*>(I.V) + (size_t)j * I.N, &I.st->s[j],
                               static_cast<T*>(I.T1), I.n1, I.n2, ax, F, group_stride<T>(ax.L, F, false),
                               &I.st->run_iter, lb, nb);
-  });
+  }, sched);
 }
 template <typename T>
 __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) precond_cols_multi_kernel(const BatchInst* __restrict__ bi,
                                                                            const int* __restrict__ prefix,
                                                                            const int* __restrict__ active,
-                                                                           int count) {
-  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+                                                                           int count, int* sched) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
     const AxisTables<T>& ay = inst_tab<T>(I, true);
     const int F = multi_groups(ay.L);
     precond_cols_body<T>(static_cast<const T*>(I.T1), static_cast<T*>(I.T2a), static_cast<T*>(I.T2b), I.n1, I.n2,
                          ay, inst_tab<T>(I, false).lam, T(I.pen), F, group_stride<T>(ay.L, F, true),
                          &I.st->run_iter, lb, nb);
-  });
+  }, sched);
 }
 template <typename T, typename Tz>
 __global__ void __launch_bounds__(kMultiThreads, sizeof(T) == 8 ? 2 : 4) precond_rows_multi_kernel(const BatchInst* __restrict__ bi,
                                                                            const int* __restrict__ prefix,
                                                                            const int* __restrict__ active, int count,
-                                                                           int j) {
-  multi_loop_fft(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+                                                                           int j, int* sched) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
     const AxisTables<T>& ax = inst_tab<T>(I, false);
     const int F = multi_groups(ax.L);
     precond_rows_body<T, Tz>(static_cast<const T*>(I.T2a), static_cast<const T*>(I.T2b), I.phi,
                              static_cast<Tz*>(I.Z) + (size_t)j * I.N, I.n1, I.n2, ax, F,
                              group_stride<T>(ax.L, F, false), &I.st->run_iter, lb, nb);
-  });
+  }, sched);
 }
 
 // Dynamic shared memory of a multi-instance transform launch: the largest any
@@ -836,9 +821,9 @@ void launch_operator_multi(const BatchInst* bi, const MultiGrid& rows, const Mul
   set_smem(kr, sr);
   set_smem(kc, sc);
   kr<<<multi_launch_grid(kr, kMultiThreads, sr, rows.total), kMultiThreads, sr, s>>>(bi, rows.prefix, rows.active,
-                                                                                   rows.count, j);
+                                                                                   rows.count, j, rows.sched);
   kc<<<multi_launch_grid(kc, kMultiThreads, sc, cols.total), kMultiThreads, sc, s>>>(bi, cols.prefix, cols.active,
-                                                                                   cols.count, j);
+                                                                                   cols.count, j, cols.sched);
 }
 
 template <typename T, typename Tv>
@@ -849,9 +834,9 @@ void launch_residual_multi(const BatchInst* bi, const MultiGrid& rows, const Mul
   set_smem(kr, sr);
   set_smem(kc, sc);
   kr<<<multi_launch_grid(kr, kMultiThreads, sr, rows.total), kMultiThreads, sr, s>>>(bi, rows.prefix, rows.active,
-                                                                                   rows.count);
+                                                                                   rows.count, rows.sched);
   kc<<<multi_launch_grid(kc, kMultiThreads, sc, cols.total), kMultiThreads, sc, s>>>(bi, cols.prefix, cols.active,
-                                                                                   cols.count);
+                                                                                   cols.count, cols.sched);
 }
 
 template <typename T, typename Tz, typename Tv>
@@ -865,11 +850,11 @@ void launch_precond_multi(const BatchInst* bi, const MultiGrid& drows, const Mul
   set_smem(k2, s2);
   set_smem(k3, s3);
   k1<<<multi_launch_grid(k1, kMultiThreads, s1, drows.total), kMultiThreads, s1, s>>>(bi, drows.prefix, drows.active,
-                                                                                    drows.count, j);
+                                                                                    drows.count, j, drows.sched);
   k2<<<multi_launch_grid(k2, kMultiThreads, s2, pcols.total), kMultiThreads, s2, s>>>(bi, pcols.prefix, pcols.active,
-                                                                                    pcols.count);
+                                                                                    pcols.count, pcols.sched);
   k3<<<multi_launch_grid(k3, kMultiThreads, s3, prows.total), kMultiThreads, s3, s>>>(bi, prows.prefix, prows.active,
-                                                                                    prows.count, j);
+                                                                                    prows.count, j, prows.sched);
 }
 
 }  // namespace rsfde
