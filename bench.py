@@ -483,8 +483,8 @@ def run_ours(args, rank, world, local_rank):
         for name, fn in (("disk64", run_plain_workload), ("ellipse512", run_plain_workload)):
             configs[name] = fn(name, peaks, dev)
         configs["batched256"] = run_batched_config(args, peaks)
-        if args.batch_precond != "bf16x3":  # the headline's split-BF16 preconditioner, labelled extra
-            configs["batched256_bf16x3"] = run_batched_config(args, peaks, precond="bf16x3")
+        if args.batch_precond != "bf16x3":  # the headline's form (split-BF16 P-hat, exact residual), labelled extra
+            configs["batched256_bf16x3"] = run_batched_config(args, peaks, precond="bf16x3", resid="exact")
         configs["disk1024_adjoint"] = run_adjoint_config(args, head_form)
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
@@ -569,7 +569,7 @@ def run_plain_workload(name, peaks, dev):
             "l2_note": "working set fits in L2" if w["n1"] * w["n2"] * 8 * (2 * w["restart"] + 8) < 120e6 else None}
 
 
-def run_batched_config(args, peaks, steps=None, count=None, precond=None):
+def run_batched_config(args, peaks, steps=None, count=None, precond=None, resid=None):
     """The 256-instance batch (grid side uniform in 64..512, random alpha, k,
     ellipse or polygon domain) in its own precisions: FP32 (FFT)
     preconditioner, FP32 operator arithmetic, FP64 basis and FP64 true
@@ -578,9 +578,10 @@ def run_batched_config(args, peaks, steps=None, count=None, precond=None):
     import torch
     from paper_2102_11576_gb300 import Batch, workloads
     precond = precond or args.batch_precond
+    resid = resid or args.batch_resid
     probs = workloads.make_batch(seed=0, count=count or args.batch_count)
     t0 = time.perf_counter()
-    b = Batch(probs, precond=precond, matvec="fp32", basis="fp64", resid="fp64",
+    b = Batch(probs, precond=precond, matvec="fp32", basis="fp64", resid=resid,
               use_graph=not args.no_graph)
     for i, p in enumerate(probs):
         b.set(i, p["u0"])
@@ -603,7 +604,8 @@ def run_batched_config(args, peaks, steps=None, count=None, precond=None):
     iters = [s["iters"] for s in st]
     return {"workload": f"batched: {len(probs)} instances, n in 64..512 (sum N = {unknowns}), random alpha/k/domain, "
                         "FGMRES(20), tol 1e-10",
-            "form": f"{precond} preconditioner, FP32 operator arithmetic, FP64 basis, FP64 residual",
+            "form": f"{precond} preconditioner, FP32 operator arithmetic, FP64 basis, "
+                    f"{RESID_TEXT[resid] if resid != 'fp64' else 'FP64'} residual",
             "steps": steps, "ms_per_batch_step": round(ms / steps, 3),
             "instance_steps_per_s": round(len(probs) * steps / (ms / 1e3), 1),
             "unknown_steps_per_s": unknowns * steps / (ms / 1e3),
@@ -764,6 +766,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--batch-precond", default="fp32")
+    ap.add_argument("--batch-resid", choices=["fp64", "exact"], default="fp64")
     ap.add_argument("--adjoint", action="store_true",
                     help="time only one differentiable march of the 1024^2 differentiation workload")
     ap.add_argument("--op", choices=["apply_M", "apply_M_df32", "apply_M_fp32", "precond_fp32", "precond_fp64",

@@ -1088,6 +1088,10 @@ struct rsfde_batch {
   // grouped GEMMs, their descriptors, and the GEMM launches' give-up flag
   bool bf16 = false;
   MultiGrid g_split, g_gemm[4];
+  // exact true residual (resid_prec RSFDE_EXACT): transforms and Chinese
+  // remaindering of the row and the column pass
+  bool exact = false;
+  MultiGrid g_nrows, g_crows, g_ncols, g_ccols;
   void* gdesc = nullptr;
   int* gemm_err = nullptr;
   int* sched = nullptr;  // device: the dynamic hand-out counters of the Gram-Schmidt launches
@@ -1126,8 +1130,9 @@ void free_batch(rsfde_batch* b) {
 // (build_batch_graph).
 enum { MV_FP32_B64, MV_FP32_B32, MV_BF16X3_B64, MV_NONE };
 int multi_form(const rsfde_opts& o) {
-  if (o.variant != RSFDE_FGMRES_RIGHT || !o.use_precond) return MV_NONE;
-  if (o.resid_prec != RSFDE_FP64 || o.matvec_prec != RSFDE_FP32) return MV_NONE;
+  if (o.variant != RSFDE_FGMRES_RIGHT || !o.use_precond || o.matvec_prec != RSFDE_FP32) return MV_NONE;
+  if (o.resid_prec == RSFDE_EXACT && o.basis_prec != RSFDE_FP64) return MV_NONE;
+  if (o.resid_prec != RSFDE_FP64 && o.resid_prec != RSFDE_EXACT) return MV_NONE;
   if (o.precond_prec == RSFDE_BF16X3) return o.basis_prec == RSFDE_FP64 ? MV_BF16X3_B64 : MV_NONE;
   if (o.precond_prec != RSFDE_FP32) return MV_NONE;
   return o.basis_prec == RSFDE_FP64 ? MV_FP32_B64 : MV_FP32_B32;
@@ -1137,7 +1142,8 @@ int multi_form(const rsfde_opts& o) {
 // true-residual arithmetic (FP64 or double-FP32).
 template <typename Tm, typename Tv>
 void enqueue_multi_residual(rsfde_batch* b, cudaStream_t s) {
-  launch_residual_multi<double, Tv>(b->inst, b->g_rrows, b->g_rcols, s);
+  if (b->exact) launch_exact_multi(b->inst, b->g_nrows, b->g_crows, b->g_ncols, b->g_ccols, s);
+  else launch_residual_multi<double, Tv>(b->inst, b->g_rrows, b->g_rcols, s);
 }
 // Active prefixes of the families a phase uses: the Arnoldi iteration at
 // column j (gate run_iter), or the cycle end (gate run_cycle).
@@ -1157,8 +1163,10 @@ void enqueue_compact_iter(rsfde_batch* b, int j, cudaStream_t s) {
 }
 void enqueue_compact_cycle(rsfde_batch* b, cudaStream_t s) {
   CompactArgs a{};
-  const MultiGrid* fam[] = {&b->g_xupd, &b->g_rrows, &b->g_rcols};
-  a.nfam = 3;
+  const MultiGrid* fft[] = {&b->g_xupd, &b->g_rrows, &b->g_rcols};
+  const MultiGrid* ex[] = {&b->g_xupd, &b->g_nrows, &b->g_crows, &b->g_ncols, &b->g_ccols};
+  const MultiGrid* const* fam = b->exact ? ex : fft;
+  a.nfam = b->exact ? 5 : 3;
   for (int f = 0; f < a.nfam; ++f) {
     a.prefix[f] = fam[f]->prefix;
     a.active[f] = fam[f]->active;
@@ -1206,7 +1214,7 @@ void enqueue_multi_residual_any(rsfde_batch* b, cudaStream_t s) {
 int64_t multi_body_launches(const rsfde_batch* b) {
   const rsfde_opts& o = b->ctx[0]->opts;
   const int per_col = 1 + (b->bf16 ? 5 : 3) + 2 + (o.arnoldi == RSFDE_CGS2 ? 4 : 2);
-  return (int64_t)o.restart * per_col + 6;
+  return (int64_t)o.restart * per_col + 6 + (b->exact ? 2 : 0);  // the exact residual: four launches
 }
 
 // Device descriptors and the prefixes of every multi-instance grid.
@@ -1255,6 +1263,9 @@ int setup_multi(rsfde_batch* b) {
     I.ydf = c->ydf.tab;
     I.a0 = I.a0_lo = nullptr;
     I.a0_ld = I.a0_hk = I.a0_fused = 0;
+    I.ex = c->xex.tab;
+    I.ey = c->yex.tab;
+    I.esc = exact_scratch(c);
     if (bf16) {
       // as the single-instance cycle: the basis update writes the next
       // operand when the plan takes it (enqueue_cycle_t's `fused`)
@@ -1305,6 +1316,15 @@ int setup_multi(rsfde_batch* b) {
       return b64 ? update_blocks<double>(c->N, j) : update_blocks<float>(c->N, j);
     }, nullptr);
   }
+  const bool exact = o.resid_prec == RSFDE_EXACT;
+  if (exact) {  // the exact residual's transforms (vector groups x primes) and remaindering
+    family(&b->g_nrows, [&](rsfde_ctx* c) { return exact_multi_ntt_blocks(c->xex.tab.L, c->n2); },
+           [](rsfde_ctx* c) { return c->xex.tab.log2L; });
+    family(&b->g_crows, [&](rsfde_ctx* c) { return vec_grid(c->N); }, nullptr);
+    family(&b->g_ncols, [&](rsfde_ctx* c) { return exact_multi_ntt_blocks(c->yex.tab.L, c->n1); },
+           [](rsfde_ctx* c) { return c->yex.tab.log2L; });
+    family(&b->g_ccols, [&](rsfde_ctx* c) { return vec_grid(c->N); }, nullptr);
+  }
   if (bf16) {  // the split (four elements a thread) and each GEMM's tiles
     std::vector<int> tiles[4];
     const int rc = bf16_group_create(gin, &b->gdesc, tiles);
@@ -1332,7 +1352,7 @@ int setup_multi(rsfde_batch* b) {
   // active prefixes: the iteration families (drows, pcols, prows, trows, tcols,
   // dot, upd) and the cycle-end ones (xupd, rrows, rcols); the right side and
   // the epilogue run every instance (active = the full prefix)
-  const int nact = bf16 ? 15 : 10;
+  const int nact = 10 + (bf16 ? 5 : 0) + (exact ? 4 : 0);
   if (e == cudaSuccess) e = cudaMalloc((void**)&b->actives, sizeof(int) * (size_t)nact * (n + 1));
   if (e == cudaSuccess && bf16) e = cudaMalloc((void**)&b->gemm_err, sizeof(int));
   if (e == cudaSuccess && bf16) e = cudaMemset(b->gemm_err, 0, sizeof(int));
@@ -1362,7 +1382,15 @@ int setup_multi(rsfde_batch* b) {
     b->g_split.active = b->actives + (size_t)10 * (n + 1);
     for (int k = 0; k < 4; ++k) b->g_gemm[k].active = b->actives + (size_t)(11 + k) * (n + 1);
   }
+  if (exact) {
+    MultiGrid* eg[] = {&b->g_nrows, &b->g_crows, &b->g_ncols, &b->g_ccols};
+    for (int k = 0; k < 4; ++k) {
+      eg[k]->active = b->actives + (size_t)(nact - 4 + k) * (n + 1);
+      eg[k]->sched = b->sched + 2;
+    }
+  }
   b->bf16 = bf16;
+  b->exact = exact;
   b->multi = true;
   return RSFDE_OK;
 }
@@ -1441,7 +1469,7 @@ int build_batch_graph_multi(rsfde_batch* b, int later) {
   // three preconditioner passes, two operator passes, multi-dot and update;
   // two more with CGS2) plus the back substitution, compaction, solution
   // update, residual (2) and loop condition, and 1 in the epilogue
-  b->launches_pro[later] = 5;
+  b->launches_pro[later] = b->exact ? 7 : 5;
   b->launches_epi = 1;
   b->launches_per_body = multi_body_launches(b);
   return RSFDE_OK;
@@ -1954,7 +1982,7 @@ int rsfde_batch_run(rsfde_batch* b, int32_t steps, rsfde_stats* stats) {
     const int later = b->steps_done > 0;
     if (direct) {
       if (b->launches_per_body == 0) {
-        b->launches_pro[0] = b->launches_pro[1] = 5;
+        b->launches_pro[0] = b->launches_pro[1] = b->exact ? 7 : 5;
         b->launches_epi = 1;
         b->launches_per_body = multi_body_launches(b);
       }

@@ -136,6 +136,82 @@ void launch_exact_cols(int mode, const double* x, double* tmpx, const uint8_t* p
   }
   note_unsupported_launch();
 }
+// ---- the lock-step batch: every instance's residual in four launches --------
+// Transforms: 256-thread blocks (the multi-instance transform width), F =
+// 256 / (L/16) vector groups per block; each virtual block is one group of
+// vectors for one prime.  The arithmetic of a vector does not depend on F, so
+// the residues equal the single-instance launch's.
+int exact_multi_ntt_blocks(int L, int nvec) {
+  const int F = kMultiThreads / (L / 16);
+  return (nvec + F - 1) / F * kNttPrimes;
+}
+template <bool COLS>
+__global__ void __launch_bounds__(kMultiThreads, 3)
+    ntt_multi_kernel(const BatchInst* __restrict__ bi, const int* __restrict__ prefix,
+                     const int* __restrict__ active, int count, int* sched) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int) {
+    const ExactAxis& ax = COLS ? I.ey : I.ex;
+    const int F = kMultiThreads / (ax.L / 16), gs = exact_stride(ax.L);
+    const int ngroups = ((COLS ? I.n1 : I.n2) + F - 1) / F;
+    const int prime = lb / ngroups, grp = lb - prime * ngroups;
+    ExactScratch sc = I.esc;
+    if (COLS) sc.ebuf += I.n2;  // the rows' exponents stay apart
+    switch (prime) {  // uniform over the block
+      case 0: ntt_body<0, COLS, 0>(I.x, sc, I.n1, I.n2, ax, F, gs, grp, ngroups); break;
+      case 1: ntt_body<1, COLS, 0>(I.x, sc, I.n1, I.n2, ax, F, gs, grp, ngroups); break;
+      case 2: ntt_body<2, COLS, 0>(I.x, sc, I.n1, I.n2, ax, F, gs, grp, ngroups); break;
+      default: ntt_body<3, COLS, 0>(I.x, sc, I.n1, I.n2, ax, F, gs, grp, ngroups); break;
+    }
+  }, sched);
+}
+// Chinese remaindering and the FP64 epilogue (FP64 basis): rows write the
+// scratch, columns b - (scratch - A_y x) into V_0 with the norm and restart.
+template <bool COLS>
+__global__ void __launch_bounds__(kBlock)
+    crt_multi_kernel(const BatchInst* __restrict__ bi, const int* __restrict__ prefix,
+                     const int* __restrict__ active, int count, int* sched) {
+  multi_loop(bi, prefix, active, count, [&](const BatchInst& I, int lb, int nb) {
+    ExactScratch sc = I.esc;
+    if (COLS) {
+      sc.ebuf += I.n2;
+      crt_body<MODE_RESIDUAL, true, double>(I.x, sc, static_cast<double*>(I.tmpx), I.phi, I.pen, I.b, I.V, I.n1,
+                                            I.n2, I.ey.St, I.partials, I.st, lb, nb);
+    } else {
+      crt_body<MODE_APPLY, false, double>(I.x, sc, static_cast<double*>(I.tmpx), I.phi, I.pen, nullptr, nullptr,
+                                          I.n1, I.n2, I.ex.St, nullptr, nullptr, lb, nb);
+    }
+  }, sched);
+}
+// dynamic shared memory of a transform launch: the largest any of its lengths needs
+static size_t exact_multi_smem(const MultiGrid& g) {
+  size_t m = 0;
+  for (int k = 4; k <= 12; ++k)
+    if (g.l2mask & (1u << k)) {
+      const int L = 1 << k;
+      const size_t b = (size_t)(kMultiThreads / (L / 16)) * exact_stride(L) * sizeof(uint32_t);
+      if (b > m) m = b;
+    }
+  return m;
+}
+void launch_exact_multi(const BatchInst* bi, const MultiGrid& nrows, const MultiGrid& crows, const MultiGrid& ncols,
+                        const MultiGrid& ccols, cudaStream_t s) {
+  auto nr = ntt_multi_kernel<false>;
+  auto nc = ntt_multi_kernel<true>;
+  auto cr = crt_multi_kernel<false>;
+  auto cc = crt_multi_kernel<true>;
+  const size_t sr = exact_multi_smem(nrows), sc = exact_multi_smem(ncols);
+  exact_smem(nr, sr);
+  exact_smem(nc, sc);
+  nr<<<multi_launch_grid(nr, kMultiThreads, sr, nrows.total), kMultiThreads, sr, s>>>(bi, nrows.prefix, nrows.active,
+                                                                                   nrows.count, nrows.sched);
+  cr<<<multi_launch_grid(cr, kBlock, 0, crows.total), kBlock, 0, s>>>(bi, crows.prefix, crows.active, crows.count,
+                                                                     crows.sched);
+  nc<<<multi_launch_grid(nc, kMultiThreads, sc, ncols.total), kMultiThreads, sc, s>>>(bi, ncols.prefix, ncols.active,
+                                                                                   ncols.count, ncols.sched);
+  cc<<<multi_launch_grid(cc, kBlock, 0, ccols.total), kBlock, 0, s>>>(bi, ccols.prefix, ccols.active, ccols.count,
+                                                                     ccols.sched);
+}
+
 template void launch_exact_cols<double>(int, const double*, double*, const uint8_t*, double, const double*,
                                         double*, int, int, const ExactAxis&, const ExactScratch&, const int*,
                                         double*, SolverState*, cudaStream_t);

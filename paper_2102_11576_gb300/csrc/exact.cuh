@@ -472,10 +472,11 @@ __device__ __forceinline__ int group_max(int e, int* slot, int G, int F) {
 // for prime PI, every vector's product modulo p at every position, into
 // sc.res[PI] (the grid's layout), and (PI = 0) each vector's largest biased
 // exponent E into sc.ebuf[vector] (2047: the vector holds an infinity or
-// NaN).  One vector per group of L/16 threads.
+// NaN).  One vector per group of L/16 threads; the block takes the vector
+// groups grp0, grp0 + gstep, ...
 template <int PI, bool COLS, int LG>
 __device__ __forceinline__ void ntt_body(const double* __restrict__ x, const ExactScratch& sc, int n1, int n2,
-                                         const ExactAxis& ax, int F, int gstride) {
+                                         const ExactAxis& ax, int F, int gstride, int grp0, int gstep) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int L = LG ? (1 << LG) : ax.L, Lq = L >> 4, G = Lq;
   const GroupIdx gi = group_idx<COLS>(G, F);
@@ -485,7 +486,7 @@ __device__ __forceinline__ void ntt_body(const double* __restrict__ x, const Exa
   const int ngroups = (nvec + F - 1) / F;
   const uint2* tw = ax.tab + (size_t)3 * PI * L;
   uint32_t* __restrict__ res = sc.res[PI];
-  for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+  for (int grp = grp0; grp < ngroups; grp += gstep) {
     const int vec = grp * F + gi.g;
     const bool has = vec < nvec;
     double xv[8];
@@ -535,18 +536,18 @@ __global__ void __launch_bounds__(COLS ? 1024 : 512, COLS ? 1 : 2)
   // the prime (uniform over the block), and the length 4096 (n 1025..2048) compiled apart
   if (ax.log2L == 12) {
     switch (blockIdx.y) {
-      case 0: ntt_body<0, COLS, 12>(x, sc, n1, n2, ax, F, gstride); break;
-      case 1: ntt_body<1, COLS, 12>(x, sc, n1, n2, ax, F, gstride); break;
-      case 2: ntt_body<2, COLS, 12>(x, sc, n1, n2, ax, F, gstride); break;
-      default: ntt_body<3, COLS, 12>(x, sc, n1, n2, ax, F, gstride); break;
+      case 0: ntt_body<0, COLS, 12>(x, sc, n1, n2, ax, F, gstride, blockIdx.x, gridDim.x); break;
+      case 1: ntt_body<1, COLS, 12>(x, sc, n1, n2, ax, F, gstride, blockIdx.x, gridDim.x); break;
+      case 2: ntt_body<2, COLS, 12>(x, sc, n1, n2, ax, F, gstride, blockIdx.x, gridDim.x); break;
+      default: ntt_body<3, COLS, 12>(x, sc, n1, n2, ax, F, gstride, blockIdx.x, gridDim.x); break;
     }
     return;
   }
   switch (blockIdx.y) {
-    case 0: ntt_body<0, COLS, 0>(x, sc, n1, n2, ax, F, gstride); break;
-    case 1: ntt_body<1, COLS, 0>(x, sc, n1, n2, ax, F, gstride); break;
-    case 2: ntt_body<2, COLS, 0>(x, sc, n1, n2, ax, F, gstride); break;
-    default: ntt_body<3, COLS, 0>(x, sc, n1, n2, ax, F, gstride); break;
+    case 0: ntt_body<0, COLS, 0>(x, sc, n1, n2, ax, F, gstride, blockIdx.x, gridDim.x); break;
+    case 1: ntt_body<1, COLS, 0>(x, sc, n1, n2, ax, F, gstride, blockIdx.x, gridDim.x); break;
+    case 2: ntt_body<2, COLS, 0>(x, sc, n1, n2, ax, F, gstride, blockIdx.x, gridDim.x); break;
+    default: ntt_body<3, COLS, 0>(x, sc, n1, n2, ax, F, gstride, blockIdx.x, gridDim.x); break;
   }
 }
 
@@ -558,15 +559,15 @@ __global__ void __launch_bounds__(COLS ? 1024 : 512, COLS ? 1 : 2)
 //          and ||out||^2 by a fixed-order block sum per block and
 //          block_sum_fixed over the blocks (the grid is a function of N), the
 //          last block restarting the solver.
+// (bid, nblk): this block's index in the pass's grid and the grid's size.
 template <int MODE, bool COLS, typename Tout>
-__global__ void __launch_bounds__(kBlock)
-    crt_kernel(const double* __restrict__ x, ExactScratch sc, double* __restrict__ tmpx,
-               const uint8_t* __restrict__ phi, double pen, const double* __restrict__ b, Tout* __restrict__ out,
-               int n1, int n2, int St, const int* gate, double* partials, SolverState* st) {
-  if (gate_closed<double>(gate)) return;
+__device__ __forceinline__ void crt_body(const double* __restrict__ x, const ExactScratch& sc,
+                                         double* __restrict__ tmpx, const uint8_t* __restrict__ phi, double pen,
+                                         const double* __restrict__ b, Tout* __restrict__ out, int n1, int n2, int St,
+                                         double* partials, SolverState* st, int bid, int nblk) {
   const size_t N = (size_t)n1 * n2;
   double acc = 0.0;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)gridDim.x * blockDim.x) {
+  for (size_t p = bid * (size_t)blockDim.x + threadIdx.x; p < N; p += (size_t)nblk * blockDim.x) {
     const int vec = COLS ? (int)(p % (size_t)n1) : (int)(p / (size_t)n1);
     const int E = __ldg(sc.ebuf + vec);
     const double az = E == 2047 ? __longlong_as_double(0x7FF8000000000000ll)
@@ -586,12 +587,20 @@ __global__ void __launch_bounds__(kBlock)
   if constexpr (MODE == MODE_RESIDUAL) {
     __shared__ double sh[kBlock / 32];
     const double bs = block_sum(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = bs;
-    if (arrive_last(&st->counter, gridDim.x)) {
-      const double tot = block_sum_fixed(partials, gridDim.x);
+    if (threadIdx.x == 0) partials[bid] = bs;
+    if (arrive_last(&st->counter, nblk)) {
+      const double tot = block_sum_fixed(partials, nblk);
       if (threadIdx.x == 0) restart_prep(st, sqrt(tot));
     }
   }
+}
+template <int MODE, bool COLS, typename Tout>
+__global__ void __launch_bounds__(kBlock)
+    crt_kernel(const double* __restrict__ x, ExactScratch sc, double* __restrict__ tmpx,
+               const uint8_t* __restrict__ phi, double pen, const double* __restrict__ b, Tout* __restrict__ out,
+               int n1, int n2, int St, const int* gate, double* partials, SolverState* st) {
+  if (gate_closed<double>(gate)) return;
+  crt_body<MODE, COLS, Tout>(x, sc, tmpx, phi, pen, b, out, n1, n2, St, partials, st, blockIdx.x, gridDim.x);
 }
 
 // Groups per block (a power of two) of the transform kernel: at least 128

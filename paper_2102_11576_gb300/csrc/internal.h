@@ -219,6 +219,9 @@ struct BatchInst {
   void* a0;
   void* a0_lo;
   int a0_ld, a0_hk, a0_fused;
+  // exact true residual (lock-step form): the instance's tables and scratch
+  ExactAxis ex, ey;
+  ExactScratch esc;
 };
 
 // The blocks of one multi-instance launch: instance i owns the blocks
@@ -363,6 +366,14 @@ void bf16_group_destroy(void* descs);
 void launch_bf16_group(int k, const void* descs, int count, const int* active, int max_tiles, int j, int* err,
                        cudaStream_t s);
 void launch_split_multi(const BatchInst* bi, const MultiGrid& g, int j, cudaStream_t s);
+// The exact true residual of every instance whose cycle ends (exact.cu): the
+// transforms of the row pass (nrows: vector groups x 4 primes per instance),
+// its Chinese remaindering (crows: vec_grid(N) per instance, as the
+// single-instance launch), then the same for the columns with b - M x, the
+// norm and the restart decision.
+void launch_exact_multi(const BatchInst* bi, const MultiGrid& nrows, const MultiGrid& crows, const MultiGrid& ncols,
+                        const MultiGrid& ccols, cudaStream_t s);
+int exact_multi_ntt_blocks(int L, int nvec);  // virtual blocks of one instance's transform launch
 void bf16_plan_a0_any(const Bf16Plan* p, Bf16Out* out);
 void launch_solve_y_multi(const BatchInst* bi, int count, cudaStream_t s);
 template <typename Tz>

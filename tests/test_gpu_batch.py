@@ -18,16 +18,18 @@ from paper_2102_11576_gb300 import Batch, Solver  # noqa: E402
 
 
 # the FP32 FFT preconditioner with the FP32 operator and the FP64 residual
-# (FP64 or FP32 basis), and the split-BF16 preconditioner with the FP32
-# operator, FP64 basis and FP64 residual, run the multi-instance form (one
-# launch per phase over all instances: the BF16 GEMMs of every instance in
-# one grouped launch per pass); the other forms the graph of per-instance
-# branches
+# (FP64 or FP32 basis), and the FP32 or split-BF16 preconditioner with the
+# FP32 operator, FP64 basis and the FP64 or exact residual, run the
+# multi-instance form (one launch per phase over all instances: the BF16 GEMMs
+# of every instance in one grouped launch per pass, the exact residual's
+# transforms and remaindering in four); the other forms the graph of
+# per-instance branches
 @pytest.mark.parametrize("precond,matvec,basis,resid,n_range", [
     ("fp32", "df32", "df32", "fp64", (9, 96)), ("bf16", "fp32", "fp32", "df32", (9, 96)),
     ("fp32", "fp32", "fp64", "fp64", (9, 96)), ("fp32", "fp32", "fp32", "fp64", (9, 96)),
     ("bf16x3", "fp32", "fp64", "exact", (9, 96)), ("bf16x3", "fp32", "fp64", "fp64", (9, 96)),
-    ("bf16x3", "fp32", "fp64", "fp64", (100, 400))])
+    ("bf16x3", "fp32", "fp64", "fp64", (100, 400)), ("fp32", "fp32", "fp64", "exact", (9, 96)),
+    ("bf16x3", "fp32", "fp64", "exact", (100, 400)), ("bf16", "fp32", "fp64", "exact", (9, 96))])
 def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, basis, resid, n_range):
     probs = workloads.make_batch(seed=5, count=7, n_range=n_range, steps=10)
     steps = 3
@@ -40,13 +42,14 @@ def test_batch_equals_single_instances_and_meets_tolerance(precond, matvec, basi
     assert all(s["converged"] and s["rel_res"] <= 1e-10 for s in st)
     launches = b.kernel_launches
     assert launches > 0
-    if precond in ("fp32", "bf16x3") and matvec == "fp32" and resid == "fp64":
-        # lock step: per step 6 launches plus, per run of the loop body, 8 per
-        # Arnoldi column (10 with the split and four grouped GEMMs) and 6
-        # more, however many instances there are (these problems need at most
-        # a few cycles a step)
+    if precond in ("fp32", "bf16x3") and matvec == "fp32" and resid in ("fp64", "exact"):
+        # lock step: per step 6 launches (8 with the exact residual's four)
+        # plus, per run of the loop body, 8 per Arnoldi column (10 with the
+        # split and four grouped GEMMs) and 6 more (8), however many instances
+        # there are (these problems need at most a few cycles a step)
         per_col = 10 if precond == "bf16x3" else 8
-        assert launches <= steps * (6 + 12 * (per_col * 20 + 6))
+        extra = 2 if resid == "exact" else 0
+        assert launches <= steps * (6 + extra + 12 * (per_col * 20 + 6 + extra))
     for i, p in enumerate(probs):
         args = (p["n1"], p["n2"], p["box"], p["in_omega"], p["alpha1"], p["alpha2"], p["kx"], p["ky"],
                 p["dt"], p["eta"])
