@@ -224,9 +224,10 @@ int rsfde_adjoint_step(rsfde_ctx* ctx, const double* u_prev, const double* u_k, 
 /* ---- batched instances ------------------------------------------------------ */
 /* Many independent problems (each its own grid, mask, alphas, k, dt, eta)
  * advanced together; one CUDA graph launch advances the whole batch by one
- * step.  With right-preconditioned FGMRES, the FP32 operator, the FP64 true
- * residual and either the FP32 preconditioner (FP64 or FP32 basis) or the
- * split-BF16 one (FP64 basis), the instances run in lock step: every kernel
+ * step.  With right-preconditioned FGMRES, the FP32 operator and either the
+ * FP32 preconditioner (FP64 basis with the FP64 or exact true residual, or FP32
+ * basis with the FP64 one) or the split-BF16 one (FP64 basis, FP64 or exact
+ * residual), the instances run in lock step: every kernel
  * of the FGMRES cycle is one launch over all instances still iterating (the
  * split-BF16 GEMMs of all instances in one grouped launch per pass), with
  * each instance's results bit-identical to its single-instance solve (up to
