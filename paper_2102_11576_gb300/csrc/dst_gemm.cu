@@ -153,17 +153,20 @@ struct Bf16Plan {
   int bn[4] = {0, 0, 0, 0};             // tile width of each GEMM of the chain (0: the default rule)
 };
 
-// S_n as a split BF16 pair: [S_n]_{ij} = sqrt(2/(n+1)) sin(pi i j/(n+1)), FP64 on the host.
-// Symmetric form (hk > 0): only the rows i <= n/2, columns in sym_perm order.
+// S_n as a split BF16 pair: [S_n]_{ij} = sqrt(2/(n+1)) sin(pi i j/(n+1)), FP64 on the host
+// (exactly zero where i j is a multiple of n + 1).  Symmetric form (hk > 0): only
+// the rows i <= (n+1)/2 (for odd n the middle row pairs with itself, its
+// odd-j entries zero), columns in sym_perm order.
 static void host_sine_matrix(int n, int ld, int hk, std::vector<__nv_bfloat16>& hi,
                              std::vector<__nv_bfloat16>& lo) {
-  const int rows = hk ? n / 2 : n;
+  const int rows = hk ? (n + 1) / 2 : n;
   hi.assign((size_t)rows * ld, __float2bfloat16(0.0f));
   lo.assign((size_t)rows * ld, __float2bfloat16(0.0f));
   const long per = 2L * (n + 1);
   const double sc = std::sqrt(2.0 / (n + 1));
   std::vector<double> sn(per);
-  for (long m = 0; m < per; ++m) sn[m] = sc * std::sin(M_PI * (double)m / (double)(n + 1));
+  for (long m = 0; m < per; ++m)
+    sn[m] = m % (n + 1) == 0 ? 0.0 : sc * std::sin(M_PI * (double)m / (double)(n + 1));
   for (int i = 1; i <= rows; ++i)
     for (int j = 1; j <= n; ++j) {
       const float x = (float)sn[((long)i * j) % per];
@@ -184,9 +187,12 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
   p->n1 = n1;
   p->n2 = n2;
   // even n1 and n2: the symmetric form (half the MMAs)
-  const bool sym = n1 % 2 == 0 && n2 % 2 == 0;
-  p->h1 = sym ? pad64(n1 / 2) : 0;
-  p->h2 = sym ? pad64(n2 / 2) : 0;
+  // the symmetric form (half the MMAs): split BF16 at every n; plain BF16,
+  // whose staged epilogue writes the two outputs of a pair from different
+  // threads, only where no output pairs with itself (even n)
+  const bool sym = nt == 3 || (n1 % 2 == 0 && n2 % 2 == 0);
+  p->h1 = sym ? pad64((n1 + 1) / 2) : 0;
+  p->h2 = sym ? pad64((n2 + 1) / 2) : 0;
   p->ld1 = sym ? 2 * p->h1 : pad64(n1);
   p->ld2 = sym ? 2 * p->h2 : pad64(n2);
   const int c1 = sym ? p->ld1 : n1, c2 = sym ? p->ld2 : n2;  // K extents of the tensor maps
@@ -195,7 +201,7 @@ int bf16_plan_create(Bf16Plan** out, int n1, int n2, int nt, const float* lamx, 
   struct Spec {
     Bf16Mat* m;
     int rows, cols, ld;
-  } specs[] = {{&p->Sx, sym ? n1 / 2 : n1, c1, p->ld1}, {&p->Sy, sym ? n2 / 2 : n2, c2, p->ld2},
+  } specs[] = {{&p->Sx, sym ? (n1 + 1) / 2 : n1, c1, p->ld1}, {&p->Sy, sym ? (n2 + 1) / 2 : n2, c2, p->ld2},
                {&p->A0, n2, c1, p->ld1},                {&p->T1t, n1, c2, p->ld2},
                {&p->Wst, 2 * n2, c1, p->ld1},           {&p->Yt, n1, 2 * p->ld2, 2 * p->ld2}};
   const int parts = nt == 3 ? 2 : 1;
@@ -333,7 +339,7 @@ template <int EPI>
 static void launch_gemm(const Bf16Plan* p, int stage, int hk, const Bf16Mat& A, const Bf16Mat& B, int M, int n,
                         int channels, GemmEpiParams ep, const int* gate, cudaStream_t s) {
   ep.M = M;
-  ep.N = hk ? n / 2 : n;
+  ep.N = hk ? (n + 1) / 2 : n;
   ep.n_full = hk ? n : 0;
   const int K = hk ? 2 * hk : n;
   const int f = p->bn[stage];
@@ -494,7 +500,7 @@ int bf16_group_create(const std::vector<Bf16GroupInst>& in, void** descs, std::v
       D.b_hi = g.B->map64_hi;
       D.b_lo = g.B->map64_lo;
       g.ep.M = g.M;
-      g.ep.N = g.hk ? g.n / 2 : g.n;
+      g.ep.N = g.hk ? (g.n + 1) / 2 : g.n;
       g.ep.n_full = g.hk ? g.n : 0;
       g.ep.nch = g.channels;
       if (k == 3) {

@@ -49,17 +49,19 @@ enum GemmEpi {
   EPI_COMBINE_T = 2  // masked combine of Eq. 4.6 into z (channel = blockIdx.z)
 };
 
-// Symmetric form (SYM): for even n the sine matrix satisfies
+// Symmetric form (SYM): the sine matrix satisfies
 //     S[n-1-i][j] = (-1)^j S[i][j]        (0-based i, j),
 // so with u_i = sum over even j and e_i = sum over odd j of S[i][j] x_j the
-// two outputs i and n-1-i are u_i + e_i and u_i - e_i (i < n/2).  The K
-// operand then holds the even-j entries in columns [0, hk) and the odd-j
-// entries in [hk, 2 hk) (hk = n/2 rounded up to 64, zero padded), the GEMM
-// has n/2 output columns and two TMEM accumulators, and half the MMAs.
+// two outputs i and n-1-i are u_i + e_i and u_i - e_i (i < (n+1)/2; for odd n
+// the middle row pairs with itself, its odd-j entries are zero and both
+// writes of that output, by the same thread, carry u_i).  The K operand then
+// holds the even-j entries in columns [0, hk) and the odd-j entries in
+// [hk, 2 hk) (hk = (n+1)/2 rounded up to 64, zero padded), the GEMM has
+// (n+1)/2 output columns and two TMEM accumulators, and half the MMAs.
 __host__ __device__ __forceinline__ int sym_perm(int x, int hk) { return hk ? (x & 1) * hk + (x >> 1) : x; }
 
 struct GemmEpiParams {
-  int M, N;       // valid extent of D (N: n/2 in the symmetric form)
+  int M, N;       // valid extent of D (N: (n+1)/2 in the symmetric form)
   int n_full;     // symmetric form: the transform length n (outputs i and n-1-i); 0 otherwise
   int hk;         // K layout the epilogue writes for the next GEMM: 0 natural, else symmetric halves of hk
   __nv_bfloat16* out_hi;
@@ -138,7 +140,7 @@ struct GemmGroupDesc {
   const double* s;
   int fused;
   int K;
-  int sym;  // symmetric form (even transform length)
+  int sym;  // symmetric form
 };
 
 // One CTA per tile over every instance's tile grid: instance i owns the CTAs
