@@ -56,11 +56,11 @@ PREC_TEXT = {"fp64": "FP64 (FFT)", "fp32": "FP32 (FFT)", "bf16x3": "split BF16 o
 # one Gram-Schmidt iteration: multi-dot + update), with the hash of the CUDA
 # sources that define those kernels; reported as null once any of them changes.
 # gram_schmidt: profiles/gram_schmidt_fp64_polygon2048.md, the multi-dot and
-# update of column j = 10 (FP64 basis): 813.2 MB of DRAM traffic against
+# update of column j = 10 (FP64 basis): 813.5 MB of DRAM traffic against
 # 805.3 MB of algorithmic bytes; the per-unit traffic reported is that ratio
 # times the mean algorithmic bytes of the profiled iterations.
 TRAFFIC = {
-    "gram_schmidt": {"traffic_over_algorithmic": 813171712 / 805306368, "src": "1319fcdb5c47b85b",
+    "gram_schmidt": {"traffic_over_algorithmic": 813473280 / 805306368, "src": "310edcbdabee4098",
                      "files": ["common.cuh", "df.cuh", "internal.h", "krylov.cu"]},
 }
 

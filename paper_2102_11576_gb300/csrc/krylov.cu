@@ -193,14 +193,61 @@ __device__ __forceinline__ void st_vec(Tv* p, const Tv* v) {
 
 // Block sums of cnt <= K accumulators: warp sums, then warp k adds the
 // per-warp FP64 sums of accumulator k (fixed order).  Thread 32k returns sum k.
+//
+// FP64 with all K (2, 4 or 8) accumulators in use: the K warp sums by
+// recursive halving -- at the step over lane bit b a lane keeps half of its
+// partial sums and adds the partner's matching half, so after log2 K steps
+// each lane holds one accumulator's partial and the last 5 - log2 K steps
+// finish it: K - 1 + 5 - log2 K additions and shuffles per lane instead of
+// 5 K.  The pairs and their order are those of warp_sum (lane bits 4 down to
+// 0), so every sum is the same number.
+template <int K>
+__device__ __forceinline__ void warp_sums_halving(const double* acc, double (*sh)[kWarps], int w, int l) {
+  constexpr int R = K == 8 ? 3 : K == 4 ? 2 : 1;
+  double v[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[i] = acc[i];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const int off = 16 >> s;
+    constexpr int kMax = K >> 1;
+    const bool up = (l & off) != 0;  // keep the upper half of the current K >> s values
+#pragma unroll
+    for (int i = 0; i < kMax; ++i) {
+      const int half = (K >> s) >> 1;
+      if (i < half) {
+        const double send = up ? v[i] : v[half + i];
+        const double keep = up ? v[half + i] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16 >> R; off; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
+  if ((l & ((32 >> R) - 1)) == 0) sh[l >> (5 - R)][w] = v[0];  // accumulator l >> (5 - R)
+}
 template <typename Tv, int K>
 __device__ __forceinline__ double block_sums(const Tv* acc, int cnt, double (*sh)[kWarps]) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if constexpr (std::is_same<Tv, double>::value && (K == 2 || K == 4 || K == 8)) {
+    if (cnt == K) {
+      warp_sums_halving<K>(acc, sh, w, l);
+    } else {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (k < cnt) {
-      const double ws = VecOps<Tv>::warp_sum(acc[k]);
-      if (l == 0) sh[k][w] = ws;
+      for (int k = 0; k < K; ++k) {
+        if (k < cnt) {
+          const double ws = VecOps<Tv>::warp_sum(acc[k]);
+          if (l == 0) sh[k][w] = ws;
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (k < cnt) {
+        const double ws = VecOps<Tv>::warp_sum(acc[k]);
+        if (l == 0) sh[k][w] = ws;
+      }
     }
   }
   __syncthreads();
