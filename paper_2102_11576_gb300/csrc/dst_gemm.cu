@@ -540,6 +540,7 @@ static void launch_group_t(const GemmGroupDesc* d, int count, const int* active,
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k<<<max_tiles, kGroupThreads, smem, s>>>(d, active, count, j, err);
 }
+static_assert(kGroupMaxInstances == kMaxBatchMulti, "the grouped GEMMs stage the batch's whole prefix");
 void launch_bf16_group(int k, const void* descs, int count, const int* active, int max_tiles, int j, int* err,
                        cudaStream_t s) {
   if (max_tiles <= 0) return;

@@ -151,6 +151,7 @@ struct GemmGroupDesc {
 // mostly pipeline fill and epilogue: two CTAs share an SM (eight warps each,
 // a two-stage ring) and one's epilogue overlaps the other's MMAs.
 constexpr int kGroupThreads = 256, kGroupStages = 2;
+constexpr int kGroupMaxInstances = 1024;  // the compacted prefix a CTA stages in shared memory
 __host__ __device__ constexpr int gemm_group_smem(int NT, int BN) {
   return kGroupStages * gemm_stage_bytes(NT, BN) + 1024;
 }
@@ -173,11 +174,16 @@ __global__ void __launch_bounds__(kGroupThreads, 2)
     dst_gemm_group_kernel(const GemmGroupDesc* __restrict__ d, const int* __restrict__ active, int count, int j,
                           int* err) {
   const int b = blockIdx.x;
-  if (b >= active[count]) return;  // uniform over the block
-  int i = 0;  // the last i with active[i] <= b (empty ranges skipped)
+  // the prefix in shared memory first (one coalesced read instead of a chain
+  // of dependent global reads in the search)
+  __shared__ int sact[kGroupMaxInstances + 1];
+  for (int k = threadIdx.x; k <= count; k += blockDim.x) sact[k] = active[k];
+  __syncthreads();
+  if (b >= sact[count]) return;  // uniform over the block
+  int i = 0;  // the last i with sact[i] <= b (empty ranges skipped)
   for (int hi = count - 1; i < hi;) {
     const int mid = (i + hi + 1) >> 1;
-    if (active[mid] <= b) i = mid;
+    if (sact[mid] <= b) i = mid;
     else hi = mid - 1;
   }
   const GemmGroupDesc& D = d[i];
@@ -190,7 +196,7 @@ __global__ void __launch_bounds__(kGroupThreads, 2)
     }
   }
   __syncthreads();
-  const int t = b - active[i];
+  const int t = b - sact[i];
   if (D.sym) group_tile<EPI, NT, true, BN>(D, sep, err, t);
   else group_tile<EPI, NT, false, BN>(D, sep, err, t);
 }
